@@ -1,0 +1,408 @@
+// Reference (oracle) implementation of the hierarchical 3DGS render path, in
+// float64, for tests and for the CPU baseline only. TEST INFRASTRUCTURE: only
+// the test-suite, the smoke entry point and the benchmark's CPU-baseline leg
+// load this library; the renderer never calls it and shares no code with it.
+//
+// What is computed (hierarchical 3D Gaussian Splatting, Sec. III-B: a tree of
+// Gaussians, a level-of-detail cut chosen per view, then 3DGS rasterisation of
+// the cut from camera intrinsics and extrinsics, Sec. III-A):
+//   1. cut       : per node n, granularity s(n) = fx * ext(n) / dist(cam, box(n))
+//                  (ext = longest box side, dist = distance from the camera
+//                  centre to the box, s = +inf inside it). n is selected iff
+//                  (n is a leaf or s(n) <= tau) and (n is the root or
+//                  s(parent(n)) > tau).
+//   2. preprocess: EWA projection of each cut Gaussian (Sigma2D = J W Sigma
+//                  W^T J^T + 0.3 I), its conic, pixel centre, view depth,
+//                  degree-3 SH colour, conservative support radius and tile
+//                  rectangle.
+//   3. binning   : one (tile, depth) key per Gaussian and overlapped tile,
+//                  ordered by a stable sort (std::stable_sort), tile ranges.
+//   4. composite : per pixel, front-to-back alpha blending over its tile's list.
+//   5. brute force: per pixel over every visible Gaussian in depth order, no
+//                  tiles, as an independent check of 3-4.
+// Every floating-point step is float64 except where a step's result decides an
+// integer that the renderer must reproduce exactly: the depth sort key is the
+// float32 rounding of a float64 depth evaluated in a fixed operation order
+// (the file is compiled with -ffp-contract=off so no fused multiply-add
+// changes that order).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+extern "C" {
+
+typedef struct {
+    int64_t n;                 // nodes
+    const float *pos;          // [n][3]
+    const float *quat;         // [n][4] w,x,y,z
+    const float *log_scale;    // [n][3]
+    const float *opacity;      // [n]
+    const float *sh;           // [n][16][3]
+    const int32_t *parent;     // [n], -1 root
+    const int32_t *child_count;// [n]
+    const float *aabb_min;     // [n][3]
+    const float *aabb_max;     // [n][3]
+} orc_scene;
+
+typedef struct {
+    double pos[3];
+    double R[9];               // world->camera rows (OpenCV: x right, y down, z forward)
+    double fx, fy, cx, cy;
+    int32_t width, height;
+    double tau;
+} orc_camera;
+
+// per cut slot, columns of the float64 preprocess table
+enum {
+    PC_VISIBLE = 0, PC_U, PC_V, PC_CONIC_A, PC_CONIC_B, PC_CONIC_C, PC_COV_A, PC_COV_B,
+    PC_COV_C, PC_DEPTH, PC_OPACITY, PC_R, PC_G, PC_B, PC_RADIUS, PC_NCOLS
+};
+
+static const double kNear = 0.2;           // near plane (view z)
+static const double kBlur = 0.3;           // screen-space dilation added to Sigma2D
+static const double kAlphaMin = 1.0 / 255.0;
+static const double kAlphaMax = 0.99;
+static const double kTMin = 1e-4;
+static const double kRectMargin = 1.0 / 64.0;   // pixels added to the support radius
+
+// ---------------------------------------------------------------------------
+// 1. cut
+// ---------------------------------------------------------------------------
+
+static double granularity(const orc_scene *sc, const orc_camera *cam, int64_t n) {
+    double d2 = 0.0, ext = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double lo = sc->aabb_min[3 * n + k], hi = sc->aabb_max[3 * n + k];
+        double p = cam->pos[k];
+        double g = 0.0;
+        if (p < lo) g = lo - p;
+        else if (p > hi) g = p - hi;
+        d2 += g * g;
+        ext = std::max(ext, hi - lo);
+    }
+    if (d2 == 0.0) return INFINITY;
+    return cam->fx * ext / std::sqrt(d2);
+}
+
+// Writes the selected node ids (ascending) and returns their count. If
+// near_out is given, near_out[n] = 1 when s(n) or s(parent(n)) lies within
+// 1e-5 relative of tau (a decision the float32 renderer may take either way).
+// If s_out is given it receives s(n).
+int64_t orc_select_cut(const orc_scene *sc, const orc_camera *cam, int32_t *ids_out,
+                       uint8_t *near_out, double *s_out) {
+    const int64_t n = sc->n;
+    std::vector<double> s(n);
+    for (int64_t i = 0; i < n; ++i) s[i] = granularity(sc, cam, i);
+    const double tau = cam->tau;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        bool leaf = sc->child_count[i] == 0;
+        int32_t par = sc->parent[i];
+        bool own = leaf || s[i] <= tau;
+        bool up = (par < 0) || s[par] > tau;
+        if (own && up) ids_out[cnt++] = (int32_t)i;
+        if (near_out) {
+            bool nr = std::fabs(s[i] - tau) <= 1e-5 * tau;
+            if (par >= 0) nr = nr || std::fabs(s[par] - tau) <= 1e-5 * tau;
+            near_out[i] = nr ? 1 : 0;
+        }
+        if (s_out) s_out[i] = s[i];
+    }
+    return cnt;
+}
+
+// ---------------------------------------------------------------------------
+// 2. preprocess
+// ---------------------------------------------------------------------------
+
+// Real spherical harmonics up to degree 3, orthonormal on the unit sphere, in
+// the sign convention of 3DGS (the standard real basis times (-1)^|m|), index
+// l*l + l + m. Direction (x, y, z) must be unit length.
+void orc_sh_basis(const double *dir, double *out) {
+    const double x = dir[0], y = dir[1], z = dir[2];
+    const double pi = M_PI;
+    const double xx = x * x, yy = y * y, zz = z * z;
+    out[0] = 0.5 * std::sqrt(1.0 / pi);
+    const double c1 = std::sqrt(3.0 / (4.0 * pi));
+    out[1] = -c1 * y;
+    out[2] = c1 * z;
+    out[3] = -c1 * x;
+    const double c2a = 0.5 * std::sqrt(15.0 / pi);
+    const double c2b = 0.25 * std::sqrt(5.0 / pi);
+    const double c2c = 0.25 * std::sqrt(15.0 / pi);
+    out[4] = c2a * x * y;
+    out[5] = -c2a * y * z;
+    out[6] = c2b * (2.0 * zz - xx - yy);
+    out[7] = -c2a * x * z;
+    out[8] = c2c * (xx - yy);
+    const double c3a = 0.25 * std::sqrt(35.0 / (2.0 * pi));
+    const double c3b = 0.5 * std::sqrt(105.0 / pi);
+    const double c3c = 0.25 * std::sqrt(21.0 / (2.0 * pi));
+    const double c3d = 0.25 * std::sqrt(7.0 / pi);
+    const double c3e = 0.25 * std::sqrt(105.0 / pi);
+    out[9] = -c3a * y * (3.0 * xx - yy);
+    out[10] = c3b * x * y * z;
+    out[11] = -c3c * y * (4.0 * zz - xx - yy);
+    out[12] = c3d * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    out[13] = -c3c * x * (4.0 * zz - xx - yy);
+    out[14] = c3e * z * (xx - yy);
+    out[15] = -c3a * x * (xx - 3.0 * yy);
+}
+
+// Sigma = R(q) S S^T R(q)^T, q = (w, x, y, z) normalised, S = diag(exp(log_scale)).
+// Output: the symmetric 3x3 matrix, row-major.
+void orc_cov3d(const float *quat, const float *log_scale, double *out) {
+    double w = quat[0], x = quat[1], y = quat[2], z = quat[3];
+    const double nq = std::sqrt(w * w + x * x + y * y + z * z);
+    w /= nq; x /= nq; y /= nq; z /= nq;
+    const double R[9] = {
+        1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y),
+        2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x),
+        2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)};
+    double s2[3];
+    for (int k = 0; k < 3; ++k) s2[k] = std::exp(2.0 * (double)log_scale[k]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * s2[k] * R[3 * j + k];
+            out[3 * i + j] = acc;
+        }
+}
+
+// View-space depth in the fixed float64 order the sort key uses:
+// d_k = mu_k - pos_k, z = (R20 d0 + R21 d1) + R22 d2, each product rounded.
+double orc_view_depth(const float *mu, const orc_camera *cam) {
+    const double d0 = (double)mu[0] - cam->pos[0];
+    const double d1 = (double)mu[1] - cam->pos[1];
+    const double d2 = (double)mu[2] - cam->pos[2];
+    const double a = cam->R[6] * d0;
+    const double b = cam->R[7] * d1;
+    const double c = cam->R[8] * d2;
+    return (a + b) + c;
+}
+
+// For each cut slot i (node ids[i]) fills out[i*PC_NCOLS + col], depth_key[i]
+// (float32 bits of the rounded depth) and rect[i*4..] = (x0, y0, x1, y1), the
+// inclusive tile range. Invisible slots get PC_VISIBLE = 0 and rect (0,0,-1,-1).
+void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *ids, int64_t n,
+                    int32_t tile_w, int32_t tile_h, double *out, uint32_t *depth_key,
+                    int32_t *rect) {
+    const int32_t tiles_x = (cam->width + tile_w - 1) / tile_w;
+    const int32_t tiles_y = (cam->height + tile_h - 1) / tile_h;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double *o = out + i * PC_NCOLS;
+        for (int c = 0; c < PC_NCOLS; ++c) o[c] = 0.0;
+        int32_t *rc = rect + 4 * i;
+        rc[0] = 0; rc[1] = 0; rc[2] = -1; rc[3] = -1;
+        depth_key[i] = 0xFFFFFFFFu;
+        const int64_t g = ids[i];
+        const float *mu = sc->pos + 3 * g;
+        const double tz = orc_view_depth(mu, cam);
+        if (!(tz > kNear)) continue;
+        const double opac = sc->opacity[g];
+        if (255.0 * opac < 1.0) continue;
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = (double)mu[k] - cam->pos[k];
+        const double tx = cam->R[0] * d[0] + cam->R[1] * d[1] + cam->R[2] * d[2];
+        const double ty = cam->R[3] * d[0] + cam->R[4] * d[1] + cam->R[5] * d[2];
+        // Jacobian of (fx x/z, fy y/z) at t
+        const double J[6] = {cam->fx / tz, 0.0, -cam->fx * tx / (tz * tz),
+                             0.0, cam->fy / tz, -cam->fy * ty / (tz * tz)};
+        double T[6];   // J * W
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += J[3 * r + k] * cam->R[3 * k + c];
+                T[3 * r + c] = acc;
+            }
+        double S[9];
+        orc_cov3d(sc->quat + 4 * g, sc->log_scale + 3 * g, S);
+        double TS[6];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += T[3 * r + k] * S[3 * k + c];
+                TS[3 * r + c] = acc;
+            }
+        double C2[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += TS[3 * r + k] * T[3 * c + k];
+                C2[2 * r + c] = acc;
+            }
+        const double a = C2[0] + kBlur, b = C2[1], cc = C2[3] + kBlur;
+        const double det = a * cc - b * b;
+        if (!(det > 0.0)) continue;
+        const double u = cam->fx * tx / tz + cam->cx;
+        const double v = cam->fy * ty / tz + cam->cy;
+        const double mid = 0.5 * (a + cc);
+        const double lmax = mid + std::sqrt(std::max(0.1, mid * mid - det));
+        const double radius = std::sqrt(2.0 * std::log(255.0 * opac) * lmax) + kRectMargin;
+        int32_t x0 = (int32_t)std::floor((u - radius) / tile_w);
+        int32_t x1 = (int32_t)std::floor((u + radius) / tile_w);
+        int32_t y0 = (int32_t)std::floor((v - radius) / tile_h);
+        int32_t y1 = (int32_t)std::floor((v + radius) / tile_h);
+        x0 = std::max(x0, 0); y0 = std::max(y0, 0);
+        x1 = std::min(x1, tiles_x - 1); y1 = std::min(y1, tiles_y - 1);
+        if (x0 > x1 || y0 > y1) continue;
+        // colour: SH evaluated at the world-space direction camera -> mean
+        double dir[3], nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int k = 0; k < 3; ++k) dir[k] = d[k] / nd;
+        double Y[16];
+        orc_sh_basis(dir, Y);
+        const float *shg = sc->sh + 48 * g;
+        double rgb[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            double acc = 0.0;
+            for (int k = 0; k < 16; ++k) acc += Y[k] * (double)shg[3 * k + ch];
+            rgb[ch] = std::max(0.0, acc + 0.5);
+        }
+        o[PC_VISIBLE] = 1.0;
+        o[PC_U] = u; o[PC_V] = v;
+        o[PC_CONIC_A] = cc / det; o[PC_CONIC_B] = -b / det; o[PC_CONIC_C] = a / det;
+        o[PC_COV_A] = a; o[PC_COV_B] = b; o[PC_COV_C] = cc;
+        o[PC_DEPTH] = tz; o[PC_OPACITY] = opac;
+        o[PC_R] = rgb[0]; o[PC_G] = rgb[1]; o[PC_B] = rgb[2];
+        o[PC_RADIUS] = radius;
+        const float kf = (float)tz;
+        std::memcpy(&depth_key[i], &kf, 4);
+        rc[0] = x0; rc[1] = y0; rc[2] = x1; rc[3] = y1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. binning
+// ---------------------------------------------------------------------------
+
+int64_t orc_count_pairs(const int32_t *rect, int64_t n) {
+    int64_t p = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t *r = rect + 4 * i;
+        if (r[2] >= r[0] && r[3] >= r[1]) p += (int64_t)(r[2] - r[0] + 1) * (r[3] - r[1] + 1);
+    }
+    return p;
+}
+
+// Emits one pair per (slot, overlapped tile) in slot order and, within a slot,
+// row-major tile order; key = tile << 32 | depth_key, value = slot. The pairs
+// are then stably sorted by key and ranges[t] = [first, end) of tile t.
+void orc_bin_pairs(const int32_t *rect, const uint32_t *depth_key, int64_t n, int32_t tiles_x,
+                   int32_t tiles_y, uint64_t *keys, uint32_t *vals, int64_t *ranges) {
+    std::vector<std::pair<uint64_t, uint32_t>> pr;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t *r = rect + 4 * i;
+        for (int32_t ty = r[1]; ty <= r[3]; ++ty)
+            for (int32_t tx = r[0]; tx <= r[2]; ++tx) {
+                const uint64_t tile = (uint64_t)ty * tiles_x + tx;
+                pr.push_back({(tile << 32) | depth_key[i], (uint32_t)i});
+            }
+    }
+    std::stable_sort(pr.begin(), pr.end(),
+                     [](const std::pair<uint64_t, uint32_t> &a,
+                        const std::pair<uint64_t, uint32_t> &b) { return a.first < b.first; });
+    const int64_t ntiles = (int64_t)tiles_x * tiles_y;
+    for (int64_t t = 0; t < ntiles; ++t) { ranges[2 * t] = 0; ranges[2 * t + 1] = 0; }
+    for (size_t k = 0; k < pr.size(); ++k) {
+        keys[k] = pr[k].first;
+        vals[k] = pr[k].second;
+        const int64_t t = (int64_t)(pr[k].first >> 32);
+        if (k == 0 || (pr[k - 1].first >> 32) != (uint64_t)t) ranges[2 * t] = (int64_t)k;
+        ranges[2 * t + 1] = (int64_t)k + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4./5. compositing
+// ---------------------------------------------------------------------------
+
+// Blends the Gaussians list[0..len) (slots into the preprocess table, front to
+// back) at pixel centre (px, py). Returns the flag: 1 when the result may
+// differ from a float32 evaluation by more than rounding, i.e. some Gaussian
+// met while T >= 0.02 had alpha within 2e-4 relative of the 1/255 cut-off.
+static int blend_pixel(const double *pre, const uint32_t *list, int64_t len, double px, double py,
+                       double *rgb_out, int64_t *n_used) {
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+    int flag = 0;
+    int64_t used = 0;
+    for (int64_t k = 0; k < len; ++k) {
+        const double *g = pre + (int64_t)list[k] * PC_NCOLS;
+        const double dx = px - g[PC_U], dy = py - g[PC_V];
+        const double power = -0.5 * (g[PC_CONIC_A] * dx * dx + g[PC_CONIC_C] * dy * dy) -
+                             g[PC_CONIC_B] * dx * dy;
+        const double a = g[PC_OPACITY] * std::exp(power);
+        if (T >= 0.02 && std::fabs(std::log(255.0 * a)) <= 2e-4) flag = 1;
+        const double alpha = std::min(kAlphaMax, a);
+        if (alpha < kAlphaMin) continue;
+        const double test_T = T * (1.0 - alpha);
+        if (test_T < kTMin) break;
+        C[0] += alpha * T * g[PC_R];
+        C[1] += alpha * T * g[PC_G];
+        C[2] += alpha * T * g[PC_B];
+        T = test_T;
+        ++used;
+    }
+    rgb_out[0] = C[0]; rgb_out[1] = C[1]; rgb_out[2] = C[2];
+    if (n_used) *n_used = used;
+    return flag;
+}
+
+// Tiled compositing. image: [3][H][W] float64, flags: [H][W].
+void orc_composite_tiled(const double *pre, const uint32_t *vals, const int64_t *ranges,
+                         int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                         double *image, uint8_t *flags) {
+    const int32_t tiles_x = (width + tile_w - 1) / tile_w;
+    const int32_t tiles_y = (height + tile_h - 1) / tile_h;
+    const int64_t hw = (int64_t)width * height;
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < (int64_t)tiles_x * tiles_y; ++t) {
+        const int32_t tx = (int32_t)(t % tiles_x), ty = (int32_t)(t / tiles_x);
+        const int64_t r0 = ranges[2 * t], r1 = ranges[2 * t + 1];
+        for (int32_t ly = 0; ly < tile_h; ++ly)
+            for (int32_t lx = 0; lx < tile_w; ++lx) {
+                const int32_t x = tx * tile_w + lx, y = ty * tile_h + ly;
+                if (x >= width || y >= height) continue;
+                double rgb[3];
+                const int f = blend_pixel(pre, vals + r0, r1 - r0, x + 0.5, y + 0.5, rgb, nullptr);
+                const int64_t p = (int64_t)y * width + x;
+                image[p] = rgb[0]; image[hw + p] = rgb[1]; image[2 * hw + p] = rgb[2];
+                if (flags) flags[p] = (uint8_t)f;
+            }
+    }
+}
+
+// Brute force: every visible slot, ordered by (depth_key, slot), at every
+// requested pixel; no tiles, no rectangles. pix: [npix][2] (x, y) integer pixel
+// coordinates; out: [npix][3]; flags: [npix].
+void orc_render_bruteforce(const double *pre, const uint32_t *depth_key, int64_t n,
+                           const int32_t *pix, int64_t npix, double *out, uint8_t *flags) {
+    std::vector<uint32_t> order;
+    for (int64_t i = 0; i < n; ++i)
+        if (pre[i * PC_NCOLS + PC_VISIBLE] != 0.0) order.push_back((uint32_t)i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return depth_key[a] < depth_key[b]; });
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npix; ++p) {
+        double rgb[3];
+        const int f = blend_pixel(pre, order.data(), (int64_t)order.size(), pix[2 * p] + 0.5,
+                                  pix[2 * p + 1] + 0.5, rgb, nullptr);
+        out[3 * p] = rgb[0]; out[3 * p + 1] = rgb[1]; out[3 * p + 2] = rgb[2];
+        if (flags) flags[p] = (uint8_t)f;
+    }
+}
+
+int32_t orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+}  // extern "C"

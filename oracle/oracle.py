@@ -1,0 +1,241 @@
+"""Python face of the float64 oracle (test infrastructure only).
+
+Each function follows one step of the render path as the C++ source states it:
+``select_cut`` (level-of-detail cut, Sec. III-B), ``preprocess`` (EWA projection
+and SH colour of 3DGS, Sec. III-A), ``bin_pairs`` ((tile, depth) keys and a
+stable sort), ``composite_tiled`` (front-to-back blending) and
+``render_bruteforce`` (per-pixel blending over every visible Gaussian, no
+tiles). ``render`` chains them for one camera.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from types import SimpleNamespace
+
+import numpy as np
+
+from . import build as _build
+
+PC = SimpleNamespace(VISIBLE=0, U=1, V=2, CONIC_A=3, CONIC_B=4, CONIC_C=5, COV_A=6, COV_B=7,
+                     COV_C=8, DEPTH=9, OPACITY=10, R=11, G=12, B=13, RADIUS=14, NCOLS=15)
+
+
+class _Scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("pos", C.c_void_p), ("quat", C.c_void_p),
+                ("log_scale", C.c_void_p), ("opacity", C.c_void_p), ("sh", C.c_void_p),
+                ("parent", C.c_void_p), ("child_count", C.c_void_p),
+                ("aabb_min", C.c_void_p), ("aabb_max", C.c_void_p)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("R", C.c_double * 9), ("fx", C.c_double),
+                ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int32), ("height", C.c_int32), ("tau", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+            L.orc_select_cut.restype = i64
+            L.orc_select_cut.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), vp, vp, vp]
+            L.orc_preprocess.restype = None
+            L.orc_preprocess.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), vp, i64, i32, i32,
+                                         vp, vp, vp]
+            L.orc_count_pairs.restype = i64
+            L.orc_count_pairs.argtypes = [vp, i64]
+            L.orc_bin_pairs.restype = None
+            L.orc_bin_pairs.argtypes = [vp, vp, i64, i32, i32, vp, vp, vp]
+            L.orc_composite_tiled.restype = None
+            L.orc_composite_tiled.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, vp]
+            L.orc_render_bruteforce.restype = None
+            L.orc_render_bruteforce.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+            L.orc_sh_basis.restype = None
+            L.orc_sh_basis.argtypes = [vp, vp]
+            L.orc_cov3d.restype = None
+            L.orc_cov3d.argtypes = [vp, vp, vp]
+            L.orc_view_depth.restype = C.c_double
+            L.orc_view_depth.argtypes = [vp, C.POINTER(_Camera)]
+            L.orc_num_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class SceneArrays:
+    """Contiguous float32/int32 views of a scene (optionally with dequantised
+    attributes substituted), kept alive while the oracle reads them."""
+
+    def __init__(self, scene, overrides=None):
+        ov = overrides or {}
+        get = lambda k, dt: np.ascontiguousarray(ov.get(k, getattr(scene, k)), dtype=dt)
+        self.pos = get("pos", np.float32)
+        self.quat = get("quat", np.float32)
+        self.log_scale = get("log_scale", np.float32)
+        self.opacity = get("opacity", np.float32)
+        self.sh = get("sh", np.float32)
+        self.parent = get("parent", np.int32)
+        self.child_count = get("child_count", np.int32)
+        self.aabb_min = get("aabb_min", np.float32)
+        self.aabb_max = get("aabb_max", np.float32)
+        self.n = int(self.parent.shape[0])
+        self.c = _Scene(self.n, _p(self.pos).value, _p(self.quat).value, _p(self.log_scale).value,
+                        _p(self.opacity).value, _p(self.sh).value, _p(self.parent).value,
+                        _p(self.child_count).value, _p(self.aabb_min).value,
+                        _p(self.aabb_max).value)
+
+
+def _as_scene(scene):
+    return scene if isinstance(scene, SceneArrays) else SceneArrays(scene)
+
+
+def camera_struct(cam) -> _Camera:
+    c = _Camera()
+    for k in range(3):
+        c.pos[k] = float(np.float32(cam.pos[k]))
+    R = np.asarray(cam.R_wc, dtype=np.float32).reshape(9)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    c.fx, c.fy = float(np.float32(cam.fx)), float(np.float32(cam.fy))
+    c.cx, c.cy = float(np.float32(cam.cx)), float(np.float32(cam.cy))
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.tau = float(np.float32(cam.tau))
+    return c
+
+
+def select_cut(scene, cam, with_s: bool = False):
+    """Level-of-detail cut at the camera's tau. Returns (ids ascending int32,
+    near uint8[M]) and, with ``with_s``, the granularity s(n) as float64."""
+    sa = _as_scene(scene)
+    ids = np.empty(sa.n, dtype=np.int32)
+    near = np.empty(sa.n, dtype=np.uint8)
+    s = np.empty(sa.n, dtype=np.float64) if with_s else None
+    cc = camera_struct(cam)
+    k = lib().orc_select_cut(C.byref(sa.c), C.byref(cc), _p(ids), _p(near),
+                             _p(s) if with_s else None)
+    out = (ids[:k].copy(), near)
+    return out + (s,) if with_s else out
+
+
+def preprocess(scene, cam, ids, tile=(16, 16)):
+    """Per cut slot: float64 table (columns PC.*), float32 depth-key bits and
+    the inclusive tile rectangle (x0, y0, x1, y1)."""
+    sa = _as_scene(scene)
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    n = len(ids)
+    pre = np.empty((n, PC.NCOLS), dtype=np.float64)
+    key = np.empty(n, dtype=np.uint32)
+    rect = np.empty((n, 4), dtype=np.int32)
+    cc = camera_struct(cam)
+    lib().orc_preprocess(C.byref(sa.c), C.byref(cc), _p(ids), n, int(tile[0]), int(tile[1]),
+                         _p(pre), _p(key), _p(rect))
+    return pre, key, rect
+
+
+def tiles_xy(cam, tile):
+    return (-(-int(cam.width) // tile[0]), -(-int(cam.height) // tile[1]))
+
+
+def bin_pairs(rect, key, cam, tile=(16, 16)):
+    """Sorted (tile << 32 | depth) keys, slot values and per-tile [start, end)."""
+    rect = np.ascontiguousarray(rect, dtype=np.int32)
+    key = np.ascontiguousarray(key, dtype=np.uint32)
+    n = len(key)
+    L = lib()
+    P = L.orc_count_pairs(_p(rect), n)
+    tx, ty = tiles_xy(cam, tile)
+    keys = np.empty(P, dtype=np.uint64)
+    vals = np.empty(P, dtype=np.uint32)
+    ranges = np.empty((tx * ty, 2), dtype=np.int64)
+    L.orc_bin_pairs(_p(rect), _p(key), n, tx, ty, _p(keys), _p(vals), _p(ranges))
+    return keys, vals, ranges
+
+
+def composite_tiled(pre, vals, ranges, cam, tile=(16, 16)):
+    """Image [3, H, W] float64 and per-pixel near-discontinuity flags [H, W]."""
+    H, W = int(cam.height), int(cam.width)
+    img = np.empty((3, H, W), dtype=np.float64)
+    flags = np.empty((H, W), dtype=np.uint8)
+    pre = np.ascontiguousarray(pre, dtype=np.float64)
+    vals = np.ascontiguousarray(vals, dtype=np.uint32)
+    ranges = np.ascontiguousarray(ranges, dtype=np.int64)
+    lib().orc_composite_tiled(_p(pre), _p(vals), _p(ranges), W, H, int(tile[0]), int(tile[1]),
+                              _p(img), _p(flags))
+    return img, flags
+
+
+def render_bruteforce(pre, key, pixels=None, cam=None):
+    """Per-pixel blending of every visible Gaussian in (depth, slot) order.
+    ``pixels`` is an (n, 2) array of integer (x, y); default: every pixel of
+    ``cam``. Returns (rgb [n, 3], flags [n])."""
+    if pixels is None:
+        yy, xx = np.mgrid[0:int(cam.height), 0:int(cam.width)]
+        pixels = np.stack([xx.ravel(), yy.ravel()], axis=1)
+    pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+    pre = np.ascontiguousarray(pre, dtype=np.float64)
+    key = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty((len(pixels), 3), dtype=np.float64)
+    flags = np.empty(len(pixels), dtype=np.uint8)
+    lib().orc_render_bruteforce(_p(pre), _p(key), len(key), _p(pixels), len(pixels), _p(out),
+                                _p(flags))
+    return out, flags
+
+
+def render(scene, cam, tile=(16, 16), ids=None):
+    """Full tiled render of one camera. Returns a namespace with the cut, the
+    preprocess table, sorted pairs, ranges, the image and its flags."""
+    sa = _as_scene(scene)
+    near = None
+    if ids is None:
+        ids, near = select_cut(sa, cam)
+    pre, key, rect = preprocess(sa, cam, ids, tile)
+    keys, vals, ranges = bin_pairs(rect, key, cam, tile)
+    img, flags = composite_tiled(pre, vals, ranges, cam, tile)
+    return SimpleNamespace(ids=ids, near=near, pre=pre, key=key, rect=rect, keys=keys, vals=vals,
+                           ranges=ranges, image=img, flags=flags, tile=tuple(tile))
+
+
+def sh_basis(dirs):
+    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    out = np.empty((len(dirs), 16), dtype=np.float64)
+    L = lib()
+    for i in range(len(dirs)):
+        L.orc_sh_basis(_p(dirs[i]), out[i].ctypes.data_as(C.c_void_p))
+    return out
+
+
+def cov3d(quat, log_scale):
+    quat = np.ascontiguousarray(np.atleast_2d(quat), dtype=np.float32)
+    log_scale = np.ascontiguousarray(np.atleast_2d(log_scale), dtype=np.float32)
+    out = np.empty((len(quat), 3, 3), dtype=np.float64)
+    L = lib()
+    for i in range(len(quat)):
+        L.orc_cov3d(_p(quat[i]), _p(log_scale[i]), out[i].ctypes.data_as(C.c_void_p))
+    return out
+
+
+def view_depth(mu, cam):
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    cc = camera_struct(cam)
+    return lib().orc_view_depth(_p(mu), C.byref(cc))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+__all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bin_pairs",
+           "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "view_depth",
+           "tiles_xy", "num_threads", "lib"]

@@ -1,0 +1,432 @@
+"""Pins of the float64 oracle against facts fixed outside it: hand-worked
+values, closed forms, library routines (scipy rotations and spherical
+harmonics, numpy sorting), invariants and brute force. CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle as O
+from scenegen import Camera, build_hierarchy, camera_c0, look_camera, yaw_rotation
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+class _Tree:
+    """Minimal scene container for hand-made hierarchies."""
+
+    def __init__(self, n, aabb_min, aabb_max, parent, child_count):
+        self.pos = np.zeros((n, 3), np.float32)
+        self.quat = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1))
+        self.log_scale = np.full((n, 3), -3.0, np.float32)
+        self.opacity = np.full(n, 0.5, np.float32)
+        self.sh = np.zeros((n, 16, 3), np.float32)
+        self.parent = np.asarray(parent, np.int32)
+        self.child_count = np.asarray(child_count, np.int32)
+        self.aabb_min = np.asarray(aabb_min, np.float32)
+        self.aabb_max = np.asarray(aabb_max, np.float32)
+
+
+def _scene_from_leaves(pos, quat=None, log_scale=None, opacity=None, sh=None):
+    n = len(pos)
+    pos = np.asarray(pos, np.float32)
+    quat = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)) if quat is None else np.asarray(quat, np.float32)
+    log_scale = np.full((n, 3), -4.0, np.float32) if log_scale is None else np.asarray(log_scale, np.float32)
+    opacity = np.full(n, 0.5, np.float32) if opacity is None else np.asarray(opacity, np.float32)
+    if sh is None:
+        sh = np.zeros((n, 16, 3), np.float32)
+    return build_hierarchy(pos, quat, log_scale, opacity, np.asarray(sh, np.float32))
+
+
+# ---------------------------------------------------------------------------
+# scene generator (shared input)
+# ---------------------------------------------------------------------------
+
+def test_hierarchy_structure(box10k):
+    s = box10k
+    M = s.n_nodes
+    assert s.parent[0] == -1 and np.all(s.parent[1:] >= 0)
+    assert int((s.child_count == 0).sum()) == s.n_leaves == 10_000
+    # breadth-first: parents precede children, children contiguous
+    assert np.all(s.parent[1:] < np.arange(1, M))
+    inner = np.flatnonzero(s.child_count > 0)
+    for n in inner[:2000]:
+        kids = np.arange(s.child_begin[n], s.child_begin[n] + s.child_count[n])
+        assert np.all(s.parent[kids] == n)
+    assert np.all(np.bincount(s.parent[1:], minlength=M) == s.child_count)
+    # no single-child chains; at most 8 children below the deepest grid level
+    assert s.child_count[inner].min() >= 2 and s.child_count[inner].max() <= 8
+    assert np.all(np.diff(s.depth) >= 0)
+
+
+def test_aabb_nesting(box10k):
+    s = box10k
+    c = np.arange(1, s.n_nodes)
+    p = s.parent[c]
+    assert np.all(s.aabb_min[c] >= s.aabb_min[p]) and np.all(s.aabb_max[c] <= s.aabb_max[p])
+    # a parent box is exactly the union of its children's boxes
+    inner = np.flatnonzero(s.child_count > 0)
+    for n in inner[:500]:
+        kids = slice(s.child_begin[n], s.child_begin[n] + s.child_count[n])
+        assert np.array_equal(s.aabb_min[kids].min(0), s.aabb_min[n])
+        assert np.array_equal(s.aabb_max[kids].max(0), s.aabb_max[n])
+
+
+def test_moment_matching_matches_weighted_mixture():
+    from scenegen import make_uniform_box_scene
+    s = make_uniform_box_scene(3000, seed=5, keep_fp64=True)
+    inner = np.flatnonzero(s.child_count > 0)
+    for n in inner[:300]:
+        kids = np.arange(s.child_begin[n], s.child_begin[n] + s.child_count[n])
+        w = s.opacity64[kids]
+        mu = s.mean64[kids]
+        # mixture mean / covariance: weighted Sigma_i plus numpy's weighted
+        # covariance of the child means
+        mix_mu = np.average(mu, axis=0, weights=w)
+        mix_cov = np.average(s.cov64[kids], axis=0, weights=w) + np.cov(mu.T, aweights=w, bias=True)
+        np.testing.assert_allclose(s.mean64[n], mix_mu, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(s.cov64[n], mix_cov, rtol=1e-10, atol=1e-15)
+    # the stored (quaternion, log-scale) of interior nodes reproduce Sigma_p to float32 precision
+    sig = O.cov3d(s.quat[inner[:300]], s.log_scale[inner[:300]])
+    np.testing.assert_allclose(sig, s.cov64[inner[:300]], rtol=2e-5, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# cut
+# ---------------------------------------------------------------------------
+
+def _golden_cut():
+    with open(os.path.join(GOLDEN, "cut_two_leaf_tree.json")) as f:
+        g = json.load(f)
+    t = _Tree(3, g["aabb_min"], g["aabb_max"], g["parent"], g["child_count"])
+    return g, t
+
+
+def test_cut_hand_worked_tree():
+    g, t = _golden_cut()
+    for tau, want in g["cuts"].items():
+        cam = Camera(pos=np.array(g["camera_pos"], np.float32), R_wc=np.eye(3, dtype=np.float32),
+                     fx=g["fx"], fy=g["fx"], cx=8, cy=8, width=16, height=16, tau=float(tau))
+        ids, near, s = O.select_cut(t, cam, with_s=True)
+        assert ids.tolist() == want, tau
+        np.testing.assert_array_equal(s, g["s"])
+        if tau == "20":
+            assert near.tolist() == g["near_at_tau_20"]
+    cam = Camera(pos=np.array(g["camera_pos"], np.float32), R_wc=np.eye(3, dtype=np.float32),
+                 fx=g["fx"], fy=g["fx"], cx=8, cy=8, width=16, height=16, tau=10.0)
+    assert O.select_cut(t, cam)[1].tolist() == g["near_at_tau_10"]
+    # camera inside the root box: s(root) = inf, the root is never taken
+    cam.pos = np.array([0.5, 0.5, 0.5], np.float32)
+    cam.tau = 1e30
+    assert O.select_cut(t, cam)[0].tolist() == [1, 2]
+
+
+def _check_antichain_cover(s, ids):
+    sel = np.zeros(s.n_nodes, bool)
+    sel[ids] = True
+    leaves = np.flatnonzero(s.child_count == 0)
+    count = sel[leaves].astype(np.int64)
+    anc = s.parent[leaves].astype(np.int64)
+    while np.any(anc >= 0):
+        a = anc >= 0
+        count[a] += sel[anc[a]]
+        anc[a] = s.parent[anc[a]]
+    assert np.all(count == 1), "every leaf must have exactly one selected ancestor-or-self"
+    # antichain: no selected node has a selected ancestor
+    anc = s.parent[ids].astype(np.int64)
+    while np.any(anc >= 0):
+        a = anc >= 0
+        assert not np.any(sel[anc[a]])
+        anc[a] = s.parent[anc[a]]
+
+
+@pytest.mark.parametrize("tau", [0.0, 4.0, 16.0, 40.0, 120.0])
+def test_cut_invariants(box10k, tau):
+    cam = camera_c0(tau)
+    ids, near = O.select_cut(box10k, cam)
+    assert np.all(np.diff(ids) > 0)
+    _check_antichain_cover(box10k, ids)
+    if tau == 0.0:
+        assert np.array_equal(ids, np.flatnonzero(box10k.child_count == 0))
+
+
+def test_cut_coarsens_with_tau(box10k):
+    prev = None
+    s = box10k
+    for tau in [0.0, 8.0, 16.0, 32.0, 64.0, 1e30]:
+        cam = look_camera((-3.0, 2.0, 1.5), 0.0, 64, 64, fx=60.0, tau=tau)
+        ids, _ = O.select_cut(s, cam)
+        if prev is not None:
+            # every node of the finer cut has an ancestor-or-self in the coarser one
+            sel = np.zeros(s.n_nodes, bool)
+            sel[ids] = True
+            cur = prev.astype(np.int64)
+            hit = sel[cur].copy()
+            while not hit.all():
+                live = ~hit
+                cur[live] = s.parent[cur[live]]
+                assert np.all(cur[live] >= 0)
+                hit[live] = sel[cur[live]]
+            assert len(ids) <= len(prev)
+        prev = ids
+    assert prev.tolist() == [0]  # tau = inf, camera outside the root box: just the root
+
+
+# ---------------------------------------------------------------------------
+# projection
+# ---------------------------------------------------------------------------
+
+def test_cov3d_matches_scipy_rotation():
+    rng = np.random.default_rng(3)
+    q = rng.normal(size=(50, 4)).astype(np.float32)
+    s = rng.normal(-2, 0.5, size=(50, 3)).astype(np.float32)
+    got = O.cov3d(q, s)
+    qn = q.astype(np.float64) / np.linalg.norm(q.astype(np.float64), axis=1, keepdims=True)
+    R = Rotation.from_quat(np.concatenate([qn[:, 1:], qn[:, :1]], 1)).as_matrix()
+    want = np.einsum("nij,nj,nkj->nik", R, np.exp(2 * s.astype(np.float64)), R)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(O.cov3d(-q, s), got, rtol=1e-13, atol=1e-16)
+
+
+def test_sigma2d_closed_form_on_axis():
+    cam = camera_c0(0.0)  # at (2, 2, 1.2) looking +x, fx = fy = 120
+    z = 1.5
+    ls = np.log(np.array([0.02, 0.05, 0.03], np.float32))
+    sc = _scene_from_leaves([[2.0 + z, 2.0, 1.2]], log_scale=[ls], opacity=[0.9])
+    pre, key, rect = O.preprocess(sc, cam, np.array([0], np.int32))
+    sx, sy, sz = np.exp(ls.astype(np.float64))
+    # camera x = -world y, camera y = -world z, camera z = world x
+    want_a = cam.fx ** 2 * sy ** 2 / z ** 2 + 0.3
+    want_c = cam.fy ** 2 * sz ** 2 / z ** 2 + 0.3
+    assert pre[0, O.PC.VISIBLE] == 1
+    np.testing.assert_allclose(pre[0, O.PC.COV_A], want_a, rtol=1e-12)
+    np.testing.assert_allclose(pre[0, O.PC.COV_C], want_c, rtol=1e-12)
+    assert abs(pre[0, O.PC.COV_B]) < 1e-12
+    np.testing.assert_allclose([pre[0, O.PC.U], pre[0, O.PC.V]], [64.0, 64.0], atol=1e-12)
+    np.testing.assert_allclose(pre[0, O.PC.DEPTH], z, rtol=1e-12)
+
+
+def _pixel_of_world(cam, x):
+    R = cam.R_wc.astype(np.float64)
+    t = R @ (np.asarray(x, np.float64) - cam.pos.astype(np.float64))
+    return np.array([cam.fx * t[0] / t[2] + cam.cx, cam.fy * t[1] / t[2] + cam.cy])
+
+
+def test_sigma2d_equals_linearised_projection():
+    """Sigma2D - 0.3 I equals Jw Sigma Jw^T with Jw the finite-difference
+    Jacobian of the world -> pixel map (the EWA local affine approximation)."""
+    rng = np.random.default_rng(7)
+    for trial in range(20):
+        cam = look_camera(rng.uniform(-1, 1, 3), rng.uniform(-3, 3), 96, 72, fx=80.0 + 40 * trial,
+                          pitch=rng.uniform(-0.4, 0.4))
+        fwd = cam.R_wc[2].astype(np.float64)
+        mu = cam.pos + fwd * rng.uniform(1, 4) + rng.normal(0, 0.3, 3)
+        q = rng.normal(size=4)
+        ls = rng.normal(-2.5, 0.4, 3)
+        sc = _scene_from_leaves([mu], quat=[q], log_scale=[ls], opacity=[0.7])
+        pre, _, _ = O.preprocess(sc, cam, np.array([0], np.int32))
+        if pre[0, O.PC.VISIBLE] == 0:
+            continue
+        mu32 = sc.pos[0].astype(np.float64)
+        h = 1e-6
+        J = np.stack([(_pixel_of_world(cam, mu32 + h * e) - _pixel_of_world(cam, mu32 - h * e)) / (2 * h)
+                      for e in np.eye(3)], axis=1)
+        S = O.cov3d(sc.quat[0], sc.log_scale[0])[0]
+        want = J @ S @ J.T
+        got = np.array([[pre[0, O.PC.COV_A], pre[0, O.PC.COV_B]],
+                        [pre[0, O.PC.COV_B], pre[0, O.PC.COV_C]]]) - 0.3 * np.eye(2)
+        np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-6 * np.abs(want).max())
+        np.testing.assert_allclose([pre[0, O.PC.U], pre[0, O.PC.V]], _pixel_of_world(cam, mu32),
+                                   rtol=0, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# spherical harmonics
+# ---------------------------------------------------------------------------
+
+def test_sh_basis_matches_scipy():
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(64, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = O.sh_basis(d)
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    for l in range(4):
+        for m in range(-l, l + 1):
+            Y = sph_harm_y(l, abs(m), theta, phi)  # complex, Condon-Shortley phase included
+            if m > 0:
+                want = math.sqrt(2) * Y.real
+            elif m < 0:
+                want = math.sqrt(2) * Y.imag
+            else:
+                want = Y.real
+            np.testing.assert_allclose(got[:, l * l + l + m], want, atol=1e-12, err_msg=f"l={l} m={m}")
+
+
+def test_sh_basis_orthonormal_by_quadrature():
+    # Gauss-Legendre in cos(theta) x uniform phi integrates these polynomials exactly
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    ct, ph = np.meshgrid(xg, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    w = (wg[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).ravel()
+    Y = O.sh_basis(dirs)
+    G = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_dc_only_colour_is_view_independent():
+    rng = np.random.default_rng(2)
+    cam = camera_c0(0.0)
+    pts = np.array([[3.0, 2.0, 1.2], [3.5, 1.6, 1.0], [2.8, 2.3, 1.5]], np.float32)
+    sh = np.zeros((3, 16, 3), np.float32)
+    sh[:, 0, :] = rng.normal(0, 0.5, (3, 3))
+    sc = _scene_from_leaves(pts, sh=sh, opacity=[0.6, 0.6, 0.6])
+    ids, _ = O.select_cut(sc, cam)
+    pre, _, _ = O.preprocess(sc, cam, ids)
+    C0 = 0.5 / math.sqrt(math.pi)
+    for row, g in zip(pre, ids):
+        want = np.maximum(0.0, C0 * sc.sh[g, 0].astype(np.float64) + 0.5)
+        np.testing.assert_allclose(row[[O.PC.R, O.PC.G, O.PC.B]], want, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# compositing
+# ---------------------------------------------------------------------------
+
+def _aim_camera():
+    """A rotated camera (yaw 30 deg, pitch 10 deg) so that a transposed rotation
+    or a swapped axis moves the projected point."""
+    return look_camera((0.3, -0.2, 1.1), math.radians(30), 32, 24, fx=100.0, pitch=math.radians(10))
+
+
+def _world_at_pixel(cam, i, j, depth):
+    t = np.array([(i + 0.5 - cam.cx) * depth / cam.fx, (j + 0.5 - cam.cy) * depth / cam.fy, depth])
+    return cam.pos.astype(np.float64) + cam.R_wc.astype(np.float64).T @ t
+
+
+def _dc_for_colour(c):
+    C0 = 0.5 / math.sqrt(math.pi)
+    sh = np.zeros((16, 3), np.float32)
+    sh[0] = (np.asarray(c) - 0.5) / C0
+    return sh
+
+
+def test_lone_gaussian_centre_pixel_is_o_times_c():
+    cam = _aim_camera()
+    mu = _world_at_pixel(cam, 20, 9, 2.0)
+    sc = _scene_from_leaves([mu], log_scale=[np.log([0.01, 0.01, 0.01])], opacity=[0.7],
+                            sh=[_dc_for_colour([0.8, 0.3, 0.55])])
+    r = O.render(sc, cam, tile=(8, 8))
+    C0 = 0.5 / math.sqrt(math.pi)
+    c = C0 * sc.sh[0, 0].astype(np.float64) + 0.5
+    o = float(sc.opacity[0])
+    np.testing.assert_allclose(r.image[:, 9, 20], o * c, rtol=1e-9)
+    lum = r.image.sum(0)
+    assert np.unravel_index(np.argmax(lum), lum.shape) == (9, 20)
+    assert lum[9, 19] < 0.6 * lum[9, 20]
+
+
+def test_two_gaussians_on_one_ray_front_first():
+    cam = _aim_camera()
+    near_mu, far_mu = _world_at_pixel(cam, 12, 12, 1.5), _world_at_pixel(cam, 12, 12, 3.0)
+    c1, c2 = [0.9, 0.2, 0.1], [0.1, 0.4, 0.95]
+    sc = _scene_from_leaves([far_mu, near_mu], log_scale=[np.log([0.01] * 3)] * 2,
+                            opacity=[0.6, 0.45], sh=[_dc_for_colour(c2), _dc_for_colour(c1)])
+    r = O.render(sc, cam)
+    C0 = 0.5 / math.sqrt(math.pi)
+    col = C0 * sc.sh[:, 0].astype(np.float64) + 0.5
+    o = sc.opacity.astype(np.float64)
+    # node order from the octree is unknown; identify front/back by depth
+    front = int(np.argmin(r.pre[:, O.PC.DEPTH]))
+    back = 1 - front
+    gid = r.ids
+    want = o[gid[front]] * col[gid[front]] + (1 - o[gid[front]]) * o[gid[back]] * col[gid[back]]
+    np.testing.assert_allclose(r.image[:, 12, 12], want, rtol=1e-8)
+
+
+def test_opacity_clamps_at_099():
+    cam = _aim_camera()
+    mu = _world_at_pixel(cam, 5, 5, 2.0)
+    sc = _scene_from_leaves([mu], log_scale=[np.log([0.01] * 3)], opacity=[0.9990],
+                            sh=[_dc_for_colour([0.5, 0.6, 0.7])])
+    r = O.render(sc, cam)
+    C0 = 0.5 / math.sqrt(math.pi)
+    c = C0 * sc.sh[0, 0].astype(np.float64) + 0.5
+    np.testing.assert_allclose(r.image[:, 5, 5], 0.99 * c, rtol=1e-9)
+
+
+def test_alpha_08_stack_stops_after_five_layers():
+    """T after k layers of alpha 0.8 is 0.2^k; the 6th would bring T to
+    6.4e-5 < 1e-4, so it and every later layer are dropped."""
+    cam = _aim_camera()
+    n = 8
+    mus = [_world_at_pixel(cam, 16, 12, 1.0 + 0.25 * k) for k in range(n)]
+    rng = np.random.default_rng(4)
+    cols = rng.uniform(0.1, 0.9, (n, 3))
+    sc = _scene_from_leaves(mus, log_scale=[np.log([0.005] * 3)] * n, opacity=[0.8] * n,
+                            sh=[_dc_for_colour(c) for c in cols])
+    r = O.render(sc, cam)
+    C0 = 0.5 / math.sqrt(math.pi)
+    gid = r.ids[np.argsort(r.pre[:, O.PC.DEPTH])]
+    col = C0 * sc.sh[gid, 0].astype(np.float64) + 0.5
+    a = float(np.float32(0.8))
+    want = sum(a * (1 - a) ** k * col[k] for k in range(5))
+    np.testing.assert_allclose(r.image[:, 12, 16], want, rtol=1e-7)
+
+
+def test_nothing_visible_is_black():
+    cam = _aim_camera()
+    behind = cam.pos - 2.0 * cam.R_wc[2]
+    sc = _scene_from_leaves([behind, behind + 0.1], opacity=[0.9, 0.9])
+    r = O.render(sc, cam)
+    assert len(r.keys) == 0 and np.all(r.image == 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bruteforce_equals_tiled(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 200
+    cam = look_camera((0.0, 0.0, 0.0), 0.0, 32, 32, fx=30.0)
+    pos = np.stack([rng.uniform(0.5, 3, n), rng.uniform(-1.5, 1.5, n), rng.uniform(-1.5, 1.5, n)], 1)
+    q = rng.normal(size=(n, 4))
+    ls = rng.normal(-2.2, 0.5, (n, 3))
+    op = 1 / (1 + np.exp(-rng.normal(0, 1.5, n)))
+    sh = rng.normal(0, 0.05, (n, 16, 3))
+    sh[:, 0] = rng.normal(0, 0.5, (n, 3))
+    sc = _scene_from_leaves(pos, quat=q, log_scale=ls, opacity=op, sh=sh)
+    for tile in [(16, 16), (8, 8), (16, 8)]:
+        r = O.render(sc, cam, tile=tile)
+        bf, fl = O.render_bruteforce(r.pre, r.key, cam=cam)
+        assert np.array_equal(bf.reshape(32, 32, 3).transpose(2, 0, 1), r.image)
+        assert np.array_equal(fl.reshape(32, 32), r.flags)
+
+
+def test_binning_sort_matches_numpy_stable_sort(small_floor):
+    from scenegen import walk_cameras
+    cam = walk_cameras(small_floor, 1, 7, 160, 120, tau=0.0)[0]
+    ids, _ = O.select_cut(small_floor, cam)
+    pre, key, rect = O.preprocess(small_floor, cam, ids, (16, 16))
+    keys, vals, ranges = O.bin_pairs(rect, key, cam, (16, 16))
+    tx, ty = O.tiles_xy(cam, (16, 16))
+    # pairs rebuilt from the rectangles; ordered by numpy's stable sort
+    rk, rv = [], []
+    for i in np.flatnonzero(pre[:, O.PC.VISIBLE] > 0):
+        x0, y0, x1, y1 = rect[i]
+        for y in range(y0, y1 + 1):
+            for x in range(x0, x1 + 1):
+                rk.append((np.uint64(y * tx + x) << np.uint64(32)) | np.uint64(key[i]))
+                rv.append(i)
+    rk, rv = np.array(rk, np.uint64), np.array(rv, np.uint32)
+    o = np.argsort(rk, kind="stable")
+    assert np.array_equal(keys, rk[o]) and np.array_equal(vals, rv[o])
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    cnt = np.bincount(tiles, minlength=tx * ty)
+    assert np.array_equal(ranges[:, 1] - ranges[:, 0], cnt)
+    assert len(keys) > 1000
