@@ -1,0 +1,196 @@
+/*
+ * ngs.h - C ABI of the GB300 hierarchical Gaussian-splatting renderer.
+ *
+ * The renderer draws camera views of a hierarchical 3D Gaussian Splatting
+ * scene: a tree whose leaves are fine anisotropic Gaussians and whose interior
+ * nodes are coarser aggregates (NavGSim, Sec. III-B). Per view it selects a
+ * level-of-detail cut of the tree at a pixel granularity tau (Sec. III-B:
+ * Gaussians are picked from different levels per view), projects the cut's
+ * Gaussians to screen with the EWA approximation and degree-3 spherical
+ * harmonic colour, bins them into screen tiles by duplicated (tile, depth)
+ * keys and a radix sort, and blends each pixel front to back (Sec. III-A: views
+ * rendered in real time from camera intrinsics and extrinsics alone).
+ *
+ * Conventions shared by every call
+ *  - All functions return an ngs_status; nothing throws or exits across the ABI.
+ *  - Device pointers ("d_" prefix) are CUDA device addresses on the context's
+ *    device; host pointers are ordinary host memory. Streams are passed as
+ *    `void *` holding a cudaStream_t (NULL = legacy default stream).
+ *  - Work enqueued on a stream is asynchronous. Errors detected on the device
+ *    (capacity overflow, a bounded wait that gave up) are latched in the
+ *    context and returned by ngs_synchronize() and by the next call; the
+ *    context stays usable after NGS_ERR_CAPACITY and NGS_ERR_INVALID_ARG.
+ *  - Scene arrays passed to ngs_load_scene are copied; the caller keeps
+ *    ownership. Images and cut buffers are caller-owned device memory.
+ *  - One context is used from one host thread at a time.
+ */
+#ifndef NGS_H
+#define NGS_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NGS_API __attribute__((visibility("default")))
+
+typedef enum {
+    NGS_OK = 0,
+    NGS_ERR_INVALID_ARG = 1,        /* bad pointer, size, camera or option */
+    NGS_ERR_INVALID_HIERARCHY = 2,  /* scene tree fails validation at load */
+    NGS_ERR_OUT_OF_MEMORY = 3,      /* device allocation failed */
+    NGS_ERR_CAPACITY = 4,           /* a work buffer (cut, records, pairs) was too small */
+    NGS_ERR_CUDA = 5,               /* a CUDA runtime call failed */
+    NGS_ERR_DEVICE_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    NGS_ERR_NOT_LOADED = 7          /* render or cut requested before ngs_load_scene */
+} ngs_status;
+
+typedef enum { NGS_F32 = 0, NGS_F16 = 1, NGS_BF16 = 2 } ngs_dtype;
+
+/* Pinhole camera, OpenCV frame (x right, y down, z forward). A world point x
+ * maps to t = R_wc (x - pos) and to pixel (fx t.x / t.z + cx, fy t.y / t.z + cy);
+ * pixel (i, j) is sampled at (i + 0.5, j + 0.5). R_wc is row-major. tau is the
+ * level-of-detail granularity in pixels (0 selects every leaf). */
+typedef struct {
+    float pos[3];
+    float R_wc[9];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float tau;
+} ngs_camera;
+
+/* One entry per hierarchy node (leaves and interior nodes alike), node ids as
+ * in ngs_hierarchy. pos [n][3] and quat [n][4] (w, x, y, z; normalised by the
+ * renderer) are float32. log_scale [n][3] (natural log of the per-axis standard
+ * deviation), opacity [n] (in (0, 1)) and sh [n][16][3] (degree-3 SH
+ * coefficients, coefficient-major, RGB minor) are of type attr_dtype: float32,
+ * float16, or bfloat16 (as uint16 bit patterns). Reduced-precision attributes
+ * are stored as given and widened to float32 in the kernels. */
+typedef struct {
+    int64_t n;
+    const float *pos;
+    const float *quat;
+    const void *log_scale;
+    const void *opacity;
+    const void *sh;
+    int32_t attr_dtype;
+} ngs_gaussians;
+
+/* Tree over the same n nodes. Node 0 is the root (parent -1); ids are
+ * breadth-first so the children of a node are child_begin .. child_begin +
+ * child_count - 1, all with larger ids than their parent; leaves have
+ * child_count 0. aabb_min/aabb_max [n][3] float32: every child's box lies in
+ * its parent's box. Validated at load (NGS_ERR_INVALID_HIERARCHY otherwise). */
+typedef struct {
+    const int32_t *parent;
+    const int32_t *child_begin;
+    const int32_t *child_count;
+    const float *aabb_min;
+    const float *aabb_max;
+} ngs_hierarchy;
+
+typedef struct ngs_ctx ngs_ctx;
+
+/* Context configuration. Zero fields take defaults. Capacities bound the work
+ * buffers of one sub-batch of cameras: cut_capacity (selected node ids),
+ * record_capacity (visible Gaussians after culling), pair_capacity ((tile,
+ * Gaussian) pairs). A render whose sub-batch exceeds a capacity latches
+ * NGS_ERR_CAPACITY and leaves the affected images undefined. */
+typedef struct {
+    int32_t device;
+    int32_t tile_w, tile_h;          /* tile shape: 8x8, 16x8 or 16x16 (default 16x16) */
+    int32_t batch;                   /* records staged per compositing round: 64, 128, 256 (default 128) */
+    int64_t cut_capacity;            /* default 2^27 */
+    int64_t record_capacity;         /* default 2^26 */
+    int64_t pair_capacity;           /* default 2^29 */
+    int32_t max_tiles_per_batch;     /* tiles per sub-batch, <= 65536 (default 65536) */
+    int32_t reserved;
+} ngs_config;
+
+/* Render paths (ngs_set_option NGS_OPT_MODE). BATCHED: all cameras of a call
+ * in sub-batches, persistent device-sized kernels, replayed from a CUDA graph
+ * when the camera layout repeats. PLAIN: one camera at a time, sizes read back
+ * to the host between stages, no graph. Both compute identical pixels. */
+enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
+enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
+       NGS_OPT_GRAPH = 5 };
+
+typedef struct {
+    int64_t cut_total;       /* selected nodes over all cameras of the last render */
+    int64_t visible_total;   /* Gaussians kept after culling */
+    int64_t pair_total;      /* (tile, Gaussian) pairs */
+    int32_t sub_batches;     /* sub-batches of the last render */
+    int32_t graph_replayed;  /* 1 if the last render replayed a captured graph */
+    int32_t tile_w, tile_h, batch, mode;
+} ngs_stats;
+
+NGS_API const char *ngs_strerror(ngs_status s);
+
+/* Creates a context on cfg->device (cfg may be NULL for defaults). */
+NGS_API ngs_status ngs_create(const ngs_config *cfg, ngs_ctx **out);
+NGS_API ngs_status ngs_destroy(ngs_ctx *ctx);
+NGS_API ngs_status ngs_set_option(ngs_ctx *ctx, int32_t option, int64_t value);
+
+/* Copies a scene (host arrays) to the device, replacing any previous one.
+ * Synchronous. Validates the hierarchy (root 0, contiguous children, parent
+ * ids, nested boxes, leaf child counts). */
+NGS_API ngs_status ngs_load_scene(ngs_ctx *ctx, const ngs_gaussians *g, const ngs_hierarchy *h);
+
+/* Level-of-detail cut (Sec. III-B): for camera c, node n is selected iff
+ * (n is a leaf or s(n) <= tau_c) and (n is the root or s(parent(n)) > tau_c),
+ * with s(n) = fx * (longest side of box(n)) / (distance from pos to box(n)),
+ * s = +inf when the camera is inside the box. Writes the selected ids of
+ * camera c, ascending, to d_ids[d_offsets[c] .. d_offsets[c+1]) (device
+ * int32, capacity cap entries; d_offsets: device int64 [n_cams + 1]).
+ * Returns NGS_ERR_CAPACITY (after synchronising) if the cut exceeds cap. */
+NGS_API ngs_status ngs_select_cut(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
+                                  int32_t *d_ids, int64_t *d_offsets, int64_t cap, void *stream);
+
+/* Renders n_cams views (host camera array) into d_images[c] (host array of
+ * device pointers), each float32 planar [3][height][width], background 0.
+ * Per pixel p and the Gaussians g of its tile in (depth, node id) order:
+ * alpha = min(0.99, o_g exp(-1/2 d^T conic_g d)), skipped if alpha < 1/255;
+ * blending stops before the Gaussian that would bring T below 1e-4;
+ * C += alpha T c_g; T *= 1 - alpha. Asynchronous on `stream`. */
+NGS_API ngs_status ngs_render(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
+                              float *const *d_images, void *stream);
+
+/* As ngs_render, then copies each image to h_images[c] (host memory, pinned
+ * or pageable) and synchronises the stream. */
+NGS_API ngs_status ngs_render_host(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
+                                   float *const *h_images, void *stream);
+
+/* Waits for the stream and returns (then clears) any latched device error. */
+NGS_API ngs_status ngs_synchronize(ngs_ctx *ctx, void *stream);
+
+NGS_API ngs_status ngs_last_stats(ngs_ctx *ctx, ngs_stats *out);
+
+/* Tile lists of the last render, for camera `cam` of a single-sub-batch
+ * render, copied to host memory after synchronising: h_ranges [tiles][2]
+ * (int64 start, end into h_nodes) and h_nodes [cap] (int32 node ids in
+ * per-tile depth order). *n_pairs receives the number of pairs; returns
+ * NGS_ERR_CAPACITY if it exceeds cap. tiles = ceil(W/tile_w)*ceil(H/tile_h). */
+NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *ctx, int32_t cam, int64_t *h_ranges,
+                                        int32_t *h_nodes, int64_t cap, int64_t *n_pairs);
+
+/* Stable LSD radix sort (onesweep: one histogram pass, then one chained-scan
+ * scatter pass per 8-bit digit) of n (key, value) pairs by key bits
+ * [begin_bit, end_bit). d_keys/d_vals: device arrays sorted in place; keys are
+ * uint32 (key_bytes 4) or uint64 (key_bytes 8), values uint32. Scratch comes
+ * from the context (grown on demand). n < 2^31. */
+NGS_API ngs_status ngs_sort_pairs(ngs_ctx *ctx, void *d_keys, uint32_t *d_vals, int64_t n,
+                                  int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
+                                  void *stream);
+
+/* Exclusive prefix sum of n uint32 values (decoupled look-back, one pass):
+ * d_out[i] = sum of d_in[0..i); d_total (device uint32, may be NULL) gets the
+ * sum of all n. d_in and d_out may alias. n < 2^31. */
+NGS_API ngs_status ngs_scan_u32(ngs_ctx *ctx, const uint32_t *d_in, uint32_t *d_out, int64_t n,
+                                uint32_t *d_total, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NGS_H */

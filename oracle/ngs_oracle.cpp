@@ -13,8 +13,9 @@
 //                  s(parent(n)) > tau).
 //   2. preprocess: EWA projection of each cut Gaussian (Sigma2D = J W Sigma
 //                  W^T J^T + 0.3 I), its conic, pixel centre, view depth,
-//                  degree-3 SH colour, conservative support radius and tile
-//                  rectangle.
+//                  degree-3 SH colour, and the tile rectangle covering the
+//                  bounding box of its support (the ellipse where alpha >= 1/255)
+//                  widened by 1/64 pixel.
 //   3. binning   : one (tile, depth) key per Gaussian and overlapped tile,
 //                  ordered by a stable sort (std::stable_sort), tile ranges.
 //   4. composite : per pixel, front-to-back alpha blending over its tile's list.
@@ -60,7 +61,7 @@ typedef struct {
 // per cut slot, columns of the float64 preprocess table
 enum {
     PC_VISIBLE = 0, PC_U, PC_V, PC_CONIC_A, PC_CONIC_B, PC_CONIC_C, PC_COV_A, PC_COV_B,
-    PC_COV_C, PC_DEPTH, PC_OPACITY, PC_R, PC_G, PC_B, PC_RADIUS, PC_NCOLS
+    PC_COV_C, PC_DEPTH, PC_OPACITY, PC_R, PC_G, PC_B, PC_HX, PC_HY, PC_NCOLS
 };
 
 static const double kNear = 0.2;           // near plane (view z)
@@ -242,15 +243,20 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         if (!(det > 0.0)) continue;
         const double u = cam->fx * tx / tz + cam->cx;
         const double v = cam->fy * ty / tz + cam->cy;
-        const double mid = 0.5 * (a + cc);
-        const double lmax = mid + std::sqrt(std::max(0.1, mid * mid - det));
-        const double radius = std::sqrt(2.0 * std::log(255.0 * opac) * lmax) + kRectMargin;
-        int32_t x0 = (int32_t)std::floor((u - radius) / tile_w);
-        int32_t x1 = (int32_t)std::floor((u + radius) / tile_w);
-        int32_t y0 = (int32_t)std::floor((v - radius) / tile_h);
-        int32_t y1 = (int32_t)std::floor((v + radius) / tile_h);
+        // support: alpha >= 1/255 <=> d^T conic d <= K = 2 ln(255 o); the
+        // ellipse's axis-aligned bounding box has half-widths sqrt(K a), sqrt(K c)
+        const double K = 2.0 * std::log(255.0 * opac);
+        const double hx = std::sqrt(K * a) + kRectMargin;
+        const double hy = std::sqrt(K * cc) + kRectMargin;
+        int32_t x0 = (int32_t)std::floor((u - hx) / tile_w);
+        int32_t x1 = (int32_t)std::floor((u + hx) / tile_w);
+        int32_t y0 = (int32_t)std::floor((v - hy) / tile_h);
+        int32_t y1 = (int32_t)std::floor((v + hy) / tile_h);
         x0 = std::max(x0, 0); y0 = std::max(y0, 0);
         x1 = std::min(x1, tiles_x - 1); y1 = std::min(y1, tiles_y - 1);
+        // centre and support box are kept even when no tile is touched, so a
+        // comparison can tell which rectangles sit on a tile boundary
+        o[PC_U] = u; o[PC_V] = v; o[PC_HX] = hx; o[PC_HY] = hy; o[PC_DEPTH] = tz;
         if (x0 > x1 || y0 > y1) continue;
         // colour: SH evaluated at the world-space direction camera -> mean
         double dir[3], nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -270,7 +276,7 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         o[PC_COV_A] = a; o[PC_COV_B] = b; o[PC_COV_C] = cc;
         o[PC_DEPTH] = tz; o[PC_OPACITY] = opac;
         o[PC_R] = rgb[0]; o[PC_G] = rgb[1]; o[PC_B] = rgb[2];
-        o[PC_RADIUS] = radius;
+        o[PC_HX] = hx; o[PC_HY] = hy;
         const float kf = (float)tz;
         std::memcpy(&depth_key[i], &kf, 4);
         rc[0] = x0; rc[1] = y0; rc[2] = x1; rc[3] = y1;

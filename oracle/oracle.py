@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 PC = SimpleNamespace(VISIBLE=0, U=1, V=2, CONIC_A=3, CONIC_B=4, CONIC_C=5, COV_A=6, COV_B=7,
-                     COV_C=8, DEPTH=9, OPACITY=10, R=11, G=12, B=13, RADIUS=14, NCOLS=15)
+                     COV_C=8, DEPTH=9, OPACITY=10, R=11, G=12, B=13, HX=14, HY=15, NCOLS=16)
 
 
 class _Scene(C.Structure):

@@ -1,0 +1,965 @@
+// Host runtime behind the C ABI of include/ngs.h: context and device
+// residency of the scene, validation, the sub-batch planner, the plain
+// (per-view, host-synchronised) and batched (device-sized, graph-replayed)
+// render paths, and the standalone sort/scan entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ngs_internal.cuh"
+
+using namespace ngs;
+
+namespace {
+
+constexpr uint32_t kEpochStride = 32;   // epoch values reserved per sub-batch
+constexpr int kMaxCamsPerBatch = 1024;
+constexpr int kMaxCamsPerCall = 1 << 16;
+
+struct SubBatch {
+    int c0, c1;          // cameras [c0, c1)
+    uint32_t n_tiles;
+    int tile_passes;     // radix passes over the tile id
+};
+
+float half_to_float(uint16_t h) {
+    const uint32_t s = (uint32_t)(h >> 15) << 31;
+    uint32_t e = (h >> 10) & 0x1f, m = h & 0x3ff;
+    uint32_t bits;
+    if (e == 0) {
+        if (m == 0) {
+            bits = s;
+        } else {  // subnormal: renormalise
+            int sh = 0;
+            while (!(m & 0x400)) { m <<= 1; ++sh; }
+            m &= 0x3ff;
+            bits = s | ((uint32_t)(127 - 15 - sh + 1) << 23) | (m << 13);
+        }
+    } else if (e == 31) {
+        bits = s | 0x7f800000u | (m << 13);
+    } else {
+        bits = s | ((e - 15 + 127) << 23) | (m << 13);
+    }
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return f;
+}
+
+float bf16_to_float(uint16_t h) {
+    const uint32_t bits = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return f;
+}
+
+}  // namespace
+
+struct ngs_ctx {
+    int device = 0;
+    int num_sms = 0;
+    ngs_config cfg{};
+    int mode = NGS_MODE_BATCHED;
+    int tile_w = 16, tile_h = 16, batch = 128;
+    bool use_graph = true;
+    SceneDev scene;
+    bool loaded = false;
+    uint64_t scene_version = 0;
+
+    Work w;
+    bool work_ready = false;
+    uint32_t *stats_dev = nullptr;     // per sub-batch: cut, visible, pairs, pad
+    int stats_cap = 0;
+    uint32_t *cut_off32 = nullptr;     // scratch for ngs_select_cut offsets
+
+    // occupancy-derived persistent grids
+    int grid_cut = 0, grid_pre = 0, grid_sort32 = 0, grid_sort64 = 0, grid_scan = 0,
+        grid_dup = 0, grid_ranges = 0;
+
+    // graph cache
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int64_t> gkey;
+    uint64_t epoch_used = 0;
+
+    // last render
+    std::vector<SubBatch> last_plan;
+    std::vector<DevCamera> host_cams;
+    ngs_stats stats{};
+    ngs_status latched = NGS_OK;
+    double pairs_per_pixel = 48.0;     // planner estimate, raised from observations
+
+    // standalone sort/scan scratch
+    void *sort_tmp_keys = nullptr;
+    uint32_t *sort_tmp_vals = nullptr;
+    int64_t sort_tmp_cap = 0;
+};
+
+namespace {
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e__ = (call);                                                           \
+        if (e__ != cudaSuccess) {                                                           \
+            std::fprintf(stderr, "ngs: %s failed: %s (%s:%d)\n", #call,                    \
+                         cudaGetErrorString(e__), __FILE__, __LINE__);                      \
+            return e__ == cudaErrorMemoryAllocation ? NGS_ERR_OUT_OF_MEMORY : NGS_ERR_CUDA; \
+        }                                                                                   \
+    } while (0)
+
+template <typename T>
+ngs_status dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return NGS_ERR_OUT_OF_MEMORY;
+    }
+    return NGS_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+__global__ void k_bump_epoch(uint32_t *epoch, uint32_t inc) { *epoch += inc; }
+
+__global__ void k_offsets_to_i64(const uint32_t *in, int64_t *out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) out[i] = in[i];
+}
+
+__global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
+    if (threadIdx.x < 3) stats[threadIdx.x] = counters[threadIdx.x];
+}
+
+void free_work(ngs_ctx *c) {
+    Work &w = c->w;
+    dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
+    dfree(w.cut_off); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.ranges);
+    dfree(w.hist); dfree(w.cams);
+    for (int i = 0; i < 2; ++i) {
+        dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
+    }
+    dfree(c->stats_dev);
+    dfree(c->cut_off32);
+    c->w = Work();
+    c->stats_dev = nullptr;
+    c->cut_off32 = nullptr;
+    c->work_ready = false;
+}
+
+void free_scene(ngs_ctx *c) {
+    SceneDev &s = c->scene;
+    dfree(s.box_lo); dfree(s.box_hi); dfree(s.pos4); dfree(s.quat); dfree(s.sop); dfree(s.sh);
+    c->scene = SceneDev();
+    c->loaded = false;
+}
+
+void drop_graph(ngs_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey.clear();
+}
+
+ngs_status ensure_work(ngs_ctx *c) {
+    if (c->work_ready) return NGS_OK;
+    Work &w = c->w;
+    w.cut_cap = c->cfg.cut_capacity;
+    w.rec_cap = c->cfg.record_capacity;
+    w.pair_cap = c->cfg.pair_capacity;
+    w.ranges_cap = 1 << 24;
+    w.cams_cap = kMaxCamsPerCall;
+    const int64_t nblk = (c->scene.n + cut_partition_nodes() - 1) / cut_partition_nodes();
+    int64_t sw = std::max<int64_t>(nblk * kMaxCamsPerBatch, 1);
+    sw = std::max<int64_t>(sw, (w.cut_cap + preprocess_partition() - 1) / preprocess_partition());
+    sw = std::max<int64_t>(sw, (std::max(w.rec_cap, w.pair_cap) + sort_partition() - 1) /
+                                   sort_partition() * 256);
+    sw = std::max<int64_t>(sw, (w.rec_cap + scan_partition() - 1) / scan_partition());
+    w.status_words = sw;
+    ngs_status st = NGS_OK;
+    auto A = [&](ngs_status s) { if (st == NGS_OK) st = s; };
+    A(dalloc(&w.counters, N_COUNTERS));
+    A(dalloc(&w.epoch, 1));
+    A(dalloc(&w.status, (size_t)sw));
+    A(dalloc(&w.err, 1));
+    A(dalloc(&w.cut_ids, (size_t)w.cut_cap));
+    A(dalloc(&w.cut_off, kMaxCamsPerBatch + 1));
+    A(dalloc((unsigned char **)&w.rec, (size_t)w.rec_cap * sizeof(Rec32)));
+    A(dalloc(&w.rect, (size_t)w.rec_cap));
+    A(dalloc(&w.poff, (size_t)w.rec_cap));
+    for (int i = 0; i < 2; ++i) {
+        A(dalloc(&w.dkey[i], (size_t)w.rec_cap));
+        A(dalloc(&w.didx[i], (size_t)w.rec_cap));
+        A(dalloc(&w.pkey[i], (size_t)w.pair_cap));
+        A(dalloc(&w.pval[i], (size_t)w.pair_cap));
+    }
+    A(dalloc(&w.ranges, (size_t)w.ranges_cap));
+    A(dalloc(&w.hist, 8 * 256));
+    A(dalloc(&w.cams, (size_t)w.cams_cap));
+    c->stats_cap = 4096;
+    A(dalloc(&c->stats_dev, (size_t)c->stats_cap * 4));
+    A(dalloc(&c->cut_off32, kMaxCamsPerBatch + 1));
+    if (st != NGS_OK) {
+        free_work(c);
+        return st;
+    }
+    CK(cudaMemset(w.status, 0, (size_t)sw * sizeof(uint64_t)));
+    CK(cudaMemset(w.epoch, 0, sizeof(uint32_t)));
+    CK(cudaMemset(w.err, 0, sizeof(int)));
+    CK(cudaMemset(w.counters, 0, N_COUNTERS * sizeof(uint32_t)));
+    CK(cudaDeviceSynchronize());
+    c->epoch_used = 0;
+    c->work_ready = true;
+    return NGS_OK;
+}
+
+// Keeps the 30-bit epoch space from wrapping: once most of it is used, the
+// status words are cleared (outside any graph) and the epoch restarts.
+ngs_status epoch_guard(ngs_ctx *c, cudaStream_t st, uint64_t need) {
+    if (c->epoch_used + need < (1ull << 29)) {
+        c->epoch_used += need;
+        return NGS_OK;
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemset(c->w.status, 0, (size_t)c->w.status_words * sizeof(uint64_t)));
+    CK(cudaMemset(c->w.epoch, 0, sizeof(uint32_t)));
+    CK(cudaDeviceSynchronize());
+    c->epoch_used = need;
+    return NGS_OK;
+}
+
+bool camera_ok(const ngs_camera &k) {
+    if (k.width <= 0 || k.height <= 0 || k.width > 32768 || k.height > 32768) return false;
+    const float v[] = {k.pos[0], k.pos[1], k.pos[2], k.fx, k.fy, k.cx, k.cy, k.tau};
+    for (float f : v)
+        if (!std::isfinite(f)) return false;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(k.R_wc[i])) return false;
+    return k.fx > 0 && k.fy > 0 && k.tau >= 0;
+}
+
+void fill_cam(DevCamera &d, const ngs_camera &k, int tw, int th, float *image) {
+    std::memset(&d, 0, sizeof(d));
+    for (int i = 0; i < 9; ++i) d.R[i] = k.R_wc[i];
+    for (int i = 0; i < 3; ++i) {
+        d.pos[i] = k.pos[i];
+        d.posd[i] = (double)k.pos[i];
+        d.Rz[i] = (double)k.R_wc[6 + i];
+    }
+    d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy; d.tau = k.tau;
+    d.width = k.width; d.height = k.height;
+    d.tiles_x = (k.width + tw - 1) / tw;
+    d.tiles_y = (k.height + th - 1) / th;
+    d.image = image;
+}
+
+int bits_for(uint32_t n) {
+    int b = 0;
+    while (b < 32 && ((uint64_t)1 << b) < n) ++b;
+    return b;
+}
+
+// Splits cameras into sub-batches: at most kMaxCamsPerBatch cameras, at most
+// max_tiles tiles (one camera alone may exceed it), cut and record bounds
+// (every camera's cut holds at most n nodes) and an estimate of the pairs.
+std::vector<SubBatch> plan(ngs_ctx *c, std::vector<DevCamera> &cams, int max_cams_per_batch) {
+    std::vector<SubBatch> out;
+    const int64_t n = c->scene.n;
+    const int64_t max_tiles = c->cfg.max_tiles_per_batch;
+    const int64_t cams_by_cut =
+        std::max<int64_t>(1, std::min(c->w.cut_cap, c->w.rec_cap) / std::max<int64_t>(n, 1));
+    int i = 0;
+    const int N = (int)cams.size();
+    while (i < N) {
+        SubBatch sb{i, i, 0, 0};
+        int64_t tiles = 0;
+        double pairs = 0;
+        while (sb.c1 < N) {
+            const DevCamera &d = cams[sb.c1];
+            const int64_t t = (int64_t)d.tiles_x * d.tiles_y;
+            const double p = c->pairs_per_pixel * (double)d.width * d.height;
+            const int cnt = sb.c1 - sb.c0;
+            if (cnt > 0 && (tiles + t > max_tiles || cnt + 1 > max_cams_per_batch ||
+                            cnt + 1 > cams_by_cut || pairs + p > (double)c->w.pair_cap))
+                break;
+            cams[sb.c1].tile_base = (uint32_t)tiles;
+            tiles += t;
+            pairs += p;
+            ++sb.c1;
+        }
+        sb.n_tiles = (uint32_t)tiles;
+        sb.tile_passes = (bits_for(sb.n_tiles) + 7) / 8;
+        out.push_back(sb);
+        i = sb.c1;
+    }
+    return out;
+}
+
+// Enqueues the whole pipeline of one sub-batch with device-resident counts
+// (no host synchronisation): suitable for graph capture.
+void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t st) {
+    Work &w = c->w;
+    const int nc = sb.c1 - sb.c0;
+    const DevCamera *cams = w.cams + sb.c0;
+    cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st);
+    cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st);
+    k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
+    uint32_t eo = 0;
+    launch_cut(c->scene, cams, nc, w.cut_ids, w.cut_cap, w.cut_off, w.counters,
+               w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->grid_cut, st);
+    launch_preprocess(c->scene, cams, nc, w.cut_ids, w.cut_off, w.rec, w.dkey[0], w.rect,
+                      w.rec_cap, w.counters, w.counters + TK_PRE, w.status, w.epoch, eo++, w.err,
+                      c->tile_w, c->tile_h, c->grid_pre, st);
+    SortArgs da{};
+    da.keys[0] = w.dkey[0]; da.keys[1] = w.dkey[1];
+    da.vals[0] = w.didx[0]; da.vals[1] = w.didx[1];
+    da.n_dev = w.counters + CNT_VIS; da.n_host = -1; da.n_max = w.rec_cap;
+    da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = true;
+    da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
+    da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
+    launch_sort(da, c->grid_sort32, st);
+    eo += 4;
+    const int dsel = 4 & 1;  // four passes: the result is back in buffer 0
+    launch_pair_offsets(w.rect, w.didx[dsel], w.counters + CNT_VIS, w.poff, w.counters,
+                        w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
+                        c->grid_scan, st);
+    launch_duplicate(w.rect, w.didx[dsel], w.poff, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
+                     w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, c->grid_dup, st);
+    int psel = 0;
+    if (sb.tile_passes > 0) {
+        SortArgs pa{};
+        pa.keys[0] = w.pkey[0]; pa.keys[1] = w.pkey[1];
+        pa.vals[0] = w.pval[0]; pa.vals[1] = w.pval[1];
+        pa.n_dev = w.counters + CNT_PAIRS; pa.n_host = -1; pa.n_max = w.pair_cap;
+        pa.key_bytes = 4; pa.begin_bit = 0; pa.end_bit = 8 * sb.tile_passes;
+        pa.vals_identity = false;
+        pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
+        pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
+        launch_sort(pa, c->grid_sort32, st);
+        eo += sb.tile_passes;
+        psel = sb.tile_passes & 1;
+    }
+    launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, c->grid_ranges, st, w.err);
+    const int cgrid = std::min<int64_t>(
+        sb.n_tiles, (int64_t)c->num_sms *
+                        std::max(1, composite_blocks_per_sm(c->scene.attr_dtype, c->tile_w,
+                                                            c->tile_h, c->batch)));
+    launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, c->batch, true, cams, nc,
+                     sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
+                     std::max(cgrid, 1), w.err, st);
+    if (sb_index < c->stats_cap / 4)
+        k_copy_stats<<<1, 32, 0, st>>>(w.counters, c->stats_dev + 4 * sb_index);
+}
+
+ngs_status read_u32(const uint32_t *d, uint32_t *h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return NGS_OK;
+}
+
+ngs_status check_err(ngs_ctx *c) {
+    int e = 0;
+    CK(cudaMemcpy(&e, c->w.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(cudaMemset(c->w.err, 0, sizeof(int)));
+        return (ngs_status)e;
+    }
+    return NGS_OK;
+}
+
+// Plain per-view path: one camera at a time, every stage sized from counts
+// read back to the host, one CTA per partition, no graph.
+ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
+    Work &w = c->w;
+    c->last_plan.clear();
+    int64_t cut_tot = 0, vis_tot = 0, pair_tot = 0;
+    for (int ci = 0; ci < n_cams; ++ci) {
+        SubBatch sb{ci, ci + 1, 0, 0};
+        DevCamera &d = c->host_cams[ci];
+        d.tile_base = 0;
+        sb.n_tiles = (uint32_t)d.tiles_x * d.tiles_y;
+        sb.tile_passes = (bits_for(sb.n_tiles) + 7) / 8;
+        CK(cudaMemcpyAsync(w.cams + ci, &d, sizeof(DevCamera), cudaMemcpyHostToDevice, st));
+        const DevCamera *cams = w.cams + ci;
+        ngs_status es = epoch_guard(c, st, kEpochStride);
+        if (es != NGS_OK) return es;
+        CK(cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st));
+        k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
+        uint32_t eo = 0;
+        const int64_t nblk = (c->scene.n + cut_partition_nodes() - 1) / cut_partition_nodes();
+        launch_cut(c->scene, cams, 1, w.cut_ids, w.cut_cap, w.cut_off, w.counters,
+                   w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, (int)nblk, st);
+        uint32_t n_cut = 0, n_vis = 0, n_pairs = 0;
+        ngs_status s = read_u32(w.counters + CNT_CUT, &n_cut, st);
+        if (s != NGS_OK) return s;
+        if ((s = check_err(c)) != NGS_OK) return s;
+        const int gpre = std::max<int64_t>(1, ((int64_t)n_cut + preprocess_partition() - 1) /
+                                                  preprocess_partition());
+        launch_preprocess(c->scene, cams, 1, w.cut_ids, w.cut_off, w.rec, w.dkey[0], w.rect,
+                          w.rec_cap, w.counters, w.counters + TK_PRE, w.status, w.epoch, eo++,
+                          w.err, c->tile_w, c->tile_h, gpre, st);
+        if ((s = read_u32(w.counters + CNT_VIS, &n_vis, st)) != NGS_OK) return s;
+        if ((s = check_err(c)) != NGS_OK) return s;
+        const int gsort_v = std::max<int64_t>(1, ((int64_t)n_vis + sort_partition() - 1) /
+                                                     sort_partition());
+        SortArgs da{};
+        da.keys[0] = w.dkey[0]; da.keys[1] = w.dkey[1];
+        da.vals[0] = w.didx[0]; da.vals[1] = w.didx[1];
+        da.n_dev = nullptr; da.n_host = n_vis; da.n_max = w.rec_cap;
+        da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = true;
+        da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
+        da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
+        launch_sort(da, std::min(gsort_v, c->grid_sort32), st);
+        eo += 4;
+        const int gscan = std::max<int64_t>(1, ((int64_t)n_vis + scan_partition() - 1) /
+                                                   scan_partition());
+        launch_pair_offsets(w.rect, w.didx[0], w.counters + CNT_VIS, w.poff, w.counters,
+                            w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
+                            gscan, st);
+        if ((s = read_u32(w.counters + CNT_PAIRS, &n_pairs, st)) != NGS_OK) return s;
+        if ((s = check_err(c)) != NGS_OK) return s;
+        if ((int64_t)n_pairs > w.pair_cap) return NGS_ERR_CAPACITY;
+        const int gdup = std::max<int64_t>(1, ((int64_t)n_vis + 255) / 256);
+        launch_duplicate(w.rect, w.didx[0], w.poff, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
+                         w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, gdup, st);
+        int psel = 0;
+        if (sb.tile_passes > 0) {
+            const int gsort_p = std::max<int64_t>(1, ((int64_t)n_pairs + sort_partition() - 1) /
+                                                         sort_partition());
+            SortArgs pa{};
+            pa.keys[0] = w.pkey[0]; pa.keys[1] = w.pkey[1];
+            pa.vals[0] = w.pval[0]; pa.vals[1] = w.pval[1];
+            pa.n_dev = nullptr; pa.n_host = n_pairs; pa.n_max = w.pair_cap;
+            pa.key_bytes = 4; pa.begin_bit = 0; pa.end_bit = 8 * sb.tile_passes;
+            pa.vals_identity = false;
+            pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
+            pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
+            launch_sort(pa, std::min(gsort_p, c->grid_sort32), st);
+            eo += sb.tile_passes;
+            psel = sb.tile_passes & 1;
+        }
+        const int grng = std::max<int64_t>(1, std::min<int64_t>(((int64_t)n_pairs + 255) / 256,
+                                                                 (int64_t)c->num_sms * 16));
+        launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, grng, st, w.err);
+        launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, c->batch, false, cams, 1,
+                         sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
+                         (int)std::max<uint32_t>(sb.n_tiles, 1), w.err, st);
+        CK(cudaGetLastError());
+        cut_tot += n_cut; vis_tot += n_vis; pair_tot += n_pairs;
+        c->last_plan.push_back(sb);
+        c->last_plan.back().c0 = ci;
+    }
+    c->stats.cut_total = cut_tot;
+    c->stats.visible_total = vis_tot;
+    c->stats.pair_total = pair_tot;
+    c->stats.sub_batches = n_cams;
+    c->stats.graph_replayed = 0;
+    return NGS_OK;
+}
+
+ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
+    Work &w = c->w;
+    std::vector<SubBatch> sbs = plan(c, c->host_cams, kMaxCamsPerBatch);
+    // graph key: layout of the cameras and every setting the launches bake in
+    std::vector<int64_t> key;
+    key.reserve(8 + 3 * n_cams);
+    key.push_back(n_cams); key.push_back(c->tile_w); key.push_back(c->tile_h);
+    key.push_back(c->batch); key.push_back((int64_t)c->scene_version);
+    for (int i = 0; i < n_cams; ++i) {
+        key.push_back(c->host_cams[i].width);
+        key.push_back(c->host_cams[i].height);
+        key.push_back(c->host_cams[i].tile_base);
+    }
+    ngs_status es = epoch_guard(c, st, kEpochStride * sbs.size());
+    if (es != NGS_OK) return es;
+    CK(cudaMemcpyAsync(w.cams, c->host_cams.data(), sizeof(DevCamera) * n_cams,
+                       cudaMemcpyHostToDevice, st));
+    if (c->use_graph) {
+        if (!(c->gexec && key == c->gkey)) {
+            drop_graph(c);
+            if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (size_t i = 0; i < sbs.size(); ++i) enqueue_batched(c, sbs[i], (int)i, c->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            if (e != cudaSuccess) {
+                std::fprintf(stderr, "ngs: graph capture failed: %s\n", cudaGetErrorString(e));
+                return NGS_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->gexec = nullptr;
+                return NGS_ERR_CUDA;
+            }
+            c->gkey = key;
+            c->stats.graph_replayed = 0;
+        } else {
+            c->stats.graph_replayed = 1;
+        }
+        CK(cudaGraphLaunch(c->gexec, st));
+    } else {
+        for (size_t i = 0; i < sbs.size(); ++i) enqueue_batched(c, sbs[i], (int)i, st);
+        c->stats.graph_replayed = 0;
+    }
+    CK(cudaGetLastError());
+    c->last_plan = sbs;
+    c->stats.sub_batches = (int32_t)sbs.size();
+    c->stats.cut_total = c->stats.visible_total = c->stats.pair_total = -1;  // filled on demand
+    return NGS_OK;
+}
+
+ngs_status render_common(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
+                         float *const *images, cudaStream_t st) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    if (!c->loaded) return NGS_ERR_NOT_LOADED;
+    if (!cams || !images || n_cams <= 0 || n_cams > kMaxCamsPerCall) return NGS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_cams; ++i)
+        if (!camera_ok(cams[i]) || !images[i]) return NGS_ERR_INVALID_ARG;
+    ngs_status s = ensure_work(c);
+    if (s != NGS_OK) return s;
+    if (c->latched != NGS_OK) {
+        s = c->latched;
+        c->latched = NGS_OK;
+        return s;
+    }
+    c->host_cams.resize(n_cams);
+    for (int i = 0; i < n_cams; ++i) {
+        fill_cam(c->host_cams[i], cams[i], c->tile_w, c->tile_h, images[i]);
+        if ((int64_t)c->host_cams[i].tiles_x * c->host_cams[i].tiles_y > (1 << 24))
+            return NGS_ERR_INVALID_ARG;
+    }
+    c->stats.tile_w = c->tile_w; c->stats.tile_h = c->tile_h;
+    c->stats.batch = c->batch; c->stats.mode = c->mode;
+    return c->mode == NGS_MODE_PLAIN ? render_plain(c, n_cams, st) : render_batched(c, n_cams, st);
+}
+
+bool valid_box(const float *lo, const float *hi) {
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(lo[k]) || !std::isfinite(hi[k]) || lo[k] > hi[k]) return false;
+    return true;
+}
+
+ngs_status validate(const ngs_gaussians *g, const ngs_hierarchy *h) {
+    const int64_t n = g->n;
+    if (n < 1 || n >= (int64_t)1 << 31) return NGS_ERR_INVALID_ARG;
+    if (!g->pos || !g->quat || !g->log_scale || !g->opacity || !g->sh) return NGS_ERR_INVALID_ARG;
+    if (g->attr_dtype != NGS_F32 && g->attr_dtype != NGS_F16 && g->attr_dtype != NGS_BF16)
+        return NGS_ERR_INVALID_ARG;
+    if (!h->parent || !h->child_begin || !h->child_count || !h->aabb_min || !h->aabb_max)
+        return NGS_ERR_INVALID_ARG;
+    if (h->parent[0] != -1) return NGS_ERR_INVALID_HIERARCHY;
+    int64_t kids = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!valid_box(h->aabb_min + 3 * i, h->aabb_max + 3 * i)) return NGS_ERR_INVALID_HIERARCHY;
+        const int32_t p = h->parent[i];
+        if (i > 0 && (p < 0 || p >= i)) return NGS_ERR_INVALID_HIERARCHY;
+        const int32_t cc = h->child_count[i], cb = h->child_begin[i];
+        if (cc < 0) return NGS_ERR_INVALID_HIERARCHY;
+        if (cc > 0) {
+            if (cb <= i || (int64_t)cb + cc > n) return NGS_ERR_INVALID_HIERARCHY;
+            for (int32_t k = cb; k < cb + cc; ++k) {
+                if (h->parent[k] != i) return NGS_ERR_INVALID_HIERARCHY;
+                for (int a = 0; a < 3; ++a)
+                    if (h->aabb_min[3 * k + a] < h->aabb_min[3 * i + a] ||
+                        h->aabb_max[3 * k + a] > h->aabb_max[3 * i + a])
+                        return NGS_ERR_INVALID_HIERARCHY;
+            }
+        }
+        kids += cc;
+    }
+    if (kids != n - 1) return NGS_ERR_INVALID_HIERARCHY;
+    return NGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+NGS_API const char *ngs_strerror(ngs_status s) {
+    switch (s) {
+    case NGS_OK: return "ok";
+    case NGS_ERR_INVALID_ARG: return "invalid argument";
+    case NGS_ERR_INVALID_HIERARCHY: return "invalid hierarchy";
+    case NGS_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case NGS_ERR_CAPACITY: return "work buffer capacity exceeded";
+    case NGS_ERR_CUDA: return "CUDA error";
+    case NGS_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case NGS_ERR_NOT_LOADED: return "no scene loaded";
+    }
+    return "unknown status";
+}
+
+NGS_API ngs_status ngs_create(const ngs_config *cfg, ngs_ctx **out) {
+    if (!out) return NGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    ngs_config c{};
+    if (cfg) c = *cfg;
+    if (c.tile_w == 0) c.tile_w = 16;
+    if (c.tile_h == 0) c.tile_h = 16;
+    if (c.batch == 0) c.batch = 128;
+    if (c.cut_capacity <= 0) c.cut_capacity = (int64_t)1 << 27;
+    if (c.record_capacity <= 0) c.record_capacity = (int64_t)1 << 26;
+    if (c.pair_capacity <= 0) c.pair_capacity = (int64_t)1 << 29;
+    if (c.max_tiles_per_batch <= 0) c.max_tiles_per_batch = 1 << 16;
+    const bool tile_ok = (c.tile_w == 16 && c.tile_h == 16) || (c.tile_w == 16 && c.tile_h == 8) ||
+                         (c.tile_w == 8 && c.tile_h == 8);
+    if (!tile_ok || (c.batch != 64 && c.batch != 128 && c.batch != 256)) return NGS_ERR_INVALID_ARG;
+    if (c.cut_capacity >= ((int64_t)1 << 31) || c.record_capacity >= ((int64_t)1 << 31) ||
+        c.pair_capacity >= ((int64_t)1 << 31) || c.max_tiles_per_batch > (1 << 24))
+        return NGS_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return NGS_ERR_CUDA;
+    }
+    if (cudaSetDevice(c.device) != cudaSuccess) return NGS_ERR_CUDA;
+    ngs_ctx *x = new (std::nothrow) ngs_ctx();
+    if (!x) return NGS_ERR_OUT_OF_MEMORY;
+    x->device = c.device;
+    x->cfg = c;
+    x->tile_w = c.tile_w; x->tile_h = c.tile_h; x->batch = c.batch;
+    cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    sort_init_attributes();
+    x->grid_cut = 4 * x->num_sms;
+    x->grid_pre = 4 * x->num_sms;
+    x->grid_sort32 = 2 * x->num_sms;
+    x->grid_sort64 = 2 * x->num_sms;
+    x->grid_scan = 4 * x->num_sms;
+    x->grid_dup = 8 * x->num_sms;
+    x->grid_ranges = 16 * x->num_sms;
+    *out = x;
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_destroy(ngs_ctx *c) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    drop_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    free_work(c);
+    free_scene(c);
+    dfree(c->sort_tmp_keys);
+    dfree(c->sort_tmp_vals);
+    delete c;
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    switch (opt) {
+    case NGS_OPT_MODE:
+        if (v != NGS_MODE_BATCHED && v != NGS_MODE_PLAIN) return NGS_ERR_INVALID_ARG;
+        c->mode = (int)v;
+        return NGS_OK;
+    case NGS_OPT_TILE_W:
+    case NGS_OPT_TILE_H: {
+        int tw = opt == NGS_OPT_TILE_W ? (int)v : c->tile_w;
+        int th = opt == NGS_OPT_TILE_H ? (int)v : c->tile_h;
+        if (!((tw == 16 || tw == 8) && (th == 16 || th == 8))) return NGS_ERR_INVALID_ARG;
+        c->tile_w = tw; c->tile_h = th;
+        drop_graph(c);
+        return NGS_OK;
+    }
+    case NGS_OPT_BATCH:
+        if (v != 64 && v != 128 && v != 256) return NGS_ERR_INVALID_ARG;
+        c->batch = (int)v;
+        drop_graph(c);
+        return NGS_OK;
+    case NGS_OPT_GRAPH:
+        c->use_graph = v != 0;
+        if (!c->use_graph) drop_graph(c);
+        return NGS_OK;
+    }
+    return NGS_ERR_INVALID_ARG;
+}
+
+NGS_API ngs_status ngs_load_scene(ngs_ctx *c, const ngs_gaussians *g, const ngs_hierarchy *h) {
+    if (!c || !g || !h) return NGS_ERR_INVALID_ARG;
+    ngs_status s = validate(g, h);
+    if (s != NGS_OK) return s;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    drop_graph(c);
+    free_scene(c);
+    free_work(c);   // status words and cut bounds depend on the node count
+    const int64_t n = g->n;
+    std::vector<float4> lo(n), hi(n), p4(n), q(n);
+    const size_t esz = g->attr_dtype == NGS_F32 ? 4 : 2;
+    std::vector<unsigned char> sop((size_t)n * 4 * esz);
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t par = h->parent[i], cc = h->child_count[i];
+        float pf, cf;
+        std::memcpy(&pf, &par, 4);
+        std::memcpy(&cf, &cc, 4);
+        lo[i] = make_float4(h->aabb_min[3 * i], h->aabb_min[3 * i + 1], h->aabb_min[3 * i + 2], pf);
+        hi[i] = make_float4(h->aabb_max[3 * i], h->aabb_max[3 * i + 1], h->aabb_max[3 * i + 2], cf);
+        double o;
+        if (g->attr_dtype == NGS_F32) {
+            o = ((const float *)g->opacity)[i];
+            float *d = (float *)sop.data() + 4 * i;
+            const float *ls = (const float *)g->log_scale + 3 * i;
+            d[0] = ls[0]; d[1] = ls[1]; d[2] = ls[2]; d[3] = (float)o;
+        } else {
+            const uint16_t ov = ((const uint16_t *)g->opacity)[i];
+            o = g->attr_dtype == NGS_F16 ? half_to_float(ov) : bf16_to_float(ov);
+            uint16_t *d = (uint16_t *)sop.data() + 4 * i;
+            const uint16_t *ls = (const uint16_t *)g->log_scale + 3 * i;
+            d[0] = ls[0]; d[1] = ls[1]; d[2] = ls[2]; d[3] = ov;
+        }
+        // alpha <= o everywhere, so a node with 255 o < 1 never reaches 1/255;
+        // 255 o is exact in float64
+        const uint32_t flags = (255.0 * o < 1.0) ? kNodeCullOpacity : 0u;
+        float ff;
+        std::memcpy(&ff, &flags, 4);
+        p4[i] = make_float4(g->pos[3 * i], g->pos[3 * i + 1], g->pos[3 * i + 2], ff);
+        q[i] = make_float4(g->quat[4 * i], g->quat[4 * i + 1], g->quat[4 * i + 2], g->quat[4 * i + 3]);
+    }
+    SceneDev &d = c->scene;
+    ngs_status st = NGS_OK;
+    auto A = [&](ngs_status x) { if (st == NGS_OK) st = x; };
+    A(dalloc(&d.box_lo, n)); A(dalloc(&d.box_hi, n)); A(dalloc(&d.pos4, n)); A(dalloc(&d.quat, n));
+    A(dalloc((unsigned char **)&d.sop, (size_t)n * 4 * esz));
+    A(dalloc((unsigned char **)&d.sh, (size_t)n * 48 * esz));
+    if (st != NGS_OK) {
+        free_scene(c);
+        return st;
+    }
+    CK(cudaMemcpy(d.box_lo, lo.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.box_hi, hi.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.pos4, p4.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.quat, q.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.sop, sop.data(), sop.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.sh, g->sh, (size_t)n * 48 * esz, cudaMemcpyHostToDevice));
+    d.n = n;
+    d.attr_dtype = g->attr_dtype;
+    c->loaded = true;
+    ++c->scene_version;
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_select_cut(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
+                                  int32_t *d_ids, int64_t *d_offsets, int64_t cap, void *stream) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    if (!c->loaded) return NGS_ERR_NOT_LOADED;
+    if (!cams || !d_ids || !d_offsets || n_cams <= 0 || n_cams > kMaxCamsPerBatch || cap < 0)
+        return NGS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_cams; ++i)
+        if (!camera_ok(cams[i])) return NGS_ERR_INVALID_ARG;
+    ngs_status s = ensure_work(c);
+    if (s != NGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<DevCamera> hc(n_cams);
+    for (int i = 0; i < n_cams; ++i) fill_cam(hc[i], cams[i], c->tile_w, c->tile_h, nullptr);
+    Work &w = c->w;
+    if ((s = epoch_guard(c, st, kEpochStride)) != NGS_OK) return s;
+    CK(cudaMemcpyAsync(w.cams, hc.data(), sizeof(DevCamera) * n_cams, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
+    k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
+    launch_cut(c->scene, w.cams, n_cams, (uint32_t *)d_ids, std::min<int64_t>(cap, (1ll << 32) - 1),
+               c->cut_off32, w.counters, w.counters + TK_CUT, w.status, w.epoch, 0, w.err,
+               c->grid_cut, st);
+    k_offsets_to_i64<<<(n_cams + 256) / 256, 256, 0, st>>>(c->cut_off32, d_offsets, n_cams);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return check_err(c);
+}
+
+NGS_API ngs_status ngs_render(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
+                              float *const *d_images, void *stream) {
+    if (c) cudaSetDevice(c->device);
+    return render_common(c, cams, n_cams, d_images, (cudaStream_t)stream);
+}
+
+NGS_API ngs_status ngs_synchronize(ngs_ctx *c, void *stream) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (c->latched != NGS_OK) {
+        ngs_status s = c->latched;
+        c->latched = NGS_OK;
+        return s;
+    }
+    if (!c->work_ready) return NGS_OK;
+    return check_err(c);
+}
+
+NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
+                                   float *const *h_images, void *stream) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    if (!cams || !h_images || n_cams <= 0) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    // device images are carved from one buffer owned by the call
+    size_t total = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        if (!camera_ok(cams[i]) || !h_images[i]) return NGS_ERR_INVALID_ARG;
+        total += (size_t)3 * cams[i].width * cams[i].height;
+    }
+    static thread_local float *dbuf = nullptr;
+    static thread_local size_t dcap = 0;
+    if (total > dcap) {
+        dfree(dbuf);
+        dbuf = nullptr;
+        dcap = 0;
+        if (dalloc(&dbuf, total) != NGS_OK) return NGS_ERR_OUT_OF_MEMORY;
+        dcap = total;
+    }
+    std::vector<float *> dimg(n_cams);
+    size_t off = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        dimg[i] = dbuf + off;
+        off += (size_t)3 * cams[i].width * cams[i].height;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ngs_status s = render_common(c, cams, n_cams, dimg.data(), st);
+    if (s != NGS_OK) return s;
+    for (int i = 0; i < n_cams; ++i)
+        CK(cudaMemcpyAsync(h_images[i], dimg[i], sizeof(float) * 3 * cams[i].width * cams[i].height,
+                           cudaMemcpyDeviceToHost, st));
+    return ngs_synchronize(c, stream);
+}
+
+NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
+    if (!c || !out) return NGS_ERR_INVALID_ARG;
+    if (c->stats.cut_total < 0 && c->work_ready) {
+        CK(cudaDeviceSynchronize());
+        const int n = std::min<int>((int)c->last_plan.size(), c->stats_cap / 4);
+        std::vector<uint32_t> h((size_t)4 * std::max(n, 1));
+        CK(cudaMemcpy(h.data(), c->stats_dev, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost));
+        int64_t a = 0, b = 0, p = 0;
+        for (int i = 0; i < n; ++i) { a += h[4 * i]; b += h[4 * i + 1]; p += h[4 * i + 2]; }
+        c->stats.cut_total = a; c->stats.visible_total = b; c->stats.pair_total = p;
+        // keep the planner's pair estimate above what was observed
+        int64_t pix = 0;
+        for (const DevCamera &d : c->host_cams) pix += (int64_t)d.width * d.height;
+        if (pix > 0) c->pairs_per_pixel = std::max(c->pairs_per_pixel, 1.25 * (double)p / pix);
+    }
+    *out = c->stats;
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_ranges,
+                                        int32_t *h_nodes, int64_t cap, int64_t *n_pairs) {
+    if (!c || !h_ranges || !n_pairs) return NGS_ERR_INVALID_ARG;
+    if (c->last_plan.empty() || cam < 0 || cam >= (int32_t)c->host_cams.size())
+        return NGS_ERR_INVALID_ARG;
+    // the work buffers hold the last sub-batch only
+    const SubBatch &sb = c->last_plan.back();
+    if (cam < sb.c0 || cam >= sb.c1) return NGS_ERR_INVALID_ARG;
+    CK(cudaDeviceSynchronize());
+    Work &w = c->w;
+    const DevCamera &d = c->host_cams[cam];
+    const int64_t nt = (int64_t)d.tiles_x * d.tiles_y;
+    std::vector<uint2> rg(nt);
+    CK(cudaMemcpy(rg.data(), w.ranges + d.tile_base, nt * sizeof(uint2), cudaMemcpyDeviceToHost));
+    uint32_t npairs = 0;
+    CK(cudaMemcpy(&npairs, w.counters + CNT_PAIRS, 4, cudaMemcpyDeviceToHost));
+    const int psel = sb.tile_passes & 1;
+    int64_t lo = INT64_MAX, hi = 0;
+    for (int64_t t = 0; t < nt; ++t)
+        if (rg[t].y > rg[t].x) { lo = std::min<int64_t>(lo, rg[t].x); hi = std::max<int64_t>(hi, rg[t].y); }
+    if (lo == INT64_MAX) lo = hi = 0;
+    *n_pairs = hi - lo;
+    for (int64_t t = 0; t < nt; ++t) {
+        h_ranges[2 * t] = rg[t].y > rg[t].x ? (int64_t)rg[t].x - lo : 0;
+        h_ranges[2 * t + 1] = rg[t].y > rg[t].x ? (int64_t)rg[t].y - lo : 0;
+    }
+    if (hi - lo > cap) return NGS_ERR_CAPACITY;
+    if (hi > lo && h_nodes) {
+        std::vector<uint32_t> vals(hi - lo);
+        CK(cudaMemcpy(vals.data(), w.pval[psel] + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost));
+        uint32_t nvis = 0;
+        CK(cudaMemcpy(&nvis, w.counters + CNT_VIS, 4, cudaMemcpyDeviceToHost));
+        std::vector<uint4> rect(nvis);
+        CK(cudaMemcpy(rect.data(), w.rect, (size_t)nvis * sizeof(uint4), cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < hi - lo; ++k) h_nodes[k] = (int32_t)rect[vals[k]].w;
+    }
+    (void)npairs;
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_sort_pairs(ngs_ctx *c, void *d_keys, uint32_t *d_vals, int64_t n,
+                                  int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
+                                  void *stream) {
+    if (!c || (key_bytes != 4 && key_bytes != 8) || n < 0 || n >= ((int64_t)1 << 31))
+        return NGS_ERR_INVALID_ARG;
+    if (begin_bit < 0 || end_bit > 8 * key_bytes || begin_bit > end_bit) return NGS_ERR_INVALID_ARG;
+    if (n > 0 && (!d_keys || !d_vals)) return NGS_ERR_INVALID_ARG;
+    if (n == 0 || begin_bit == end_bit) return NGS_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->loaded && !c->work_ready) {
+        // no scene: size the shared work state for sorting alone
+        c->scene.n = 1;
+    }
+    ngs_status s = ensure_work(c);
+    if (s != NGS_OK) return s;
+    const int64_t parts = (n + sort_partition() - 1) / sort_partition();
+    if (parts * 256 > c->w.status_words) return NGS_ERR_CAPACITY;
+    if (n > c->sort_tmp_cap) {
+        dfree(c->sort_tmp_keys);
+        dfree(c->sort_tmp_vals);
+        c->sort_tmp_keys = nullptr;
+        c->sort_tmp_vals = nullptr;
+        c->sort_tmp_cap = 0;
+        if (dalloc((unsigned char **)&c->sort_tmp_keys, (size_t)n * key_bytes) != NGS_OK ||
+            dalloc(&c->sort_tmp_vals, (size_t)n) != NGS_OK)
+            return NGS_ERR_OUT_OF_MEMORY;
+        c->sort_tmp_cap = n;
+    }
+    const int passes = sort_passes(begin_bit, end_bit);
+    if ((s = epoch_guard(c, st, kEpochStride)) != NGS_OK) return s;
+    CK(cudaMemsetAsync(c->w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
+    k_bump_epoch<<<1, 1, 0, st>>>(c->w.epoch, kEpochStride);
+    SortArgs a{};
+    a.keys[0] = d_keys; a.keys[1] = c->sort_tmp_keys;
+    a.vals[0] = d_vals; a.vals[1] = c->sort_tmp_vals;
+    a.n_dev = nullptr; a.n_host = n; a.n_max = n;
+    a.key_bytes = key_bytes; a.begin_bit = begin_bit; a.end_bit = end_bit;
+    a.vals_identity = false;
+    a.hist = c->w.hist; a.tickets = c->w.counters + TK_SORT0; a.status = c->w.status;
+    a.epoch = c->w.epoch; a.epoch_off = 0; a.err = c->w.err;
+    const int grid = (int)std::min<int64_t>(parts, key_bytes == 8 ? c->grid_sort64 : c->grid_sort32);
+    launch_sort(a, std::max(grid, 1), st);
+    if (passes & 1) {
+        CK(cudaMemcpyAsync(d_keys, c->sort_tmp_keys, (size_t)n * key_bytes,
+                           cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(d_vals, c->sort_tmp_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaGetLastError());
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_scan_u32(ngs_ctx *c, const uint32_t *d_in, uint32_t *d_out, int64_t n,
+                                uint32_t *d_total, void *stream) {
+    if (!c || n < 0 || n >= ((int64_t)1 << 31)) return NGS_ERR_INVALID_ARG;
+    if (n > 0 && (!d_in || !d_out)) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->loaded && !c->work_ready) c->scene.n = 1;
+    ngs_status s = ensure_work(c);
+    if (s != NGS_OK) return s;
+    const int64_t parts = (n + scan_partition() - 1) / scan_partition();
+    if (parts > c->w.status_words) return NGS_ERR_CAPACITY;
+    if ((s = epoch_guard(c, st, kEpochStride)) != NGS_OK) return s;
+    CK(cudaMemsetAsync(c->w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
+    k_bump_epoch<<<1, 1, 0, st>>>(c->w.epoch, kEpochStride);
+    if (n == 0) {
+        if (d_total) CK(cudaMemsetAsync(d_total, 0, 4, st));
+        return NGS_OK;
+    }
+    launch_scan_u32(d_in, d_out, nullptr, n, d_total, c->w.counters + TK_SCAN, c->w.status,
+                    c->w.epoch, 0, c->w.err, (int)std::min<int64_t>(parts, c->grid_scan), st);
+    CK(cudaGetLastError());
+    return NGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+// K3/K4/K6: tile binning by duplicated keys.
+//
+// The (tile, depth) ordering of the pairs is produced in two stable stages
+// that together equal one stable sort on the 64-bit key (tile << 32 | depth):
+//   1. the visible Gaussians (records, in camera-major, node-id order) are
+//      radix-sorted by their 32-bit depth key;
+//   2. K3 scans, in that depth order, the number of tiles each one touches
+//      (decoupled look-back, one pass) and K4 writes one (tile, record) pair per
+//      touched tile at those offsets, so the pair array is ordered by
+//      (depth, node id, tile);
+//   3. the pairs are radix-sorted stably by tile id (16 bits for a sub-batch of
+//      at most 65536 tiles), which leaves each tile's list in (depth, node id)
+//      order;
+//   4. K6 finds each tile's [first, end) in the sorted pair array.
+// The radix passes on the depth digits thus run over Gaussians, not over
+// pairs, which is where the bytes are saved.
+#include "ngs_internal.cuh"
+
+namespace ngs {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanPart = kScanThreads * kScanItems;
+
+int scan_partition() { return kScanPart; }
+
+__device__ __forceinline__ uint32_t rect_area(const uint4 r) {
+    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
+    return (x1 - x0 + 1u) * (y1 - y0 + 1u);
+}
+
+// Block-wide exclusive scan of kScanItems values per thread (blocked layout:
+// thread t holds items t*kScanItems .. +kScanItems-1); returns the block total.
+__device__ __forceinline__ uint32_t block_scan(uint32_t v[kScanItems], uint32_t *s_warp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const uint32_t t = v[i];
+        v[i] = sum;
+        sum += t;
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < warp) wbase += s_warp[w];
+        total += s_warp[w];
+    }
+    const uint32_t off = wbase + incl - sum;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] += off;
+    return total;
+}
+
+// Exclusive scan with one-pass decoupled look-back. Input element i is
+// in[i] (kGather = false) or area(rect[idx[i]]) (kGather = true).
+template <bool kGather>
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
+       const uint32_t *__restrict__ idx, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
+       uint32_t *total_out, int64_t total_cap, uint32_t *ticket, uint64_t *status,
+       const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_part, s_prev;
+    if (*err) return;
+    const int tid = threadIdx.x;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    const int64_t nparts = (n + kScanPart - 1) / kScanPart;
+    const uint32_t epoch = *epoch_ptr + epoch_off;
+    if (nparts == 0 && blockIdx.x == 0 && tid == 0 && total_out) *total_out = 0;
+    for (;;) {
+        if (tid == 0) s_part = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int64_t part = s_part;
+        if (part >= nparts) break;
+        const int64_t base = part * kScanPart + (int64_t)tid * kScanItems;
+        uint32_t v[kScanItems];
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int64_t j = base + i;
+            if (j < n) v[i] = kGather ? rect_area(rect[idx[j]]) : in[j];
+            else v[i] = 0;
+        }
+        const uint32_t total = block_scan(v, s_warp);
+        if (tid == 0) {
+            uint64_t *slot = status + part;
+            uint32_t prev = 0;
+            if (part == 0) {
+                publish(slot, pack_status(kFlagPrefix, epoch, total));
+            } else {
+                publish(slot, pack_status(kFlagAgg, epoch, total));
+                look_back(status, part, 1, epoch, &prev, err);
+                publish(slot, pack_status(kFlagPrefix, epoch, prev + total));
+            }
+            s_prev = prev;
+            // a running total that crosses 2^32 wraps in the partition where it happens
+            if (total_cap >= 0 && prev + total < prev) latch_error(err, kErrCapacity);
+            if (part == nparts - 1) {
+                const uint64_t all = (uint64_t)prev + total;
+                if (total_out) *total_out = (uint32_t)all;
+                if (total_cap >= 0 && (int64_t)all > total_cap) latch_error(err, kErrCapacity);
+            }
+        }
+        __syncthreads();
+        const uint32_t prev = s_prev;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int64_t j = base + i;
+            if (j < n) out[j] = prev + v[i];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
+                     uint32_t *total, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                     uint32_t epoch_off, int *err, int grid, cudaStream_t st) {
+    k_scan<false><<<grid, kScanThreads, 0, st>>>(in, nullptr, nullptr, out, n_dev, n_host, total,
+                                                 -1, ticket, status, epoch, epoch_off, err);
+}
+
+void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
+                         uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
+                         uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
+                         int grid, cudaStream_t st) {
+    k_scan<true><<<grid, kScanThreads, 0, st>>>(nullptr, rect, sorted_idx, poff, n_vis, -1,
+                                                counters + CNT_PAIRS, pair_cap, ticket, status,
+                                                epoch, epoch_off, err);
+}
+
+// K4: one CTA takes 256 consecutive records in depth order, and its threads
+// then walk the CTA's contiguous pair range, each pair finding its record by
+// binary search over the CTA's offsets in shared memory (so a Gaussian that
+// covers hundreds of tiles is spread over all threads of the CTA).
+constexpr int kDupThreads = 256;
+
+__global__ void __launch_bounds__(kDupThreads)
+k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_idx,
+            const uint32_t *__restrict__ poff, const uint32_t *n_vis_p,
+            const uint32_t *n_pairs_p, int64_t pair_cap, const DevCamera *__restrict__ cams,
+            uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval, int *err) {
+    __shared__ uint32_t s_off[kDupThreads + 1];
+    __shared__ uint4 s_rect[kDupThreads];
+    __shared__ uint32_t s_idx[kDupThreads];
+    __shared__ uint2 s_cam[kDupThreads];   // (tile base, tiles_x) of each record's camera
+    if (*err) return;
+    const uint32_t n_vis = *n_vis_p, n_pairs = *n_pairs_p;
+    if ((int64_t)n_pairs > pair_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(err, kErrCapacity);
+        return;
+    }
+    const int tid = threadIdx.x;
+    for (int64_t blk = blockIdx.x; blk * kDupThreads < n_vis; blk += gridDim.x) {
+        const int64_t first = blk * kDupThreads;
+        const int64_t rem = (int64_t)n_vis - first;
+        const int cnt = rem < kDupThreads ? (int)rem : kDupThreads;
+        if (tid < cnt) {
+            const uint32_t r = sorted_idx[first + tid];
+            s_idx[tid] = r;
+            const uint4 rr = rect[r];
+            s_rect[tid] = rr;
+            s_cam[tid] = make_uint2(cams[rr.z].tile_base, (uint32_t)cams[rr.z].tiles_x);
+            s_off[tid] = poff[first + tid];
+        }
+        if (tid == 0)
+            s_off[cnt] = (first + cnt < (int64_t)n_vis) ? poff[first + cnt] : n_pairs;
+        __syncthreads();
+        const uint32_t p0 = s_off[0], p1 = s_off[cnt];
+        for (uint32_t p = p0 + tid; p < p1; p += kDupThreads) {
+            int lo = 0, hi = cnt - 1;   // last j with s_off[j] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            const uint4 r = s_rect[lo];
+            const uint32_t k = p - s_off[lo];
+            const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
+            const uint32_t w = x1 - x0 + 1u;
+            const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+            const uint2 cm = s_cam[lo];
+            pkey[p] = cm.x + ty * cm.y + tx;
+            pval[p] = s_idx[lo];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
+                      const uint32_t *n_vis, const uint32_t *n_pairs, int64_t pair_cap,
+                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, int *err, int grid,
+                      cudaStream_t st) {
+    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect, sorted_idx, poff, n_vis, n_pairs, pair_cap,
+                                              cams, pkey, pval, err);
+}
+
+// K6: ranges[t] = [first, end) of tile t in the sorted pair keys (ranges of
+// tiles without pairs stay as zeroed beforehand).
+__global__ void k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *n_pairs_p,
+                         uint2 *__restrict__ ranges, const int *err) {
+    if (*err) return;
+    const int64_t n = *n_pairs_p;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = pkey[i];
+        if (i == 0 || pkey[i - 1] != k) ranges[k].x = (uint32_t)i;
+        if (i == n - 1 || pkey[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+    }
+}
+
+void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges, int grid,
+                   cudaStream_t st, const int *err) {
+    k_ranges<<<grid, 256, 0, st>>>(pkey, n_pairs, ranges, err);
+}
+
+}  // namespace ngs

@@ -1,0 +1,181 @@
+// K7: per-tile front-to-back alpha compositing (3DGS rasterisation as used by
+// the H3DGS engine, Sec. III-A/III-B).
+//
+// One CTA renders one tile (TW x TH threads, one pixel each). The tile's
+// Gaussians, in (depth, node id) order, are staged in shared memory BATCH
+// records at a time (one cooperative gather of 48 B (float32) or 32 B
+// (float16 colour) records); every thread then walks the batch:
+//   q = A dx^2 + B dx dy + C dy^2 + L      (log2 of o * Gaussian falloff)
+//   skip if q < log2(1/255)                (alpha < 1/255)
+//   alpha = min(0.99, 2^q)
+//   stop if T (1 - alpha) < 1e-4           (this Gaussian is not blended)
+//   C += alpha T c;  T *= 1 - alpha
+// and the CTA leaves its list as soon as a block-wide ballot
+// (__syncthreads_count) finds every pixel finished. Every floating-point step
+// is an explicitly rounded intrinsic, so a pixel's value depends only on its
+// own Gaussian sequence: the same bits for any tile shape, batch size, camera
+// batch or launch form.
+//
+// Launch forms: one CTA per tile (grid = tiles), or persistent CTAs that take
+// tiles from an atomic ticket (batched renders, where one launch covers the
+// tiles of many cameras).
+#include "ngs_internal.cuh"
+
+namespace ngs {
+
+__device__ __forceinline__ void rec_colour(const Rec32 &r, float &cr, float &cg, float &cb) {
+    cr = r.b.z; cg = r.b.w; cb = r.c.x;
+}
+__device__ __forceinline__ void rec_colour(const Rec16 &r, float &cr, float &cg, float &cb) {
+    const uint32_t u = __float_as_uint(r.b.z), w = __float_as_uint(r.b.w);
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&u));
+    const float2 b0 = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    cr = rg.x; cg = rg.y; cb = b0.x;
+}
+
+template <typename R, int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(TW *TH)
+k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
+            const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
+            const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err) {
+    constexpr int NT = TW * TH;
+    __shared__ R s_rec[BATCH];
+    __shared__ uint32_t s_tile;
+    if (*err) return;
+    const int tid = threadIdx.x;
+    const int lx = tid % TW, ly = tid / TW;
+    uint32_t tile = blockIdx.x;
+    for (;;) {
+        if (persistent) {
+            if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+            __syncthreads();
+            tile = s_tile;
+        }
+        if (tile >= n_tiles) break;
+        int lo = 0, hi = n_cams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cams[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+        }
+        const DevCamera &cam = cams[lo];
+        const uint32_t local = tile - cam.tile_base;
+        const int tx = (int)(local % (uint32_t)cam.tiles_x), ty = (int)(local / (uint32_t)cam.tiles_x);
+        const int px = tx * TW + lx, py = ty * TH + ly;
+        const bool inside = px < cam.width && py < cam.height;
+        const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const uint2 rg = ranges[tile];
+        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+        bool done = !inside;
+        for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+            if (__syncthreads_count(!done) == 0) break;
+            const int n = (int)min((uint32_t)BATCH, rg.y - start);
+            for (int j = tid; j < n; j += NT) s_rec[j] = rec[pval[start + j]];
+            __syncthreads();
+            if (!done) {
+                for (int j = 0; j < n; ++j) {
+                    const R &r = s_rec[j];
+                    const float dx = __fsub_rn(fpx, r.a.x), dy = __fsub_rn(fpy, r.a.y);
+                    const float q = __fmaf_rn(r.a.z, __fmul_rn(dx, dx),
+                                              __fmaf_rn(r.a.w, __fmul_rn(dx, dy),
+                                                        __fmaf_rn(r.b.x, __fmul_rn(dy, dy), r.b.y)));
+                    if (q < kLog2AlphaMin) continue;
+                    const float alpha = fminf(kAlphaMax, exp2f(q));
+                    const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                    if (test_T < kTMin) { done = true; break; }
+                    float gr, gg, gb;
+                    rec_colour(r, gr, gg, gb);
+                    const float w = __fmul_rn(alpha, T);
+                    cr = __fmaf_rn(w, gr, cr);
+                    cg = __fmaf_rn(w, gg, cg);
+                    cb = __fmaf_rn(w, gb, cb);
+                    T = test_T;
+                }
+            }
+        }
+        if (inside) {
+            const int64_t plane = (int64_t)cam.width * cam.height;
+            const int64_t p = (int64_t)py * cam.width + px;
+            cam.image[p] = cr;
+            cam.image[plane + p] = cg;
+            cam.image[2 * plane + p] = cb;
+        }
+        if (!persistent) break;
+        __syncthreads();
+    }
+}
+
+template <typename R, int TW, int TH>
+static void launch_b(int batch, const DevCamera *cams, int n_cams, uint32_t n_tiles,
+                     const uint2 *ranges, const uint32_t *pval, const void *rec, uint32_t *ticket,
+                     int persistent, int grid, const int *err, cudaStream_t st) {
+    const R *r = (const R *)rec;
+    switch (batch) {
+    case 64:
+        k_composite<R, TW, TH, 64><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
+                                                             r, ticket, persistent, err);
+        break;
+    case 256:
+        k_composite<R, TW, TH, 256><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
+                                                              r, ticket, persistent, err);
+        break;
+    default:
+        k_composite<R, TW, TH, 128><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
+                                                              r, ticket, persistent, err);
+        break;
+    }
+}
+
+template <typename R>
+static void launch_r(int tile_w, int tile_h, int batch, const DevCamera *cams, int n_cams,
+                     uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval, const void *rec,
+                     uint32_t *ticket, int persistent, int grid, const int *err,
+                     cudaStream_t st) {
+    if (tile_w == 8 && tile_h == 8)
+        launch_b<R, 8, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent, grid,
+                          err, st);
+    else if (tile_w == 16 && tile_h == 8)
+        launch_b<R, 16, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
+                           grid, err, st);
+    else
+        launch_b<R, 16, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
+                            grid, err, st);
+}
+
+void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool persistent,
+                      const DevCamera *cams, int n_cams, uint32_t n_tiles, const uint2 *ranges,
+                      const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
+                      const int *err, cudaStream_t st) {
+    if (attr_dtype == NGS_F32)
+        launch_r<Rec32>(tile_w, tile_h, batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket,
+                        persistent ? 1 : 0, grid, err, st);
+    else
+        launch_r<Rec16>(tile_w, tile_h, batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket,
+                        persistent ? 1 : 0, grid, err, st);
+}
+
+template <typename R, int TW, int TH, int BATCH>
+static int occ() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_composite<R, TW, TH, BATCH>, TW * TH, 0);
+    return n;
+}
+
+template <typename R, int TW, int TH>
+static int occ_b(int batch) {
+    return batch == 64 ? occ<R, TW, TH, 64>() : batch == 256 ? occ<R, TW, TH, 256>()
+                                                              : occ<R, TW, TH, 128>();
+}
+
+template <typename R>
+static int occ_r(int tile_w, int tile_h, int batch) {
+    if (tile_w == 8 && tile_h == 8) return occ_b<R, 8, 8>(batch);
+    if (tile_w == 16 && tile_h == 8) return occ_b<R, 16, 8>(batch);
+    return occ_b<R, 16, 16>(batch);
+}
+
+int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch) {
+    return attr_dtype == NGS_F32 ? occ_r<Rec32>(tile_w, tile_h, batch)
+                                 : occ_r<Rec16>(tile_w, tile_h, batch);
+}
+
+}  // namespace ngs

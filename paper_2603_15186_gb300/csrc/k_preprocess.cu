@@ -1,0 +1,361 @@
+// K2: per cut Gaussian, the 3DGS screen-space preprocess that NavGSim's
+// renderer inherits (Sec. III-A/III-B): view transform, near-plane cull, EWA
+// projection of the 3D covariance, Sigma2D = J W Sigma W^T J^T + 0.3 I, its
+// inverse (the conic), the pixel centre, degree-3 SH colour seen from the
+// camera, the tile rectangle of the support, and the depth sort key.
+//
+// Support: alpha = min(0.99, o exp(-1/2 d^T conic d)) reaches 1/255 only inside
+// the ellipse d^T conic d <= K = 2 ln(255 o), whose axis-aligned bounding box
+// has half-widths sqrt(K Sigma2D_xx), sqrt(K Sigma2D_yy); the rectangle covers
+// the tiles touched by that box widened by 1/64 pixel, so it is conservative
+// under float32 rounding and the pixels do not depend on the tile shape.
+//
+// Depth key: the view depth is evaluated in float64 in a fixed operation order
+// (d_k = mu_k - c_k; z = (R20 d0 + R21 d1) + R22 d2, every product and sum
+// rounded separately) and rounded to float32; its bits are the sort key. The
+// near-plane test uses the same float64 value. Everything else is float32.
+//
+// Output is compacted in slot order (camera-major, then ascending node id) by
+// a one-pass chained scan, so the record index order breaks depth ties by
+// node id. HBM per cut Gaussian: 4 B id + 16 B position (always); quaternion
+// 16 B and scale/opacity 16 B (f32) or 8 B (f16/bf16) for those in front of
+// the near plane; SH 192 B (f32) or 96 B for those with a non-empty rectangle;
+// written per visible one: record 48 B (f32) or 32 B, key 4 B, rect 16 B
+// (tile rectangle, camera index, node id).
+#include "ngs_internal.cuh"
+
+namespace ngs {
+
+constexpr int kPreThreads = 256;
+constexpr int kPreItems = 2;
+constexpr int kPrePart = kPreThreads * kPreItems;
+constexpr int kMaxCamsPerBatch = 1024;
+
+int preprocess_partition() { return kPrePart; }
+
+template <typename A> struct Attr;
+template <> struct Attr<float> {
+    static __device__ __forceinline__ void load4(const void *p, int64_t i, float v[4]) {
+        const float4 t = reinterpret_cast<const float4 *>(p)[i];
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    static __device__ __forceinline__ void load_sh(const void *p, int64_t i, float v[48]) {
+        const float4 *s = reinterpret_cast<const float4 *>(p) + i * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float4 t = s[k];
+            v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+        }
+    }
+};
+template <> struct Attr<__half> {
+    static __device__ __forceinline__ void load4(const void *p, int64_t i, float v[4]) {
+        const uint2 t = reinterpret_cast<const uint2 *>(p)[i];
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void load_sh(const void *p, int64_t i, float v[48]) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(p) + i * 6;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const uint4 t = s[k];
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[j]));
+                v[8 * k + 2 * j] = f.x; v[8 * k + 2 * j + 1] = f.y;
+            }
+        }
+    }
+};
+template <> struct Attr<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 bf2(uint32_t w) {
+        // bfloat16 -> float32 is exact: the 16 bits are the high half of the float
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    static __device__ __forceinline__ void load4(const void *p, int64_t i, float v[4]) {
+        const uint2 t = reinterpret_cast<const uint2 *>(p)[i];
+        const float2 a = bf2(t.x), b = bf2(t.y);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void load_sh(const void *p, int64_t i, float v[48]) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(p) + i * 6;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const uint4 t = s[k];
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = bf2(w[j]);
+                v[8 * k + 2 * j] = f.x; v[8 * k + 2 * j + 1] = f.y;
+            }
+        }
+    }
+};
+
+// Real SH basis to degree 3 in the 3DGS sign convention (standard real SH
+// times (-1)^|m|), index l*l + l + m; constants are the normalisations
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0) folded with
+// the polynomial coefficients.
+__device__ __forceinline__ void sh_colour(const float sh[48], float x, float y, float z,
+                                          float rgb[3]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    float Y[16];
+    Y[0] = 0.28209479177387814f;
+    Y[1] = -0.48860251190291992f * y;
+    Y[2] = 0.48860251190291992f * z;
+    Y[3] = -0.48860251190291992f * x;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.54627421529603959f * (xx - yy);
+    Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+    Y[10] = 2.8906114426405538f * x * y * z;
+    Y[11] = -0.45704579946446572f * y * (4.0f * zz - xx - yy);
+    Y[12] = 0.37317633259011540f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
+    Y[14] = 1.4453057213202769f * z * (xx - yy);
+    Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = __fmaf_rn(Y[k], sh[3 * k + ch], acc);
+        rgb[ch] = fmaxf(acc, 0.0f);
+    }
+}
+
+struct PreOut {
+    float x, y, A, B, C, L, r, g, bl;
+    uint32_t key;
+    uint4 rect;
+};
+
+template <typename A>
+__device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCamera &cam,
+                                               uint32_t node, int tile_w, int tile_h,
+                                               PreOut &o) {
+    const float4 p = sc.pos4[node];
+    // float64 depth in the stated order; the key and the near test use it
+    const double d0 = __dsub_rn((double)p.x, cam.posd[0]);
+    const double d1 = __dsub_rn((double)p.y, cam.posd[1]);
+    const double d2 = __dsub_rn((double)p.z, cam.posd[2]);
+    const double zd = __dadd_rn(__dadd_rn(__dmul_rn(cam.Rz[0], d0), __dmul_rn(cam.Rz[1], d1)),
+                                __dmul_rn(cam.Rz[2], d2));
+    if (!(zd > kNearZd)) return false;
+    if (__float_as_uint(p.w) & kNodeCullOpacity) return false;
+    const float tz = __double2float_rn(zd);
+    const float dx = __fsub_rn(p.x, cam.pos[0]);
+    const float dy = __fsub_rn(p.y, cam.pos[1]);
+    const float dz = __fsub_rn(p.z, cam.pos[2]);
+    const float tx = __fmaf_rn(cam.R[0], dx, __fmaf_rn(cam.R[1], dy, __fmul_rn(cam.R[2], dz)));
+    const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
+
+    // 3D covariance from the normalised quaternion and the scales
+    const float4 q4 = sc.quat[node];
+    float so[4];
+    Attr<A>::load4(sc.sop, node, so);
+    const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
+    const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z),
+                R02 = 2.f * (x * z + w * y);
+    const float R10 = 2.f * (x * y + w * z), R11 = 1.f - 2.f * (x * x + z * z),
+                R12 = 2.f * (y * z - w * x);
+    const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x),
+                R22 = 1.f - 2.f * (x * x + y * y);
+    const float s0 = expf(so[0]), s1 = expf(so[1]), s2 = expf(so[2]);
+    const float opac = so[3];
+    const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+    const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+    const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+    const float S00 = M00 * M00 + M01 * M01 + M02 * M02;
+    const float S01 = M00 * M10 + M01 * M11 + M02 * M12;
+    const float S02 = M00 * M20 + M01 * M21 + M02 * M22;
+    const float S11 = M10 * M10 + M11 * M11 + M12 * M12;
+    const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
+    const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
+
+    // T = J W (2x3): rows (fx/z) W0 - (fx x/z^2) W2 and (fy/z) W1 - (fy y/z^2) W2
+    const float iz = 1.0f / tz;
+    const float ax = cam.fx * iz, bx = -cam.fx * tx * iz * iz;
+    const float ay = cam.fy * iz, by = -cam.fy * ty * iz * iz;
+    const float T00 = ax * cam.R[0] + bx * cam.R[6], T01 = ax * cam.R[1] + bx * cam.R[7],
+                T02 = ax * cam.R[2] + bx * cam.R[8];
+    const float T10 = ay * cam.R[3] + by * cam.R[6], T11 = ay * cam.R[4] + by * cam.R[7],
+                T12 = ay * cam.R[5] + by * cam.R[8];
+    // U = T Sigma
+    const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
+    const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
+    const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
+    const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
+    const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
+    const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
+    const float ca = U00 * T00 + U01 * T01 + U02 * T02 + kBlur;
+    const float cb = U00 * T10 + U01 * T11 + U02 * T12;
+    const float cc = U10 * T10 + U11 * T11 + U12 * T12 + kBlur;
+    const float det = ca * cc - cb * cb;
+    if (!(det > 0.0f)) return false;
+    const float idet = 1.0f / det;
+    const float u = __fmaf_rn(cam.fx * iz, tx, cam.cx);
+    const float v = __fmaf_rn(cam.fy * iz, ty, cam.cy);
+
+    // support box and tile rectangle
+    const float K = 2.0f * logf(255.0f * opac);
+    const float hx = sqrtf(K * ca) + kRectMargin;
+    const float hy = sqrtf(K * cc) + kRectMargin;
+    const float itw = 1.0f / (float)tile_w, ith = 1.0f / (float)tile_h;
+    int x0 = (int)floorf((u - hx) * itw), x1 = (int)floorf((u + hx) * itw);
+    int y0 = (int)floorf((v - hy) * ith), y1 = (int)floorf((v + hy) * ith);
+    x0 = max(x0, 0); y0 = max(y0, 0);
+    x1 = min(x1, cam.tiles_x - 1); y1 = min(y1, cam.tiles_y - 1);
+    if (x0 > x1 || y0 > y1) return false;
+
+    // colour seen along camera -> mean
+    float sh[48];
+    Attr<A>::load_sh(sc.sh, node, sh);
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float rgb[3];
+    sh_colour(sh, dx * inv, dy * inv, dz * inv, rgb);
+
+    o.x = u;
+    o.y = v;
+    o.A = -0.5f * kLog2e * (cc * idet);
+    o.B = kLog2e * (cb * idet);
+    o.C = -0.5f * kLog2e * (ca * idet);
+    o.L = log2f(opac);
+    o.r = rgb[0]; o.g = rgb[1]; o.bl = rgb[2];
+    o.key = __float_as_uint(tz);
+    o.rect = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16),
+                        0u, node);
+    return true;
+}
+
+__device__ __forceinline__ void store_rec(Rec32 *rec, int64_t i, const PreOut &o) {
+    rec[i].a = make_float4(o.x, o.y, o.A, o.B);
+    rec[i].b = make_float4(o.C, o.L, o.r, o.g);
+    rec[i].c = make_float4(o.bl, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void store_rec(Rec16 *rec, int64_t i, const PreOut &o) {
+    const __half2 rg = __floats2half2_rn(o.r, o.g);
+    const __half2 b0 = __floats2half2_rn(o.bl, 0.0f);
+    rec[i].a = make_float4(o.x, o.y, o.A, o.B);
+    rec[i].b = make_float4(o.C, o.L, __uint_as_float(*reinterpret_cast<const uint32_t *>(&rg)),
+                           __uint_as_float(*reinterpret_cast<const uint32_t *>(&b0)));
+}
+
+template <typename A, typename R>
+__global__ void __launch_bounds__(kPreThreads)
+k_preprocess(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams,
+             const uint32_t *__restrict__ cut_ids, const uint32_t *__restrict__ cut_off,
+             R *__restrict__ rec, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
+             int64_t rec_cap, uint32_t *counters, uint32_t *ticket, uint64_t *status,
+             const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, int tile_w, int tile_h) {
+    __shared__ uint32_t s_off[kMaxCamsPerBatch + 1];
+    __shared__ uint32_t s_cnt[kPreItems * 8];
+    __shared__ uint32_t s_part, s_excl;
+    if (*err) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i <= n_cams; i += kPreThreads) s_off[i] = cut_off[i];
+    __syncthreads();
+    const uint32_t n_slots = s_off[n_cams];
+    const int64_t nparts = ((int64_t)n_slots + kPrePart - 1) / kPrePart;
+    const uint32_t epoch = *epoch_ptr + epoch_off;
+    for (;;) {
+        if (tid == 0) s_part = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int64_t part = s_part;
+        if (part >= nparts) break;
+        PreOut out[kPreItems];
+        uint32_t bal[kPreItems];
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k) {
+            const int64_t slot = part * kPrePart + k * kPreThreads + tid;
+            bool vis = false;
+            if (slot < n_slots) {
+                int lo = 0, hi = n_cams - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= (uint32_t)slot) lo = mid; else hi = mid - 1;
+                }
+                vis = preprocess_one<A>(sc, cams[lo], cut_ids[slot], tile_w, tile_h, out[k]);
+                out[k].rect.z = (uint32_t)lo;
+            }
+            bal[k] = __ballot_sync(0xffffffffu, vis);
+            if (lane == 0) s_cnt[k * 8 + warp] = __popc(bal[k]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t v = lane < kPreItems * 8 ? s_cnt[lane] : 0u;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < kPreItems * 8) s_cnt[lane] = incl - v;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (lane == 0) {
+                uint64_t *slotp = status + part;
+                uint32_t prev = 0;
+                if (part == 0) {
+                    publish(slotp, pack_status(kFlagPrefix, epoch, total));
+                } else {
+                    publish(slotp, pack_status(kFlagAgg, epoch, total));
+                    look_back(status, part, 1, epoch, &prev, err);
+                    publish(slotp, pack_status(kFlagPrefix, epoch, prev + total));
+                }
+                s_excl = prev;
+                if (part == nparts - 1) {
+                    counters[CNT_VIS] = prev + total;
+                    if ((int64_t)prev + total > rec_cap) latch_error(err, kErrCapacity);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t base = s_excl;
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k) {
+            if ((bal[k] >> lane) & 1u) {
+                const int64_t pos = (int64_t)base + s_cnt[k * 8 + warp] +
+                                    __popc(bal[k] & lanemask_lt());
+                if (pos < rec_cap) {
+                    store_rec(rec, pos, out[k]);
+                    dkey[pos] = out[k].key;
+                    rect[pos] = out[k].rect;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // an empty cut never enters the loop: the visible count is zero
+    if (nparts == 0 && blockIdx.x == 0 && tid == 0) counters[CNT_VIS] = 0;
+}
+
+void launch_preprocess(const SceneDev &sc, const DevCamera *cams, int n_cams,
+                       const uint32_t *cut_ids, const uint32_t *cut_off, void *rec,
+                       uint32_t *dkey, uint4 *rect, int64_t rec_cap, uint32_t *counters,
+                       uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                       uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
+                       cudaStream_t st) {
+    switch (sc.attr_dtype) {
+    case NGS_F16:
+        k_preprocess<__half, Rec16><<<grid, kPreThreads, 0, st>>>(
+            sc, cams, n_cams, cut_ids, cut_off, (Rec16 *)rec, dkey, rect, rec_cap, counters,
+            ticket, status, epoch, epoch_off, err, tile_w, tile_h);
+        break;
+    case NGS_BF16:
+        k_preprocess<__nv_bfloat16, Rec16><<<grid, kPreThreads, 0, st>>>(
+            sc, cams, n_cams, cut_ids, cut_off, (Rec16 *)rec, dkey, rect, rec_cap, counters,
+            ticket, status, epoch, epoch_off, err, tile_w, tile_h);
+        break;
+    default:
+        k_preprocess<float, Rec32><<<grid, kPreThreads, 0, st>>>(
+            sc, cams, n_cams, cut_ids, cut_off, (Rec32 *)rec, dkey, rect, rec_cap, counters,
+            ticket, status, epoch, epoch_off, err, tile_w, tile_h);
+        break;
+    }
+}
+
+}  // namespace ngs

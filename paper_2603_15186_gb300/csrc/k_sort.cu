@@ -1,0 +1,252 @@
+// K5: stable least-significant-digit radix sort of (key, value) pairs in the
+// "onesweep" arrangement: one upsweep kernel builds the digit histograms of
+// every pass from a single read of the keys, then each 8-bit digit pass is one
+// kernel that ranks a 4096-key partition in shared memory and finds, for each
+// of the 256 digits, the partition's global offset by decoupled look-back over
+// the preceding partitions (no separate scan kernel per pass).
+//
+// Stability: keys are loaded warp-striped (item i of lane l is key
+// base + 512 w + 32 i + l), each warp ranks its items in that order with
+// eight ballots per item (peers = lanes holding the same digit), warps are
+// offset in order, and partitions in ticket order; equal digits therefore keep
+// their input order, which is what the two-stage binning needs.
+//
+// Forward progress: partition ids come from an atomic ticket, so every
+// partition a look-back waits on is held by a CTA that is already running.
+// Every wait is bounded (kSpinLimit) and latches kErrTimeout if it runs out.
+//
+// HBM per pass: read key + value, write key + value (16 B/pair for 32-bit
+// keys, 24 B for 64-bit), plus the upsweep's one read of the keys.
+#include "ngs_internal.cuh"
+
+namespace ngs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortPart = kSortThreads * kSortItems;   // 4096 keys
+constexpr int kRadix = 256;
+constexpr int kMaxPasses = 8;
+
+int sort_partition() { return kSortPart; }
+int sort_passes(int begin_bit, int end_bit) { return (end_bit - begin_bit + 7) / 8; }
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift, uint32_t mask) {
+    return (uint32_t)(key >> shift) & mask;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+k_upsweep(const K *__restrict__ keys, const uint32_t *n_dev, int64_t n_host, int begin_bit,
+          int end_bit, uint32_t *__restrict__ hist, const int *err) {
+    __shared__ uint32_t s_h[kMaxPasses][kRadix];
+    if (*err) return;
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    for (int64_t i = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kSortThreads) {
+        const K k = keys[i];
+        for (int p = 0; p < passes; ++p) {
+            const int sh = begin_bit + 8 * p;
+            const int bits = min(8, end_bit - sh);
+            atomicAdd(&s_h[p][digit_of(k, sh, (1u << bits) - 1u)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
+        const uint32_t v = (&s_h[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// hist[p][d] -> exclusive prefix over d (one block per pass)
+__global__ void k_digit_scan(uint32_t *hist, const int *err) {
+    __shared__ uint32_t s_w[kSortWarps];
+    if (*err) return;
+    uint32_t *h = hist + blockIdx.x * kRadix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t v = h[tid];
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += s_w[w];
+    h[tid] = wbase + incl - v;
+}
+
+template <typename K>
+struct SortSmem {
+    uint32_t whist[kSortWarps][kRadix];   // per-warp digit counts, then warp offsets
+    uint32_t dstart[kRadix];              // block-local start of each digit
+    uint32_t gstart[kRadix];              // global start of each digit for this partition
+    uint32_t wtot[kSortWarps];
+    K keys[kSortPart];
+    uint32_t vals[kSortPart];
+    uint32_t part;
+};
+
+template <typename K, bool kIdentity>
+__global__ void __launch_bounds__(kSortThreads)
+k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+           uint32_t *__restrict__ vout, const uint32_t *n_dev, int64_t n_host, int shift,
+           uint32_t mask, const uint32_t *__restrict__ digit_base, uint64_t *status,
+           uint32_t *ticket, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem<K> &S = *reinterpret_cast<SortSmem<K> *>(smem_raw);
+    if (*err) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    const int64_t nparts = (n + kSortPart - 1) / kSortPart;
+    const uint32_t epoch = *epoch_ptr + epoch_off;
+    const uint32_t lt = lanemask_lt();
+    for (;;) {
+        if (tid == 0) S.part = atomicAdd(ticket, 1u);
+        for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t part = S.part;
+        if (part >= nparts) break;
+        const int64_t base = part * kSortPart + (int64_t)warp * (kSortItems * 32);
+        K key[kSortItems];
+        uint32_t val[kSortItems];
+        uint32_t rank[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            const bool valid = idx < n;
+            key[i] = valid ? kin[idx] : (K)0;
+            val[i] = kIdentity ? (uint32_t)idx : (valid ? vin[idx] : 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            const bool valid = idx < n;
+            const uint32_t d = digit_of(key[i], shift, mask);
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t bit = (d >> b) & 1u;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
+            uint32_t before = 0;
+            if (valid) before = S.whist[warp][d];
+            __syncwarp();
+            if (valid && (peers & lt) == 0) S.whist[warp][d] = before + __popc(peers);
+            __syncwarp();
+            rank[i] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+        // thread d owns digit d: warp offsets, partition total, look-back
+        {
+            const int d = tid;
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t t = S.whist[w][d];
+                S.whist[w][d] = run;
+                run += t;
+            }
+            uint64_t *slot = status + part * kRadix + d;
+            uint32_t prev = 0;
+            if (part == 0) {
+                publish(slot, pack_status(kFlagPrefix, epoch, run));
+            } else {
+                publish(slot, pack_status(kFlagAgg, epoch, run));
+                look_back(status + d, part, kRadix, epoch, &prev, err);
+                publish(slot, pack_status(kFlagPrefix, epoch, prev + run));
+            }
+            S.gstart[d] = digit_base[d] + prev;
+            // block-local exclusive scan of the digit totals
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) S.wtot[warp] = incl;
+            __syncthreads();
+            uint32_t wbase = 0;
+            for (int w = 0; w < warp; ++w) wbase += S.wtot[w];
+            S.dstart[d] = wbase + incl - run;
+        }
+        __syncthreads();
+        // stage the partition in shared memory in digit order
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            if (idx < n) {
+                const uint32_t d = digit_of(key[i], shift, mask);
+                const uint32_t lp = S.dstart[d] + S.whist[warp][d] + rank[i];
+                S.keys[lp] = key[i];
+                S.vals[lp] = val[i];
+            }
+        }
+        __syncthreads();
+        const int64_t rem = n - part * kSortPart;
+        const int cnt = rem < kSortPart ? (int)rem : kSortPart;
+        for (int j = tid; j < cnt; j += kSortThreads) {
+            const K k = S.keys[j];
+            const uint32_t d = digit_of(k, shift, mask);
+            const int64_t g = (int64_t)S.gstart[d] + (j - S.dstart[d]);
+            kout[g] = k;
+            vout[g] = S.vals[j];
+        }
+        __syncthreads();
+    }
+}
+
+size_t sort_smem_bytes(int key_bytes) {
+    return key_bytes == 8 ? sizeof(SortSmem<uint64_t>) : sizeof(SortSmem<uint32_t>);
+}
+
+void sort_init_attributes() {
+    cudaFuncSetAttribute(k_onesweep<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SortSmem<uint32_t>));
+    cudaFuncSetAttribute(k_onesweep<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SortSmem<uint32_t>));
+    cudaFuncSetAttribute(k_onesweep<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SortSmem<uint64_t>));
+    cudaFuncSetAttribute(k_onesweep<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SortSmem<uint64_t>));
+}
+
+template <typename K>
+static void launch_sort_t(const SortArgs &a, int grid, cudaStream_t st) {
+    const int passes = sort_passes(a.begin_bit, a.end_bit);
+    const size_t smem = sizeof(SortSmem<K>);
+    cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kRadix * passes, st);
+    k_upsweep<K><<<grid, kSortThreads, 0, st>>>((const K *)a.keys[0], a.n_dev, a.n_host,
+                                                a.begin_bit, a.end_bit, a.hist, a.err);
+    k_digit_scan<<<passes, kRadix, 0, st>>>(a.hist, a.err);
+    for (int p = 0; p < passes; ++p) {
+        const int src = p & 1, dst = src ^ 1;
+        const int sh = a.begin_bit + 8 * p;
+        const int bits = std::min(8, a.end_bit - sh);
+        const uint32_t mask = (1u << bits) - 1u;
+        if (p == 0 && a.vals_identity)
+            k_onesweep<K, true><<<grid, kSortThreads, smem, st>>>(
+                (const K *)a.keys[src], nullptr, (K *)a.keys[dst], a.vals[dst], a.n_dev, a.n_host,
+                sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch, a.epoch_off + p,
+                a.err);
+        else
+            k_onesweep<K, false><<<grid, kSortThreads, smem, st>>>(
+                (const K *)a.keys[src], a.vals[src], (K *)a.keys[dst], a.vals[dst], a.n_dev,
+                a.n_host, sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch,
+                a.epoch_off + p, a.err);
+    }
+}
+
+void launch_sort(const SortArgs &a, int grid, cudaStream_t st) {
+    if (a.key_bytes == 8) launch_sort_t<uint64_t>(a, grid, st);
+    else launch_sort_t<uint32_t>(a, grid, st);
+}
+
+}  // namespace ngs

@@ -1,0 +1,256 @@
+// Internal declarations shared by the renderer's translation units.
+//
+// Device data layout (structure of arrays, one entry per hierarchy node):
+//   box_lo[n]  float4 (min.x, min.y, min.z, parent id as int bits)
+//   box_hi[n]  float4 (max.x, max.y, max.z, child count as int bits)
+//   pos4[n]    float4 (mean.x, mean.y, mean.z, flags as int bits)
+//   quat[n]    float4 (w, x, y, z)
+//   sop[n]     4 x A  (log_scale.x, .y, .z, opacity), A = float | half | bf16
+//   sh[n]      48 x A (16 coefficients x RGB)
+// Per render sub-batch (work buffers):
+//   cut ids (uint32), compositing records (Rec32 / Rec16), depth keys and
+//   record indices (double-buffered for the sort), tile rectangles, pair keys
+//   and values (double-buffered), tile ranges.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "ngs.h"
+
+namespace ngs {
+
+// ---------------------------------------------------------------------------
+// constants of the render definition
+// ---------------------------------------------------------------------------
+constexpr float kNearZ = 0.2f;               // near plane on view z
+constexpr double kNearZd = 0.2;
+constexpr float kBlur = 0.3f;                // dilation added to the 2D covariance
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kRectMargin = 1.0f / 64.0f;  // pixels added to the support box
+constexpr float kLog2e = 1.4426950408889634f;
+// log2(1/255): alpha >= 1/255  <=>  log2(alpha) >= -log2(255)
+constexpr float kLog2AlphaMin = -7.9943534368588578f;
+
+constexpr uint32_t kNodeCullOpacity = 1u;    // pos4.w flag: 255 * opacity < 1
+
+// error codes latched in the device status word (same values as ngs_status)
+constexpr int kErrCapacity = NGS_ERR_CAPACITY;
+constexpr int kErrTimeout = NGS_ERR_DEVICE_TIMEOUT;
+
+// spin limit of every bounded device-side wait (look-back); a wait that runs
+// out latches kErrTimeout and the kernel leaves the partition unfinished
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+// ---------------------------------------------------------------------------
+// per-camera table in device memory
+// ---------------------------------------------------------------------------
+struct DevCamera {
+    float R[9];
+    float pos[3];
+    float fx, fy, cx, cy, tau;
+    int32_t width, height, tiles_x, tiles_y;
+    uint32_t tile_base;      // first tile id of this camera within its sub-batch
+    uint32_t pad0;
+    double posd[3];          // camera centre and depth row of R_wc in float64
+    double Rz[3];
+    float *image;            // [3][height][width]
+    int64_t pad1;
+};
+static_assert(sizeof(DevCamera) % 16 == 0, "DevCamera alignment");
+
+// compositing records: centre (x, y), the conic scaled to log2 units
+// (A dx^2 + B dx dy + C dy^2 = log2 of the Gaussian falloff), L = log2(opacity)
+// and the colour
+struct __align__(16) Rec32 {
+    float4 a;   // x, y, A, B
+    float4 b;   // C, L, r, g
+    float4 c;   // bl, 0, 0, 0
+};
+struct __align__(16) Rec16 {
+    float4 a;   // x, y, A, B
+    float4 b;   // C, L, half2(r, g) bits, half2(bl, 0) bits
+};
+
+struct SceneDev {
+    int64_t n = 0;
+    int32_t attr_dtype = NGS_F32;
+    float4 *box_lo = nullptr, *box_hi = nullptr, *pos4 = nullptr, *quat = nullptr;
+    void *sop = nullptr;     // [n][4] of attr type
+    void *sh = nullptr;      // [n][48] of attr type
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void latch_error(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Chained-scan status word: [63:62] flag (1 aggregate, 2 inclusive prefix),
+// [61:32] epoch (30 bits), [31:0] value. A word whose epoch differs from the
+// reader's belongs to an earlier scan and counts as "not yet published".
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint32_t kEpochMask = (1u << 30) - 1u;
+
+__device__ __forceinline__ uint64_t pack_status(uint64_t flag, uint32_t epoch, uint32_t v) {
+    return flag | ((uint64_t)(epoch & kEpochMask) << 32) | (uint64_t)v;
+}
+
+__device__ __forceinline__ void publish(uint64_t *slot, uint64_t word) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(word) : "memory");
+}
+
+__device__ __forceinline__ uint64_t peek(const uint64_t *slot) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(slot) : "memory");
+    return v;
+}
+
+// Decoupled look-back for one running sum: returns the exclusive prefix of
+// partition `part` over the chain whose words sit at status[j * stride]. The
+// caller has already published its own aggregate. Returns false (and latches
+// kErrTimeout) if a predecessor never publishes within the spin limit.
+__device__ __forceinline__ bool look_back(const uint64_t *status, int64_t part, int64_t stride,
+                                          uint32_t epoch, uint32_t *excl, int *err) {
+    uint32_t acc = 0;
+    int64_t j = part - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        const uint64_t w = peek(status + j * stride);
+        const uint32_t e = (uint32_t)(w >> 32) & kEpochMask;
+        const uint64_t flag = w & (3ull << 62);
+        if (e != (epoch & kEpochMask) || flag == 0) {
+            if (++spins > kSpinLimit) {
+                latch_error(err, kErrTimeout);
+                *excl = acc;
+                return false;
+            }
+            continue;
+        }
+        acc += (uint32_t)w;
+        if (flag == kFlagPrefix) break;
+        --j;
+    }
+    *excl = acc;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// work-buffer bundle for one render sub-batch
+// ---------------------------------------------------------------------------
+struct Work {
+    // counters (device): [0] cut total, [1] visible total, [2] pair total,
+    // [3..] tickets; zeroed at the start of each sub-batch
+    uint32_t *counters = nullptr;
+    uint32_t *epoch = nullptr;        // device epoch base, bumped per sub-batch
+    uint64_t *status = nullptr;       // chained-scan words
+    int64_t status_words = 0;
+    int *err = nullptr;               // latched device error
+    uint32_t *cut_ids = nullptr;      int64_t cut_cap = 0;
+    uint32_t *cut_off = nullptr;      // [cams + 1]
+    void *rec = nullptr;              int64_t rec_cap = 0;
+    uint32_t *dkey[2] = {nullptr, nullptr};
+    uint32_t *didx[2] = {nullptr, nullptr};
+    uint4 *rect = nullptr;            // x0|y0<<16, x1|y1<<16, camera index, node id
+    uint32_t *poff = nullptr;         // pair offsets per sorted record
+    uint32_t *pkey[2] = {nullptr, nullptr};
+    uint32_t *pval[2] = {nullptr, nullptr};
+    int64_t pair_cap = 0;
+    uint2 *ranges = nullptr;          int64_t ranges_cap = 0;
+    uint32_t *hist = nullptr;         // [passes][256] radix histograms
+    DevCamera *cams = nullptr;        int64_t cams_cap = 0;
+};
+
+// ticket slots in Work::counters
+enum : int {
+    CNT_CUT = 0, CNT_VIS = 1, CNT_PAIRS = 2, TK_CUT = 3, TK_PRE = 4, TK_SCAN = 5, TK_DUP = 6,
+    TK_SORT0 = 8,             // 8 .. 8 + 16: one ticket per sort pass
+    TK_COMPOSITE = 28, N_COUNTERS = 32
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+// cut: cameras [0, n_cams) of the table; writes ids (ascending per camera),
+// offsets [n_cams + 1] and counters[CNT_CUT]
+void launch_cut(const SceneDev &sc, const DevCamera *cams, int n_cams, uint32_t *ids,
+                int64_t cap, uint32_t *offsets, uint32_t *counters, uint32_t *ticket,
+                uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
+                int grid, cudaStream_t st);
+int cut_partition_nodes();
+
+// preprocess: cut slots -> compacted records, depth keys, rectangles
+void launch_preprocess(const SceneDev &sc, const DevCamera *cams, int n_cams,
+                       const uint32_t *cut_ids, const uint32_t *cut_off, void *rec,
+                       uint32_t *dkey, uint4 *rect, int64_t rec_cap, uint32_t *counters,
+                       uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                       uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
+                       cudaStream_t st);
+int preprocess_partition();
+
+// radix sort (onesweep) of (uint32 | uint64 key, uint32 value) pairs; n from
+// device memory (*n_dev) or host (n_host >= 0). Result lands in buffer
+// `out_sel` (0 or 1) of the double buffers; the number of passes decides it.
+struct SortArgs {
+    void *keys[2];
+    uint32_t *vals[2];
+    const uint32_t *n_dev;
+    int64_t n_host;
+    int64_t n_max;            // bound on n (status array and grid sizing)
+    int key_bytes;
+    int begin_bit, end_bit;
+    bool vals_identity;       // first pass takes value = input index
+    uint32_t *hist;           // [passes][256]
+    uint32_t *tickets;        // one per pass
+    uint64_t *status;
+    const uint32_t *epoch;
+    uint32_t epoch_off;
+    int *err;
+};
+int sort_passes(int begin_bit, int end_bit);
+int sort_partition();
+size_t sort_smem_bytes(int key_bytes);
+void sort_init_attributes();
+void launch_sort(const SortArgs &a, int grid, cudaStream_t st);
+
+// exclusive scan of uint32 (device-count or host-count)
+void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
+                     uint32_t *total, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                     uint32_t epoch_off, int *err, int grid, cudaStream_t st);
+int scan_partition();
+
+// binning: tiles-touched scan over depth order, then pair emission
+void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
+                         uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
+                         uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
+                         int grid, cudaStream_t st);
+void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
+                      const uint32_t *n_vis, const uint32_t *n_pairs, int64_t pair_cap,
+                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, int *err, int grid,
+                      cudaStream_t st);
+void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges, int grid,
+                   cudaStream_t st, const int *err);
+
+// compositing of tiles [0, n_tiles) of a sub-batch
+void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool persistent,
+                      const DevCamera *cams, int n_cams, uint32_t n_tiles, const uint2 *ranges,
+                      const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
+                      const int *err, cudaStream_t st);
+int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch);
+
+inline size_t rec_bytes(int attr_dtype) {
+    return attr_dtype == NGS_F32 ? sizeof(Rec32) : sizeof(Rec16);
+}
+
+}  // namespace ngs

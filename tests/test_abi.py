@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads and exports every entry point the header
+declares, and the binding's struct layouts match the header's. CPU only (no
+compute calls)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ngs.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"NGS_API\s+[\w\s\*]+?\b(ngs_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_15186_gb300 import build
+    path = build.build()
+    return C.CDLL(path), path
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ["ngs_create", "ngs_load_scene", "ngs_select_cut", "ngs_render", "ngs_destroy",
+                 "ngs_strerror", "ngs_sort_pairs", "ngs_scan_u32"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L, path = lib
+    for name in _declared():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (ngs_\w+)", out))
+    assert set(_declared()) <= exported
+    # nothing else of the renderer leaks out of the library
+    assert exported == set(_declared())
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2603_15186_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == _declared()
+
+
+def test_strerror_without_gpu(lib):
+    L, _ = lib
+    L.ngs_strerror.restype = C.c_char_p
+    assert L.ngs_strerror(0) == b"ok"
+    assert L.ngs_strerror(4) == b"work buffer capacity exceeded"
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_2603_15186_gb300 import _lib
+    prog = tmp_path / "layout.c"
+    prog.write_text(r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "ngs.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(ngs_camera), sizeof(ngs_gaussians),
+         sizeof(ngs_hierarchy), sizeof(ngs_config), sizeof(ngs_stats));
+  printf("%zu %zu %zu %zu\n", offsetof(ngs_camera, tau), offsetof(ngs_gaussians, attr_dtype),
+         offsetof(ngs_config, max_tiles_per_batch), offsetof(ngs_stats, mode));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    sizes = [int(x) for x in a.split()]
+    offs = [int(x) for x in b.split()]
+    assert sizes == [C.sizeof(_lib.Camera), C.sizeof(_lib.Gaussians), C.sizeof(_lib.Hierarchy),
+                     C.sizeof(_lib.Config), C.sizeof(_lib.Stats)]
+    assert offs == [_lib.Camera.tau.offset, _lib.Gaussians.attr_dtype.offset,
+                    _lib.Config.max_tiles_per_batch.offset, _lib.Stats.mode.offset]
+
+
+def test_renderer_fails_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2603_15186_gb300 import Renderer, NgsError
+    with pytest.raises((NgsError, RuntimeError)):
+        Renderer(device=0)

@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path through the C ABI against the float64 oracle (and,
+for the sort and scan primitives, against numpy's stable sort and cumsum) on
+seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from scenegen import camera_c0, look_camera, make_floor_scene, quantize_attributes, walk_cameras
+from tests.gpu_helpers import clear_tau, compare_cut, compare_image, compare_tile_lists
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_15186_gb300 import Renderer
+    r = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22, pair_capacity=1 << 24)
+    yield r
+    r.close()
+
+
+# ---------------------------------------------------------------------------
+# primitives: onesweep radix sort and chained scan
+# ---------------------------------------------------------------------------
+
+def _sort_check(R, keys_np, begin=0, end=None):
+    kb = keys_np.dtype.itemsize
+    end = 8 * kb if end is None else end
+    n = len(keys_np)
+    vals_np = np.arange(n, dtype=np.uint32)
+    tdt = torch.int32 if kb == 4 else torch.int64
+    k = torch.from_numpy(keys_np.view(np.int32 if kb == 4 else np.int64).copy()).cuda()
+    v = torch.from_numpy(vals_np.view(np.int32).copy()).cuda()
+    R.sort_pairs(k, v, begin, end)
+    R.synchronize()
+    gk = k.cpu().numpy().view(keys_np.dtype)
+    gv = v.cpu().numpy().view(np.uint32)
+    mask = (1 << (end - begin)) - 1 if end - begin < 64 else (1 << 64) - 1
+    dig = (keys_np.astype(np.uint64) >> np.uint64(begin)) & np.uint64(mask)
+    o = np.argsort(dig, kind="stable")
+    assert np.array_equal(gv, vals_np[o])
+    assert np.array_equal(gk, keys_np[o])
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 4095, 4096, 4097, 100_003])
+def test_sort_u32_random(R, n):
+    rng = np.random.default_rng(n)
+    _sort_check(R, rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32))
+
+
+def test_sort_u32_few_distinct_and_partial_bits(R):
+    rng = np.random.default_rng(1)
+    _sort_check(R, rng.integers(0, 5, 50_000).astype(np.uint32))         # heavy ties: stability
+    _sort_check(R, np.full(20_000, 77, np.uint32))                         # all equal
+    _sort_check(R, rng.integers(0, 2 ** 32, 30_000, dtype=np.uint64).astype(np.uint32), 4, 20)
+    _sort_check(R, np.arange(30_000, 0, -1).astype(np.uint32) << np.uint32(16), 16, 32)
+
+
+@pytest.mark.parametrize("n", [1, 12_345, 200_001])
+def test_sort_u64(R, n):
+    rng = np.random.default_rng(7 + n)
+    keys = rng.integers(0, 2 ** 63, n, dtype=np.uint64) ^ (rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63))
+    _sort_check(R, keys)
+    # (tile << 32 | depth bits) keys with all-distinct tiles and shared depths
+    tiles = rng.permutation(n).astype(np.uint64)
+    _sort_check(R, (tiles << np.uint64(32)) | np.uint64(0x3F800000), 0, 64)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2047, 2048, 2049, 1_000_003])
+def test_scan_u32(R, n):
+    rng = np.random.default_rng(n)
+    x = rng.integers(0, 100, n).astype(np.int32)
+    t = torch.from_numpy(x).cuda()
+    out, total = R.scan_u32(t)
+    R.synchronize()
+    want = np.concatenate([[0], np.cumsum(x)[:-1]]) if n else np.zeros(0)
+    assert np.array_equal(out.cpu().numpy(), want.astype(np.int32))
+    assert int(total.item()) == int(x.sum())
+
+
+# ---------------------------------------------------------------------------
+# cut
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tau", [0.0, 4.0, 16.0, 40.0, 200.0])
+def test_cut_matches_oracle(R, box10k, tau):
+    R.load_scene(box10k)
+    cams = [camera_c0(tau), look_camera((-3.0, 2.0, 1.5), 0.0, 64, 64, fx=60.0, tau=tau)]
+    ids, off = R.select_cut(cams)
+    ids, off = ids.cpu().numpy(), off.cpu().numpy()
+    for c, cam in enumerate(cams):
+        compare_cut(ids[off[c]:off[c + 1]], box10k, cam)
+
+
+# ---------------------------------------------------------------------------
+# full render
+# ---------------------------------------------------------------------------
+
+def _render_one(R, scene, cam, tile=(16, 16)):
+    R.set_tile(*tile)
+    img = R.render([cam])[0].cpu().numpy()
+    return img
+
+
+@pytest.mark.parametrize("tau", [0.0, 4.0])
+def test_render_small_box_view(R, box10k, tau):
+    """The 10k-leaf box scene seen by the 128x128 camera at (2, 2, 1.2)."""
+    R.load_scene(box10k)
+    cam = camera_c0(tau)
+    ref = O.render(box10k, cam, tile=(16, 16))
+    assert ref.near.sum() == 0
+    img = _render_one(R, box10k, cam)
+    compare_image(img, ref)
+    n_tiles = len(ref.ranges)
+    rng, nodes = R.tile_lists(0, n_tiles, len(ref.keys) + 4096)
+    compare_tile_lists(rng, nodes, ref, (16, 16))
+
+
+def _floor_cams(scene):
+    cams = walk_cameras(scene, 4, 77, 160, 120, fx=150.0, tau=0.0)
+    cams[1].width, cams[1].height, cams[1].cx, cams[1].cy = 97, 61, 48.5, 30.5   # ragged tiles
+    cams[1].tau = 2.0
+    cams[2].width, cams[2].height, cams[2].cx, cams[2].cy = 320, 240, 160.0, 120.0
+    cams[2].fx = cams[2].fy = 300.0
+    cams[2].tau = 5.0
+    cams[3].tau = 9.0
+    return [clear_tau(scene, c) for c in cams]
+
+
+def test_render_batch_matches_oracle_and_plain(R, small_floor):
+    R.load_scene(small_floor)
+    cams = _floor_cams(small_floor)
+    R.set_tile(16, 16)
+    R.set_mode("batched")
+    imgs = [t.cpu().numpy() for t in R.render(cams)]
+    for cam, img in zip(cams, imgs):
+        ref = O.render(small_floor, cam)
+        assert ref.near.sum() == 0
+        compare_image(img, ref)
+    # the plain per-view path computes the same bits
+    R.set_mode("plain")
+    plain = [t.cpu().numpy() for t in R.render(cams)]
+    R.set_mode("batched")
+    for a, b in zip(imgs, plain):
+        assert np.array_equal(a, b)
+    # tile lists of the last camera (plain mode leaves each camera's buffers in turn)
+    R.set_mode("plain")
+    R.render([cams[2]])
+    ref = O.render(small_floor, cams[2])
+    rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
+    compare_tile_lists(rng, nodes, ref, (16, 16))
+    R.set_mode("batched")
+
+
+def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
+    R.load_scene(small_floor)
+    cams = _floor_cams(small_floor)
+    R.set_tile(16, 16)
+    R.set_batch(128)
+    base = [t.cpu().numpy() for t in R.render(cams)]
+    again = [t.cpu().numpy() for t in R.render(cams)]   # replays the captured graph
+    assert R.stats()["graph_replayed"] == 1
+    for tile in [(8, 8), (16, 8)]:
+        for batch in [64, 256]:
+            R.set_tile(*tile)
+            R.set_batch(batch)
+            out = [t.cpu().numpy() for t in R.render(cams)]
+            for a, b in zip(base, out):
+                assert np.array_equal(a, b), (tile, batch)
+    for a, b in zip(base, again):
+        assert np.array_equal(a, b)
+    # alone vs in a batch
+    R.set_tile(16, 16)
+    R.set_batch(128)
+    for i, cam in enumerate(cams):
+        alone = R.render([cam])[0].cpu().numpy()
+        assert np.array_equal(alone, base[i])
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_reduced_precision_attributes(R, small_floor, dtype):
+    stored, deq = quantize_attributes(small_floor, dtype)
+    R.load_scene(small_floor, attr_dtype=dtype, stored=stored)
+    cams = _floor_cams(small_floor)[:2]
+    imgs = [t.cpu().numpy() for t in R.render(cams)]
+    sa = O.SceneArrays(small_floor, overrides=deq)
+    for cam, img in zip(cams, imgs):
+        ref = O.render(sa, cam)
+        compare_image(img, ref)
+
+
+def test_edge_cases(R, small_floor):
+    R.load_scene(small_floor)
+    base = walk_cameras(small_floor, 1, 5, 64, 48, fx=60.0, tau=0.0)[0]
+    away = look_camera((-3.0, 3.0, 1.5), math.pi, 33, 17, fx=30.0)   # outside, facing away
+    tiny = look_camera(base.pos, 1.0, 1, 1, fx=1.0)
+    coarse = look_camera((-20.0, -20.0, 10.0), math.radians(40), 40, 30, fx=35.0, tau=1e30)
+    cams = [base, away, tiny, coarse]
+    imgs = [t.cpu().numpy() for t in R.render(cams)]
+    for cam, img in zip(cams, imgs):
+        ref = O.render(small_floor, cam)
+        compare_image(img, ref)
+    ids, off = R.select_cut([coarse])
+    assert ids[: int(off[1].item())].cpu().tolist() == [0]
+
+
+def test_capacity_error_is_reported_and_context_survives(small_floor):
+    from paper_2603_15186_gb300 import NgsError, Renderer
+    r = Renderer(device=0, cut_capacity=1 << 20, record_capacity=1 << 20, pair_capacity=1000)
+    r.load_scene(small_floor)
+    cam = walk_cameras(small_floor, 1, 5, 160, 120, fx=150.0, tau=0.0)[0]
+    with pytest.raises(NgsError) as e:
+        r.render([cam])
+    assert e.value.status == 4
+    r.close()
+    r2 = Renderer(device=0, cut_capacity=1 << 20, record_capacity=1 << 20, pair_capacity=1 << 22)
+    r2.load_scene(small_floor)
+    img = r2.render([cam])[0].cpu().numpy()
+    compare_image(img, O.render(small_floor, cam))
+    r2.close()
+
+
+def test_invalid_hierarchy_rejected(R, box10k):
+    from paper_2603_15186_gb300 import NgsError
+    import copy
+    bad = copy.copy(box10k)
+    bad.parent = box10k.parent.copy()
+    bad.parent[5] = 7   # a child whose parent id is not smaller than its own
+    with pytest.raises(NgsError) as e:
+        R.load_scene(bad)
+    assert e.value.status == 2
