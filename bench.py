@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the batched render path on a 4M-leaf multi-room floor.
+
+One step renders a batch of 256 cameras of mixed resolution (64 x 320x240,
+128 x 640x480, 64 x 1280x720; fx = 0.9375 W; per-camera tau ~ U[2, 8] px)
+from a 25 x 12 x 3 m floor of 4M leaf Gaussians (~4.6M hierarchy nodes) with
+float16 SH / scale / opacity storage, through one captured CUDA graph. The same
+cameras are also rendered by the plain per-view float32 path (one camera per
+call, host-synchronised stage sizes, no graph) for the comparison the metric
+names, and end to end through the host-buffer entry point.
+
+`--impl reference` times the float64 CPU oracle on the same workload instead.
+Prints one JSON line (rank 0)."""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s batched render vs plain per-view FP32 on same GB300 at <=2e-3 err; p99 ms"
+WORKLOAD = "batch256_floor4m_f16"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cams", type=int, default=256)
+    ap.add_argument("--leaves", default="floor4m")
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-stage-timing", action="store_true")
+    ap.add_argument("--cpu-cams", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def make_workload(args, rank):
+    from scenegen import make_scene, mixed_batch_cameras
+    scene = make_scene(args.leaves)
+    cams = mixed_batch_cameras(scene, args.cams, seed=1002 + rank)
+    return scene, cams
+
+
+def config_dict(args, scene, cams, world):
+    pix = sum(c.width * c.height for c in cams)
+    return {"workload": WORKLOAD, "scene": args.leaves, "leaves": int(scene.n_leaves),
+            "nodes": int(scene.n_nodes), "cameras_per_step": len(cams),
+            "resolutions": "320x240:640x480:1280x720 = 1:2:1", "tau_px": "U[2,8]",
+            "mpix_per_step": round(pix / 1e6, 4), "attr_storage": "f16 sh/scale/opacity",
+            "tile": args.tile, "smem_batch": args.batch, "cuda_graph": True,
+            "l2": "inputs exceed L2 (scene ~0.6 GB, pair buffers GBs)",
+            "parallelism": f"replicas{world}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per stage (what each kernel must move at minimum)
+# ---------------------------------------------------------------------------
+
+def stage_bytes(st, n_nodes, n_cams, pixels, tiles, attr="f16"):
+    sop, sh, rec = (16, 192, 48) if attr == "f32" else (8, 96, 32)
+    C, V, P = st["cut_total"], st["visible_total"], st["pair_total"]
+    return {
+        "cut": 32 * n_nodes * n_cams + 4 * C,
+        "preprocess": 20 * C + V * (16 + sop + sh + rec + 4 + 16),
+        "depth_hist": 4 * V,
+        "depth_pass0": 12 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 16 * V,
+        "pair_offsets": 24 * V,
+        "duplicate": 24 * V + 8 * P,
+        "tile_hist": 4 * P,
+        "tile_pass0": 16 * P, "tile_pass1": 16 * P, "tile_pass2": 16 * P,
+        "ranges": 4 * P + 8 * tiles,
+        "composite": 12 * pixels + st["records_staged"] * (4 + rec),
+    }
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    import oracle as O
+    from paper_2603_15186_gb300 import Renderer
+    from scenegen import quantize_attributes
+
+    torch.cuda.set_device(local)
+    t0 = time.time()
+    scene, cams = make_workload(args, rank)
+    gen_s = time.time() - t0
+    stored, deq = quantize_attributes(scene, "f16")
+    tw, th = (int(x) for x in args.tile.split("x"))
+    pixels = sum(c.width * c.height for c in cams)
+    tiles = sum(-(-c.width // tw) * -(-c.height // th) for c in cams)
+
+    R = Renderer(device=local, tile=(tw, th), batch=args.batch, cut_capacity=1 << 27,
+                 record_capacity=1 << 27, pair_capacity=(1 << 30) + (1 << 29))
+    R.load_scene(scene, attr_dtype="f16", stored=stored)
+    R.set_mode("batched")
+    R.set_stage_timing(not args.no_stage_timing)
+    imgs = R.new_images(cams)
+    for _ in range(max(args.warmup, 3)):
+        R.render(cams, imgs)
+    stats = R.stats()
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_acc = {}
+    g0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        R.render(cams, imgs, stream=stream, sync=False)
+        ev[k][1].record(stream)
+        if not args.no_stage_timing:
+            for name, ms in R.stage_times().items():
+                stage_acc[name] = stage_acc.get(name, 0.0) + ms
+    g1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    R.synchronize()
+    total_ms = g0.elapsed_time(g1)
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    if pg:
+        t = torch.tensor([total_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * pixels * args.steps / (total_ms * 1e3)   # Mpix/s over all ranks
+    stats = R.stats()
+    kernels_per_step = stats["kernels"]
+
+    # roofline of the dominant kernel, from this run's events and counters
+    roof = None
+    if stage_acc:
+        per_step = {k: v / args.steps for k, v in stage_acc.items()}
+        byts = stage_bytes(stats, scene.n_nodes, len(cams), pixels, tiles, "f16")
+        launches = {k: stats["sub_batches"] for k in per_step}
+        peak, peak_kind = measured_peaks()
+        # kernels: group the digit passes of one sort into one kernel
+        groups = {"onesweep_pairs": ["tile_pass0", "tile_pass1", "tile_pass2"],
+                  "onesweep_depth": ["depth_pass0", "depth_pass1", "depth_pass2", "depth_pass3"],
+                  "composite": ["composite"], "preprocess": ["preprocess"], "cut": ["cut"],
+                  "duplicate": ["duplicate"], "pair_offsets": ["pair_offsets"],
+                  "ranges": ["ranges"], "histograms": ["depth_hist", "tile_hist"]}
+        gt = {g: sum(per_step.get(s, 0.0) for s in ss) for g, ss in groups.items()}
+        dom = max(gt, key=gt.get)
+        n_launch = sum(1 for s in groups[dom] if per_step.get(s, 0.0) > 0) * stats["sub_batches"]
+        b = sum(byts[s] for s in groups[dom])
+        dur_ms = gt[dom] / max(n_launch, 1)
+        achieved = (b / max(n_launch, 1)) / (dur_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                "launches_per_step": n_launch, "avg_launch_ms": round(dur_ms, 4),
+                "algorithmic_bytes_per_launch": int(b / max(n_launch, 1))}
+        if dom == "composite":
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            mhz = clk.get("sm_mhz") or 2070.0
+            # 9 FP32 lane operations per evaluation at least (2 sub, 3 mul, 3 fma, 1 compare)
+            alu_peak = sms * 128 * mhz * 1e6 / 9.0 / 1e12
+            evals = stats["evaluations"] / max(n_launch, 1)
+            ach = evals / (dur_ms * 1e-3) / 1e12
+            roof.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 3),
+                         "unit": "Teval/s", "frac": round(ach / alu_peak, 4),
+                         "hbm_achieved_gbs": round(achieved, 1)})
+        roof["stage_ms_per_step"] = {k: round(v, 4) for k, v in per_step.items()}
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": config_dict(args, scene, cams, world),
+           "p50_ms": round(float(np.percentile(step_ms, 50)), 3),
+           "p99_ms": round(float(np.percentile(step_ms, 99)), 3),
+           "frames_per_s": round(world * len(cams) * args.steps / (total_ms * 1e-3), 1),
+           "gpu_launches": int(kernels_per_step * args.steps),
+           "clocks": clk, "roofline": roof,
+           "work": {k: stats[k] for k in ("cut_total", "visible_total", "pair_total",
+                                          "records_staged", "evaluations", "sub_batches")},
+           "scene_gen_s": round(gen_s, 1)}
+
+    # plain per-view float32 path on the same cameras
+    plain_imgs = None
+    if not args.no_plain:
+        P = Renderer(device=local, tile=(tw, th), batch=args.batch, cut_capacity=1 << 23,
+                     record_capacity=1 << 23, pair_capacity=1 << 27)
+        P.load_scene(scene, attr_dtype="f32")
+        P.set_mode("plain")
+        plain_imgs = P.new_images(cams)
+        P.render(cams[:8], plain_imgs[:8])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.render(cams, plain_imgs, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        diff = max(float((x - y).abs().max().item()) for x, y in zip(imgs, plain_imgs))
+        out["plain_fp32"] = {"value": round(pixels / (pms * 1e3), 2), "unit": "Mpix/s",
+                             "ms_per_step": round(pms, 3),
+                             "speedup_batched_over_plain": round(value / world / (pixels / (pms * 1e3)), 3),
+                             "max_abs_diff_vs_batched_f16": diff}
+        P.close()
+
+    # end to end through the host-buffer entry point (pinned host images)
+    if not args.no_e2e:
+        import ctypes as C
+        from paper_2603_15186_gb300.renderer import camera_array
+        host = torch.empty(3 * pixels, dtype=torch.float32, pin_memory=True)
+        hp = host.data_ptr()
+        ptrs, off = [], 0
+        for c in cams:
+            ptrs.append(C.c_void_p(hp + 4 * off))
+            off += 3 * c.width * c.height
+        parr = (C.c_void_p * len(cams))(*ptrs)
+        carr = camera_array(cams)
+        R.set_stage_timing(False)
+        R.render_host_ptrs(carr, len(cams), parr)
+        ke = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(ke):
+            carr = camera_array(cams)           # cameras come from the host every step
+            R.render_host_ptrs(carr, len(cams), parr)
+        e2e_s = (time.perf_counter() - t) / ke
+        from paper_2603_15186_gb300 import _lib
+        out["e2e"] = {"value": round(world * pixels / (e2e_s * 1e6), 2), "unit": "Mpix/s",
+                      "h2d_bytes_per_step": len(cams) * C.sizeof(_lib.Camera),
+                      "d2h_bytes_per_step": 12 * pixels, "ms_per_step": round(e2e_s * 1e3, 3),
+                      "path": "ngs_render_host: camera table H2D, render, images D2H to pinned host"}
+
+    # CPU oracle baseline on a bounded sample, and parity of the batched images
+    if rank == 0 and not args.no_cpu:
+        sa = O.SceneArrays(scene, overrides=deq)
+        order = np.argsort([c.width * c.height for c in cams], kind="stable")[:args.cpu_cams]
+        t = time.time()
+        refs = [O.render(sa, cams[i], tile=(tw, th)) for i in order]
+        cpu_s = time.time() - t
+        cpu_pix = sum(cams[i].width * cams[i].height for i in order)
+        errs, flagged = [], []
+        for i, ref in zip(order, refs):
+            got = imgs[i].cpu().numpy().astype(np.float64)
+            ok = ref.flags == 0
+            errs.append(float(np.abs(got - ref.image)[:, ok].max()))
+            flagged.append(float(1 - ok.mean()))
+        out["cpu_baseline"] = {"value": round(cpu_pix / (cpu_s * 1e6), 4), "unit": "Mpix/s",
+                               "cores": O.num_threads(), "kind": "oracle",
+                               "sample": f"{len(order)} full views ({cpu_pix} px) of the batch, "
+                                         f"float64 oracle incl. cut/preprocess/binning, {cpu_s:.1f} s"}
+        out["parity_vs_oracle"] = {"max_abs_err": max(errs), "tolerance": 2e-3,
+                                   "flagged_pixel_frac": max(flagged),
+                                   "views": [int(i) for i in order]}
+    R.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the float64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    from scenegen import quantize_attributes
+    scene, cams = make_workload(args, 0)
+    _, deq = quantize_attributes(scene, "f16")
+    sa = O.SceneArrays(scene, overrides=deq)
+    tw, th = (int(x) for x in args.tile.split("x"))
+    # each step: one view of the batch (cycling through it), full oracle pipeline
+    order = list(range(len(cams)))
+    for k in range(args.warmup):
+        O.render(sa, cams[order[k % len(order)]], tile=(tw, th))
+    t = time.time()
+    pix = 0
+    for k in range(args.steps):
+        c = cams[order[(args.warmup + k) % len(order)]]
+        O.render(sa, c, tile=(tw, th))
+        pix += c.width * c.height
+    s = time.time() - t
+    val = pix / (s * 1e6)
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "Mpix/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * s / args.steps, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(args, scene, cams, world),
+           "cpu_baseline": {"value": round(val, 4), "unit": "Mpix/s", "cores": O.num_threads(),
+                            "kind": "oracle",
+                            "sample": "one view of the 256-camera batch per step (cycling)"},
+           "e2e": {"value": round(val, 4), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

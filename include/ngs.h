@@ -115,15 +115,19 @@ typedef struct {
  * to the host between stages, no graph. Both compute identical pixels. */
 enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
-       NGS_OPT_GRAPH = 5 };
+       NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6 };
 
 typedef struct {
     int64_t cut_total;       /* selected nodes over all cameras of the last render */
     int64_t visible_total;   /* Gaussians kept after culling */
     int64_t pair_total;      /* (tile, Gaussian) pairs */
+    int64_t records_staged;  /* records gathered into shared memory by compositing */
+    int64_t evaluations;     /* pixel-Gaussian evaluations done by compositing */
     int32_t sub_batches;     /* sub-batches of the last render */
     int32_t graph_replayed;  /* 1 if the last render replayed a captured graph */
     int32_t tile_w, tile_h, batch, mode;
+    int32_t kernels;         /* kernel launches of the last render */
+    int32_t reserved;
 } ngs_stats;
 
 NGS_API const char *ngs_strerror(ngs_status s);
@@ -165,7 +169,17 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *ctx, const ngs_camera *cams, int32_t
 /* Waits for the stream and returns (then clears) any latched device error. */
 NGS_API ngs_status ngs_synchronize(ngs_ctx *ctx, void *stream);
 
+/* Synchronises the device and fills *out for the last render. */
 NGS_API ngs_status ngs_last_stats(ngs_ctx *ctx, ngs_stats *out);
+
+/* With NGS_OPT_STAGE_TIMING on, every kernel of a render is bracketed by CUDA
+ * events on the render stream (captured into the graph when one is used).
+ * After synchronising, ms[k] (k < n, n <= 15) receives the milliseconds of
+ * stage k summed over the last render's sub-batches (batched) or cameras
+ * (plain): 0 cut, 1 preprocess, 2 depth histogram, 3..6 depth digit passes,
+ * 7 pair offsets, 8 pair duplication, 9 tile histogram, 10..12 tile digit
+ * passes, 13 tile ranges, 14 compositing. Unused passes read 0. */
+NGS_API ngs_status ngs_stage_times(ngs_ctx *ctx, double *ms, int32_t n);
 
 /* Tile lists of the last render, for camera `cam` of a single-sub-batch
  * render, copied to host memory after synchronising: h_ranges [tiles][2]

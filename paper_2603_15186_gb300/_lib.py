@@ -11,11 +11,16 @@ STATUS_NAMES = {0: "NGS_OK", 1: "NGS_ERR_INVALID_ARG", 2: "NGS_ERR_INVALID_HIERA
 NGS_F32, NGS_F16, NGS_BF16 = 0, 1, 2
 NGS_MODE_BATCHED, NGS_MODE_PLAIN = 0, 1
 NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H, NGS_OPT_BATCH, NGS_OPT_GRAPH = 1, 2, 3, 4, 5
+NGS_OPT_STAGE_TIMING = 6
+STAGES = ["cut", "preprocess", "depth_hist", "depth_pass0", "depth_pass1", "depth_pass2",
+          "depth_pass3", "pair_offsets", "duplicate", "tile_hist", "tile_pass0", "tile_pass1",
+          "tile_pass2", "ranges", "composite"]
 
 # every entry point include/ngs.h declares
 EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_load_scene",
            "ngs_select_cut", "ngs_render", "ngs_render_host", "ngs_synchronize",
-           "ngs_last_stats", "ngs_debug_tile_lists", "ngs_sort_pairs", "ngs_scan_u32"]
+           "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
+           "ngs_scan_u32"]
 
 
 class NgsError(RuntimeError):
@@ -50,9 +55,11 @@ class Config(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("cut_total", C.c_int64), ("visible_total", C.c_int64),
-                ("pair_total", C.c_int64), ("sub_batches", C.c_int32),
+                ("pair_total", C.c_int64), ("records_staged", C.c_int64),
+                ("evaluations", C.c_int64), ("sub_batches", C.c_int32),
                 ("graph_replayed", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("batch", C.c_int32), ("mode", C.c_int32)]
+                ("batch", C.c_int32), ("mode", C.c_int32), ("kernels", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -91,6 +98,8 @@ def load(build_if_missing: bool = True):
     L.ngs_synchronize.argtypes = [vp, vp]
     L.ngs_last_stats.restype = i32
     L.ngs_last_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.ngs_stage_times.restype = i32
+    L.ngs_stage_times.argtypes = [vp, vp, i32]
     L.ngs_debug_tile_lists.restype = i32
     L.ngs_debug_tile_lists.argtypes = [vp, i32, vp, vp, i64, C.POINTER(i64)]
     L.ngs_sort_pairs.restype = i32

@@ -93,6 +93,13 @@ struct ngs_ctx {
     ngs_status latched = NGS_OK;
     double pairs_per_pixel = 48.0;     // planner estimate, raised from observations
 
+    // optional per-kernel timing: kMarks events per sub-batch (or per camera
+    // in the plain path), recorded on the render stream / into the graph
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_groups = 0;
+    int kernels_per_render = 0;
+
     // standalone sort/scan scratch
     void *sort_tmp_keys = nullptr;
     uint32_t *sort_tmp_vals = nullptr;
@@ -143,7 +150,7 @@ void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
     dfree(w.cut_off); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.ranges);
-    dfree(w.hist); dfree(w.cams);
+    dfree(w.hist); dfree(w.cams); dfree(w.work64);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
     }
@@ -166,6 +173,42 @@ void drop_graph(ngs_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
     c->gkey.clear();
+}
+
+// Event marks inside one sub-batch; stage k runs between mark k and k + 1.
+enum : int {
+    MK_START = 0, MK_CUT = 1, MK_PRE = 2, MK_DHIST = 3, MK_DPASS0 = 4, MK_POFF = 8, MK_DUP = 9,
+    MK_THIST = 10, MK_TPASS0 = 11, MK_RANGES = 14, MK_COMPOSITE = 15, kMarks = 16
+};
+
+ngs_status ensure_events(ngs_ctx *c, int groups) {
+    if (!c->timing) return NGS_OK;
+    const int need = groups * kMarks;
+    while ((int)c->ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->ev.push_back(e);
+    }
+    c->ev_groups = groups;
+    return NGS_OK;
+}
+
+void mark(ngs_ctx *c, int group, int k, cudaStream_t st) {
+    // external: under stream capture this becomes an event-record node that
+    // the host can wait on and time after each graph launch
+    if (c->timing)
+        cudaEventRecordWithFlags(c->ev[(size_t)group * kMarks + k], st, cudaEventRecordExternal);
+}
+
+struct SortHook {
+    ngs_ctx *c;
+    int group, first_mark;
+    cudaStream_t st;
+};
+
+void sort_hook(void *user, int step) {
+    SortHook *h = (SortHook *)user;
+    mark(h->c, h->group, h->first_mark + step, h->st);
 }
 
 ngs_status ensure_work(ngs_ctx *c) {
@@ -206,6 +249,7 @@ ngs_status ensure_work(ngs_ctx *c) {
     c->stats_cap = 4096;
     A(dalloc(&c->stats_dev, (size_t)c->stats_cap * 4));
     A(dalloc(&c->cut_off32, kMaxCamsPerBatch + 1));
+    A(dalloc(&w.work64, 2));
     if (st != NGS_OK) {
         free_work(c);
         return st;
@@ -308,15 +352,19 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     Work &w = c->w;
     const int nc = sb.c1 - sb.c0;
     const DevCamera *cams = w.cams + sb.c0;
+    mark(c, sb_index, MK_START, st);
     cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st);
     cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st);
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
     uint32_t eo = 0;
     launch_cut(c->scene, cams, nc, w.cut_ids, w.cut_cap, w.cut_off, w.counters,
                w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->grid_cut, st);
+    mark(c, sb_index, MK_CUT, st);
     launch_preprocess(c->scene, cams, nc, w.cut_ids, w.cut_off, w.rec, w.dkey[0], w.rect,
                       w.rec_cap, w.counters, w.counters + TK_PRE, w.status, w.epoch, eo++, w.err,
                       c->tile_w, c->tile_h, c->grid_pre, st);
+    mark(c, sb_index, MK_PRE, st);
+    SortHook dh{c, sb_index, MK_DHIST, st};
     SortArgs da{};
     da.keys[0] = w.dkey[0]; da.keys[1] = w.dkey[1];
     da.vals[0] = w.didx[0]; da.vals[1] = w.didx[1];
@@ -324,15 +372,19 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = true;
     da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
     da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
+    da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
     launch_sort(da, c->grid_sort32, st);
     eo += 4;
     const int dsel = 4 & 1;  // four passes: the result is back in buffer 0
     launch_pair_offsets(w.rect, w.didx[dsel], w.counters + CNT_VIS, w.poff, w.counters,
                         w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
                         c->grid_scan, st);
+    mark(c, sb_index, MK_POFF, st);
     launch_duplicate(w.rect, w.didx[dsel], w.poff, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
                      w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, c->grid_dup, st);
+    mark(c, sb_index, MK_DUP, st);
     int psel = 0;
+    SortHook th{c, sb_index, MK_THIST, st};
     if (sb.tile_passes > 0) {
         SortArgs pa{};
         pa.keys[0] = w.pkey[0]; pa.keys[1] = w.pkey[1];
@@ -342,20 +394,32 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
         pa.vals_identity = false;
         pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
         pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
+        pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
         launch_sort(pa, c->grid_sort32, st);
         eo += sb.tile_passes;
         psel = sb.tile_passes & 1;
     }
+    for (int k = MK_THIST + 1 + sb.tile_passes; k < MK_RANGES; ++k) mark(c, sb_index, k, st);
+    if (sb.tile_passes == 0) mark(c, sb_index, MK_THIST, st);
     launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, c->grid_ranges, st, w.err);
+    mark(c, sb_index, MK_RANGES, st);
     const int cgrid = std::min<int64_t>(
         sb.n_tiles, (int64_t)c->num_sms *
                         std::max(1, composite_blocks_per_sm(c->scene.attr_dtype, c->tile_w,
                                                             c->tile_h, c->batch)));
     launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, c->batch, true, cams, nc,
                      sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
-                     std::max(cgrid, 1), w.err, st);
+                     std::max(cgrid, 1), w.err, w.work64, st);
+    mark(c, sb_index, MK_COMPOSITE, st);
     if (sb_index < c->stats_cap / 4)
         k_copy_stats<<<1, 32, 0, st>>>(w.counters, c->stats_dev + 4 * sb_index);
+}
+
+int kernels_of(const SubBatch &sb, bool batched) {
+    // bump, cut, preprocess, depth sort (histogram, digit scan, 4 passes), pair
+    // offsets, duplicate, tile sort (histogram, digit scan, passes), ranges,
+    // composite, and in the batched path the stats copy
+    return 3 + 6 + 2 + (sb.tile_passes > 0 ? 2 + sb.tile_passes : 0) + 2 + (batched ? 1 : 0);
 }
 
 ngs_status read_u32(const uint32_t *d, uint32_t *h, cudaStream_t st) {
@@ -380,6 +444,10 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
     Work &w = c->w;
     c->last_plan.clear();
     int64_t cut_tot = 0, vis_tot = 0, pair_tot = 0;
+    ngs_status es0 = ensure_events(c, n_cams);
+    if (es0 != NGS_OK) return es0;
+    CK(cudaMemsetAsync(w.work64, 0, 2 * sizeof(unsigned long long), st));
+    c->kernels_per_render = 0;
     for (int ci = 0; ci < n_cams; ++ci) {
         SubBatch sb{ci, ci + 1, 0, 0};
         DevCamera &d = c->host_cams[ci];
@@ -390,6 +458,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         const DevCamera *cams = w.cams + ci;
         ngs_status es = epoch_guard(c, st, kEpochStride);
         if (es != NGS_OK) return es;
+        mark(c, ci, MK_START, st);
         CK(cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
         CK(cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st));
         k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
@@ -397,6 +466,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         const int64_t nblk = (c->scene.n + cut_partition_nodes() - 1) / cut_partition_nodes();
         launch_cut(c->scene, cams, 1, w.cut_ids, w.cut_cap, w.cut_off, w.counters,
                    w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, (int)nblk, st);
+        mark(c, ci, MK_CUT, st);
         uint32_t n_cut = 0, n_vis = 0, n_pairs = 0;
         ngs_status s = read_u32(w.counters + CNT_CUT, &n_cut, st);
         if (s != NGS_OK) return s;
@@ -406,6 +476,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         launch_preprocess(c->scene, cams, 1, w.cut_ids, w.cut_off, w.rec, w.dkey[0], w.rect,
                           w.rec_cap, w.counters, w.counters + TK_PRE, w.status, w.epoch, eo++,
                           w.err, c->tile_w, c->tile_h, gpre, st);
+        mark(c, ci, MK_PRE, st);
         if ((s = read_u32(w.counters + CNT_VIS, &n_vis, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
         const int gsort_v = std::max<int64_t>(1, ((int64_t)n_vis + sort_partition() - 1) /
@@ -417,6 +488,8 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = true;
         da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
         da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
+        SortHook dh{c, ci, MK_DHIST, st};
+        da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
         launch_sort(da, std::min(gsort_v, c->grid_sort32), st);
         eo += 4;
         const int gscan = std::max<int64_t>(1, ((int64_t)n_vis + scan_partition() - 1) /
@@ -424,13 +497,16 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         launch_pair_offsets(w.rect, w.didx[0], w.counters + CNT_VIS, w.poff, w.counters,
                             w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
                             gscan, st);
+        mark(c, ci, MK_POFF, st);
         if ((s = read_u32(w.counters + CNT_PAIRS, &n_pairs, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
         if ((int64_t)n_pairs > w.pair_cap) return NGS_ERR_CAPACITY;
         const int gdup = std::max<int64_t>(1, ((int64_t)n_vis + 255) / 256);
         launch_duplicate(w.rect, w.didx[0], w.poff, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
                          w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, gdup, st);
+        mark(c, ci, MK_DUP, st);
         int psel = 0;
+        SortHook th{c, ci, MK_THIST, st};
         if (sb.tile_passes > 0) {
             const int gsort_p = std::max<int64_t>(1, ((int64_t)n_pairs + sort_partition() - 1) /
                                                          sort_partition());
@@ -442,17 +518,23 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
             pa.vals_identity = false;
             pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
             pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
+            pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
             launch_sort(pa, std::min(gsort_p, c->grid_sort32), st);
             eo += sb.tile_passes;
             psel = sb.tile_passes & 1;
         }
         const int grng = std::max<int64_t>(1, std::min<int64_t>(((int64_t)n_pairs + 255) / 256,
                                                                  (int64_t)c->num_sms * 16));
+        for (int k = MK_THIST + 1 + sb.tile_passes; k < MK_RANGES; ++k) mark(c, ci, k, st);
+        if (sb.tile_passes == 0) mark(c, ci, MK_THIST, st);
         launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, grng, st, w.err);
+        mark(c, ci, MK_RANGES, st);
         launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, c->batch, false, cams, 1,
                          sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
-                         (int)std::max<uint32_t>(sb.n_tiles, 1), w.err, st);
+                         (int)std::max<uint32_t>(sb.n_tiles, 1), w.err, w.work64, st);
+        mark(c, ci, MK_COMPOSITE, st);
         CK(cudaGetLastError());
+        c->kernels_per_render += kernels_of(sb, false);
         cut_tot += n_cut; vis_tot += n_vis; pair_tot += n_pairs;
         c->last_plan.push_back(sb);
         c->last_plan.back().c0 = ci;
@@ -480,6 +562,10 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     }
     ngs_status es = epoch_guard(c, st, kEpochStride * sbs.size());
     if (es != NGS_OK) return es;
+    if ((es = ensure_events(c, (int)sbs.size())) != NGS_OK) return es;
+    key.push_back(c->timing ? 1 : 0);
+    c->kernels_per_render = 0;
+    for (const SubBatch &sb : sbs) c->kernels_per_render += kernels_of(sb, true);
     CK(cudaMemcpyAsync(w.cams, c->host_cams.data(), sizeof(DevCamera) * n_cams,
                        cudaMemcpyHostToDevice, st));
     if (c->use_graph) {
@@ -487,6 +573,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
             drop_graph(c);
             if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaMemsetAsync(w.work64, 0, 2 * sizeof(unsigned long long), c->cap_stream);
             for (size_t i = 0; i < sbs.size(); ++i) enqueue_batched(c, sbs[i], (int)i, c->cap_stream);
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -507,6 +594,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
         }
         CK(cudaGraphLaunch(c->gexec, st));
     } else {
+        CK(cudaMemsetAsync(w.work64, 0, 2 * sizeof(unsigned long long), st));
         for (size_t i = 0; i < sbs.size(); ++i) enqueue_batched(c, sbs[i], (int)i, st);
         c->stats.graph_replayed = 0;
     }
@@ -646,6 +734,7 @@ NGS_API ngs_status ngs_destroy(ngs_ctx *c) {
     cudaDeviceSynchronize();
     drop_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     free_work(c);
     free_scene(c);
     dfree(c->sort_tmp_keys);
@@ -678,6 +767,10 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
     case NGS_OPT_GRAPH:
         c->use_graph = v != 0;
         if (!c->use_graph) drop_graph(c);
+        return NGS_OK;
+    case NGS_OPT_STAGE_TIMING:
+        c->timing = v != 0;
+        drop_graph(c);
         return NGS_OK;
     }
     return NGS_ERR_INVALID_ARG;
@@ -829,6 +922,14 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n
 
 NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
     if (!c || !out) return NGS_ERR_INVALID_ARG;
+    if (c->work_ready) {
+        unsigned long long w64[2] = {0, 0};
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(w64, c->w.work64, sizeof(w64), cudaMemcpyDeviceToHost));
+        c->stats.records_staged = (int64_t)w64[0];
+        c->stats.evaluations = (int64_t)w64[1];
+    }
+    c->stats.kernels = c->kernels_per_render;
     if (c->stats.cut_total < 0 && c->work_ready) {
         CK(cudaDeviceSynchronize());
         const int n = std::min<int>((int)c->last_plan.size(), c->stats_cap / 4);
@@ -843,6 +944,24 @@ NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
         if (pix > 0) c->pairs_per_pixel = std::max(c->pairs_per_pixel, 1.25 * (double)p / pix);
     }
     *out = c->stats;
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_stage_times(ngs_ctx *c, double *ms, int32_t n) {
+    if (!c || !ms || n <= 0) return NGS_ERR_INVALID_ARG;
+    if (!c->timing || c->ev_groups == 0) return NGS_ERR_INVALID_ARG;
+    const int groups = c->mode == NGS_MODE_PLAIN ? (int)c->host_cams.size()
+                                                 : (int)c->last_plan.size();
+    for (int k = 0; k < n; ++k) ms[k] = 0.0;
+    for (int g = 0; g < groups && g < c->ev_groups; ++g) {
+        CK(cudaEventSynchronize(c->ev[(size_t)g * kMarks + kMarks - 1]));
+        for (int k = 0; k + 1 < kMarks && k < n; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, c->ev[(size_t)g * kMarks + k],
+                                    c->ev[(size_t)g * kMarks + k + 1]));
+            ms[k] += t;
+        }
+    }
     return NGS_OK;
 }
 

@@ -37,10 +37,13 @@ template <typename R, int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW *TH)
 k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
-            const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err) {
+            const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
+            unsigned long long *work64) {
     constexpr int NT = TW * TH;
     __shared__ R s_rec[BATCH];
     __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_evals;
+    __shared__ uint32_t s_staged;
     if (*err) return;
     const int tid = threadIdx.x;
     const int lx = tid % TW, ly = tid / TW;
@@ -66,13 +69,17 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         const uint2 rg = ranges[tile];
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
+        uint32_t evals = 0;
+        if (work64 && tid == 0) { s_evals = 0; s_staged = 0; }
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
             if (__syncthreads_count(!done) == 0) break;
             const int n = (int)min((uint32_t)BATCH, rg.y - start);
             for (int j = tid; j < n; j += NT) s_rec[j] = rec[pval[start + j]];
+            if (work64 && tid == 0) s_staged += n;
             __syncthreads();
             if (!done) {
-                for (int j = 0; j < n; ++j) {
+                int j = 0;
+                for (; j < n; ++j) {
                     const R &r = s_rec[j];
                     const float dx = __fsub_rn(fpx, r.a.x), dy = __fsub_rn(fpy, r.a.y);
                     const float q = __fmaf_rn(r.a.z, __fmul_rn(dx, dx),
@@ -81,7 +88,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     if (q < kLog2AlphaMin) continue;
                     const float alpha = fminf(kAlphaMax, exp2f(q));
                     const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                    if (test_T < kTMin) { done = true; break; }
+                    if (test_T < kTMin) { done = true; ++j; break; }
                     float gr, gg, gb;
                     rec_colour(r, gr, gg, gb);
                     const float w = __fmul_rn(alpha, T);
@@ -90,6 +97,16 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     cb = __fmaf_rn(w, gb, cb);
                     T = test_T;
                 }
+                evals += (uint32_t)j;
+            }
+        }
+        if (work64) {
+            __syncthreads();
+            atomicAdd(&s_evals, (unsigned long long)evals);
+            __syncthreads();
+            if (tid == 0) {
+                atomicAdd(&work64[0], (unsigned long long)s_staged);
+                atomicAdd(&work64[1], s_evals);
             }
         }
         if (inside) {
@@ -107,20 +124,21 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
 template <typename R, int TW, int TH>
 static void launch_b(int batch, const DevCamera *cams, int n_cams, uint32_t n_tiles,
                      const uint2 *ranges, const uint32_t *pval, const void *rec, uint32_t *ticket,
-                     int persistent, int grid, const int *err, cudaStream_t st) {
+                     int persistent, int grid, const int *err, unsigned long long *work64,
+                     cudaStream_t st) {
     const R *r = (const R *)rec;
     switch (batch) {
     case 64:
         k_composite<R, TW, TH, 64><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
-                                                             r, ticket, persistent, err);
+                                                             r, ticket, persistent, err, work64);
         break;
     case 256:
         k_composite<R, TW, TH, 256><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
-                                                              r, ticket, persistent, err);
+                                                              r, ticket, persistent, err, work64);
         break;
     default:
         k_composite<R, TW, TH, 128><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
-                                                              r, ticket, persistent, err);
+                                                              r, ticket, persistent, err, work64);
         break;
     }
 }
@@ -129,28 +147,28 @@ template <typename R>
 static void launch_r(int tile_w, int tile_h, int batch, const DevCamera *cams, int n_cams,
                      uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval, const void *rec,
                      uint32_t *ticket, int persistent, int grid, const int *err,
-                     cudaStream_t st) {
+                     unsigned long long *work64, cudaStream_t st) {
     if (tile_w == 8 && tile_h == 8)
         launch_b<R, 8, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent, grid,
-                          err, st);
+                          err, work64, st);
     else if (tile_w == 16 && tile_h == 8)
         launch_b<R, 16, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                           grid, err, st);
+                           grid, err, work64, st);
     else
         launch_b<R, 16, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                            grid, err, st);
+                            grid, err, work64, st);
 }
 
 void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool persistent,
                       const DevCamera *cams, int n_cams, uint32_t n_tiles, const uint2 *ranges,
                       const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
-                      const int *err, cudaStream_t st) {
+                      const int *err, unsigned long long *work64, cudaStream_t st) {
     if (attr_dtype == NGS_F32)
         launch_r<Rec32>(tile_w, tile_h, batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket,
-                        persistent ? 1 : 0, grid, err, st);
+                        persistent ? 1 : 0, grid, err, work64, st);
     else
         launch_r<Rec16>(tile_w, tile_h, batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket,
-                        persistent ? 1 : 0, grid, err, st);
+                        persistent ? 1 : 0, grid, err, work64, st);
 }
 
 template <typename R, int TW, int TH, int BATCH>

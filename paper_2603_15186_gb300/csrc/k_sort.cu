@@ -226,6 +226,7 @@ static void launch_sort_t(const SortArgs &a, int grid, cudaStream_t st) {
     k_upsweep<K><<<grid, kSortThreads, 0, st>>>((const K *)a.keys[0], a.n_dev, a.n_host,
                                                 a.begin_bit, a.end_bit, a.hist, a.err);
     k_digit_scan<<<passes, kRadix, 0, st>>>(a.hist, a.err);
+    if (a.hook) a.hook(a.hook_user, 0);
     for (int p = 0; p < passes; ++p) {
         const int src = p & 1, dst = src ^ 1;
         const int sh = a.begin_bit + 8 * p;
@@ -241,6 +242,7 @@ static void launch_sort_t(const SortArgs &a, int grid, cudaStream_t st) {
                 (const K *)a.keys[src], a.vals[src], (K *)a.keys[dst], a.vals[dst], a.n_dev,
                 a.n_host, sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch,
                 a.epoch_off + p, a.err);
+        if (a.hook) a.hook(a.hook_user, p + 1);
     }
 }
 

@@ -170,6 +170,8 @@ struct Work {
     uint2 *ranges = nullptr;          int64_t ranges_cap = 0;
     uint32_t *hist = nullptr;         // [passes][256] radix histograms
     DevCamera *cams = nullptr;        int64_t cams_cap = 0;
+    // compositing work counters: [0] records staged, [1] pixel-Gaussian evaluations
+    unsigned long long *work64 = nullptr;
 };
 
 // ticket slots in Work::counters
@@ -217,6 +219,10 @@ struct SortArgs {
     const uint32_t *epoch;
     uint32_t epoch_off;
     int *err;
+    // optional hook run on the host after the histogram (step 0) and after
+    // every digit pass (step p + 1): used to record timing events
+    void (*hook)(void *user, int step);
+    void *hook_user;
 };
 int sort_passes(int begin_bit, int end_bit);
 int sort_partition();
@@ -246,7 +252,7 @@ void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges,
 void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool persistent,
                       const DevCamera *cams, int n_cams, uint32_t n_tiles, const uint2 *ranges,
                       const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
-                      const int *err, cudaStream_t st);
+                      const int *err, unsigned long long *work64, cudaStream_t st);
 int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch);
 
 inline size_t rec_bytes(int attr_dtype) {

@@ -91,6 +91,17 @@ class Renderer:
     def set_graph(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_GRAPH, 1 if on else 0), "graph")
 
+    def set_stage_timing(self, on: bool):
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_STAGE_TIMING, 1 if on else 0),
+              "stage timing")
+
+    def stage_times(self) -> dict:
+        """Milliseconds per stage of the last render (stage timing must be on)."""
+        ms = np.zeros(len(_lib.STAGES), dtype=np.float64)
+        check(self.L.ngs_stage_times(self.h, ms.ctypes.data_as(C.c_void_p), len(ms)),
+              "ngs_stage_times")
+        return dict(zip(_lib.STAGES, ms.tolist()))
+
     # -- scene ---------------------------------------------------------------
     def load_scene(self, scene, attr_dtype: str = "f32", stored=None):
         """``scene``: arrays pos, quat, log_scale, opacity, sh, parent, child_begin,
