@@ -204,6 +204,25 @@ NGS_API ngs_status ngs_sort_pairs(ngs_ctx *ctx, void *d_keys, uint32_t *d_vals, 
 NGS_API ngs_status ngs_scan_u32(ngs_ctx *ctx, const uint32_t *d_in, uint32_t *d_out, int64_t n,
                                 uint32_t *d_total, void *stream);
 
+/* Allocation-free form of ngs_sort_pairs, for callers that cannot allocate
+ * device memory where they sort (a host application whose own pool owns all
+ * device memory, loops where cudaMalloc/cudaFree would synchronise the device,
+ * or code without a renderer context). The paper has no counterpart; it is a
+ * service of this library. Same sort, same arguments and results as
+ * ngs_sort_pairs, but its scratch is one fixed device array inside the
+ * library (about 6.3 MB, held by every GPU that loads the library until the
+ * process exits), so it needs no context and calls no allocator.
+ *  - n <= 524288 (2^19) pairs; larger n returns NGS_ERR_CAPACITY.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the array: calls whose work overlaps on the GPU
+ *    (different streams, unordered threads) race and give undefined results.
+ *  - Asynchronous on `stream`; a device-side wait that gives up is not
+ *    reported by this call (its kernels still finish). */
+NGS_API ngs_status ngs_sort_pairs_static(void *d_keys, uint32_t *d_vals, int64_t n,
+                                         int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
+                                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ STAGES = ["cut", "preprocess", "depth_hist", "depth_pass0", "depth_pass1", "dept
 EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_load_scene",
            "ngs_select_cut", "ngs_render", "ngs_render_host", "ngs_synchronize",
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
-           "ngs_scan_u32"]
+           "ngs_scan_u32", "ngs_sort_pairs_static"]
 
 
 class NgsError(RuntimeError):
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
     L.ngs_debug_tile_lists.argtypes = [vp, i32, vp, vp, i64, C.POINTER(i64)]
     L.ngs_sort_pairs.restype = i32
     L.ngs_sort_pairs.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp]
+    L.ngs_sort_pairs_static.restype = i32
+    L.ngs_sort_pairs_static.argtypes = [vp, vp, i64, i32, i32, i32, vp]
     L.ngs_scan_u32.restype = i32
     L.ngs_scan_u32.argtypes = [vp, vp, vp, i64, vp, vp]
     _lib = L
