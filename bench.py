@@ -142,13 +142,18 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 
 def stage_bytes(st, n_nodes, n_cams, pixels, tiles, attr="f16"):
+    """Minimum HBM bytes per stage for one step. The fused cut + preprocess
+    must read every node's box, position, quaternion, scale/opacity and SH once
+    per sub-batch (the cameras of a sub-batch share them through L2) and write
+    one record, key and rect per visible Gaussian."""
     sop, sh, rec = (16, 192, 48) if attr == "f32" else (8, 96, 32)
-    C, V, P = st["cut_total"], st["visible_total"], st["pair_total"]
+    V, P = st["visible_total"], st["pair_total"]
     return {
-        "cut": 32 * n_nodes * n_cams + 4 * C,
-        "preprocess": 20 * C + V * (16 + sop + sh + rec + 4 + 16),
+        "cut_preprocess": st["sub_batches"] * n_nodes * (32 + 16 + 16 + sop + sh)
+                          + V * (rec + 4 + 16),
+        "gather_keys": 12 * V,
         "depth_hist": 4 * V,
-        "depth_pass0": 12 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 16 * V,
+        "depth_pass0": 16 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 16 * V,
         "pair_offsets": 24 * V,
         "duplicate": 24 * V + 8 * P,
         "tile_hist": 4 * P,
@@ -233,7 +238,8 @@ def run_ours(args, world, rank, local, pg):
         # kernels: group the digit passes of one sort into one kernel
         groups = {"onesweep_pairs": ["tile_pass0", "tile_pass1", "tile_pass2"],
                   "onesweep_depth": ["depth_pass0", "depth_pass1", "depth_pass2", "depth_pass3"],
-                  "composite": ["composite"], "preprocess": ["preprocess"], "cut": ["cut"],
+                  "composite": ["composite"], "cut_preprocess": ["cut_preprocess"],
+                  "gather_keys": ["gather_keys"],
                   "duplicate": ["duplicate"], "pair_offsets": ["pair_offsets"],
                   "ranges": ["ranges"], "histograms": ["depth_hist", "tile_hist"]}
         gt = {g: sum(per_step.get(s, 0.0) for s in ss) for g, ss in groups.items()}

@@ -176,7 +176,8 @@ NGS_API ngs_status ngs_last_stats(ngs_ctx *ctx, ngs_stats *out);
  * events on the render stream (captured into the graph when one is used).
  * After synchronising, ms[k] (k < n, n <= 15) receives the milliseconds of
  * stage k summed over the last render's sub-batches (batched) or cameras
- * (plain): 0 cut, 1 preprocess, 2 depth histogram, 3..6 depth digit passes,
+ * (plain): 0 fused cut + preprocess, 1 dense depth keys, 2 depth histogram,
+ * 3..6 depth digit passes,
  * 7 pair offsets, 8 pair duplication, 9 tile histogram, 10..12 tile digit
  * passes, 13 tile ranges, 14 compositing. Unused passes read 0. */
 NGS_API ngs_status ngs_stage_times(ngs_ctx *ctx, double *ms, int32_t n);

@@ -91,6 +91,7 @@ struct ngs_ctx {
     std::vector<DevCamera> host_cams;
     ngs_stats stats{};
     ngs_status latched = NGS_OK;
+    bool stats_pending = false;
     double pairs_per_pixel = 48.0;     // planner estimate, raised from observations
 
     // optional per-kernel timing: kMarks events per sub-batch (or per camera
@@ -149,7 +150,7 @@ __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
 void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
-    dfree(w.cut_off); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.ranges);
+    dfree(w.cut_off); dfree(w.vis_count); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.ranges);
     dfree(w.hist); dfree(w.cams); dfree(w.work64);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
@@ -221,7 +222,8 @@ ngs_status ensure_work(ngs_ctx *c) {
     w.cams_cap = kMaxCamsPerCall;
     const int64_t nblk = (c->scene.n + cut_partition_nodes() - 1) / cut_partition_nodes();
     int64_t sw = std::max<int64_t>(nblk * kMaxCamsPerBatch, 1);
-    sw = std::max<int64_t>(sw, (w.cut_cap + preprocess_partition() - 1) / preprocess_partition());
+    sw = std::max<int64_t>(sw, (c->scene.n + cutpre_partition_nodes() - 1) /
+                                   cutpre_partition_nodes() * kMaxCamsPerBatch);
     sw = std::max<int64_t>(sw, (std::max(w.rec_cap, w.pair_cap) + sort_partition() - 1) /
                                    sort_partition() * 256);
     sw = std::max<int64_t>(sw, (w.rec_cap + scan_partition() - 1) / scan_partition());
@@ -234,6 +236,7 @@ ngs_status ensure_work(ngs_ctx *c) {
     A(dalloc(&w.err, 1));
     A(dalloc(&w.cut_ids, (size_t)w.cut_cap));
     A(dalloc(&w.cut_off, kMaxCamsPerBatch + 1));
+    A(dalloc(&w.vis_count, kMaxCamsPerBatch));
     A(dalloc((unsigned char **)&w.rec, (size_t)w.rec_cap * sizeof(Rec32)));
     A(dalloc(&w.rect, (size_t)w.rec_cap));
     A(dalloc(&w.poff, (size_t)w.rec_cap));
@@ -317,8 +320,8 @@ std::vector<SubBatch> plan(ngs_ctx *c, std::vector<DevCamera> &cams, int max_cam
     std::vector<SubBatch> out;
     const int64_t n = c->scene.n;
     const int64_t max_tiles = c->cfg.max_tiles_per_batch;
-    const int64_t cams_by_cut =
-        std::max<int64_t>(1, std::min(c->w.cut_cap, c->w.rec_cap) / std::max<int64_t>(n, 1));
+    // each camera of a sub-batch owns a region of n record slots
+    const int64_t cams_by_cut = std::max<int64_t>(1, c->w.rec_cap / std::max<int64_t>(n, 1));
     int i = 0;
     const int N = (int)cams.size();
     while (i < N) {
@@ -357,19 +360,19 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st);
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
     uint32_t eo = 0;
-    launch_cut(c->scene, cams, nc, w.cut_ids, w.cut_cap, w.cut_off, w.counters,
-               w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->grid_cut, st);
+    launch_cutpre(c->scene, cams, nc, c->scene.n, w.rec, w.dkey[1], w.rect, w.vis_count,
+                  w.counters + CNT_CUT, w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->tile_w, c->tile_h,
+                  c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
-    launch_preprocess(c->scene, cams, nc, w.cut_ids, w.cut_off, w.rec, w.dkey[0], w.rect,
-                      w.rec_cap, w.counters, w.counters + TK_PRE, w.status, w.epoch, eo++, w.err,
-                      c->tile_w, c->tile_h, c->grid_pre, st);
+    launch_gather_keys(w.vis_count, nc, c->scene.n, w.dkey[1], w.dkey[0], w.didx[0], w.counters,
+                       w.rec_cap, w.err, c->num_sms * 2, st);
     mark(c, sb_index, MK_PRE, st);
     SortHook dh{c, sb_index, MK_DHIST, st};
     SortArgs da{};
     da.keys[0] = w.dkey[0]; da.keys[1] = w.dkey[1];
     da.vals[0] = w.didx[0]; da.vals[1] = w.didx[1];
     da.n_dev = w.counters + CNT_VIS; da.n_host = -1; da.n_max = w.rec_cap;
-    da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = true;
+    da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = false;
     da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
     da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
     da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
@@ -380,8 +383,10 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
                         w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
                         c->grid_scan, st);
     mark(c, sb_index, MK_POFF, st);
+    cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st);
     launch_duplicate(w.rect, w.didx[dsel], w.poff, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
-                     w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, c->grid_dup, st);
+                     w.pair_cap, cams, w.pkey[0], w.pval[0], w.hist, sb.tile_passes, w.err,
+                     c->grid_dup, st);
     mark(c, sb_index, MK_DUP, st);
     int psel = 0;
     SortHook th{c, sb_index, MK_THIST, st};
@@ -392,6 +397,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
         pa.n_dev = w.counters + CNT_PAIRS; pa.n_host = -1; pa.n_max = w.pair_cap;
         pa.key_bytes = 4; pa.begin_bit = 0; pa.end_bit = 8 * sb.tile_passes;
         pa.vals_identity = false;
+        pa.hist_ready = true;   // counted by the duplication kernel
         pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
         pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
         pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
@@ -463,21 +469,22 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         CK(cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st));
         k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
         uint32_t eo = 0;
-        const int64_t nblk = (c->scene.n + cut_partition_nodes() - 1) / cut_partition_nodes();
-        launch_cut(c->scene, cams, 1, w.cut_ids, w.cut_cap, w.cut_off, w.counters,
-                   w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, (int)nblk, st);
+        const int64_t nblk = (c->scene.n + cutpre_partition_nodes() - 1) / cutpre_partition_nodes();
+        launch_cutpre(c->scene, cams, 1, c->scene.n, w.rec, w.dkey[1], w.rect, w.vis_count,
+                      w.counters + CNT_CUT, w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->tile_w, c->tile_h,
+                      (int)nblk, st);
         mark(c, ci, MK_CUT, st);
         uint32_t n_cut = 0, n_vis = 0, n_pairs = 0;
-        ngs_status s = read_u32(w.counters + CNT_CUT, &n_cut, st);
+        ngs_status s = read_u32(w.vis_count, &n_vis, st);
         if (s != NGS_OK) return s;
+        if ((s = read_u32(w.counters + CNT_CUT, &n_cut, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
-        const int gpre = std::max<int64_t>(1, ((int64_t)n_cut + preprocess_partition() - 1) /
-                                                  preprocess_partition());
-        launch_preprocess(c->scene, cams, 1, w.cut_ids, w.cut_off, w.rec, w.dkey[0], w.rect,
-                          w.rec_cap, w.counters, w.counters + TK_PRE, w.status, w.epoch, eo++,
-                          w.err, c->tile_w, c->tile_h, gpre, st);
+        launch_gather_keys(w.vis_count, 1, c->scene.n, w.dkey[1], w.dkey[0], w.didx[0],
+                           w.counters, w.rec_cap, w.err,
+                           (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n_vis + 1023) / 1024,
+                                                                       4 * c->num_sms)), st);
         mark(c, ci, MK_PRE, st);
-        if ((s = read_u32(w.counters + CNT_VIS, &n_vis, st)) != NGS_OK) return s;
+        eo++;
         if ((s = check_err(c)) != NGS_OK) return s;
         const int gsort_v = std::max<int64_t>(1, ((int64_t)n_vis + sort_partition() - 1) /
                                                      sort_partition());
@@ -485,7 +492,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         da.keys[0] = w.dkey[0]; da.keys[1] = w.dkey[1];
         da.vals[0] = w.didx[0]; da.vals[1] = w.didx[1];
         da.n_dev = nullptr; da.n_host = n_vis; da.n_max = w.rec_cap;
-        da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = true;
+        da.key_bytes = 4; da.begin_bit = 0; da.end_bit = 32; da.vals_identity = false;
         da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
         da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
         SortHook dh{c, ci, MK_DHIST, st};
@@ -502,8 +509,10 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         if ((s = check_err(c)) != NGS_OK) return s;
         if ((int64_t)n_pairs > w.pair_cap) return NGS_ERR_CAPACITY;
         const int gdup = std::max<int64_t>(1, ((int64_t)n_vis + 255) / 256);
+        CK(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st));
         launch_duplicate(w.rect, w.didx[0], w.poff, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
-                         w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, gdup, st);
+                         w.pair_cap, cams, w.pkey[0], w.pval[0], w.hist, sb.tile_passes, w.err,
+                         gdup, st);
         mark(c, ci, MK_DUP, st);
         int psel = 0;
         SortHook th{c, ci, MK_THIST, st};
@@ -516,6 +525,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
             pa.n_dev = nullptr; pa.n_host = n_pairs; pa.n_max = w.pair_cap;
             pa.key_bytes = 4; pa.begin_bit = 0; pa.end_bit = 8 * sb.tile_passes;
             pa.vals_identity = false;
+            pa.hist_ready = true;   // counted by the duplication kernel
             pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
             pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
             pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
@@ -540,6 +550,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         c->last_plan.back().c0 = ci;
     }
     c->stats.cut_total = cut_tot;
+    c->stats_pending = false;
     c->stats.visible_total = vis_tot;
     c->stats.pair_total = pair_tot;
     c->stats.sub_batches = n_cams;
@@ -602,6 +613,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     c->last_plan = sbs;
     c->stats.sub_batches = (int32_t)sbs.size();
     c->stats.cut_total = c->stats.visible_total = c->stats.pair_total = -1;  // filled on demand
+    c->stats_pending = true;
     return NGS_OK;
 }
 
@@ -930,7 +942,8 @@ NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
         c->stats.evaluations = (int64_t)w64[1];
     }
     c->stats.kernels = c->kernels_per_render;
-    if (c->stats.cut_total < 0 && c->work_ready) {
+    if (c->stats_pending && c->work_ready) {
+        c->stats_pending = false;
         CK(cudaDeviceSynchronize());
         const int n = std::min<int>((int)c->last_plan.size(), c->stats_cap / 4);
         std::vector<uint32_t> h((size_t)4 * std::max(n, 1));
@@ -995,11 +1008,12 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     if (hi > lo && h_nodes) {
         std::vector<uint32_t> vals(hi - lo);
         CK(cudaMemcpy(vals.data(), w.pval[psel] + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost));
-        uint32_t nvis = 0;
-        CK(cudaMemcpy(&nvis, w.counters + CNT_VIS, 4, cudaMemcpyDeviceToHost));
-        std::vector<uint4> rect(nvis);
-        CK(cudaMemcpy(rect.data(), w.rect, (size_t)nvis * sizeof(uint4), cudaMemcpyDeviceToHost));
-        for (int64_t k = 0; k < hi - lo; ++k) h_nodes[k] = (int32_t)rect[vals[k]].w;
+        // records live in per-camera regions of n slots; fetch each one's rect
+        for (int64_t k = 0; k < hi - lo; ++k) {
+            uint4 r;
+            CK(cudaMemcpy(&r, w.rect + vals[k], sizeof(uint4), cudaMemcpyDeviceToHost));
+            h_nodes[k] = (int32_t)r.w;
+        }
     }
     (void)npairs;
     return NGS_OK;

@@ -146,7 +146,9 @@ __global__ void __launch_bounds__(kDupThreads)
 k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_idx,
             const uint32_t *__restrict__ poff, const uint32_t *n_vis_p,
             const uint32_t *n_pairs_p, int64_t pair_cap, const DevCamera *__restrict__ cams,
-            uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval, int *err) {
+            uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval, uint32_t *hist, int passes,
+            int *err) {
+    __shared__ uint32_t s_h[3][256];       // digit counts of the tile keys, per radix pass
     __shared__ uint32_t s_off[kDupThreads + 1];
     __shared__ uint4 s_rect[kDupThreads];
     __shared__ uint32_t s_idx[kDupThreads];
@@ -157,7 +159,9 @@ k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_
         if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(err, kErrCapacity);
         return;
     }
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (hist)
+        for (int i = tid; i < 3 * 256; i += kDupThreads) (&s_h[0][0])[i] = 0;
     for (int64_t blk = blockIdx.x; blk * kDupThreads < n_vis; blk += gridDim.x) {
         const int64_t first = blk * kDupThreads;
         const int64_t rem = (int64_t)n_vis - first;
@@ -174,31 +178,64 @@ k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_
             s_off[cnt] = (first + cnt < (int64_t)n_vis) ? poff[first + cnt] : n_pairs;
         __syncthreads();
         const uint32_t p0 = s_off[0], p1 = s_off[cnt];
-        for (uint32_t p = p0 + tid; p < p1; p += kDupThreads) {
-            int lo = 0, hi = cnt - 1;   // last j with s_off[j] <= p
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+        // uniform trip count: every lane of a warp reaches the warp collectives
+        for (uint32_t base = p0; base < p1; base += kDupThreads) {
+            const uint32_t p = base + tid;
+            const bool valid = p < p1;
+            uint32_t key = 0;
+            if (valid) {
+                int lo = 0, hi = cnt - 1;   // last j with s_off[j] <= p
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+                }
+                const uint4 r = s_rect[lo];
+                const uint32_t k = p - s_off[lo];
+                const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
+                const uint32_t w = x1 - x0 + 1u;
+                const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+                const uint2 cm = s_cam[lo];
+                key = cm.x + ty * cm.y + tx;
+                pkey[p] = key;
+                pval[p] = s_idx[lo];
             }
-            const uint4 r = s_rect[lo];
-            const uint32_t k = p - s_off[lo];
-            const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
-            const uint32_t w = x1 - x0 + 1u;
-            const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-            const uint2 cm = s_cam[lo];
-            pkey[p] = cm.x + ty * cm.y + tx;
-            pval[p] = s_idx[lo];
+            if (hist) {
+                // neighbouring pairs mostly share their high digits: a warp whose
+                // valid lanes agree adds its count once
+                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                if (vmask) {
+                    const int leader = __ffs(vmask) - 1;
+                    for (int q = 0; q < passes; ++q) {
+                        const uint32_t d = (key >> (8 * q)) & 255u;
+                        const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+                        const bool same = __all_sync(0xffffffffu, !valid || d == dl);
+                        if (same) {
+                            if (lane == leader) atomicAdd(&s_h[q][d], (uint32_t)__popc(vmask));
+                        } else if (valid) {
+                            atomicAdd(&s_h[q][d], 1u);
+                        }
+                    }
+                }
+            }
         }
         __syncthreads();
+    }
+    if (hist) {
+        __syncthreads();
+        for (int i = tid; i < passes * 256; i += kDupThreads) {
+            const uint32_t v = (&s_h[0][0])[i];
+            if (v) atomicAdd(&hist[i], v);
+        }
     }
 }
 
 void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
                       const uint32_t *n_vis, const uint32_t *n_pairs, int64_t pair_cap,
-                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, int *err, int grid,
-                      cudaStream_t st) {
+                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, uint32_t *hist,
+                      int passes, int *err, int grid, cudaStream_t st) {
     k_duplicate<<<grid, kDupThreads, 0, st>>>(rect, sorted_idx, poff, n_vis, n_pairs, pair_cap,
-                                              cams, pkey, pval, err);
+                                              cams, pkey, pval, passes > 0 ? hist : nullptr,
+                                              passes, err);
 }
 
 // K6: ranges[t] = [first, end) of tile t in the sorted pair keys (ranges of

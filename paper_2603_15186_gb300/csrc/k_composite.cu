@@ -29,8 +29,8 @@ __device__ __forceinline__ void rec_colour(const Rec32 &r, float &cr, float &cg,
 __device__ __forceinline__ void rec_colour(const Rec16 &r, float &cr, float &cg, float &cb) {
     const uint32_t u = __float_as_uint(r.b.z), w = __float_as_uint(r.b.w);
     const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&u));
-    const float2 b0 = __half22float2(*reinterpret_cast<const __half2 *>(&w));
-    cr = rg.x; cg = rg.y; cb = b0.x;
+    cr = rg.x; cg = rg.y;
+    cb = __low2float(*reinterpret_cast<const __half2 *>(&w));   // high half: support size
 }
 
 template <typename R, int TW, int TH, int BATCH>

@@ -26,18 +26,6 @@ constexpr int kCutPart = kCutThreads * kCutItems;
 
 int cut_partition_nodes() { return kCutPart; }
 
-__device__ __forceinline__ float granularity(const float4 lo, const float4 hi, const float px,
-                                             const float py, const float pz, const float fx) {
-    const float gx = fmaxf(fmaxf(__fsub_rn(lo.x, px), 0.0f), __fsub_rn(px, hi.x));
-    const float gy = fmaxf(fmaxf(__fsub_rn(lo.y, py), 0.0f), __fsub_rn(py, hi.y));
-    const float gz = fmaxf(fmaxf(__fsub_rn(lo.z, pz), 0.0f), __fsub_rn(pz, hi.z));
-    const float d2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
-    const float ext = fmaxf(fmaxf(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y)),
-                            __fsub_rn(hi.z, lo.z));
-    if (d2 == 0.0f) return __int_as_float(0x7f800000);  // +inf: camera inside the box
-    return __fdiv_rn(__fmul_rn(fx, ext), __fsqrt_rn(d2));
-}
-
 __global__ void __launch_bounds__(kCutThreads)
 k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int64_t n_nodes,
       const DevCamera *__restrict__ cams, int n_cams, uint32_t *__restrict__ ids, int64_t cap,
@@ -64,17 +52,8 @@ k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int6
 #pragma unroll
         for (int k = 0; k < kCutItems; ++k) {
             const int64_t node = b * kCutPart + k * kCutThreads + tid;
-            bool sel = false;
-            if (node < n_nodes) {
-                const float4 lo = box_lo[node], hi = box_hi[node];
-                const int parent = __float_as_int(lo.w);
-                const int nchild = __float_as_int(hi.w);
-                const bool own = (nchild == 0) || granularity(lo, hi, px, py, pz, fx) <= tau;
-                bool up = true;
-                if (own && parent >= 0)
-                    up = granularity(box_lo[parent], box_hi[parent], px, py, pz, fx) > tau;
-                sel = own && up;
-            }
+            const bool sel =
+                node < n_nodes && cut_selects(box_lo, box_hi, node, px, py, pz, fx, tau);
             bal[k] = __ballot_sync(0xffffffffu, sel);
             if (lane == 0) s_cnt[k * 8 + warp] = __popc(bal[k]);
         }

@@ -31,7 +31,6 @@ constexpr int kPreItems = 2;
 constexpr int kPrePart = kPreThreads * kPreItems;
 constexpr int kMaxCamsPerBatch = 1024;
 
-int preprocess_partition() { return kPrePart; }
 
 template <typename A> struct Attr;
 template <> struct Attr<float> {
@@ -128,16 +127,73 @@ __device__ __forceinline__ void sh_colour(const float sh[48], float x, float y, 
 }
 
 struct PreOut {
-    float x, y, A, B, C, L, r, g, bl;
+    float x, y, A, B, C, L, r, g, bl, hx, hy;
     uint32_t key;
     uint4 rect;
 };
 
+// Cheap conservative test (phase A of the fused kernel): false only for a
+// Gaussian that cannot touch any tile of the camera.
+template <typename A>
+__device__ __forceinline__ bool precull(const SceneDev &sc, const DevCamera &cam, uint32_t node,
+                                        int tile_w, int tile_h) {
+    const float4 p = sc.pos4[node];
+    if (__float_as_uint(p.w) & kNodeCullOpacity) return false;
+    const float dx = __fsub_rn(p.x, cam.pos[0]);
+    const float dy = __fsub_rn(p.y, cam.pos[1]);
+    const float dz = __fsub_rn(p.z, cam.pos[2]);
+    // float32 view depth: its distance from the float64 depth is below
+    // 1e-6 (|dx| + |dy| + |dz|), so a Gaussian this far behind the near plane is
+    // culled without evaluating the float64 depth
+    const float tz32 = __fmaf_rn(cam.R[6], dx, __fmaf_rn(cam.R[7], dy, __fmul_rn(cam.R[8], dz)));
+    const float margin = 1e-6f * (fabsf(dx) + fabsf(dy) + fabsf(dz)) + 1e-6f;
+    if (tz32 < kNearZ - margin) return false;
+    if (tz32 <= 2.0f * kNearZ) return true;
+    // Lateral test: with T0, T1 the rows of J W, Sigma2D_xx = T0 Sigma T0^T + 0.3
+    // <= |T0|^2 smax^2 + 0.3 (smax the largest scale), so the support box of the
+    // tile rectangle is no wider than hb; a box that misses the tile grid by more
+    // than the float32 slack can have no tile.
+    const float tx = __fmaf_rn(cam.R[0], dx, __fmaf_rn(cam.R[1], dy, __fmul_rn(cam.R[2], dz)));
+    const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
+    float so[4];
+    Attr<A>::load4(sc.sop, node, so);
+    const float K = 2.0f * logf(255.0f * so[3]);
+    const float smax = expf(fmaxf(fmaxf(so[0], so[1]), so[2]));
+    const float iz = 1.0f / tz32;
+    const float ax = cam.fx * iz, bx = -cam.fx * tx * iz * iz;
+    const float ay = cam.fy * iz, by = -cam.fy * ty * iz * iz;
+    const float t00 = ax * cam.R[0] + bx * cam.R[6], t01 = ax * cam.R[1] + bx * cam.R[7],
+                t02 = ax * cam.R[2] + bx * cam.R[8];
+    const float t10 = ay * cam.R[3] + by * cam.R[6], t11 = ay * cam.R[4] + by * cam.R[7],
+                t12 = ay * cam.R[5] + by * cam.R[8];
+    const float s2 = smax * smax;
+    const float hxb =
+        sqrtf(K * ((t00 * t00 + t01 * t01 + t02 * t02) * s2 + kBlur)) * 1.0002f + kRectMargin;
+    const float hyb =
+        sqrtf(K * ((t10 * t10 + t11 * t11 + t12 * t12) * s2 + kBlur)) * 1.0002f + kRectMargin;
+    const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
+    const float sx = 1e-4f * (fabsf(u) + hxb) + 0.02f, sy = 1e-4f * (fabsf(v) + hyb) + 0.02f;
+    if (u + hxb + sx < 0.0f || u - hxb - sx >= (float)(cam.tiles_x * tile_w)) return false;
+    if (v + hyb + sy < 0.0f || v - hyb - sy >= (float)(cam.tiles_y * tile_h)) return false;
+    return true;
+}
+
+// Full preprocess of a Gaussian that passed precull (phase B); returns whether
+// it is visible (in front of the near plane and touching at least one tile).
 template <typename A>
 __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCamera &cam,
                                                uint32_t node, int tile_w, int tile_h,
                                                PreOut &o) {
     const float4 p = sc.pos4[node];
+    const float dx = __fsub_rn(p.x, cam.pos[0]);
+    const float dy = __fsub_rn(p.y, cam.pos[1]);
+    const float dz = __fsub_rn(p.z, cam.pos[2]);
+    const float tx = __fmaf_rn(cam.R[0], dx, __fmaf_rn(cam.R[1], dy, __fmul_rn(cam.R[2], dz)));
+    const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
+    float so[4];
+    Attr<A>::load4(sc.sop, node, so);
+    const float opac = so[3];
+    const float K = 2.0f * logf(255.0f * opac);
     // float64 depth in the stated order; the key and the near test use it
     const double d0 = __dsub_rn((double)p.x, cam.posd[0]);
     const double d1 = __dsub_rn((double)p.y, cam.posd[1]);
@@ -145,18 +201,10 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     const double zd = __dadd_rn(__dadd_rn(__dmul_rn(cam.Rz[0], d0), __dmul_rn(cam.Rz[1], d1)),
                                 __dmul_rn(cam.Rz[2], d2));
     if (!(zd > kNearZd)) return false;
-    if (__float_as_uint(p.w) & kNodeCullOpacity) return false;
     const float tz = __double2float_rn(zd);
-    const float dx = __fsub_rn(p.x, cam.pos[0]);
-    const float dy = __fsub_rn(p.y, cam.pos[1]);
-    const float dz = __fsub_rn(p.z, cam.pos[2]);
-    const float tx = __fmaf_rn(cam.R[0], dx, __fmaf_rn(cam.R[1], dy, __fmul_rn(cam.R[2], dz)));
-    const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
 
     // 3D covariance from the normalised quaternion and the scales
     const float4 q4 = sc.quat[node];
-    float so[4];
-    Attr<A>::load4(sc.sop, node, so);
     const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
     const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z),
@@ -166,7 +214,6 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x),
                 R22 = 1.f - 2.f * (x * x + y * y);
     const float s0 = expf(so[0]), s1 = expf(so[1]), s2 = expf(so[2]);
-    const float opac = so[3];
     const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
     const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
     const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
@@ -202,7 +249,6 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     const float v = __fmaf_rn(cam.fy * iz, ty, cam.cy);
 
     // support box and tile rectangle
-    const float K = 2.0f * logf(255.0f * opac);
     const float hx = sqrtf(K * ca) + kRectMargin;
     const float hy = sqrtf(K * cc) + kRectMargin;
     const float itw = 1.0f / (float)tile_w, ith = 1.0f / (float)tile_h;
@@ -226,6 +272,7 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     o.C = -0.5f * kLog2e * (ca * idet);
     o.L = log2f(opac);
     o.r = rgb[0]; o.g = rgb[1]; o.bl = rgb[2];
+    o.hx = hx; o.hy = hy;
     o.key = __float_as_uint(tz);
     o.rect = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16),
                         0u, node);
@@ -235,53 +282,94 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
 __device__ __forceinline__ void store_rec(Rec32 *rec, int64_t i, const PreOut &o) {
     rec[i].a = make_float4(o.x, o.y, o.A, o.B);
     rec[i].b = make_float4(o.C, o.L, o.r, o.g);
-    rec[i].c = make_float4(o.bl, 0.f, 0.f, 0.f);
+    rec[i].c = make_float4(o.bl, o.hx, o.hy, 0.f);
 }
 __device__ __forceinline__ void store_rec(Rec16 *rec, int64_t i, const PreOut &o) {
     const __half2 rg = __floats2half2_rn(o.r, o.g);
-    const __half2 b0 = __floats2half2_rn(o.bl, 0.0f);
+    const __half2 b0 = __halves2half2(__float2half_rn(o.bl), __float2half_ru(fmaxf(o.hx, o.hy)));
     rec[i].a = make_float4(o.x, o.y, o.A, o.B);
     rec[i].b = make_float4(o.C, o.L, __uint_as_float(*reinterpret_cast<const uint32_t *>(&rg)),
                            __uint_as_float(*reinterpret_cast<const uint32_t *>(&b0)));
 }
 
+// Fused cut + preprocess. Partitions are (block of kPrePart nodes, camera) with
+// the camera varying fastest, so CTAs that run at the same time work on the same
+// node block for different cameras and share its attributes through L2. Each
+// camera has its own look-back chain over the node blocks, so camera c's
+// visible Gaussians land in node-id order in its region
+// [c * region, c * region + vis_count[c]) of the record, key and rect arrays.
 template <typename A, typename R>
 __global__ void __launch_bounds__(kPreThreads)
-k_preprocess(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams,
-             const uint32_t *__restrict__ cut_ids, const uint32_t *__restrict__ cut_off,
-             R *__restrict__ rec, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
-             int64_t rec_cap, uint32_t *counters, uint32_t *ticket, uint64_t *status,
-             const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, int tile_w, int tile_h) {
-    __shared__ uint32_t s_off[kMaxCamsPerBatch + 1];
+k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t region,
+         R *__restrict__ rec, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
+         uint32_t *__restrict__ vis_count, uint32_t *cut_count, uint32_t *ticket,
+         uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, int tile_w,
+         int tile_h) {
+    __shared__ uint32_t s_cand[kPrePart];      // candidates of the partition, node order
     __shared__ uint32_t s_cnt[kPreItems * 8];
-    __shared__ uint32_t s_part, s_excl;
+    __shared__ uint32_t s_part, s_excl, s_ncand, s_sel;
     if (*err) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i <= n_cams; i += kPreThreads) s_off[i] = cut_off[i];
-    __syncthreads();
-    const uint32_t n_slots = s_off[n_cams];
-    const int64_t nparts = ((int64_t)n_slots + kPrePart - 1) / kPrePart;
+    const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
+    const int64_t nparts = nblk * n_cams;
     const uint32_t epoch = *epoch_ptr + epoch_off;
+    const uint32_t lt = lanemask_lt();
     for (;;) {
-        if (tid == 0) s_part = atomicAdd(ticket, 1u);
+        if (tid == 0) {
+            s_part = atomicAdd(ticket, 1u);
+            s_sel = 0;
+        }
         __syncthreads();
         const int64_t part = s_part;
         if (part >= nparts) break;
-        PreOut out[kPreItems];
+        const int64_t b = part / n_cams;
+        const int c = (int)(part - b * n_cams);
+        const DevCamera &cam = cams[c];
+        // phase A: cut rule and conservative cull over the block's nodes; the
+        // survivors are compacted, in node order, into s_cand
         uint32_t bal[kPreItems];
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k) {
-            const int64_t slot = part * kPrePart + k * kPreThreads + tid;
-            bool vis = false;
-            if (slot < n_slots) {
-                int lo = 0, hi = n_cams - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= (uint32_t)slot) lo = mid; else hi = mid - 1;
-                }
-                vis = preprocess_one<A>(sc, cams[lo], cut_ids[slot], tile_w, tile_h, out[k]);
-                out[k].rect.z = (uint32_t)lo;
+            const int64_t node = b * kPrePart + k * kPreThreads + tid;
+            const bool sel = node < sc.n &&
+                             cut_selects(sc.box_lo, sc.box_hi, node, cam.pos[0], cam.pos[1],
+                                         cam.pos[2], cam.fx, cam.tau);
+            const bool cand = sel && precull<A>(sc, cam, (uint32_t)node, tile_w, tile_h);
+            const uint32_t sb = __ballot_sync(0xffffffffu, sel);
+            bal[k] = __ballot_sync(0xffffffffu, cand);
+            if (lane == 0) {
+                s_cnt[k * 8 + warp] = __popc(bal[k]);
+                atomicAdd(&s_sel, (uint32_t)__popc(sb));
             }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t v = lane < kPreItems * 8 ? s_cnt[lane] : 0u;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < kPreItems * 8) s_cnt[lane] = incl - v;
+            if (lane == 31) s_ncand = incl;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k)
+            if ((bal[k] >> lane) & 1u)
+                s_cand[s_cnt[k * 8 + warp] + __popc(bal[k] & lt)] =
+                    (uint32_t)(b * kPrePart + k * kPreThreads + tid);
+        if (tid == 0) atomicAdd(cut_count, s_sel);
+        __syncthreads();
+        // phase B: the full preprocess, densely over the candidates
+        const int ncand = (int)s_ncand;
+        PreOut out[kPreItems];
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k) {
+            const int j = k * kPreThreads + tid;
+            bool vis = false;
+            if (j < ncand) vis = preprocess_one<A>(sc, cam, s_cand[j], tile_w, tile_h, out[k]);
             bal[k] = __ballot_sync(0xffffffffu, vis);
             if (lane == 0) s_cnt[k * 8 + warp] = __popc(bal[k]);
         }
@@ -297,65 +385,110 @@ k_preprocess(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams,
             if (lane < kPreItems * 8) s_cnt[lane] = incl - v;
             const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
             if (lane == 0) {
-                uint64_t *slotp = status + part;
+                uint64_t *chain = status + (int64_t)c * nblk;
                 uint32_t prev = 0;
-                if (part == 0) {
-                    publish(slotp, pack_status(kFlagPrefix, epoch, total));
+                if (b == 0) {
+                    publish(chain, pack_status(kFlagPrefix, epoch, total));
                 } else {
-                    publish(slotp, pack_status(kFlagAgg, epoch, total));
-                    look_back(status, part, 1, epoch, &prev, err);
-                    publish(slotp, pack_status(kFlagPrefix, epoch, prev + total));
+                    publish(chain + b, pack_status(kFlagAgg, epoch, total));
+                    look_back(chain, b, 1, epoch, &prev, err);
+                    publish(chain + b, pack_status(kFlagPrefix, epoch, prev + total));
                 }
                 s_excl = prev;
-                if (part == nparts - 1) {
-                    counters[CNT_VIS] = prev + total;
-                    if ((int64_t)prev + total > rec_cap) latch_error(err, kErrCapacity);
-                }
+                if (b == nblk - 1) vis_count[c] = prev + total;
             }
         }
         __syncthreads();
-        const uint32_t base = s_excl;
+        const int64_t base = (int64_t)c * region + s_excl;
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k) {
             if ((bal[k] >> lane) & 1u) {
-                const int64_t pos = (int64_t)base + s_cnt[k * 8 + warp] +
-                                    __popc(bal[k] & lanemask_lt());
-                if (pos < rec_cap) {
-                    store_rec(rec, pos, out[k]);
-                    dkey[pos] = out[k].key;
-                    rect[pos] = out[k].rect;
-                }
+                const int64_t pos = base + s_cnt[k * 8 + warp] + __popc(bal[k] & lt);
+                store_rec(rec, pos, out[k]);
+                dkey[pos] = out[k].key;
+                out[k].rect.z = (uint32_t)c;
+                rect[pos] = out[k].rect;
             }
         }
         __syncthreads();
     }
-    // an empty cut never enters the loop: the visible count is zero
-    if (nparts == 0 && blockIdx.x == 0 && tid == 0) counters[CNT_VIS] = 0;
 }
 
-void launch_preprocess(const SceneDev &sc, const DevCamera *cams, int n_cams,
-                       const uint32_t *cut_ids, const uint32_t *cut_off, void *rec,
-                       uint32_t *dkey, uint4 *rect, int64_t rec_cap, uint32_t *counters,
-                       uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
-                       uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
-                       cudaStream_t st) {
+// Dense (key, record index) arrays for the depth sort: element i of the
+// concatenation of the per-camera regions, and the visible total.
+__global__ void k_gather_keys(const uint32_t *__restrict__ vis_count, int n_cams, int64_t region,
+                              const uint32_t *__restrict__ dkey_sparse,
+                              uint32_t *__restrict__ dkey, uint32_t *__restrict__ didx,
+                              uint32_t *counters, int64_t cap, int *err) {
+    __shared__ uint32_t s_off[kMaxCamsPerBatch + 1];
+    __shared__ uint32_t s_w[32];
+    if (*err) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // exclusive scan of up to 1024 per-camera counts (blockDim = 1024)
+    const uint32_t v = tid < n_cams ? vis_count[tid] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t wb = 0;
+    for (int w = 0; w < warp; ++w) wb += s_w[w];
+    if (tid <= n_cams) s_off[tid] = wb + incl - v;
+    if (tid == n_cams - 1) s_off[n_cams] = wb + incl;
+    __syncthreads();
+    const uint32_t total = s_off[n_cams];
+    if (blockIdx.x == 0 && tid == 0) {
+        counters[CNT_VIS] = total;
+        if ((int64_t)total > cap) latch_error(err, kErrCapacity);
+    }
+    if ((int64_t)total > cap) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_cams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= (uint32_t)i) lo = mid; else hi = mid - 1;
+        }
+        const int64_t sp = (int64_t)lo * region + (i - s_off[lo]);
+        dkey[i] = dkey_sparse[sp];
+        didx[i] = (uint32_t)sp;
+    }
+}
+
+void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_t region,
+                   void *rec, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
+                   uint32_t *cut_count, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
+                   cudaStream_t st) {
     switch (sc.attr_dtype) {
     case NGS_F16:
-        k_preprocess<__half, Rec16><<<grid, kPreThreads, 0, st>>>(
-            sc, cams, n_cams, cut_ids, cut_off, (Rec16 *)rec, dkey, rect, rec_cap, counters,
+        k_cutpre<__half, Rec16><<<grid, kPreThreads, 0, st>>>(
+            sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
             ticket, status, epoch, epoch_off, err, tile_w, tile_h);
         break;
     case NGS_BF16:
-        k_preprocess<__nv_bfloat16, Rec16><<<grid, kPreThreads, 0, st>>>(
-            sc, cams, n_cams, cut_ids, cut_off, (Rec16 *)rec, dkey, rect, rec_cap, counters,
+        k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, 0, st>>>(
+            sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
             ticket, status, epoch, epoch_off, err, tile_w, tile_h);
         break;
     default:
-        k_preprocess<float, Rec32><<<grid, kPreThreads, 0, st>>>(
-            sc, cams, n_cams, cut_ids, cut_off, (Rec32 *)rec, dkey, rect, rec_cap, counters,
+        k_cutpre<float, Rec32><<<grid, kPreThreads, 0, st>>>(
+            sc, cams, n_cams, region, (Rec32 *)rec, dkey_sparse, rect, vis_count, cut_count,
             ticket, status, epoch, epoch_off, err, tile_w, tile_h);
         break;
     }
 }
+
+void launch_gather_keys(const uint32_t *vis_count, int n_cams, int64_t region,
+                        const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,
+                        uint32_t *counters, int64_t cap, int *err, int grid, cudaStream_t st) {
+    k_gather_keys<<<grid, 1024, 0, st>>>(vis_count, n_cams, region, dkey_sparse, dkey, didx,
+                                         counters, cap, err);
+}
+
+int cutpre_partition_nodes() { return kPrePart; }
 
 }  // namespace ngs

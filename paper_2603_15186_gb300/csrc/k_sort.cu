@@ -17,6 +17,9 @@
 //
 // HBM per pass: read key + value, write key + value (16 B/pair for 32-bit
 // keys, 24 B for 64-bit), plus the upsweep's one read of the keys.
+// Partitions are 8192 keys (32-bit) or 4096 (64-bit) over 512 threads: long
+// runs per digit keep the scattered writes close to whole sectors, and values
+// are read only once the keys are ranked, which keeps two CTAs resident.
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -28,7 +31,7 @@ constexpr int kSortPart = kSortThreads * kSortItems;   // 4096 keys
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 8;
 
-int sort_partition() { return kSortPart; }
+int sort_partition() { return kSortPart; }   // smallest partition of any key width
 int sort_passes(int begin_bit, int end_bit) { return (end_bit - begin_bit + 7) / 8; }
 
 template <typename K>
@@ -82,52 +85,60 @@ __global__ void k_digit_scan(uint32_t *hist, const int *err) {
     h[tid] = wbase + incl - v;
 }
 
+// Partition shape per key width: 512 threads; 16 (32-bit keys) or 8 (64-bit
+// keys) items per thread, i.e. 8192 or 4096 keys per partition.
+template <typename K> struct SortShape;
+template <> struct SortShape<uint32_t> { static constexpr int kItems = 16; };
+template <> struct SortShape<uint64_t> { static constexpr int kItems = 8; };
+constexpr int kOsThreads = 512;
+constexpr int kOsWarps = kOsThreads / 32;
+
 template <typename K>
 struct SortSmem {
-    uint32_t whist[kSortWarps][kRadix];   // per-warp digit counts, then warp offsets
+    static constexpr int kPart = kOsThreads * SortShape<K>::kItems;
+    uint32_t whist[kOsWarps][kRadix];     // per-warp digit counts, then warp offsets
     uint32_t dstart[kRadix];              // block-local start of each digit
     uint32_t gstart[kRadix];              // global start of each digit for this partition
-    uint32_t wtot[kSortWarps];
-    K keys[kSortPart];
-    uint32_t vals[kSortPart];
+    uint32_t wtot[kRadix / 32];
+    K keys[kPart];
+    uint32_t vals[kPart];
     uint32_t part;
 };
 
 template <typename K, bool kIdentity>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kOsThreads, 2)
 k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
            uint32_t *__restrict__ vout, const uint32_t *n_dev, int64_t n_host, int shift,
            uint32_t mask, const uint32_t *__restrict__ digit_base, uint64_t *status,
            uint32_t *ticket, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+    constexpr int ITEMS = SortShape<K>::kItems;
+    constexpr int PART = SortSmem<K>::kPart;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem<K> &S = *reinterpret_cast<SortSmem<K> *>(smem_raw);
     if (*err) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
-    const int64_t nparts = (n + kSortPart - 1) / kSortPart;
+    const int64_t nparts = (n + PART - 1) / PART;
     const uint32_t epoch = *epoch_ptr + epoch_off;
     const uint32_t lt = lanemask_lt();
     for (;;) {
         if (tid == 0) S.part = atomicAdd(ticket, 1u);
-        for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+        for (int i = tid; i < kOsWarps * kRadix; i += kOsThreads) (&S.whist[0][0])[i] = 0;
         __syncthreads();
         const int64_t part = S.part;
         if (part >= nparts) break;
-        const int64_t base = part * kSortPart + (int64_t)warp * (kSortItems * 32);
-        K key[kSortItems];
-        uint32_t val[kSortItems];
-        uint32_t rank[kSortItems];
+        const int64_t base = part * PART + (int64_t)warp * (ITEMS * 32);
+        // keys first; values are loaded only after ranking, to keep few live registers
+        K key[ITEMS];
+        uint32_t rank[ITEMS];
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
+        for (int i = 0; i < ITEMS; ++i) {
             const int64_t idx = base + i * 32 + lane;
-            const bool valid = idx < n;
-            key[i] = valid ? kin[idx] : (K)0;
-            val[i] = kIdentity ? (uint32_t)idx : (valid ? vin[idx] : 0u);
+            key[i] = idx < n ? kin[idx] : (K)0;
         }
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const int64_t idx = base + i * 32 + lane;
-            const bool valid = idx < n;
+        for (int i = 0; i < ITEMS; ++i) {
+            const bool valid = base + i * 32 + lane < n;
             const uint32_t d = digit_of(key[i], shift, mask);
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
@@ -144,12 +155,13 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             rank[i] = before + __popc(peers & lt);
         }
         __syncthreads();
-        // thread d owns digit d: warp offsets, partition total, look-back
-        {
+        // threads 0..255 own one digit each: warp offsets, partition total,
+        // look-back, and the block-local scan of the totals
+        uint32_t run = 0, incl = 0;
+        if (tid < kRadix) {
             const int d = tid;
-            uint32_t run = 0;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) {
+            for (int w = 0; w < kOsWarps; ++w) {
                 const uint32_t t = S.whist[w][d];
                 S.whist[w][d] = run;
                 run += t;
@@ -164,35 +176,39 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
                 publish(slot, pack_status(kFlagPrefix, epoch, prev + run));
             }
             S.gstart[d] = digit_base[d] + prev;
-            // block-local exclusive scan of the digit totals
-            uint32_t incl = run;
+            incl = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
             if (lane == 31) S.wtot[warp] = incl;
-            __syncthreads();
+        }
+        __syncthreads();
+        if (tid < kRadix) {
             uint32_t wbase = 0;
             for (int w = 0; w < warp; ++w) wbase += S.wtot[w];
-            S.dstart[d] = wbase + incl - run;
+            S.dstart[tid] = wbase + incl - run;
         }
         __syncthreads();
-        // stage the partition in shared memory in digit order
+        // stage keys, then values, in digit order
 #pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            const int64_t idx = base + i * 32 + lane;
-            if (idx < n) {
+        for (int i = 0; i < ITEMS; ++i) {
+            if (base + i * 32 + lane < n) {
                 const uint32_t d = digit_of(key[i], shift, mask);
-                const uint32_t lp = S.dstart[d] + S.whist[warp][d] + rank[i];
-                S.keys[lp] = key[i];
-                S.vals[lp] = val[i];
+                rank[i] += S.dstart[d] + S.whist[warp][d];
+                S.keys[rank[i]] = key[i];
             }
         }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int64_t idx = base + i * 32 + lane;
+            if (idx < n) S.vals[rank[i]] = kIdentity ? (uint32_t)idx : vin[idx];
+        }
         __syncthreads();
-        const int64_t rem = n - part * kSortPart;
-        const int cnt = rem < kSortPart ? (int)rem : kSortPart;
-        for (int j = tid; j < cnt; j += kSortThreads) {
+        const int64_t rem = n - part * PART;
+        const int cnt = rem < PART ? (int)rem : PART;
+        for (int j = tid; j < cnt; j += kOsThreads) {
             const K k = S.keys[j];
             const uint32_t d = digit_of(k, shift, mask);
             const int64_t g = (int64_t)S.gstart[d] + (j - S.dstart[d]);
@@ -222,9 +238,11 @@ template <typename K>
 static void launch_sort_t(const SortArgs &a, int grid, cudaStream_t st) {
     const int passes = sort_passes(a.begin_bit, a.end_bit);
     const size_t smem = sizeof(SortSmem<K>);
-    cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kRadix * passes, st);
-    k_upsweep<K><<<grid, kSortThreads, 0, st>>>((const K *)a.keys[0], a.n_dev, a.n_host,
-                                                a.begin_bit, a.end_bit, a.hist, a.err);
+    if (!a.hist_ready) {
+        cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kRadix * passes, st);
+        k_upsweep<K><<<grid, kSortThreads, 0, st>>>((const K *)a.keys[0], a.n_dev, a.n_host,
+                                                    a.begin_bit, a.end_bit, a.hist, a.err);
+    }
     k_digit_scan<<<passes, kRadix, 0, st>>>(a.hist, a.err);
     if (a.hook) a.hook(a.hook_user, 0);
     for (int p = 0; p < passes; ++p) {
@@ -233,12 +251,12 @@ static void launch_sort_t(const SortArgs &a, int grid, cudaStream_t st) {
         const int bits = std::min(8, a.end_bit - sh);
         const uint32_t mask = (1u << bits) - 1u;
         if (p == 0 && a.vals_identity)
-            k_onesweep<K, true><<<grid, kSortThreads, smem, st>>>(
+            k_onesweep<K, true><<<grid, kOsThreads, smem, st>>>(
                 (const K *)a.keys[src], nullptr, (K *)a.keys[dst], a.vals[dst], a.n_dev, a.n_host,
                 sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch, a.epoch_off + p,
                 a.err);
         else
-            k_onesweep<K, false><<<grid, kSortThreads, smem, st>>>(
+            k_onesweep<K, false><<<grid, kOsThreads, smem, st>>>(
                 (const K *)a.keys[src], a.vals[src], (K *)a.keys[dst], a.vals[dst], a.n_dev,
                 a.n_host, sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch,
                 a.epoch_off + p, a.err);

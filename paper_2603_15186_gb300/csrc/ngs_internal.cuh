@@ -65,14 +65,16 @@ static_assert(sizeof(DevCamera) % 16 == 0, "DevCamera alignment");
 // compositing records: centre (x, y), the conic scaled to log2 units
 // (A dx^2 + B dx dy + C dy^2 = log2 of the Gaussian falloff), L = log2(opacity)
 // and the colour
+// and the colour, plus the half-widths of the support box (for the per-warp
+// skip test; float16 rounded up in the compact record)
 struct __align__(16) Rec32 {
     float4 a;   // x, y, A, B
     float4 b;   // C, L, r, g
-    float4 c;   // bl, 0, 0, 0
+    float4 c;   // bl, hx, hy, 0
 };
 struct __align__(16) Rec16 {
     float4 a;   // x, y, A, B
-    float4 b;   // C, L, half2(r, g) bits, half2(bl, 0) bits
+    float4 b;   // C, L, half2(r, g) bits, half2(bl, max(hx, hy)) bits
 };
 
 struct SceneDev {
@@ -117,6 +119,34 @@ __device__ __forceinline__ uint64_t peek(const uint64_t *slot) {
     return v;
 }
 
+// Granularity of a node box seen from camera centre (px, py, pz):
+// s = fx * (longest box side) / (distance from the centre to the box), +inf
+// when the centre is inside the box (level-of-detail cut, Sec. III-B).
+__device__ __forceinline__ float granularity(const float4 lo, const float4 hi, const float px,
+                                             const float py, const float pz, const float fx) {
+    const float gx = fmaxf(fmaxf(__fsub_rn(lo.x, px), 0.0f), __fsub_rn(px, hi.x));
+    const float gy = fmaxf(fmaxf(__fsub_rn(lo.y, py), 0.0f), __fsub_rn(py, hi.y));
+    const float gz = fmaxf(fmaxf(__fsub_rn(lo.z, pz), 0.0f), __fsub_rn(pz, hi.z));
+    const float d2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
+    const float ext = fmaxf(fmaxf(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y)),
+                            __fsub_rn(hi.z, lo.z));
+    if (d2 == 0.0f) return __int_as_float(0x7f800000);
+    return __fdiv_rn(__fmul_rn(fx, ext), __fsqrt_rn(d2));
+}
+
+// The cut rule for node `node`: (leaf or s(n) <= tau) and (root or s(parent) > tau).
+__device__ __forceinline__ bool cut_selects(const float4 *__restrict__ box_lo,
+                                            const float4 *__restrict__ box_hi, int64_t node,
+                                            float px, float py, float pz, float fx, float tau) {
+    const float4 lo = box_lo[node], hi = box_hi[node];
+    const int parent = __float_as_int(lo.w);
+    const int nchild = __float_as_int(hi.w);
+    const bool own = (nchild == 0) || granularity(lo, hi, px, py, pz, fx) <= tau;
+    if (!own) return false;
+    if (parent < 0) return true;
+    return granularity(box_lo[parent], box_hi[parent], px, py, pz, fx) > tau;
+}
+
 // Decoupled look-back for one running sum: returns the exclusive prefix of
 // partition `part` over the chain whose words sit at status[j * stride]. The
 // caller has already published its own aggregate. Returns false (and latches
@@ -159,6 +189,7 @@ struct Work {
     int *err = nullptr;               // latched device error
     uint32_t *cut_ids = nullptr;      int64_t cut_cap = 0;
     uint32_t *cut_off = nullptr;      // [cams + 1]
+    uint32_t *vis_count = nullptr;    // [cams] visible Gaussians per camera
     void *rec = nullptr;              int64_t rec_cap = 0;
     uint32_t *dkey[2] = {nullptr, nullptr};
     uint32_t *didx[2] = {nullptr, nullptr};
@@ -192,14 +223,18 @@ void launch_cut(const SceneDev &sc, const DevCamera *cams, int n_cams, uint32_t 
                 int grid, cudaStream_t st);
 int cut_partition_nodes();
 
-// preprocess: cut slots -> compacted records, depth keys, rectangles
-void launch_preprocess(const SceneDev &sc, const DevCamera *cams, int n_cams,
-                       const uint32_t *cut_ids, const uint32_t *cut_off, void *rec,
-                       uint32_t *dkey, uint4 *rect, int64_t rec_cap, uint32_t *counters,
-                       uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
-                       uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
-                       cudaStream_t st);
-int preprocess_partition();
+// fused cut + preprocess: per camera c, visible Gaussians of the cut in node
+// order at [c * region, c * region + vis_count[c]) of rec / dkey_sparse / rect
+void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_t region,
+                   void *rec, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
+                   uint32_t *cut_count, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
+                   cudaStream_t st);
+int cutpre_partition_nodes();
+// dense depth keys and sparse record indices for the sort; counters[CNT_VIS]
+void launch_gather_keys(const uint32_t *vis_count, int n_cams, int64_t region,
+                        const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,
+                        uint32_t *counters, int64_t cap, int *err, int grid, cudaStream_t st);
 
 // radix sort (onesweep) of (uint32 | uint64 key, uint32 value) pairs; n from
 // device memory (*n_dev) or host (n_host >= 0). Result lands in buffer
@@ -213,6 +248,7 @@ struct SortArgs {
     int key_bytes;
     int begin_bit, end_bit;
     bool vals_identity;       // first pass takes value = input index
+    bool hist_ready;          // hist already holds the digit counts (no upsweep)
     uint32_t *hist;           // [passes][256]
     uint32_t *tickets;        // one per pass
     uint64_t *status;
@@ -241,10 +277,12 @@ void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const ui
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
                          int grid, cudaStream_t st);
+// emits the pairs and, if hist is given, adds the digit counts of their tile
+// keys for `passes` 8-bit radix passes to hist (zeroed by the caller)
 void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
                       const uint32_t *n_vis, const uint32_t *n_pairs, int64_t pair_cap,
-                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, int *err, int grid,
-                      cudaStream_t st);
+                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, uint32_t *hist,
+                      int passes, int *err, int grid, cudaStream_t st);
 void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges, int grid,
                    cudaStream_t st, const int *err);
 
