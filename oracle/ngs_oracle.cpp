@@ -22,10 +22,10 @@
 //   5. brute force: per pixel over every visible Gaussian in depth order, no
 //                  tiles, as an independent check of 3-4.
 // Every floating-point step is float64 except where a step's result decides an
-// integer that the renderer must reproduce exactly: the depth sort key is the
-// float32 rounding of a float64 depth evaluated in a fixed operation order
-// (the file is compiled with -ffp-contract=off so no fused multiply-add
-// changes that order).
+// integer that the renderer must reproduce exactly: the near-plane cull and the
+// depth sort key use the float32 view depth computed by one fixed sequence of
+// IEEE float operations, the renderer's own precision (the file is compiled
+// with -ffp-contract=off so that no other fused multiply-add appears).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -175,16 +175,16 @@ void orc_cov3d(const float *quat, const float *log_scale, double *out) {
         }
 }
 
-// View-space depth in the fixed float64 order the sort key uses:
-// d_k = mu_k - pos_k, z = (R20 d0 + R21 d1) + R22 d2, each product rounded.
-double orc_view_depth(const float *mu, const orc_camera *cam) {
-    const double d0 = (double)mu[0] - cam->pos[0];
-    const double d1 = (double)mu[1] - cam->pos[1];
-    const double d2 = (double)mu[2] - cam->pos[2];
-    const double a = cam->R[6] * d0;
-    const double b = cam->R[7] * d1;
-    const double c = cam->R[8] * d2;
-    return (a + b) + c;
+// The view depth that decides integers: the near-plane cull and the depth
+// sort key. Both are taken in the renderer's precision, float32, with one
+// fixed sequence of IEEE operations so that both sides agree bit for bit:
+// d_k = mu_k - c_k (float subtraction), z = fma(R20, d0, fma(R21, d1, R22 * d2)).
+float orc_depth_f32(const float *mu, const orc_camera *cam) {
+    const float d0 = mu[0] - (float)cam->pos[0];
+    const float d1 = mu[1] - (float)cam->pos[1];
+    const float d2 = mu[2] - (float)cam->pos[2];
+    const float p2 = (float)cam->R[8] * d2;
+    return std::fma((float)cam->R[6], d0, std::fma((float)cam->R[7], d1, p2));
 }
 
 // For each cut slot i (node ids[i]) fills out[i*PC_NCOLS + col], depth_key[i]
@@ -204,12 +204,13 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         depth_key[i] = 0xFFFFFFFFu;
         const int64_t g = ids[i];
         const float *mu = sc->pos + 3 * g;
-        const double tz = orc_view_depth(mu, cam);
-        if (!(tz > kNear)) continue;
+        const float z32 = orc_depth_f32(mu, cam);
+        if (!(z32 > (float)kNear)) continue;
         const double opac = sc->opacity[g];
         if (255.0 * opac < 1.0) continue;
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = (double)mu[k] - cam->pos[k];
+        const double tz = cam->R[6] * d[0] + cam->R[7] * d[1] + cam->R[8] * d[2];
         const double tx = cam->R[0] * d[0] + cam->R[1] * d[1] + cam->R[2] * d[2];
         const double ty = cam->R[3] * d[0] + cam->R[4] * d[1] + cam->R[5] * d[2];
         // Jacobian of (fx x/z, fy y/z) at t
@@ -277,8 +278,7 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         o[PC_DEPTH] = tz; o[PC_OPACITY] = opac;
         o[PC_R] = rgb[0]; o[PC_G] = rgb[1]; o[PC_B] = rgb[2];
         o[PC_HX] = hx; o[PC_HY] = hy;
-        const float kf = (float)tz;
-        std::memcpy(&depth_key[i], &kf, 4);
+        std::memcpy(&depth_key[i], &z32, 4);
         rc[0] = x0; rc[1] = y0; rc[2] = x1; rc[3] = y1;
     }
 }

@@ -63,8 +63,8 @@ def lib():
             L.orc_sh_basis.argtypes = [vp, vp]
             L.orc_cov3d.restype = None
             L.orc_cov3d.argtypes = [vp, vp, vp]
-            L.orc_view_depth.restype = C.c_double
-            L.orc_view_depth.argtypes = [vp, C.POINTER(_Camera)]
+            L.orc_depth_f32.restype = C.c_float
+            L.orc_depth_f32.argtypes = [vp, C.POINTER(_Camera)]
             L.orc_num_threads.restype = i32
             _lib = L
     return _lib
@@ -226,10 +226,11 @@ def cov3d(quat, log_scale):
     return out
 
 
-def view_depth(mu, cam):
+def depth_f32(mu, cam):
+    """The float32 view depth used for the near-plane cull and the sort key."""
     mu = np.ascontiguousarray(mu, dtype=np.float32)
     cc = camera_struct(cam)
-    return lib().orc_view_depth(_p(mu), C.byref(cc))
+    return lib().orc_depth_f32(_p(mu), C.byref(cc))
 
 
 def num_threads() -> int:
@@ -237,5 +238,5 @@ def num_threads() -> int:
 
 
 __all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bin_pairs",
-           "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "view_depth",
+           "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "depth_f32",
            "tiles_xy", "num_threads", "lib"]
