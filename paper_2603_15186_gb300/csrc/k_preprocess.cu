@@ -10,10 +10,10 @@
 // the tiles touched by that box widened by 1/64 pixel, so it is conservative
 // under float32 rounding and the pixels do not depend on the tile shape.
 //
-// Depth key: the view depth is evaluated in float64 in a fixed operation order
-// (d_k = mu_k - c_k; z = (R20 d0 + R21 d1) + R22 d2, every product and sum
-// rounded separately) and rounded to float32; its bits are the sort key. The
-// near-plane test uses the same float64 value. Everything else is float32.
+// Depth key: the view depth z = fma(R20, d0, fma(R21, d1, R22 d2)) with
+// d_k = mu_k - c_k, every operation a single IEEE float32 rounding; its bits
+// are the sort key and it decides the near-plane cull. The oracle evaluates
+// the same sequence, so keys and culls agree bit for bit. No float64 anywhere.
 //
 // Output is compacted in slot order (camera-major, then ascending node id) by
 // a one-pass chained scan, so the record index order breaks depth ties by
@@ -194,14 +194,10 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     Attr<A>::load4(sc.sop, node, so);
     const float opac = so[3];
     const float K = 2.0f * logf(255.0f * opac);
-    // float64 depth in the stated order; the key and the near test use it
-    const double d0 = __dsub_rn((double)p.x, cam.posd[0]);
-    const double d1 = __dsub_rn((double)p.y, cam.posd[1]);
-    const double d2 = __dsub_rn((double)p.z, cam.posd[2]);
-    const double zd = __dadd_rn(__dadd_rn(__dmul_rn(cam.Rz[0], d0), __dmul_rn(cam.Rz[1], d1)),
-                                __dmul_rn(cam.Rz[2], d2));
-    if (!(zd > kNearZd)) return false;
-    const float tz = __double2float_rn(zd);
+    // view depth in the fixed float32 operation sequence that the near-plane
+    // cull and the sort key use
+    const float tz = __fmaf_rn(cam.R[6], dx, __fmaf_rn(cam.R[7], dy, __fmul_rn(cam.R[8], dz)));
+    if (!(tz > kNearZ)) return false;
 
     // 3D covariance from the normalised quaternion and the scales
     const float4 q4 = sc.quat[node];
