@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stage-timing", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-cams", type=int, default=3)
     return ap.parse_args()
 
@@ -188,6 +189,13 @@ def run_ours(args, world, rank, local, pg):
     R.set_mode("batched")
     R.set_stage_timing(not args.no_stage_timing)
     imgs = R.new_images(cams)
+    tune = None
+    if not args.no_autotune:
+        # tile shape x compositing batch, picked on this very camera batch
+        tune = R.autotune(cams, imgs, reps=2)
+        tw, th = tune["tile"]
+        args.tile, args.batch = f"{tw}x{th}", tune["batch"]
+        tiles = sum(-(-c.width // tw) * -(-c.height // th) for c in cams)
     for _ in range(max(args.warmup, 3)):
         R.render(cams, imgs)
     stats = R.stats()
@@ -276,7 +284,7 @@ def run_ours(args, world, rank, local, pg):
            "clocks": clk, "roofline": roof,
            "work": {k: stats[k] for k in ("cut_total", "visible_total", "pair_total",
                                           "records_staged", "evaluations", "sub_batches")},
-           "scene_gen_s": round(gen_s, 1)}
+           "scene_gen_s": round(gen_s, 1), "autotune": tune}
 
     # plain per-view float32 path on the same cameras
     plain_imgs = None

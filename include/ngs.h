@@ -169,6 +169,25 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *ctx, const ngs_camera *cams, int32_t
 /* Waits for the stream and returns (then clears) any latched device error. */
 NGS_API ngs_status ngs_synchronize(ngs_ctx *ctx, void *stream);
 
+/* Result of ngs_autotune: the chosen tile shape and staging batch, and the
+ * measured milliseconds of one render of the given cameras for every
+ * candidate (index = tile index * 3 + batch index over tiles {8x8, 16x8,
+ * 16x16} and batches {64, 128, 256}). */
+typedef struct {
+    int32_t tile_w, tile_h, batch;
+    int32_t reserved;
+    float ms[9];
+} ngs_tune_result;
+
+/* Autotuner of the batched path: renders `cams` (into d_images) with every
+ * tile shape {8x8, 16x8, 16x16} and compositing batch {64, 128, 256}, each
+ * captured in its CUDA graph, warmed up and timed over `reps` replays with
+ * CUDA events on `stream`, then keeps the fastest setting in the context.
+ * All candidates give bit-identical images. Synchronous. */
+NGS_API ngs_status ngs_autotune(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
+                                float *const *d_images, int32_t reps, void *stream,
+                                ngs_tune_result *out);
+
 /* Synchronises the device and fills *out for the last render. */
 NGS_API ngs_status ngs_last_stats(ngs_ctx *ctx, ngs_stats *out);
 

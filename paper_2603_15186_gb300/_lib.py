@@ -20,7 +20,7 @@ STAGES = ["cut_preprocess", "gather_keys", "depth_hist", "depth_pass0", "depth_p
 EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_load_scene",
            "ngs_select_cut", "ngs_render", "ngs_render_host", "ngs_synchronize",
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
-           "ngs_scan_u32", "ngs_sort_pairs_static"]
+           "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune"]
 
 
 class NgsError(RuntimeError):
@@ -51,6 +51,11 @@ class Config(C.Structure):
                 ("batch", C.c_int32), ("cut_capacity", C.c_int64),
                 ("record_capacity", C.c_int64), ("pair_capacity", C.c_int64),
                 ("max_tiles_per_batch", C.c_int32), ("reserved", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
+                ("reserved", C.c_int32), ("ms", C.c_float * 9)]
 
 
 class Stats(C.Structure):
@@ -106,6 +111,9 @@ def load(build_if_missing: bool = True):
     L.ngs_sort_pairs.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp]
     L.ngs_sort_pairs_static.restype = i32
     L.ngs_sort_pairs_static.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    L.ngs_autotune.restype = i32
+    L.ngs_autotune.argtypes = [vp, C.POINTER(Camera), i32, C.POINTER(vp), i32, vp,
+                               C.POINTER(TuneResult)]
     L.ngs_scan_u32.restype = i32
     L.ngs_scan_u32.argtypes = [vp, vp, vp, i64, vp, vp]
     _lib = L

@@ -729,6 +729,7 @@ NGS_API ngs_status ngs_create(const ngs_config *cfg, ngs_ctx **out) {
     x->tile_w = c.tile_w; x->tile_h = c.tile_h; x->batch = c.batch;
     cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, c.device);
     sort_init_attributes();
+    cutpre_init_attributes();
     x->grid_cut = 4 * x->num_sms;
     x->grid_pre = 4 * x->num_sms;
     x->grid_sort32 = 2 * x->num_sms;
@@ -958,6 +959,60 @@ NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
     }
     *out = c->stats;
     return NGS_OK;
+}
+
+NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
+                                float *const *d_images, int32_t reps, void *stream,
+                                ngs_tune_result *out) {
+    if (!c || !out || reps <= 0) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    static const int kTiles[3][2] = {{8, 8}, {16, 8}, {16, 16}};
+    static const int kBatches[3] = {64, 128, 256};
+    cudaStream_t st = (cudaStream_t)stream;
+    const int mode = c->mode;
+    const bool graph = c->use_graph, timing = c->timing;
+    c->mode = NGS_MODE_BATCHED;
+    c->use_graph = true;
+    c->timing = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 3.4e38f;
+    int bt = 2, bb = 1;
+    ngs_status s = NGS_OK;
+    for (int t = 0; t < 3 && s == NGS_OK; ++t)
+        for (int b = 0; b < 3 && s == NGS_OK; ++b) {
+            c->tile_w = kTiles[t][0];
+            c->tile_h = kTiles[t][1];
+            c->batch = kBatches[b];
+            drop_graph(c);
+            // capture + one warm-up replay, then the timed replays
+            for (int k = 0; k < 2 && s == NGS_OK; ++k) s = render_common(c, cams, n_cams, d_images, st);
+            if (s == NGS_OK) s = ngs_synchronize(c, stream);
+            if (s != NGS_OK) break;
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < reps && s == NGS_OK; ++k) s = render_common(c, cams, n_cams, d_images, st);
+            cudaEventRecord(e1, st);
+            if (s == NGS_OK) s = ngs_synchronize(c, stream);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            out->ms[t * 3 + b] = ms / reps;
+            if (s == NGS_OK && ms / reps < best) { best = ms / reps; bt = t; bb = b; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tile_w = kTiles[bt][0];
+    c->tile_h = kTiles[bt][1];
+    c->batch = kBatches[bb];
+    c->mode = mode;
+    c->use_graph = graph;
+    c->timing = timing;
+    drop_graph(c);
+    out->tile_w = c->tile_w;
+    out->tile_h = c->tile_h;
+    out->batch = c->batch;
+    out->reserved = 0;
+    return s;
 }
 
 NGS_API ngs_status ngs_stage_times(ngs_ctx *c, double *ms, int32_t n) {

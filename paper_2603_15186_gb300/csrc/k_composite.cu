@@ -33,6 +33,24 @@ __device__ __forceinline__ void rec_colour(const Rec16 &r, float &cr, float &cg,
     cb = __low2float(*reinterpret_cast<const __half2 *>(&w));   // high half: support size
 }
 
+__device__ __forceinline__ void set_sentinel(Rec32 &r) {
+    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.b = make_float4(0.f, __int_as_float(0xff800000), 0.f, 0.f);
+    r.c = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void set_sentinel(Rec16 &r) {
+    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.b = make_float4(0.f, __int_as_float(0xff800000), 0.f, 0.f);
+}
+
+// log2 of o times the Gaussian falloff at pixel centre (fpx, fpy)
+template <typename R>
+__device__ __forceinline__ float exponent(const R &r, float fpx, float fpy) {
+    const float dx = __fsub_rn(fpx, r.a.x), dy = __fsub_rn(fpy, r.a.y);
+    return __fmaf_rn(r.a.z, __fmul_rn(dx, dx),
+                     __fmaf_rn(r.a.w, __fmul_rn(dx, dy), __fmaf_rn(r.b.x, __fmul_rn(dy, dy), r.b.y)));
+}
+
 template <typename R, int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW *TH)
 k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
@@ -74,30 +92,39 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
             if (__syncthreads_count(!done) == 0) break;
             const int n = (int)min((uint32_t)BATCH, rg.y - start);
-            for (int j = tid; j < n; j += NT) s_rec[j] = rec[pval[start + j]];
+            const int n4 = (n + 3) & ~3;
+            for (int j = tid; j < n4; j += NT) {
+                if (j < n) s_rec[j] = rec[pval[start + j]];
+                else set_sentinel(s_rec[j]);   // q = -inf: never contributes
+            }
             if (work64 && tid == 0) s_staged += n;
             __syncthreads();
             if (!done) {
                 int j = 0;
-                for (; j < n; ++j) {
-                    const R &r = s_rec[j];
-                    const float dx = __fsub_rn(fpx, r.a.x), dy = __fsub_rn(fpy, r.a.y);
-                    const float q = __fmaf_rn(r.a.z, __fmul_rn(dx, dx),
-                                              __fmaf_rn(r.a.w, __fmul_rn(dx, dy),
-                                                        __fmaf_rn(r.b.x, __fmul_rn(dy, dy), r.b.y)));
-                    if (q < kLog2AlphaMin) continue;
-                    const float alpha = fminf(kAlphaMax, exp2f(q));
-                    const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                    if (test_T < kTMin) { done = true; ++j; break; }
-                    float gr, gg, gb;
-                    rec_colour(r, gr, gg, gb);
-                    const float w = __fmul_rn(alpha, T);
-                    cr = __fmaf_rn(w, gr, cr);
-                    cg = __fmaf_rn(w, gg, cg);
-                    cb = __fmaf_rn(w, gb, cb);
-                    T = test_T;
+                for (; j < n4; j += 4) {
+                    // the four exponents do not depend on T: evaluate them together,
+                    // then blend in list order
+                    float q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) q[u] = exponent(s_rec[j + u], fpx, fpy);
+                    int u = 0;
+#pragma unroll
+                    for (; u < 4; ++u) {
+                        if (q[u] < kLog2AlphaMin) continue;
+                        const float alpha = fminf(kAlphaMax, exp2f(q[u]));
+                        const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                        if (test_T < kTMin) { done = true; break; }
+                        float gr, gg, gb;
+                        rec_colour(s_rec[j + u], gr, gg, gb);
+                        const float w = __fmul_rn(alpha, T);
+                        cr = __fmaf_rn(w, gr, cr);
+                        cg = __fmaf_rn(w, gg, cg);
+                        cb = __fmaf_rn(w, gb, cb);
+                        T = test_T;
+                    }
+                    if (done) { j += u + 1; break; }
                 }
-                evals += (uint32_t)j;
+                evals += (uint32_t)min(j, n);
             }
         }
         if (work64) {

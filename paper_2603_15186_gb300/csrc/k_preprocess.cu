@@ -27,8 +27,8 @@
 namespace ngs {
 
 constexpr int kPreThreads = 256;
-constexpr int kPreItems = 2;
-constexpr int kPrePart = kPreThreads * kPreItems;
+constexpr int kPreItems = 4;                          // phase-A nodes per thread
+constexpr int kPrePart = kPreThreads * kPreItems;     // nodes per partition
 constexpr int kMaxCamsPerBatch = 1024;
 
 
@@ -38,12 +38,13 @@ template <> struct Attr<float> {
         const float4 t = reinterpret_cast<const float4 *>(p)[i];
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
-    static __device__ __forceinline__ void load_sh(const void *p, int64_t i, float v[48]) {
+    template <int kUnused, typename F>
+    static __device__ __forceinline__ void stream_sh(const void *p, int64_t i, F f) {
         const float4 *s = reinterpret_cast<const float4 *>(p) + i * 12;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const float4 t = s[k];
-            v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+            f(4 * k, t.x); f(4 * k + 1, t.y); f(4 * k + 2, t.z); f(4 * k + 3, t.w);
         }
     }
 };
@@ -54,7 +55,8 @@ template <> struct Attr<__half> {
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
-    static __device__ __forceinline__ void load_sh(const void *p, int64_t i, float v[48]) {
+    template <int kUnused, typename F>
+    static __device__ __forceinline__ void stream_sh(const void *p, int64_t i, F f) {
         const uint4 *s = reinterpret_cast<const uint4 *>(p) + i * 6;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -62,8 +64,8 @@ template <> struct Attr<__half> {
             const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[j]));
-                v[8 * k + 2 * j] = f.x; v[8 * k + 2 * j + 1] = f.y;
+                const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&w[j]));
+                f(8 * k + 2 * j, v.x); f(8 * k + 2 * j + 1, v.y);
             }
         }
     }
@@ -78,7 +80,8 @@ template <> struct Attr<__nv_bfloat16> {
         const float2 a = bf2(t.x), b = bf2(t.y);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
-    static __device__ __forceinline__ void load_sh(const void *p, int64_t i, float v[48]) {
+    template <int kUnused, typename F>
+    static __device__ __forceinline__ void stream_sh(const void *p, int64_t i, F f) {
         const uint4 *s = reinterpret_cast<const uint4 *>(p) + i * 6;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -86,8 +89,8 @@ template <> struct Attr<__nv_bfloat16> {
             const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float2 f = bf2(w[j]);
-                v[8 * k + 2 * j] = f.x; v[8 * k + 2 * j + 1] = f.y;
+                const float2 v = bf2(w[j]);
+                f(8 * k + 2 * j, v.x); f(8 * k + 2 * j + 1, v.y);
             }
         }
     }
@@ -96,9 +99,11 @@ template <> struct Attr<__nv_bfloat16> {
 // Real SH basis to degree 3 in the 3DGS sign convention (standard real SH
 // times (-1)^|m|), index l*l + l + m; constants are the normalisations
 // sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0) folded with
-// the polynomial coefficients.
-__device__ __forceinline__ void sh_colour(const float sh[48], float x, float y, float z,
-                                          float rgb[3]) {
+// the polynomial coefficients. The 48 coefficients are streamed from memory
+// in storage order (coefficient-major), each channel accumulating k = 0..15.
+template <typename A>
+__device__ __forceinline__ void sh_colour(const void *sh, int64_t node, float x, float y,
+                                          float z, float rgb[3]) {
     const float xx = x * x, yy = y * y, zz = z * z;
     float Y[16];
     Y[0] = 0.28209479177387814f;
@@ -117,13 +122,13 @@ __device__ __forceinline__ void sh_colour(const float sh[48], float x, float y, 
     Y[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
     Y[14] = 1.4453057213202769f * z * (xx - yy);
     Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) acc = __fmaf_rn(Y[k], sh[3 * k + ch], acc);
-        rgb[ch] = fmaxf(acc, 0.0f);
-    }
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    Attr<A>::template stream_sh<3>(sh, node, [&](int h, float v) {
+        acc[h % 3] = __fmaf_rn(Y[h / 3], v, acc[h % 3]);
+    });
+    rgb[0] = fmaxf(acc[0], 0.0f);
+    rgb[1] = fmaxf(acc[1], 0.0f);
+    rgb[2] = fmaxf(acc[2], 0.0f);
 }
 
 struct PreOut {
@@ -255,11 +260,9 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     if (x0 > x1 || y0 > y1) return false;
 
     // colour seen along camera -> mean
-    float sh[48];
-    Attr<A>::load_sh(sc.sh, node, sh);
     const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
     float rgb[3];
-    sh_colour(sh, dx * inv, dy * inv, dz * inv, rgb);
+    sh_colour<A>(sc.sh, node, dx * inv, dy * inv, dz * inv, rgb);
 
     o.x = u;
     o.y = v;
@@ -294,6 +297,20 @@ __device__ __forceinline__ void store_rec(Rec16 *rec, int64_t i, const PreOut &o
 // camera has its own look-back chain over the node blocks, so camera c's
 // visible Gaussians land in node-id order in its region
 // [c * region, c * region + vis_count[c]) of the record, key and rect arrays.
+// Phase-B results of one partition, staged until the partition's output
+// offset is known (candidate j of the partition in slot j).
+template <typename R>
+struct CutPreSmem {
+    uint32_t cand[kPrePart];      // candidate node ids, node order
+    R rec[kPrePart];
+    uint32_t key[kPrePart];
+    uint4 rect[kPrePart];
+    uint32_t vis[kPrePart];       // visible flag, then (rank | 1 << 31)
+    uint32_t cnt[kPreItems * 8];
+    uint32_t wsum[kPreThreads / 32];
+    uint32_t part, excl, ncand, sel;
+};
+
 template <typename A, typename R>
 __global__ void __launch_bounds__(kPreThreads)
 k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t region,
@@ -301,9 +318,8 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
          uint32_t *__restrict__ vis_count, uint32_t *cut_count, uint32_t *ticket,
          uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, int tile_w,
          int tile_h) {
-    __shared__ uint32_t s_cand[kPrePart];      // candidates of the partition, node order
-    __shared__ uint32_t s_cnt[kPreItems * 8];
-    __shared__ uint32_t s_part, s_excl, s_ncand, s_sel;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CutPreSmem<R> &S = *reinterpret_cast<CutPreSmem<R> *>(smem_raw);
     if (*err) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
@@ -312,18 +328,19 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
     const uint32_t lt = lanemask_lt();
     for (;;) {
         if (tid == 0) {
-            s_part = atomicAdd(ticket, 1u);
-            s_sel = 0;
+            S.part = atomicAdd(ticket, 1u);
+            S.sel = 0;
         }
         __syncthreads();
-        const int64_t part = s_part;
+        const int64_t part = S.part;
         if (part >= nparts) break;
         const int64_t b = part / n_cams;
         const int c = (int)(part - b * n_cams);
         const DevCamera &cam = cams[c];
-        // phase A: cut rule and conservative cull over the block's nodes; the
-        // survivors are compacted, in node order, into s_cand
+        // phase A: cut rule and conservative cull; survivors compacted into
+        // S.cand in node order
         uint32_t bal[kPreItems];
+        uint32_t nsel = 0;
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k) {
             const int64_t node = b * kPrePart + k * kPreThreads + tid;
@@ -331,79 +348,96 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
                              cut_selects(sc.box_lo, sc.box_hi, node, cam.pos[0], cam.pos[1],
                                          cam.pos[2], cam.fx, cam.tau);
             const bool cand = sel && precull<A>(sc, cam, (uint32_t)node, tile_w, tile_h);
-            const uint32_t sb = __ballot_sync(0xffffffffu, sel);
+            nsel += __popc(__ballot_sync(0xffffffffu, sel));
             bal[k] = __ballot_sync(0xffffffffu, cand);
-            if (lane == 0) {
-                s_cnt[k * 8 + warp] = __popc(bal[k]);
-                atomicAdd(&s_sel, (uint32_t)__popc(sb));
-            }
+            if (lane == 0) S.cnt[k * 8 + warp] = __popc(bal[k]);
         }
+        if (lane == 0) atomicAdd(&S.sel, nsel);
         __syncthreads();
         if (warp == 0) {
-            const uint32_t v = lane < kPreItems * 8 ? s_cnt[lane] : 0u;
+            const uint32_t v = lane < kPreItems * 8 ? S.cnt[lane] : 0u;
             uint32_t incl = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
-            if (lane < kPreItems * 8) s_cnt[lane] = incl - v;
-            if (lane == 31) s_ncand = incl;
+            if (lane < kPreItems * 8) S.cnt[lane] = incl - v;
+            if (lane == 31) S.ncand = incl;
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k)
             if ((bal[k] >> lane) & 1u)
-                s_cand[s_cnt[k * 8 + warp] + __popc(bal[k] & lt)] =
+                S.cand[S.cnt[k * 8 + warp] + __popc(bal[k] & lt)] =
                     (uint32_t)(b * kPrePart + k * kPreThreads + tid);
-        if (tid == 0) atomicAdd(cut_count, s_sel);
+        if (tid == 0) atomicAdd(cut_count, S.sel);
         __syncthreads();
-        // phase B: the full preprocess, densely over the candidates
-        const int ncand = (int)s_ncand;
-        PreOut out[kPreItems];
-#pragma unroll
-        for (int k = 0; k < kPreItems; ++k) {
-            const int j = k * kPreThreads + tid;
-            bool vis = false;
-            if (j < ncand) vis = preprocess_one<A>(sc, cam, s_cand[j], tile_w, tile_h, out[k]);
-            bal[k] = __ballot_sync(0xffffffffu, vis);
-            if (lane == 0) s_cnt[k * 8 + warp] = __popc(bal[k]);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t v = lane < kPreItems * 8 ? s_cnt[lane] : 0u;
-            uint32_t incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            if (lane < kPreItems * 8) s_cnt[lane] = incl - v;
-            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-            if (lane == 0) {
-                uint64_t *chain = status + (int64_t)c * nblk;
-                uint32_t prev = 0;
-                if (b == 0) {
-                    publish(chain, pack_status(kFlagPrefix, epoch, total));
-                } else {
-                    publish(chain + b, pack_status(kFlagAgg, epoch, total));
-                    look_back(chain, b, 1, epoch, &prev, err);
-                    publish(chain + b, pack_status(kFlagPrefix, epoch, prev + total));
-                }
-                s_excl = prev;
-                if (b == nblk - 1) vis_count[c] = prev + total;
+        // phase B: full preprocess, densely over the candidates, results staged
+        const int ncand = (int)S.ncand;
+        for (int j = tid; j < ncand; j += kPreThreads) {
+            PreOut o;
+            const bool vis = preprocess_one<A>(sc, cam, S.cand[j], tile_w, tile_h, o);
+            S.vis[j] = vis ? 1u : 0u;
+            if (vis) {
+                store_rec(S.rec, j, o);
+                S.key[j] = o.key;
+                o.rect.z = (uint32_t)c;
+                S.rect[j] = o.rect;
             }
         }
         __syncthreads();
-        const int64_t base = (int64_t)c * region + s_excl;
+        // ranks of the visible candidates (thread t owns slots 4t .. 4t + 3)
+        uint32_t f[kPreItems], run = 0;
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k) {
-            if ((bal[k] >> lane) & 1u) {
-                const int64_t pos = base + s_cnt[k * 8 + warp] + __popc(bal[k] & lt);
-                store_rec(rec, pos, out[k]);
-                dkey[pos] = out[k].key;
-                out[k].rect.z = (uint32_t)c;
-                rect[pos] = out[k].rect;
+            const int j = tid * kPreItems + k;
+            f[k] = j < ncand ? S.vis[j] : 0u;
+            run += f[k];
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        uint32_t wb = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kPreThreads / 32; ++w) {
+            if (w < warp) wb += S.wsum[w];
+            total += S.wsum[w];
+        }
+        uint32_t r = wb + incl - run;
+#pragma unroll
+        for (int k = 0; k < kPreItems; ++k) {
+            const int j = tid * kPreItems + k;
+            if (j < ncand) S.vis[j] = f[k] ? (r | 0x80000000u) : 0u;
+            r += f[k];
+        }
+        if (tid == 0) {
+            uint64_t *chain = status + (int64_t)c * nblk;
+            uint32_t prev = 0;
+            if (b == 0) {
+                publish(chain, pack_status(kFlagPrefix, epoch, total));
+            } else {
+                publish(chain + b, pack_status(kFlagAgg, epoch, total));
+                look_back(chain, b, 1, epoch, &prev, err);
+                publish(chain + b, pack_status(kFlagPrefix, epoch, prev + total));
+            }
+            S.excl = prev;
+            if (b == nblk - 1) vis_count[c] = prev + total;
+        }
+        __syncthreads();
+        const int64_t base = (int64_t)c * region + S.excl;
+        for (int j = tid; j < ncand; j += kPreThreads) {
+            const uint32_t v = S.vis[j];
+            if (v) {
+                const int64_t pos = base + (v & 0x7fffffffu);
+                rec[pos] = S.rec[j];
+                dkey[pos] = S.key[j];
+                rect[pos] = S.rect[j];
             }
         }
         __syncthreads();
@@ -461,17 +495,17 @@ void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_
                    cudaStream_t st) {
     switch (sc.attr_dtype) {
     case NGS_F16:
-        k_cutpre<__half, Rec16><<<grid, kPreThreads, 0, st>>>(
+        k_cutpre<__half, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
             ticket, status, epoch, epoch_off, err, tile_w, tile_h);
         break;
     case NGS_BF16:
-        k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, 0, st>>>(
+        k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
             ticket, status, epoch, epoch_off, err, tile_w, tile_h);
         break;
     default:
-        k_cutpre<float, Rec32><<<grid, kPreThreads, 0, st>>>(
+        k_cutpre<float, Rec32><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
             sc, cams, n_cams, region, (Rec32 *)rec, dkey_sparse, rect, vis_count, cut_count,
             ticket, status, epoch, epoch_off, err, tile_w, tile_h);
         break;
@@ -486,5 +520,15 @@ void launch_gather_keys(const uint32_t *vis_count, int n_cams, int64_t region,
 }
 
 int cutpre_partition_nodes() { return kPrePart; }
+
+void cutpre_init_attributes() {
+    cudaFuncSetAttribute(k_cutpre<float, Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(CutPreSmem<Rec32>));
+    cudaFuncSetAttribute(k_cutpre<__half, Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(CutPreSmem<Rec16>));
+    cudaFuncSetAttribute(k_cutpre<__nv_bfloat16, Rec16>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(CutPreSmem<Rec16>));
+}
 
 }  // namespace ngs

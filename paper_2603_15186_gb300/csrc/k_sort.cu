@@ -6,8 +6,8 @@
 // the preceding partitions (no separate scan kernel per pass).
 //
 // Stability: keys are loaded warp-striped (item i of lane l is key
-// base + 512 w + 32 i + l), each warp ranks its items in that order with
-// eight ballots per item (peers = lanes holding the same digit), warps are
+// base + 32 ITEMS w + 32 i + l), each warp ranks its items in that order (peers
+// = lanes holding the same digit, from eight ballots per item), warps are
 // offset in order, and partitions in ticket order; equal digits therefore keep
 // their input order, which is what the two-stage binning needs.
 //

@@ -231,6 +231,7 @@ void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_
                    uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
                    cudaStream_t st);
 int cutpre_partition_nodes();
+void cutpre_init_attributes();
 // dense depth keys and sparse record indices for the sort; counters[CNT_VIS]
 void launch_gather_keys(const uint32_t *vis_count, int n_cams, int64_t region,
                         const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,

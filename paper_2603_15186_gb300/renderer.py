@@ -146,6 +146,19 @@ class Renderer:
             check(self.L.ngs_synchronize(self.h, st), "ngs_synchronize")
         return images
 
+    def autotune(self, cams, images: Optional[list] = None, reps: int = 3, stream=None) -> dict:
+        """Times every tile shape x staging batch on ``cams`` and keeps the fastest."""
+        if images is None:
+            images = self.new_images(cams)
+        arr = camera_array(cams)
+        ptrs = (C.c_void_p * len(cams))(*[C.c_void_p(t.data_ptr()) for t in images])
+        res = _lib.TuneResult()
+        check(self.L.ngs_autotune(self.h, arr, len(cams), ptrs, int(reps), _stream_ptr(stream),
+                                  C.byref(res)), "ngs_autotune")
+        names = [f"{tw}x{th}/{b}" for tw, th in ((8, 8), (16, 8), (16, 16)) for b in (64, 128, 256)]
+        return {"tile": (res.tile_w, res.tile_h), "batch": res.batch,
+                "ms": dict(zip(names, [round(x, 3) for x in res.ms]))}
+
     def render_host(self, cams, out: Optional[List[np.ndarray]] = None, stream=None):
         """Renders and copies every image into host arrays [3, H, W] float32."""
         if out is None:

@@ -183,6 +183,24 @@ def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
         assert np.array_equal(alone, base[i])
 
 
+def test_autotune_keeps_pixels(R, small_floor):
+    R.load_scene(small_floor)
+    cams = _floor_cams(small_floor)
+    R.set_tile(16, 16)
+    R.set_batch(128)
+    base = [t.cpu().numpy() for t in R.render(cams)]
+    res = R.autotune(cams, reps=1)
+    assert res["tile"] in [(8, 8), (16, 8), (16, 16)] and res["batch"] in (64, 128, 256)
+    assert all(v > 0 for v in res["ms"].values()) and len(res["ms"]) == 9
+    out = [t.cpu().numpy() for t in R.render(cams)]
+    st = R.stats()
+    assert (st["tile_w"], st["tile_h"], st["batch"]) == (*res["tile"], res["batch"])
+    for a, b in zip(base, out):
+        assert np.array_equal(a, b)
+    R.set_tile(16, 16)
+    R.set_batch(128)
+
+
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 def test_reduced_precision_attributes(R, small_floor, dtype):
     stored, deq = quantize_attributes(small_floor, dtype)
