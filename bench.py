@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stage-timing", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=5.0,
+                    help="seconds of simulated agent load for the serving leg (0: skip)")
+    ap.add_argument("--serving-scene", default="floor8m")
     ap.add_argument("--cpu-cams", type=int, default=3)
     return ap.parse_args()
 
@@ -358,8 +361,83 @@ def run_ours(args, world, rank, local, pg):
                                    "flagged_pixel_frac": max(flagged),
                                    "views": [int(i) for i in order]}
     R.close()
+    if args.serving_seconds > 0:
+        out["serving"] = run_serving(args, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving leg: many agents, Poisson arrivals, continuous batching
+# ---------------------------------------------------------------------------
+
+def run_serving(args, local):
+    """64 agents on independent collision-free walks through the two-wing
+    8M-leaf floor, Poisson arrivals at 31.25 requests/s each (2000/s in all),
+    resolutions 320x240 : 640x480 : 1280x720 = 1 : 2 : 1 per agent, tau ~ U[2, 8].
+    Requests are submitted at their arrival times to the serving loop; latency
+    is submission to completion."""
+    import torch
+    from paper_2603_15186_gb300 import Renderer, Server, camera_struct
+    from scenegen import make_scene, quantize_attributes, walk_cameras
+    t0 = time.time()
+    scene = make_scene(args.serving_scene)
+    stored, _ = quantize_attributes(scene, "f16")
+    gen_s = time.time() - t0
+    rng = np.random.default_rng(4004)
+    n_agents, rate = 64, 2000.0 / 64
+    res = [(320, 240)] * 16 + [(640, 480)] * 32 + [(1280, 720)] * 16
+    rng.shuffle(res)
+    steps = int(args.serving_seconds * rate * 2) + 8
+    walks = []
+    for a in range(n_agents):
+        w, h = res[a]
+        taus = rng.uniform(2.0, 8.0, size=steps)
+        walks.append([camera_struct(c) for c in
+                      walk_cameras(scene, steps, 5000 + a, w, h, tau=0.0, taus=taus)])
+    events = []
+    for a in range(n_agents):
+        t, k = rng.exponential(1.0 / rate), 0
+        while t < args.serving_seconds:
+            events.append((t, a, k))
+            k += 1
+            t += rng.exponential(1.0 / rate)
+    events.sort()
+    R = Renderer(device=local, cut_capacity=1 << 20, record_capacity=1 << 27,
+                 pair_capacity=1 << 29)
+    R.load_scene(scene, attr_dtype="f16", stored=stored)
+    ring = 4
+    bufs = [[torch.empty((3, res[a][1], res[a][0]), device="cuda") for _ in range(ring)]
+            for a in range(n_agents)]
+    S = Server(R, lanes=2, max_cams=64, lane_record_capacity=1 << 27,
+               lane_pair_capacity=(1 << 29) + (1 << 28))
+    # warm-up burst, not counted
+    for a in range(n_agents):
+        S.submit_struct(walks[a][0], bufs[a][0].data_ptr())
+    S.wait_all()
+    S.stop()
+    S = Server(R, lanes=2, max_cams=64, lane_record_capacity=1 << 27,
+               lane_pair_capacity=(1 << 29) + (1 << 28))
+    offered = sum(res[a][0] * res[a][1] for _, a, _ in events) / 1e6 / args.serving_seconds
+    start = time.perf_counter()
+    for t, a, k in events:
+        delay = start + t - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        S.submit_struct(walks[a][k % len(walks[a])], bufs[a][k % ring].data_ptr())
+    S.wait_all()
+    st = S.stats()
+    S.stop()
+    R.close()
+    return {"scene": args.serving_scene, "leaves": int(scene.n_leaves), "agents": n_agents,
+            "offered_req_per_s": round(len(events) / args.serving_seconds, 1),
+            "offered_mpix_per_s": round(offered, 1), "load_seconds": args.serving_seconds,
+            "requests": st["submitted"], "completed": st["completed"], "failed": st["failed"],
+            "launches": st["launches"], "p50_ms": round(st["p50_ms"], 3),
+            "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3),
+            "mpix_per_s": round(st["mpix"] / max(st["span_s"], 1e-9), 1),
+            "span_s": round(st["span_s"], 3), "lanes": 2, "max_cams_per_launch": 64,
+            "attr_storage": "f16", "scene_gen_s": round(gen_s, 1)}
 
 
 # ---------------------------------------------------------------------------

@@ -224,6 +224,54 @@ NGS_API ngs_status ngs_sort_pairs(ngs_ctx *ctx, void *d_keys, uint32_t *d_vals, 
 NGS_API ngs_status ngs_scan_u32(ngs_ctx *ctx, const uint32_t *d_in, uint32_t *d_out, int64_t n,
                                 uint32_t *d_total, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Serving loop: continuous batching of render requests from many agents
+ * against the scene resident in `ctx` (the simulator's agents render views as
+ * they walk, Sec. IV-B). A worker thread owns `lanes` render lanes (a stream
+ * and work buffers each; the scene is shared, not copied). A free lane admits
+ * the oldest waiting requests while they fit its camera limit and its
+ * sort-buffer budget (estimated pairs = pixels x pairs_per_pixel, at least one
+ * request per launch) and renders them as one batch; requests arriving
+ * meanwhile join the next launch, and launches of different lanes overlap on
+ * the device. Each request's image is the same bits as when rendered alone.
+ * The scene must not be reloaded while a server runs.
+ * ------------------------------------------------------------------------ */
+typedef struct ngs_server ngs_server;
+
+typedef struct {
+    int32_t lanes;                  /* concurrent render lanes (default 2, max 8) */
+    int32_t max_cams;               /* cameras per launch (default 64, max 1024) */
+    int64_t pair_budget;            /* admission budget per launch, pairs (default 2^29) */
+    double pairs_per_pixel;         /* admission estimate (default 48) */
+    int64_t lane_record_capacity;   /* per-lane work buffers (0: the context's) */
+    int64_t lane_pair_capacity;
+} ngs_server_config;
+
+typedef struct {
+    int64_t submitted, completed, failed, launches;
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> completion latency */
+    double mpix;                              /* megapixels of completed requests */
+    double span_s;                            /* first submit -> last completion */
+} ngs_serving_stats;
+
+/* Starts the worker thread on the calling thread's current device. */
+NGS_API ngs_status ngs_server_start(ngs_ctx *ctx, const ngs_server_config *cfg,
+                                    ngs_server **out);
+/* Queues one request (thread-safe, non-blocking): camera *cam rendered into
+ * d_image (device float32 [3][H][W], caller-owned, untouched until the
+ * request completes). *ticket identifies it for ngs_server_poll. */
+NGS_API ngs_status ngs_server_submit(ngs_server *s, const ngs_camera *cam, float *d_image,
+                                     uint64_t *ticket);
+/* *done = 1 once the request's image is complete; *latency_ms its latency. */
+NGS_API ngs_status ngs_server_poll(ngs_server *s, uint64_t ticket, int32_t *done,
+                                   double *latency_ms);
+/* Waits until every submitted request completed (NGS_ERR_DEVICE_TIMEOUT after
+ * timeout_ms). */
+NGS_API ngs_status ngs_server_wait_all(ngs_server *s, int32_t timeout_ms);
+NGS_API ngs_status ngs_server_stats(ngs_server *s, ngs_serving_stats *out);
+/* Drains the queue, joins the worker and frees the lanes. */
+NGS_API ngs_status ngs_server_stop(ngs_server *s);
+
 /* Allocation-free form of ngs_sort_pairs, for callers that cannot allocate
  * device memory where they sort (a host application whose own pool owns all
  * device memory, loops where cudaMalloc/cudaFree would synchronise the device,

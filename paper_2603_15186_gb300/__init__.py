@@ -5,6 +5,6 @@ binning by duplicated keys and a radix sort, front-to-back compositing) runs
 in the hand-written CUDA kernels of libngs.so behind the C ABI of
 include/ngs.h; ``Renderer`` marshals arguments to it."""
 from ._lib import NgsError, EXPORTS  # noqa: F401
-from .renderer import Renderer, camera_struct, camera_array  # noqa: F401
+from .renderer import Renderer, Server, camera_struct, camera_array  # noqa: F401
 
-__all__ = ["Renderer", "NgsError", "camera_struct", "camera_array", "EXPORTS"]
+__all__ = ["Renderer", "Server", "NgsError", "camera_struct", "camera_array", "EXPORTS"]

@@ -20,7 +20,9 @@ STAGES = ["cut_preprocess", "gather_keys", "depth_hist", "depth_pass0", "depth_p
 EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_load_scene",
            "ngs_select_cut", "ngs_render", "ngs_render_host", "ngs_synchronize",
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
-           "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune"]
+           "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune", "ngs_server_start",
+           "ngs_server_submit", "ngs_server_poll", "ngs_server_wait_all", "ngs_server_stats",
+           "ngs_server_stop"]
 
 
 class NgsError(RuntimeError):
@@ -56,6 +58,19 @@ class Config(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
                 ("reserved", C.c_int32), ("ms", C.c_float * 9)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("max_cams", C.c_int32), ("pair_budget", C.c_int64),
+                ("pairs_per_pixel", C.c_double), ("lane_record_capacity", C.c_int64),
+                ("lane_pair_capacity", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("launches", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("mean_ms", C.c_double), ("max_ms", C.c_double), ("mpix", C.c_double),
+                ("span_s", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -114,6 +129,18 @@ def load(build_if_missing: bool = True):
     L.ngs_autotune.restype = i32
     L.ngs_autotune.argtypes = [vp, C.POINTER(Camera), i32, C.POINTER(vp), i32, vp,
                                C.POINTER(TuneResult)]
+    L.ngs_server_start.restype = i32
+    L.ngs_server_start.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
+    L.ngs_server_submit.restype = i32
+    L.ngs_server_submit.argtypes = [vp, C.POINTER(Camera), vp, C.POINTER(C.c_uint64)]
+    L.ngs_server_poll.restype = i32
+    L.ngs_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(i32), C.POINTER(C.c_double)]
+    L.ngs_server_wait_all.restype = i32
+    L.ngs_server_wait_all.argtypes = [vp, i32]
+    L.ngs_server_stats.restype = i32
+    L.ngs_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.ngs_server_stop.restype = i32
+    L.ngs_server_stop.argtypes = [vp]
     L.ngs_scan_u32.restype = i32
     L.ngs_scan_u32.argtypes = [vp, vp, vp, i64, vp, vp]
     _lib = L

@@ -68,6 +68,7 @@ struct ngs_ctx {
     bool use_graph = true;
     SceneDev scene;
     bool loaded = false;
+    bool owns_scene = true;           // false for serving lanes sharing a scene
     uint64_t scene_version = 0;
 
     Work w;
@@ -165,7 +166,9 @@ void free_work(ngs_ctx *c) {
 
 void free_scene(ngs_ctx *c) {
     SceneDev &s = c->scene;
-    dfree(s.box_lo); dfree(s.box_hi); dfree(s.pos4); dfree(s.quat); dfree(s.sop); dfree(s.sh);
+    if (c->owns_scene) {
+        dfree(s.box_lo); dfree(s.box_hi); dfree(s.pos4); dfree(s.quat); dfree(s.sop); dfree(s.sh);
+    }
     c->scene = SceneDev();
     c->loaded = false;
 }
@@ -681,6 +684,26 @@ ngs_status validate(const ngs_gaussians *g, const ngs_hierarchy *h) {
 }
 
 }  // namespace
+
+// A context that renders the parent's resident scene (no copy) with its own
+// work buffers, streams and graph cache: one lane of the serving loop.
+ngs_status ngs::lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pair_capacity,
+                            ngs_ctx **out) {
+    if (!parent || !out || !parent->loaded) return NGS_ERR_NOT_LOADED;
+    ngs_config cfg = parent->cfg;
+    if (record_capacity > 0) cfg.record_capacity = record_capacity;
+    if (pair_capacity > 0) cfg.pair_capacity = pair_capacity;
+    ngs_status s = ngs_create(&cfg, out);
+    if (s != NGS_OK) return s;
+    ngs_ctx *l = *out;
+    l->scene = parent->scene;
+    l->owns_scene = false;
+    l->loaded = true;
+    l->scene_version = parent->scene_version;
+    l->tile_w = parent->tile_w; l->tile_h = parent->tile_h; l->batch = parent->batch;
+    l->use_graph = false;   // every launch has a different camera mix
+    return NGS_OK;
+}
 
 extern "C" {
 

@@ -294,6 +294,10 @@ void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool pe
                       const int *err, unsigned long long *work64, cudaStream_t st);
 int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch);
 
+// serving lanes: contexts sharing a parent's resident scene
+ngs_status lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pair_capacity,
+                       ngs_ctx **out);
+
 inline size_t rec_bytes(int attr_dtype) {
     return attr_dtype == NGS_F32 ? sizeof(Rec32) : sizeof(Rec16);
 }

@@ -222,3 +222,56 @@ class Renderer:
                                   x.numel(), C.c_void_p(total.data_ptr()), _stream_ptr(stream)),
               "ngs_scan_u32")
         return out, total
+
+
+class Server:
+    """Continuous-batching render service over a Renderer's resident scene."""
+
+    def __init__(self, renderer: Renderer, lanes: int = 2, max_cams: int = 64,
+                 pair_budget: int = 0, pairs_per_pixel: float = 0.0,
+                 lane_record_capacity: int = 0, lane_pair_capacity: int = 0):
+        self.L = renderer.L
+        self.renderer = renderer
+        cfg = _lib.ServerConfig(int(lanes), int(max_cams), int(pair_budget), float(pairs_per_pixel),
+                                int(lane_record_capacity), int(lane_pair_capacity))
+        h = C.c_void_p()
+        _torch().cuda.set_device(renderer.device)
+        check(self.L.ngs_server_start(renderer.h, C.byref(cfg), C.byref(h)), "ngs_server_start")
+        self.h = h
+
+    def submit(self, cam, image) -> int:
+        t = C.c_uint64()
+        check(self.L.ngs_server_submit(self.h, C.byref(camera_struct(cam)),
+                                       C.c_void_p(image.data_ptr()), C.byref(t)),
+              "ngs_server_submit")
+        return t.value
+
+    def submit_struct(self, cam_struct, image_ptr: int) -> int:
+        t = C.c_uint64()
+        check(self.L.ngs_server_submit(self.h, C.byref(cam_struct), C.c_void_p(image_ptr),
+                                       C.byref(t)), "ngs_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        done, lat = C.c_int32(), C.c_double()
+        check(self.L.ngs_server_poll(self.h, ticket, C.byref(done), C.byref(lat)), "ngs_server_poll")
+        return bool(done.value), lat.value
+
+    def wait_all(self, timeout_ms: int = 600_000):
+        check(self.L.ngs_server_wait_all(self.h, int(timeout_ms)), "ngs_server_wait_all")
+
+    def stats(self) -> dict:
+        s = _lib.ServerStats()
+        check(self.L.ngs_server_stats(self.h, C.byref(s)), "ngs_server_stats")
+        return {k: getattr(s, k) for k, _ in _lib.ServerStats._fields_}
+
+    def stop(self):
+        if getattr(self, "h", None):
+            check(self.L.ngs_server_stop(self.h), "ngs_server_stop")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -1,0 +1,48 @@
+"""GPU: the continuous-batching serving loop. A request's image is the same
+bits alone and mixed into batches with other agents' requests, matches the
+oracle, and the loop really batches (fewer launches than requests)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from scenegen import mixed_batch_cameras, walk_cameras
+from tests.gpu_helpers import clear_tau, compare_image
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_serving_alone_equals_mixed(small_floor):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_15186_gb300 import Renderer, Server
+    R = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22, pair_capacity=1 << 24)
+    R.load_scene(small_floor)
+    probe = clear_tau(small_floor, walk_cameras(small_floor, 1, 9, 120, 90, fx=110.0, tau=3.0)[0])
+    others = mixed_batch_cameras(small_floor, 48, seed=33, resolutions=((64, 48), (96, 72), (160, 120)),
+                                 n_walkers=6)
+    S = Server(R, lanes=2, max_cams=8)
+    alone = torch.zeros((3, probe.height, probe.width), device="cuda")
+    S.submit(probe, alone)
+    S.wait_all()
+    imgs = [torch.zeros((3, c.height, c.width), device="cuda") for c in others]
+    mixed = torch.zeros_like(alone)
+    tickets = []
+    for i, (c, im) in enumerate(zip(others, imgs)):
+        tickets.append(S.submit(c, im))
+        if i == 20:
+            tp = S.submit(probe, mixed)
+    S.wait_all()
+    st = S.stats()
+    S.stop()
+    assert st["completed"] == st["submitted"] == len(others) + 2 and st["failed"] == 0
+    assert st["launches"] < st["submitted"]            # requests were batched together
+    assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+    assert torch.equal(alone, mixed)
+    # every served image equals the same camera rendered alone by the renderer
+    for c, im in list(zip(others, imgs))[::7]:
+        ref = R.render([c])[0]
+        assert torch.equal(ref, im)
+    compare_image(alone.cpu().numpy(), O.render(small_floor, probe))
+    R.close()
