@@ -166,6 +166,13 @@ NGS_API ngs_status ngs_render(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_ca
 NGS_API ngs_status ngs_render_host(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                                    float *const *h_images, void *stream);
 
+/* Failure-detection self-test: launches one device-side wait on a status
+ * word that nothing will ever publish. The wait is bounded (about 2^20 polls,
+ * well under a second): it gives up, latches NGS_ERR_DEVICE_TIMEOUT, and the
+ * kernel returns. Synchronises and returns that status; the context stays
+ * usable. */
+NGS_API ngs_status ngs_selftest_wait_timeout(ngs_ctx *ctx, void *stream);
+
 /* Waits for the stream and returns (then clears) any latched device error. */
 NGS_API ngs_status ngs_synchronize(ngs_ctx *ctx, void *stream);
 

@@ -22,7 +22,7 @@ EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_l
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
            "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune", "ngs_server_start",
            "ngs_server_submit", "ngs_server_poll", "ngs_server_wait_all", "ngs_server_stats",
-           "ngs_server_stop"]
+           "ngs_server_stop", "ngs_selftest_wait_timeout"]
 
 
 class NgsError(RuntimeError):
@@ -141,6 +141,8 @@ def load(build_if_missing: bool = True):
     L.ngs_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
     L.ngs_server_stop.restype = i32
     L.ngs_server_stop.argtypes = [vp]
+    L.ngs_selftest_wait_timeout.restype = i32
+    L.ngs_selftest_wait_timeout.argtypes = [vp, vp]
     L.ngs_scan_u32.restype = i32
     L.ngs_scan_u32.argtypes = [vp, vp, vp, i64, vp, vp]
     _lib = L

@@ -144,6 +144,13 @@ __global__ void k_offsets_to_i64(const uint32_t *in, int64_t *out, int n) {
     if (i <= n) out[i] = in[i];
 }
 
+// One look-back whose predecessor never publishes in this epoch: the bounded
+// wait gives up and latches kErrTimeout (failure-detection self-test).
+__global__ void k_wait_probe(const uint64_t *status, const uint32_t *epoch_ptr, int *err) {
+    uint32_t prev = 0;
+    look_back(status, 1, 1, *epoch_ptr + kEpochStride - 1, &prev, err);
+}
+
 __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
     if (threadIdx.x < 3) stats[threadIdx.x] = counters[threadIdx.x];
 }
@@ -753,6 +760,7 @@ NGS_API ngs_status ngs_create(const ngs_config *cfg, ngs_ctx **out) {
     cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, c.device);
     sort_init_attributes();
     cutpre_init_attributes();
+    composite_init_attributes();
     x->grid_cut = 4 * x->num_sms;
     x->grid_pre = 4 * x->num_sms;
     x->grid_sort32 = 2 * x->num_sms;
@@ -907,6 +915,21 @@ NGS_API ngs_status ngs_render(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams
                               float *const *d_images, void *stream) {
     if (c) cudaSetDevice(c->device);
     return render_common(c, cams, n_cams, d_images, (cudaStream_t)stream);
+}
+
+NGS_API ngs_status ngs_selftest_wait_timeout(ngs_ctx *c, void *stream) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (!c->loaded && !c->work_ready) c->scene.n = 1;
+    ngs_status s = ensure_work(c);
+    if (s != NGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // a fresh epoch value: no status word carries it
+    if ((s = epoch_guard(c, st, kEpochStride)) != NGS_OK) return s;
+    k_bump_epoch<<<1, 1, 0, st>>>(c->w.epoch, kEpochStride);
+    k_wait_probe<<<1, 1, 0, st>>>(c->w.status, c->w.epoch, c->w.err);
+    CK(cudaGetLastError());
+    return ngs_synchronize(c, stream);
 }
 
 NGS_API ngs_status ngs_synchronize(ngs_ctx *c, void *stream) {

@@ -4,17 +4,22 @@
 // One CTA renders one tile (TW x TH threads, one pixel each). The tile's
 // Gaussians, in (depth, node id) order, are staged in shared memory BATCH
 // records at a time (one cooperative gather of 48 B (float32) or 32 B
-// (float16 colour) records); every thread then walks the batch:
-//   q = A dx^2 + B dx dy + C dy^2 + L      (log2 of o * Gaussian falloff)
+// (float16 colour) records), and for every record and tile row the falloff
+// exponent is rewritten as a quadratic in the pixel's column offset lx within
+// its 16-pixel column block, so that per pixel it costs two fused
+// multiply-adds; every thread then walks the batch:
+//   q = (A lx + a1) lx + a0 = A dx^2 + B dx dy + C dy^2 + L
+//                                          (log2 of o * Gaussian falloff)
 //   skip if q < log2(1/255)                (alpha < 1/255)
 //   alpha = min(0.99, 2^q)
 //   stop if T (1 - alpha) < 1e-4           (this Gaussian is not blended)
 //   C += alpha T c;  T *= 1 - alpha
 // and the CTA leaves its list as soon as a block-wide ballot
 // (__syncthreads_count) finds every pixel finished. Every floating-point step
-// is an explicitly rounded intrinsic, so a pixel's value depends only on its
-// own Gaussian sequence: the same bits for any tile shape, batch size, camera
-// batch or launch form.
+// is an explicitly rounded operation whose inputs depend only on the pixel and
+// the Gaussian (the column block is fixed by the pixel, not by the tile), so a
+// pixel's value depends only on its own Gaussian sequence: the same bits for any
+// tile shape, batch size, camera batch or launch form.
 //
 // Launch forms: one CTA per tile (grid = tiles), or persistent CTAs that take
 // tiles from an atomic ticket (batched renders, where one launch covers the
@@ -51,6 +56,12 @@ __device__ __forceinline__ float exponent(const R &r, float fpx, float fpy) {
                      __fmaf_rn(r.a.w, __fmul_rn(dx, dy), __fmaf_rn(r.b.x, __fmul_rn(dy, dy), r.b.y)));
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <typename R, int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW *TH)
 k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
@@ -58,7 +69,12 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
             unsigned long long *work64) {
     constexpr int NT = TW * TH;
-    __shared__ R s_rec[BATCH];
+    // dynamic shared memory: BATCH records, then per (record, tile row) the
+    // exponent as a quadratic in the pixel's column offset lx within its
+    // 16-pixel column block: q = (A lx + a1) lx + a0, stored (a1, a0, A, 0)
+    extern __shared__ float4 smem_dyn[];
+    R *s_rec = reinterpret_cast<R *>(smem_dyn);
+    float4 *s_coef = smem_dyn + BATCH * (sizeof(R) / sizeof(float4));
     __shared__ uint32_t s_tile;
     __shared__ unsigned long long s_evals;
     __shared__ uint32_t s_staged;
@@ -81,9 +97,14 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         const DevCamera &cam = cams[lo];
         const uint32_t local = tile - cam.tile_base;
         const int tx = (int)(local % (uint32_t)cam.tiles_x), ty = (int)(local / (uint32_t)cam.tiles_x);
-        const int px = tx * TW + lx, py = ty * TH + ly;
+        const int x0 = tx * TW, y0 = ty * TH;
+        const int px = x0 + lx, py = y0 + ly;
         const bool inside = px < cam.width && py < cam.height;
-        const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        // column reference: the centre of the first pixel of px's 16-pixel block
+        // (the same for every tile shape, so a pixel's arithmetic never depends
+        // on how the image is tiled)
+        const float xref = (float)(x0 & ~15) + 0.5f;
+        const float lxf = (float)(px & 15);
         const uint2 rg = ranges[tile];
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
@@ -99,6 +120,19 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             }
             if (work64 && tid == 0) s_staged += n;
             __syncthreads();
+            for (int e = tid; e < n4 * TH; e += NT) {
+                const int j = e / TH, r = e - j * TH;
+                const R &rr = s_rec[j];
+                const float A = rr.a.z, B = rr.a.w, C = rr.b.x, L = rr.b.y;
+                const float dxt = __fsub_rn(xref, rr.a.x);
+                const float dy = __fsub_rn((float)(y0 + r) + 0.5f, rr.a.y);
+                const float bdy = __fmul_rn(B, dy);
+                const float a1 = __fmaf_rn(__fadd_rn(A, A), dxt, bdy);
+                const float a0 = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt,
+                                           __fmaf_rn(C, __fmul_rn(dy, dy), L));
+                s_coef[j * TH + r] = make_float4(a1, a0, A, 0.0f);
+            }
+            __syncthreads();
             if (!done) {
                 int j = 0;
                 for (; j < n4; j += 4) {
@@ -106,12 +140,15 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     // then blend in list order
                     float q[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) q[u] = exponent(s_rec[j + u], fpx, fpy);
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 c = s_coef[(j + u) * TH + ly];
+                        q[u] = __fmaf_rn(__fmaf_rn(c.z, lxf, c.x), lxf, c.y);
+                    }
                     int u = 0;
 #pragma unroll
                     for (; u < 4; ++u) {
                         if (q[u] < kLog2AlphaMin) continue;
-                        const float alpha = fminf(kAlphaMax, exp2f(q[u]));
+                        const float alpha = fminf(kAlphaMax, ex2_approx(q[u]));
                         const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
                         if (test_T < kTMin) { done = true; break; }
                         float gr, gg, gb;
@@ -148,6 +185,29 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
     }
 }
 
+template <typename R, int TW, int TH, int BATCH>
+constexpr size_t comp_smem() {
+    return (size_t)BATCH * sizeof(R) + (size_t)BATCH * TH * sizeof(float4);
+}
+
+template <typename R, int TW, int TH, int BATCH>
+static void set_attr() {
+    cudaFuncSetAttribute(k_composite<R, TW, TH, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)comp_smem<R, TW, TH, BATCH>());
+}
+
+template <typename R>
+static void set_attr_r() {
+    set_attr<R, 8, 8, 64>(); set_attr<R, 8, 8, 128>(); set_attr<R, 8, 8, 256>();
+    set_attr<R, 16, 8, 64>(); set_attr<R, 16, 8, 128>(); set_attr<R, 16, 8, 256>();
+    set_attr<R, 16, 16, 64>(); set_attr<R, 16, 16, 128>(); set_attr<R, 16, 16, 256>();
+}
+
+void composite_init_attributes() {
+    set_attr_r<Rec32>();
+    set_attr_r<Rec16>();
+}
+
 template <typename R, int TW, int TH>
 static void launch_b(int batch, const DevCamera *cams, int n_cams, uint32_t n_tiles,
                      const uint2 *ranges, const uint32_t *pval, const void *rec, uint32_t *ticket,
@@ -156,15 +216,15 @@ static void launch_b(int batch, const DevCamera *cams, int n_cams, uint32_t n_ti
     const R *r = (const R *)rec;
     switch (batch) {
     case 64:
-        k_composite<R, TW, TH, 64><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
+        k_composite<R, TW, TH, 64><<<grid, TW * TH, comp_smem<R, TW, TH, 64>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
                                                              r, ticket, persistent, err, work64);
         break;
     case 256:
-        k_composite<R, TW, TH, 256><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
+        k_composite<R, TW, TH, 256><<<grid, TW * TH, comp_smem<R, TW, TH, 256>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
                                                               r, ticket, persistent, err, work64);
         break;
     default:
-        k_composite<R, TW, TH, 128><<<grid, TW * TH, 0, st>>>(cams, n_cams, n_tiles, ranges, pval,
+        k_composite<R, TW, TH, 128><<<grid, TW * TH, comp_smem<R, TW, TH, 128>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
                                                               r, ticket, persistent, err, work64);
         break;
     }
@@ -201,7 +261,8 @@ void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool pe
 template <typename R, int TW, int TH, int BATCH>
 static int occ() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_composite<R, TW, TH, BATCH>, TW * TH, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_composite<R, TW, TH, BATCH>, TW * TH,
+                                                  comp_smem<R, TW, TH, BATCH>());
     return n;
 }
 

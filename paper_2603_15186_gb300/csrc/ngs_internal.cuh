@@ -293,6 +293,7 @@ void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool pe
                       const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
                       const int *err, unsigned long long *work64, cudaStream_t st);
 int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch);
+void composite_init_attributes();
 
 // serving lanes: contexts sharing a parent's resident scene
 ngs_status lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pair_capacity,

@@ -244,6 +244,24 @@ def test_capacity_error_is_reported_and_context_survives(small_floor):
     r2.close()
 
 
+def test_bounded_wait_times_out_and_context_survives(small_floor):
+    """A device-side wait that can never be satisfied gives up by itself and
+    reports NGS_ERR_DEVICE_TIMEOUT; no trap, no hang, and the same context then
+    renders correctly."""
+    import ctypes as C
+    import time
+    from paper_2603_15186_gb300 import Renderer
+    r = Renderer(device=0, cut_capacity=1 << 20, record_capacity=1 << 20, pair_capacity=1 << 22)
+    r.load_scene(small_floor)
+    t = time.time()
+    st = r.L.ngs_selftest_wait_timeout(r.h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 6  # NGS_ERR_DEVICE_TIMEOUT
+    assert time.time() - t < 30
+    cam = walk_cameras(small_floor, 1, 5, 96, 72, fx=90.0, tau=0.0)[0]
+    compare_image(r.render([cam])[0].cpu().numpy(), O.render(small_floor, cam))
+    r.close()
+
+
 def test_invalid_hierarchy_rejected(R, box10k):
     from paper_2603_15186_gb300 import NgsError
     import copy
