@@ -115,7 +115,9 @@ typedef struct {
  * to the host between stages, no graph. Both compute identical pixels. */
 enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
-       NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6 };
+       NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7 };
+/* NGS_OPT_BLOCK_CULL (default 1): skip, per camera, node blocks that provably
+ * hold no visible Gaussian; 0 tests every node (same images, slower). */
 
 typedef struct {
     int64_t cut_total;       /* selected nodes over all cameras of the last render */

@@ -12,6 +12,7 @@ NGS_F32, NGS_F16, NGS_BF16 = 0, 1, 2
 NGS_MODE_BATCHED, NGS_MODE_PLAIN = 0, 1
 NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H, NGS_OPT_BATCH, NGS_OPT_GRAPH = 1, 2, 3, 4, 5
 NGS_OPT_STAGE_TIMING = 6
+NGS_OPT_BLOCK_CULL = 7
 STAGES = ["cut_preprocess", "gather_keys", "depth_hist", "depth_pass0", "depth_pass1", "depth_pass2",
           "depth_pass3", "pair_offsets", "duplicate", "tile_hist", "tile_pass0", "tile_pass1",
           "tile_pass2", "ranges", "composite"]

@@ -66,6 +66,7 @@ struct ngs_ctx {
     int mode = NGS_MODE_BATCHED;
     int tile_w = 16, tile_h = 16, batch = 128;
     bool use_graph = true;
+    bool block_cull = true;
     SceneDev scene;
     bool loaded = false;
     bool owns_scene = true;           // false for serving lanes sharing a scene
@@ -175,6 +176,7 @@ void free_scene(ngs_ctx *c) {
     SceneDev &s = c->scene;
     if (c->owns_scene) {
         dfree(s.box_lo); dfree(s.box_hi); dfree(s.pos4); dfree(s.quat); dfree(s.sop); dfree(s.sh);
+        dfree(s.blk_lo); dfree(s.blk_hi);
     }
     c->scene = SceneDev();
     c->loaded = false;
@@ -372,7 +374,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     uint32_t eo = 0;
     launch_cutpre(c->scene, cams, nc, c->scene.n, w.rec, w.dkey[1], w.rect, w.vis_count,
                   w.counters + CNT_CUT, w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->tile_w, c->tile_h,
-                  c->grid_pre, st);
+                  c->block_cull ? 1 : 0, c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
     launch_gather_keys(w.vis_count, nc, c->scene.n, w.dkey[1], w.dkey[0], w.didx[0], w.counters,
                        w.rec_cap, w.err, c->num_sms * 2, st);
@@ -482,7 +484,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         const int64_t nblk = (c->scene.n + cutpre_partition_nodes() - 1) / cutpre_partition_nodes();
         launch_cutpre(c->scene, cams, 1, c->scene.n, w.rec, w.dkey[1], w.rect, w.vis_count,
                       w.counters + CNT_CUT, w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->tile_w, c->tile_h,
-                      (int)nblk, st);
+                      c->block_cull ? 1 : 0, (int)nblk, st);
         mark(c, ci, MK_CUT, st);
         uint32_t n_cut = 0, n_vis = 0, n_pairs = 0;
         ngs_status s = read_u32(w.vis_count, &n_vis, st);
@@ -709,6 +711,7 @@ ngs_status ngs::lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pa
     l->scene_version = parent->scene_version;
     l->tile_w = parent->tile_w; l->tile_h = parent->tile_h; l->batch = parent->batch;
     l->use_graph = false;   // every launch has a different camera mix
+    l->block_cull = parent->block_cull;
     return NGS_OK;
 }
 
@@ -816,6 +819,10 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         c->timing = v != 0;
         drop_graph(c);
         return NGS_OK;
+    case NGS_OPT_BLOCK_CULL:
+        c->block_cull = v != 0;
+        drop_graph(c);
+        return NGS_OK;
     }
     return NGS_ERR_INVALID_ARG;
 }
@@ -861,10 +868,42 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *c, const ngs_gaussians *g, const ngs_
         p4[i] = make_float4(g->pos[3 * i], g->pos[3 * i + 1], g->pos[3 * i + 2], ff);
         q[i] = make_float4(g->quat[4 * i], g->quat[4 * i + 1], g->quat[4 * i + 2], g->quat[4 * i + 3]);
     }
+    // per-block bounds for the block-level cull of the fused cut + preprocess
+    const int64_t bs = cutpre_partition_nodes();
+    const int64_t nb = (n + bs - 1) / bs;
+    std::vector<float4> blo(nb), bhi(nb);
+    for (int64_t b = 0; b < nb; ++b) {
+        float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double smax = 0.0, kmax = 0.0;
+        for (int64_t i = b * bs; i < std::min(n, (b + 1) * bs); ++i) {
+            for (int k = 0; k < 3; ++k) {
+                mn[k] = std::min(mn[k], g->pos[3 * i + k]);
+                mx[k] = std::max(mx[k], g->pos[3 * i + k]);
+            }
+            double ls[3], o;
+            for (int k = 0; k < 3; ++k) {
+                if (g->attr_dtype == NGS_F32) ls[k] = ((const float *)g->log_scale)[3 * i + k];
+                else {
+                    const uint16_t h = ((const uint16_t *)g->log_scale)[3 * i + k];
+                    ls[k] = g->attr_dtype == NGS_F16 ? half_to_float(h) : bf16_to_float(h);
+                }
+            }
+            if (g->attr_dtype == NGS_F32) o = ((const float *)g->opacity)[i];
+            else {
+                const uint16_t h = ((const uint16_t *)g->opacity)[i];
+                o = g->attr_dtype == NGS_F16 ? half_to_float(h) : bf16_to_float(h);
+            }
+            smax = std::max(smax, std::exp(std::max(ls[0], std::max(ls[1], ls[2]))));
+            if (255.0 * o >= 1.0) kmax = std::max(kmax, 2.0 * std::log(255.0 * o));
+        }
+        blo[b] = make_float4(mn[0], mn[1], mn[2], (float)(smax * (1.0 + 1e-5)));
+        bhi[b] = make_float4(mx[0], mx[1], mx[2], (float)(kmax * (1.0 + 1e-5) + 1e-6));
+    }
     SceneDev &d = c->scene;
     ngs_status st = NGS_OK;
     auto A = [&](ngs_status x) { if (st == NGS_OK) st = x; };
     A(dalloc(&d.box_lo, n)); A(dalloc(&d.box_hi, n)); A(dalloc(&d.pos4, n)); A(dalloc(&d.quat, n));
+    A(dalloc(&d.blk_lo, nb)); A(dalloc(&d.blk_hi, nb));
     A(dalloc((unsigned char **)&d.sop, (size_t)n * 4 * esz));
     A(dalloc((unsigned char **)&d.sh, (size_t)n * 48 * esz));
     if (st != NGS_OK) {
@@ -877,6 +916,9 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *c, const ngs_gaussians *g, const ngs_
     CK(cudaMemcpy(d.quat, q.data(), n * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.sop, sop.data(), sop.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.sh, g->sh, (size_t)n * 48 * esz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.blk_lo, blo.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.blk_hi, bhi.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
+    d.nblk = nb;
     d.n = n;
     d.attr_dtype = g->attr_dtype;
     c->loaded = true;

@@ -183,6 +183,71 @@ __device__ __forceinline__ bool precull(const SceneDev &sc, const DevCamera &cam
     return true;
 }
 
+// Block-level form of precull: true only if no Gaussian whose mean lies in the
+// box lo.xyz..hi.xyz, with scales <= lo.w and 2 ln(255 o) <= hi.w, can pass
+// precull for this camera. Depth and the normalised image coordinate
+// r = t.x / t.z (linear-fractional, so extreme at box corners when t.z > 0)
+// are bounded over the 8 corners; the support half-width is bounded with the
+// smallest depth and the largest |T0|^2 = (fx / z)^2 |W0 - r W2|^2 over the r
+// range (convex in r); every bound carries slack well above float32 error.
+__device__ __forceinline__ bool block_culled(const float4 lo, const float4 hi,
+                                             const DevCamera &cam, int tile_w, int tile_h) {
+    float tzmin = INFINITY, tzmax = -INFINITY, dmax = 0.0f;
+    float t[8][3];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float dx = ((k & 1) ? hi.x : lo.x) - cam.pos[0];
+        const float dy = ((k & 2) ? hi.y : lo.y) - cam.pos[1];
+        const float dz = ((k & 4) ? hi.z : lo.z) - cam.pos[2];
+        t[k][0] = cam.R[0] * dx + cam.R[1] * dy + cam.R[2] * dz;
+        t[k][1] = cam.R[3] * dx + cam.R[4] * dy + cam.R[5] * dz;
+        t[k][2] = cam.R[6] * dx + cam.R[7] * dy + cam.R[8] * dz;
+        tzmin = fminf(tzmin, t[k][2]);
+        tzmax = fmaxf(tzmax, t[k][2]);
+        dmax = fmaxf(dmax, fabsf(dx) + fabsf(dy) + fabsf(dz));
+    }
+    const float eps = 4e-6f * dmax + 4e-6f;
+    if (tzmax + eps < kNearZ) return true;           // all behind the near plane
+    if (tzmin - eps <= 2.0f * kNearZ) return false;  // precull keeps these unconditionally
+    float rx0 = INFINITY, rx1 = -INFINITY, ry0 = INFINITY, ry1 = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float iz = 1.0f / t[k][2];
+        rx0 = fminf(rx0, t[k][0] * iz); rx1 = fmaxf(rx1, t[k][0] * iz);
+        ry0 = fminf(ry0, t[k][1] * iz); ry1 = fmaxf(ry1, t[k][1] * iz);
+    }
+    rx0 -= 1e-5f * (fabsf(rx0) + 1.0f); rx1 += 1e-5f * (fabsf(rx1) + 1.0f);
+    ry0 -= 1e-5f * (fabsf(ry0) + 1.0f); ry1 += 1e-5f * (fabsf(ry1) + 1.0f);
+    const float sK = sqrtf(fmaxf(hi.w, 0.0f)), sig = lo.w;
+    const float izmax = 1.0f / (tzmin - eps);
+    const float n2 = cam.R[6] * cam.R[6] + cam.R[7] * cam.R[7] + cam.R[8] * cam.R[8];
+    {
+        const float n0 = cam.R[0] * cam.R[0] + cam.R[1] * cam.R[1] + cam.R[2] * cam.R[2];
+        const float d02 = cam.R[0] * cam.R[6] + cam.R[1] * cam.R[7] + cam.R[2] * cam.R[8];
+        const float q = fmaxf(n0 - 2.0f * rx0 * d02 + rx0 * rx0 * n2,
+                              n0 - 2.0f * rx1 * d02 + rx1 * rx1 * n2);
+        const float H = (sK * sig * cam.fx * izmax * sqrtf(fmaxf(q, 0.0f)) + sqrtf(kBlur) * sK) *
+                            1.001f + kRectMargin + 0.05f;
+        const float umin = cam.fx * rx0 + cam.cx, umax = cam.fx * rx1 + cam.cx;
+        const float sl = 1e-4f * (fmaxf(fabsf(umin), fabsf(umax)) + H) + 0.05f;
+        if (umax + H + sl < 0.0f) return true;
+        if (umin - H - sl >= (float)(cam.tiles_x * tile_w)) return true;
+    }
+    {
+        const float n1 = cam.R[3] * cam.R[3] + cam.R[4] * cam.R[4] + cam.R[5] * cam.R[5];
+        const float d12 = cam.R[3] * cam.R[6] + cam.R[4] * cam.R[7] + cam.R[5] * cam.R[8];
+        const float q = fmaxf(n1 - 2.0f * ry0 * d12 + ry0 * ry0 * n2,
+                              n1 - 2.0f * ry1 * d12 + ry1 * ry1 * n2);
+        const float H = (sK * sig * cam.fy * izmax * sqrtf(fmaxf(q, 0.0f)) + sqrtf(kBlur) * sK) *
+                            1.001f + kRectMargin + 0.05f;
+        const float vmin = cam.fy * ry0 + cam.cy, vmax = cam.fy * ry1 + cam.cy;
+        const float sl = 1e-4f * (fmaxf(fabsf(vmin), fabsf(vmax)) + H) + 0.05f;
+        if (vmax + H + sl < 0.0f) return true;
+        if (vmin - H - sl >= (float)(cam.tiles_y * tile_h)) return true;
+    }
+    return false;
+}
+
 // Full preprocess of a Gaussian that passed precull (phase B); returns whether
 // it is visible (in front of the near plane and touching at least one tile).
 template <typename A>
@@ -308,7 +373,7 @@ struct CutPreSmem {
     uint32_t vis[kPrePart];       // visible flag, then (rank | 1 << 31)
     uint32_t cnt[kPreItems * 8];
     uint32_t wsum[kPreThreads / 32];
-    uint32_t part, excl, ncand, sel;
+    uint32_t part, excl, ncand, sel, skip;
 };
 
 template <typename A, typename R>
@@ -317,7 +382,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
          R *__restrict__ rec, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
          uint32_t *__restrict__ vis_count, uint32_t *cut_count, uint32_t *ticket,
          uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, int tile_w,
-         int tile_h) {
+         int tile_h, int use_block_cull) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CutPreSmem<R> &S = *reinterpret_cast<CutPreSmem<R> *>(smem_raw);
     if (*err) return;
@@ -328,8 +393,15 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
     const uint32_t lt = lanemask_lt();
     for (;;) {
         if (tid == 0) {
-            S.part = atomicAdd(ticket, 1u);
+            const uint32_t t = atomicAdd(ticket, 1u);
+            S.part = t;
             S.sel = 0;
+            S.skip = 0;
+            if (use_block_cull && (int64_t)t < nparts) {
+                const int64_t bb = (int64_t)t / n_cams;
+                S.skip = block_culled(sc.blk_lo[bb], sc.blk_hi[bb], cams[(int)((int64_t)t - bb * n_cams)],
+                                      tile_w, tile_h) ? 1u : 0u;
+            }
         }
         __syncthreads();
         const int64_t part = S.part;
@@ -337,6 +409,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
         const int64_t b = part / n_cams;
         const int c = (int)(part - b * n_cams);
         const DevCamera &cam = cams[c];
+        const bool skip = S.skip != 0;
         // phase A: cut rule and conservative cull; survivors compacted into
         // S.cand in node order
         uint32_t bal[kPreItems];
@@ -344,7 +417,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k) {
             const int64_t node = b * kPrePart + k * kPreThreads + tid;
-            const bool sel = node < sc.n &&
+            const bool sel = !skip && node < sc.n &&
                              cut_selects(sc.box_lo, sc.box_hi, node, cam.pos[0], cam.pos[1],
                                          cam.pos[2], cam.fx, cam.tau);
             const bool cand = sel && precull<A>(sc, cam, (uint32_t)node, tile_w, tile_h);
@@ -491,23 +564,23 @@ __global__ void k_gather_keys(const uint32_t *__restrict__ vis_count, int n_cams
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_t region,
                    void *rec, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
                    uint32_t *cut_count, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
-                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
-                   cudaStream_t st) {
+                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int use_block_cull,
+                   int grid, cudaStream_t st) {
     switch (sc.attr_dtype) {
     case NGS_F16:
         k_cutpre<__half, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
-            ticket, status, epoch, epoch_off, err, tile_w, tile_h);
+            ticket, status, epoch, epoch_off, err, tile_w, tile_h, use_block_cull);
         break;
     case NGS_BF16:
         k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
-            ticket, status, epoch, epoch_off, err, tile_w, tile_h);
+            ticket, status, epoch, epoch_off, err, tile_w, tile_h, use_block_cull);
         break;
     default:
         k_cutpre<float, Rec32><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
             sc, cams, n_cams, region, (Rec32 *)rec, dkey_sparse, rect, vis_count, cut_count,
-            ticket, status, epoch, epoch_off, err, tile_w, tile_h);
+            ticket, status, epoch, epoch_off, err, tile_w, tile_h, use_block_cull);
         break;
     }
 }

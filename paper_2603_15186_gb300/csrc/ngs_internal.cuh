@@ -83,6 +83,10 @@ struct SceneDev {
     float4 *box_lo = nullptr, *box_hi = nullptr, *pos4 = nullptr, *quat = nullptr;
     void *sop = nullptr;     // [n][4] of attr type
     void *sh = nullptr;      // [n][48] of attr type
+    // per block of cutpre_partition_nodes() consecutive nodes: box of the means
+    // (xyz) with the largest scale (lo.w) and the largest 2 ln(255 o) (hi.w)
+    float4 *blk_lo = nullptr, *blk_hi = nullptr;
+    int64_t nblk = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -228,8 +232,8 @@ int cut_partition_nodes();
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_t region,
                    void *rec, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
                    uint32_t *cut_count, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
-                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int grid,
-                   cudaStream_t st);
+                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int use_block_cull,
+                   int grid, cudaStream_t st);
 int cutpre_partition_nodes();
 void cutpre_init_attributes();
 // dense depth keys and sparse record indices for the sort; counters[CNT_VIS]

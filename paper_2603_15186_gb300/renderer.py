@@ -91,6 +91,9 @@ class Renderer:
     def set_graph(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_GRAPH, 1 if on else 0), "graph")
 
+    def set_block_cull(self, on: bool):
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_BLOCK_CULL, 1 if on else 0), "block cull")
+
     def set_stage_timing(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_STAGE_TIMING, 1 if on else 0),
               "stage timing")

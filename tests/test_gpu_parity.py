@@ -183,6 +183,24 @@ def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
         assert np.array_equal(alone, base[i])
 
 
+def test_block_cull_is_conservative(R, small_floor, box10k):
+    """Skipping node blocks that provably hold no visible Gaussian changes
+    nothing: same visible Gaussians, same pairs, same image bits."""
+    for scene, cams in [(small_floor, _floor_cams(small_floor)),
+                        (box10k, [camera_c0(0.0), look_camera((-3.0, 2.0, 1.5), 0.3, 64, 48, fx=60.0)])]:
+        R.load_scene(scene)
+        outs, work = [], []
+        for on in (True, False):
+            R.set_block_cull(on)
+            outs.append([t.cpu().numpy() for t in R.render(cams)])
+            st = R.stats()
+            work.append((st["visible_total"], st["pair_total"]))
+        R.set_block_cull(True)
+        assert work[0] == work[1]
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
+
+
 def test_autotune_keeps_pixels(R, small_floor):
     R.load_scene(small_floor)
     cams = _floor_cams(small_floor)
