@@ -56,6 +56,25 @@ __device__ __forceinline__ float exponent(const R &r, float fpx, float fpy) {
                      __fmaf_rn(r.a.w, __fmul_rn(dx, dy), __fmaf_rn(r.b.x, __fmul_rn(dy, dy), r.b.y)));
 }
 
+// Largest q = A dx^2 + B dx dy + C dy^2 + L (A, C < 0) over the rectangle
+// [ex0, ex1] x [ey0, ey1] of offsets from the Gaussian centre: L when the
+// centre is inside, else the best of the four edges, each a 1D concave
+// quadratic maximised in closed form and clamped to the edge.
+__device__ __forceinline__ float rect_qmax(float A, float B, float C, float L, float ex0,
+                                           float ex1, float ey0, float ey1) {
+    if (ex0 <= 0.0f && 0.0f <= ex1 && ey0 <= 0.0f && 0.0f <= ey1) return L;
+    const float sy = -B / (2.0f * C), sx = -B / (2.0f * A);
+    float y = fminf(fmaxf(sy * ex0, ey0), ey1);
+    float best = A * ex0 * ex0 + B * ex0 * y + C * y * y;
+    y = fminf(fmaxf(sy * ex1, ey0), ey1);
+    best = fmaxf(best, A * ex1 * ex1 + B * ex1 * y + C * y * y);
+    float x = fminf(fmaxf(sx * ey0, ex0), ex1);
+    best = fmaxf(best, A * x * x + B * x * ey0 + C * ey0 * ey0);
+    x = fminf(fmaxf(sx * ey1, ex0), ex1);
+    best = fmaxf(best, A * x * x + B * x * ey1 + C * ey1 * ey1);
+    return best + L;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -69,6 +88,8 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
             unsigned long long *work64) {
     constexpr int NT = TW * TH;
+    constexpr int kPer = (BATCH + NT - 1) / NT;   // records gathered per thread per round
+    __shared__ uint32_t s_wsum[(NT + 31) / 32];
     // dynamic shared memory: BATCH records, then per (record, tile row) the
     // exponent as a quadratic in the pixel's column offset lx within its
     // 16-pixel column block: q = (A lx + a1) lx + a0, stored (a1, a0, A, 0)
@@ -104,20 +125,71 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         // (the same for every tile shape, so a pixel's arithmetic never depends
         // on how the image is tiled)
         const float xref = (float)(x0 & ~15) + 0.5f;
+        // the tile's pixel-centre rectangle (whole tile, also where it overhangs)
+        const float tile_x0c = (float)x0 + 0.5f, tile_x1c = (float)(x0 + TW) - 0.5f;
+        const float tile_y0c = (float)y0 + 0.5f, tile_y1c = (float)(y0 + TH) - 0.5f;
         const float lxf = (float)(px & 15);
         const uint2 rg = ranges[tile];
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
         uint32_t evals = 0;
         if (work64 && tid == 0) { s_evals = 0; s_staged = 0; }
+        // round r's records are requested during round r - 1 (software pipeline)
+        R mine[kPer];
+        if (rg.x < rg.y) {
+            const int n0 = (int)min((uint32_t)BATCH, rg.y - rg.x);
+#pragma unroll
+            for (int f = 0; f < kPer; ++f)
+                if (tid * kPer + f < n0) mine[f] = rec[pval[rg.x + tid * kPer + f]];
+        }
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
             if (__syncthreads_count(!done) == 0) break;
             const int n = (int)min((uint32_t)BATCH, rg.y - start);
-            const int n4 = (n + 3) & ~3;
-            for (int j = tid; j < n4; j += NT) {
-                if (j < n) s_rec[j] = rec[pval[start + j]];
-                else set_sentinel(s_rec[j]);   // q = -inf: never contributes
+            // keep, in list order, the records whose support reaches the tile's
+            // pixel-centre rectangle
+            uint32_t keepmask = 0, nkeep = 0;
+#pragma unroll
+            for (int f = 0; f < kPer; ++f) {
+                const int j = tid * kPer + f;
+                if (j < n) {
+                    const float q = rect_qmax(mine[f].a.z, mine[f].a.w, mine[f].b.x, mine[f].b.y,
+                                              tile_x0c - mine[f].a.x, tile_x1c - mine[f].a.x,
+                                              tile_y0c - mine[f].a.y, tile_y1c - mine[f].a.y);
+                    if (q >= kLog2AlphaMin - kTileMarginLog2) {
+                        keepmask |= 1u << f;
+                        ++nkeep;
+                    }
+                }
             }
+            uint32_t incl = nkeep;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((tid & 31) >= o) incl += t;
+            }
+            if ((tid & 31) == 31) s_wsum[tid >> 5] = incl;
+            __syncthreads();
+            uint32_t wb = 0, nk = 0;
+#pragma unroll
+            for (int w = 0; w < (NT + 31) / 32; ++w) {
+                if (w < (tid >> 5)) wb += s_wsum[w];
+                nk += s_wsum[w];
+            }
+            uint32_t pos = wb + incl - nkeep;
+#pragma unroll
+            for (int f = 0; f < kPer; ++f)
+                if ((keepmask >> f) & 1u) s_rec[pos++] = mine[f];
+            {
+                const uint32_t nxt = start + BATCH;
+                if (nxt < rg.y) {
+                    const int nn = (int)min((uint32_t)BATCH, rg.y - nxt);
+#pragma unroll
+                    for (int f = 0; f < kPer; ++f)
+                        if (tid * kPer + f < nn) mine[f] = rec[pval[nxt + tid * kPer + f]];
+                }
+            }
+            const int n4 = ((int)nk + 3) & ~3;
+            for (int j = (int)nk + tid; j < n4; j += NT) set_sentinel(s_rec[j]);   // q = -inf
             if (work64 && tid == 0) s_staged += n;
             __syncthreads();
             for (int e = tid; e < n4 * TH; e += NT) {
@@ -161,7 +233,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     }
                     if (done) { j += u + 1; break; }
                 }
-                evals += (uint32_t)min(j, n);
+                evals += (uint32_t)min(j, (int)nk);
             }
         }
         if (work64) {

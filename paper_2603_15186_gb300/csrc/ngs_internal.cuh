@@ -34,6 +34,10 @@ constexpr float kRectMargin = 1.0f / 64.0f;  // pixels added to the support box
 constexpr float kLog2e = 1.4426950408889634f;
 // log2(1/255): alpha >= 1/255  <=>  log2(alpha) >= -log2(255)
 constexpr float kLog2AlphaMin = -7.9943534368588578f;
+// compositing drops a tile-list record whose largest log2 falloff over the
+// tile's pixel-centre rectangle stays below log2(1/255) - kTileMarginLog2 (a
+// margin far above float32 error, so no pixel that could reach 1/255 is lost)
+constexpr float kTileMarginLog2 = 0.014426950408889634f;
 
 constexpr uint32_t kNodeCullOpacity = 1u;    // pos4.w flag: 255 * opacity < 1
 
