@@ -38,24 +38,6 @@ __device__ __forceinline__ void rec_colour(const Rec16 &r, float &cr, float &cg,
     cb = __low2float(*reinterpret_cast<const __half2 *>(&w));   // high half: support size
 }
 
-__device__ __forceinline__ void set_sentinel(Rec32 &r) {
-    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-    r.b = make_float4(0.f, __int_as_float(0xff800000), 0.f, 0.f);
-    r.c = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-__device__ __forceinline__ void set_sentinel(Rec16 &r) {
-    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-    r.b = make_float4(0.f, __int_as_float(0xff800000), 0.f, 0.f);
-}
-
-// log2 of o times the Gaussian falloff at pixel centre (fpx, fpy)
-template <typename R>
-__device__ __forceinline__ float exponent(const R &r, float fpx, float fpy) {
-    const float dx = __fsub_rn(fpx, r.a.x), dy = __fsub_rn(fpy, r.a.y);
-    return __fmaf_rn(r.a.z, __fmul_rn(dx, dx),
-                     __fmaf_rn(r.a.w, __fmul_rn(dx, dy), __fmaf_rn(r.b.x, __fmul_rn(dy, dy), r.b.y)));
-}
-
 // Largest q = A dx^2 + B dx dy + C dy^2 + L (A, C < 0) over the rectangle
 // [ex0, ex1] x [ey0, ey1] of offsets from the Gaussian centre: L when the
 // centre is inside, else the best of the four edges, each a 1D concave
@@ -81,27 +63,95 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Conservative bounding box of the pixel-centre offsets where a record can
+// still pass the alpha threshold: the ellipse -(A dx^2 + B dx dy + C dy^2) <=
+// kappa, kappa = L - log2(1/255) + kTileMarginLog2, has half-widths
+// sqrt(kappa (-C) / det) and sqrt(kappa (-A) / det), det = A C - B^2 / 4. The
+// box is widened by a relative 2^-10 plus a term that grows with A C / det
+// (the cancellation in det and in the exponent of an elongated footprint) and
+// by 1/64 px; a form that is not negative definite gets an unbounded box.
+// Returned as (xmin, xmax, ymin, ymax) in pixel coordinates.
+__device__ __forceinline__ float4 record_box(float x, float y, float A, float B, float C, float L) {
+    const float kappa = L - (kLog2AlphaMin - kTileMarginLog2);
+    const float ac = A * C;
+    const float det = fmaf(-0.25f * B, B, ac);
+    const float inf = __int_as_float(0x7f800000);
+    if (!(kappa >= 0.0f)) return make_float4(inf, -inf, inf, -inf);   // empty
+    if (!(A < 0.0f) || !(C < 0.0f) || !(det > 0.0f) || !(ac < inf))
+        return make_float4(-inf, inf, -inf, inf);
+    const float grow = 1.0f + 0.0009765625f + 9.5367431640625e-07f * (ac / det);
+    const float s = kappa / det;
+    const float hx = fmaf(sqrtf(s * -C), grow, 0.015625f);
+    const float hy = fmaf(sqrtf(s * -A), grow, 0.015625f);
+    return make_float4(x - hx, x + hx, y - hy, y + hy);
+}
+
+// colour and A of a staged record, each value twice, as register pairs for
+// packed two-pixel arithmetic: (r, r, g, g), (b, b, A, A)
+struct PairRec {
+    float4 rg;
+    float4 bA;
+};
+
 template <typename R, int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW *TH)
+struct CompLayout {
+    static constexpr int BH = 64 / TW;                 // rows of a warp's block
+    static constexpr int NW = TH / BH;                 // warps per tile
+    static constexpr int NT = 32 * NW;                 // threads: two pixels each
+    static constexpr int NRP = TH / 2;                 // row pairs per tile
+    static constexpr int kListStride = BATCH + 4;      // u32 entries per warp list
+    static constexpr size_t rec_off = 0;
+    static constexpr size_t coef_off = rec_off + (size_t)BATCH * sizeof(R);
+    static constexpr size_t pair_off = coef_off + (size_t)(BATCH + 1) * NRP * sizeof(float4);
+    static constexpr size_t box_off = pair_off + (size_t)(BATCH + 1) * sizeof(PairRec);
+    static constexpr size_t list_off = box_off + (size_t)BATCH * sizeof(float4);
+    static constexpr size_t bytes = list_off + (size_t)NW * kListStride * sizeof(uint32_t);
+    static_assert(TW == 8 || TW == 16, "tile width 8 or 16");
+    static_assert(TH % BH == 0, "tile of whole warp blocks");
+    static_assert(BATCH % 4 == 0, "lists padded to groups of four");
+};
+
+__device__ __forceinline__ float finite_or_max(float v) { return fminf(v, 3.402823466e38f); }
+
+template <typename R, int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(CompLayout<R, TW, TH, BATCH>::NT)
 k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
             const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
             unsigned long long *work64) {
-    constexpr int NT = TW * TH;
+    using Lay = CompLayout<R, TW, TH, BATCH>;
+    constexpr int NT = Lay::NT, NRP = Lay::NRP, BH = Lay::BH;
     constexpr int kPer = (BATCH + NT - 1) / NT;   // records gathered per thread per round
-    __shared__ uint32_t s_wsum[(NT + 31) / 32];
-    // dynamic shared memory: BATCH records, then per (record, tile row) the
-    // exponent as a quadratic in the pixel's column offset lx within its
-    // 16-pixel column block: q = (A lx + a1) lx + a0, stored (a1, a0, A, 0)
+    __shared__ uint32_t s_wsum[Lay::NW];
+    // dynamic shared memory, per round: the tile's kept records; per (record,
+    // pair of tile rows r, r + 1) the exponent as a quadratic in the pixel's
+    // column offset lx within its 16-pixel column block, q = (A lx + a1) lx + a0,
+    // stored (a1_r, a1_r+1, a0_r, a0_r+1); the records' PairRec; their reach
+    // boxes; one record list per warp. Index BATCH holds a sentinel record
+    // (q = -inf everywhere).
     extern __shared__ float4 smem_dyn[];
-    R *s_rec = reinterpret_cast<R *>(smem_dyn);
-    float4 *s_coef = smem_dyn + BATCH * (sizeof(R) / sizeof(float4));
+    unsigned char *sm = reinterpret_cast<unsigned char *>(smem_dyn);
+    R *s_rec = reinterpret_cast<R *>(sm + Lay::rec_off);
+    float4 *s_coef = reinterpret_cast<float4 *>(sm + Lay::coef_off);
+    PairRec *s_pair = reinterpret_cast<PairRec *>(sm + Lay::pair_off);
+    float4 *s_box = reinterpret_cast<float4 *>(sm + Lay::box_off);
+    uint32_t *s_list = reinterpret_cast<uint32_t *>(sm + Lay::list_off);
     __shared__ uint32_t s_tile;
-    __shared__ unsigned long long s_evals;
-    __shared__ uint32_t s_staged;
     if (*err) return;
-    const int tid = threadIdx.x;
-    const int lx = tid % TW, ly = tid / TW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // warp -> TW x BH pixel block of the tile; thread -> the pixels (lx, ly)
+    // and (lx, ly + 1)
+    const int lx = lane % TW, by = warp * BH, ly = by + 2 * (lane / TW);
+    const int rp = ly >> 1;
+    uint32_t *my_list = s_list + warp * Lay::kListStride;
+    const float inf = __int_as_float(0x7f800000);
+    if (tid < NRP) s_coef[BATCH * NRP + tid] = make_float4(0.0f, 0.0f, -inf, -inf);
+    if (tid == 0) {
+        s_pair[BATCH].rg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_pair[BATCH].bA = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    const float2 kOne2 = make_float2(1.0f, 1.0f), kMinusOne2 = make_float2(-1.0f, -1.0f);
+    unsigned long long evals = 0, staged = 0;
     uint32_t tile = blockIdx.x;
     for (;;) {
         if (persistent) {
@@ -120,20 +170,22 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         const int tx = (int)(local % (uint32_t)cam.tiles_x), ty = (int)(local / (uint32_t)cam.tiles_x);
         const int x0 = tx * TW, y0 = ty * TH;
         const int px = x0 + lx, py = y0 + ly;
-        const bool inside = px < cam.width && py < cam.height;
+        const bool in0 = px < cam.width && py < cam.height;
+        const bool in1 = px < cam.width && py + 1 < cam.height;
         // column reference: the centre of the first pixel of px's 16-pixel block
         // (the same for every tile shape, so a pixel's arithmetic never depends
         // on how the image is tiled)
         const float xref = (float)(x0 & ~15) + 0.5f;
-        // the tile's pixel-centre rectangle (whole tile, also where it overhangs)
+        // the tile's and the warp block's pixel-centre rectangles (whole tile,
+        // also where it overhangs the image)
         const float tile_x0c = (float)x0 + 0.5f, tile_x1c = (float)(x0 + TW) - 0.5f;
         const float tile_y0c = (float)y0 + 0.5f, tile_y1c = (float)(y0 + TH) - 0.5f;
+        const float blk_y0c = (float)(y0 + by) + 0.5f, blk_y1c = blk_y0c + (float)(BH - 1);
         const float lxf = (float)(px & 15);
+        const float2 lx2 = make_float2(lxf, lxf);
         const uint2 rg = ranges[tile];
-        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-        bool done = !inside;
-        uint32_t evals = 0;
-        if (work64 && tid == 0) { s_evals = 0; s_staged = 0; }
+        float2 T2 = kOne2, cr2 = make_float2(0.0f, 0.0f), cg2 = cr2, cb2 = cr2;
+        bool done0 = !in0, done1 = !in1;
         // round r's records are requested during round r - 1 (software pipeline)
         R mine[kPer];
         if (rg.x < rg.y) {
@@ -143,7 +195,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                 if (tid * kPer + f < n0) mine[f] = rec[pval[rg.x + tid * kPer + f]];
         }
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-            if (__syncthreads_count(!done) == 0) break;
+            if (__syncthreads_count(!(done0 && done1)) == 0) break;
             const int n = (int)min((uint32_t)BATCH, rg.y - start);
             // keep, in list order, the records whose support reaches the tile's
             // pixel-centre rectangle
@@ -165,20 +217,32 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((tid & 31) >= o) incl += t;
+                if (lane >= o) incl += t;
             }
-            if ((tid & 31) == 31) s_wsum[tid >> 5] = incl;
+            if (lane == 31) s_wsum[warp] = incl;
             __syncthreads();
             uint32_t wb = 0, nk = 0;
 #pragma unroll
-            for (int w = 0; w < (NT + 31) / 32; ++w) {
-                if (w < (tid >> 5)) wb += s_wsum[w];
+            for (int w = 0; w < Lay::NW; ++w) {
+                if (w < warp) wb += s_wsum[w];
                 nk += s_wsum[w];
             }
             uint32_t pos = wb + incl - nkeep;
 #pragma unroll
             for (int f = 0; f < kPer; ++f)
-                if ((keepmask >> f) & 1u) s_rec[pos++] = mine[f];
+                if ((keepmask >> f) & 1u) {
+                    const R &m = mine[f];
+                    s_rec[pos] = m;
+                    float gr, gg, gb;
+                    rec_colour(m, gr, gg, gb);
+                    // finite colours: a record blended with weight 0 then leaves
+                    // the sums unchanged
+                    gr = finite_or_max(gr); gg = finite_or_max(gg); gb = finite_or_max(gb);
+                    s_pair[pos].rg = make_float4(gr, gr, gg, gg);
+                    s_pair[pos].bA = make_float4(gb, gb, m.a.z, m.a.z);
+                    s_box[pos] = record_box(m.a.x, m.a.y, m.a.z, m.a.w, m.b.x, m.b.y);
+                    ++pos;
+                }
             {
                 const uint32_t nxt = start + BATCH;
                 if (nxt < rg.y) {
@@ -188,78 +252,115 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                         if (tid * kPer + f < nn) mine[f] = rec[pval[nxt + tid * kPer + f]];
                 }
             }
-            const int n4 = ((int)nk + 3) & ~3;
-            for (int j = (int)nk + tid; j < n4; j += NT) set_sentinel(s_rec[j]);   // q = -inf
-            if (work64 && tid == 0) s_staged += n;
+            if (tid == 0) staged += (unsigned long long)n;
             __syncthreads();
-            for (int e = tid; e < n4 * TH; e += NT) {
-                const int j = e / TH, r = e - j * TH;
+            // each warp lists, in order, the kept records whose reach box meets
+            // its block (skipped records have q < log2(1/255) at all its pixels)
+            const bool warp_live = __any_sync(0xffffffffu, !(done0 && done1));
+            int len = 0;
+            if (warp_live) {
+                for (int c = 0; c < (int)nk; c += 32) {
+                    const int j = c + lane;
+                    bool hit = false;
+                    if (j < (int)nk) {
+                        const float4 b = s_box[j];
+                        hit = b.y >= tile_x0c && b.x <= tile_x1c && b.w >= blk_y0c && b.z <= blk_y1c;
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+                    if (hit) my_list[len + __popc(bal & lanemask_lt())] = (uint32_t)j;
+                    len += __popc(bal);
+                }
+                if (lane < ((4 - (len & 3)) & 3)) my_list[len + lane] = (uint32_t)BATCH;
+            }
+            for (int e = tid; e < (int)nk * NRP; e += NT) {
+                const int j = e / NRP, p = e - j * NRP;
                 const R &rr = s_rec[j];
                 const float A = rr.a.z, B = rr.a.w, C = rr.b.x, L = rr.b.y;
                 const float dxt = __fsub_rn(xref, rr.a.x);
-                const float dy = __fsub_rn((float)(y0 + r) + 0.5f, rr.a.y);
-                const float bdy = __fmul_rn(B, dy);
-                const float a1 = __fmaf_rn(__fadd_rn(A, A), dxt, bdy);
-                const float a0 = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt,
-                                           __fmaf_rn(C, __fmul_rn(dy, dy), L));
-                s_coef[j * TH + r] = make_float4(a1, a0, A, 0.0f);
+                const float axb = __fadd_rn(A, A);
+                float a1[2], a0[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float dy = __fsub_rn((float)(y0 + 2 * p + h) + 0.5f, rr.a.y);
+                    const float bdy = __fmul_rn(B, dy);
+                    a1[h] = __fmaf_rn(axb, dxt, bdy);
+                    a0[h] = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt, __fmaf_rn(C, __fmul_rn(dy, dy), L));
+                }
+                s_coef[j * NRP + p] = make_float4(a1[0], a1[1], a0[0], a0[1]);
             }
             __syncthreads();
-            if (!done) {
-                int j = 0;
-                for (; j < n4; j += 4) {
-                    // the four exponents do not depend on T: evaluate them together,
-                    // then blend in list order
-                    float q[4];
+            if (!(done0 && done1)) {
+                // both pixels in packed (f32x2) arithmetic, every step the same
+                // rounded operation per pixel as a scalar evaluation:
+                //   q = (A lx + a1) lx + a0; alpha = min(0.99, 2^q), 0 if
+                //   q < log2(1/255); T' = T (1 - alpha); a pixel ends (unblended)
+                //   at the record with T' < 1e-4; else C += (alpha T) c, T = T'.
+                // A record that is not blended gets weight 0 and T' = T, exact
+                // no-ops, so there are no per-record branches; a lane leaves
+                // after the group of four in which both its pixels ended.
+                const int len4 = (len + 3) & ~3;
+                for (int i = 0; i < len4; i += 4) {
+                    const uint4 jv = *reinterpret_cast<const uint4 *>(my_list + i);
+                    const uint32_t jj[4] = {jv.x, jv.y, jv.z, jv.w};
+                    float2 q[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float4 c = s_coef[(j + u) * TH + ly];
-                        q[u] = __fmaf_rn(__fmaf_rn(c.z, lxf, c.x), lxf, c.y);
+                        const float4 cf = s_coef[jj[u] * NRP + rp];
+                        const float4 bA = s_pair[jj[u]].bA;
+                        const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
+                        q[u] = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
                     }
-                    int u = 0;
+                    evals += (done0 ? 0u : 4u) + (done1 ? 0u : 4u);
 #pragma unroll
-                    for (; u < 4; ++u) {
-                        if (q[u] < kLog2AlphaMin) continue;
-                        const float alpha = fminf(kAlphaMax, ex2_approx(q[u]));
-                        const float test_T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                        if (test_T < kTMin) { done = true; break; }
-                        float gr, gg, gb;
-                        rec_colour(s_rec[j + u], gr, gg, gb);
-                        const float w = __fmul_rn(alpha, T);
-                        cr = __fmaf_rn(w, gr, cr);
-                        cg = __fmaf_rn(w, gg, cg);
-                        cb = __fmaf_rn(w, gb, cb);
-                        T = test_T;
+                    for (int u = 0; u < 4; ++u) {
+                        float al0 = fminf(kAlphaMax, ex2_approx(q[u].x));
+                        float al1 = fminf(kAlphaMax, ex2_approx(q[u].y));
+                        al0 = q[u].x < kLog2AlphaMin ? 0.0f : al0;
+                        al1 = q[u].y < kLog2AlphaMin ? 0.0f : al1;
+                        const float2 t2 = __fmul2_rn(T2, __ffma2_rn(make_float2(al0, al1), kMinusOne2, kOne2));
+                        done0 = done0 || t2.x < kTMin;
+                        done1 = done1 || t2.y < kTMin;
+                        const float2 w2 = __fmul2_rn(make_float2(done0 ? 0.0f : al0, done1 ? 0.0f : al1), T2);
+                        const PairRec &pr = s_pair[jj[u]];
+                        const float4 c_rg = pr.rg;
+                        const float4 c_b = pr.bA;
+                        cr2 = __ffma2_rn(w2, make_float2(c_rg.x, c_rg.y), cr2);
+                        cg2 = __ffma2_rn(w2, make_float2(c_rg.z, c_rg.w), cg2);
+                        cb2 = __ffma2_rn(w2, make_float2(c_b.x, c_b.y), cb2);
+                        T2.x = done0 ? T2.x : t2.x;
+                        T2.y = done1 ? T2.y : t2.y;
                     }
-                    if (done) { j += u + 1; break; }
+                    if (done0 && done1) break;
                 }
-                evals += (uint32_t)min(j, (int)nk);
             }
         }
-        if (work64) {
-            __syncthreads();
-            atomicAdd(&s_evals, (unsigned long long)evals);
-            __syncthreads();
-            if (tid == 0) {
-                atomicAdd(&work64[0], (unsigned long long)s_staged);
-                atomicAdd(&work64[1], s_evals);
-            }
+        const int64_t plane = (int64_t)cam.width * cam.height;
+        const int64_t p0 = (int64_t)py * cam.width + px;
+        if (in0) {
+            cam.image[p0] = cr2.x;
+            cam.image[plane + p0] = cg2.x;
+            cam.image[2 * plane + p0] = cb2.x;
         }
-        if (inside) {
-            const int64_t plane = (int64_t)cam.width * cam.height;
-            const int64_t p = (int64_t)py * cam.width + px;
-            cam.image[p] = cr;
-            cam.image[plane + p] = cg;
-            cam.image[2 * plane + p] = cb;
+        if (in1) {
+            const int64_t p1 = p0 + cam.width;
+            cam.image[p1] = cr2.y;
+            cam.image[plane + p1] = cg2.y;
+            cam.image[2 * plane + p1] = cb2.y;
         }
         if (!persistent) break;
         __syncthreads();
+    }
+    if (work64) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) evals += __shfl_down_sync(0xffffffffu, evals, o);
+        if (lane == 0 && evals) atomicAdd(&work64[1], evals);
+        if (tid == 0 && staged) atomicAdd(&work64[0], staged);
     }
 }
 
 template <typename R, int TW, int TH, int BATCH>
 constexpr size_t comp_smem() {
-    return (size_t)BATCH * sizeof(R) + (size_t)BATCH * TH * sizeof(float4);
+    return CompLayout<R, TW, TH, BATCH>::bytes;
 }
 
 template <typename R, int TW, int TH, int BATCH>
@@ -288,15 +389,15 @@ static void launch_b(int batch, const DevCamera *cams, int n_cams, uint32_t n_ti
     const R *r = (const R *)rec;
     switch (batch) {
     case 64:
-        k_composite<R, TW, TH, 64><<<grid, TW * TH, comp_smem<R, TW, TH, 64>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
+        k_composite<R, TW, TH, 64><<<grid, (CompLayout<R, TW, TH, 64>::NT), comp_smem<R, TW, TH, 64>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
                                                              r, ticket, persistent, err, work64);
         break;
     case 256:
-        k_composite<R, TW, TH, 256><<<grid, TW * TH, comp_smem<R, TW, TH, 256>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
+        k_composite<R, TW, TH, 256><<<grid, (CompLayout<R, TW, TH, 64>::NT), comp_smem<R, TW, TH, 256>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
                                                               r, ticket, persistent, err, work64);
         break;
     default:
-        k_composite<R, TW, TH, 128><<<grid, TW * TH, comp_smem<R, TW, TH, 128>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
+        k_composite<R, TW, TH, 128><<<grid, (CompLayout<R, TW, TH, 64>::NT), comp_smem<R, TW, TH, 128>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
                                                               r, ticket, persistent, err, work64);
         break;
     }
@@ -333,7 +434,7 @@ void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool pe
 template <typename R, int TW, int TH, int BATCH>
 static int occ() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_composite<R, TW, TH, BATCH>, TW * TH,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_composite<R, TW, TH, BATCH>, CompLayout<R, TW, TH, BATCH>::NT,
                                                   comp_smem<R, TW, TH, BATCH>());
     return n;
 }
