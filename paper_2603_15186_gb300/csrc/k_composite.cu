@@ -184,8 +184,9 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         const float lxf = (float)(px & 15);
         const float2 lx2 = make_float2(lxf, lxf);
         const uint2 rg = ranges[tile];
-        float2 T2 = kOne2, cr2 = make_float2(0.0f, 0.0f), cg2 = cr2, cb2 = cr2;
-        bool done0 = !in0, done1 = !in1;
+        // T = 0 marks a finished pixel (also one outside the image)
+        float2 T2 = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
+        float2 cr2 = make_float2(0.0f, 0.0f), cg2 = cr2, cb2 = cr2;
         // round r's records are requested during round r - 1 (software pipeline)
         R mine[kPer];
         if (rg.x < rg.y) {
@@ -195,7 +196,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                 if (tid * kPer + f < n0) mine[f] = rec[pval[rg.x + tid * kPer + f]];
         }
         for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-            if (__syncthreads_count(!(done0 && done1)) == 0) break;
+            if (__syncthreads_count(T2.x > 0.0f || T2.y > 0.0f) == 0) break;
             const int n = (int)min((uint32_t)BATCH, rg.y - start);
             // keep, in list order, the records whose support reaches the tile's
             // pixel-centre rectangle
@@ -256,7 +257,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             __syncthreads();
             // each warp lists, in order, the kept records whose reach box meets
             // its block (skipped records have q < log2(1/255) at all its pixels)
-            const bool warp_live = __any_sync(0xffffffffu, !(done0 && done1));
+            const bool warp_live = __any_sync(0xffffffffu, T2.x > 0.0f || T2.y > 0.0f);
             int len = 0;
             if (warp_live) {
                 for (int c = 0; c < (int)nk; c += 32) {
@@ -289,15 +290,18 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                 s_coef[j * NRP + p] = make_float4(a1[0], a1[1], a0[0], a0[1]);
             }
             __syncthreads();
-            if (!(done0 && done1)) {
+            if (T2.x > 0.0f || T2.y > 0.0f) {
                 // both pixels in packed (f32x2) arithmetic, every step the same
                 // rounded operation per pixel as a scalar evaluation:
                 //   q = (A lx + a1) lx + a0; alpha = min(0.99, 2^q), 0 if
                 //   q < log2(1/255); T' = T (1 - alpha); a pixel ends (unblended)
                 //   at the record with T' < 1e-4; else C += (alpha T) c, T = T'.
-                // A record that is not blended gets weight 0 and T' = T, exact
-                // no-ops, so there are no per-record branches; a lane leaves
-                // after the group of four in which both its pixels ended.
+                // The two decisions are 0/1 factors (mq, m): a record below the
+                // threshold gets alpha = 0 and T' = T; the ending record gets
+                // weight alpha (T m) = 0 and leaves T = T' m = 0, which keeps the
+                // pixel ended (every later T' is 0). All of these are exact, so
+                // there are no per-record branches; a lane leaves after the
+                // group of four in which both its pixels ended.
                 const int len4 = (len + 3) & ~3;
                 for (int i = 0; i < len4; i += 4) {
                     const uint4 jv = *reinterpret_cast<const uint4 *>(my_list + i);
@@ -310,27 +314,27 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                         const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
                         q[u] = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
                     }
-                    evals += (done0 ? 0u : 4u) + (done1 ? 0u : 4u);
+                    evals += (T2.x > 0.0f ? 4u : 0u) + (T2.y > 0.0f ? 4u : 0u);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        float al0 = fminf(kAlphaMax, ex2_approx(q[u].x));
-                        float al1 = fminf(kAlphaMax, ex2_approx(q[u].y));
-                        al0 = q[u].x < kLog2AlphaMin ? 0.0f : al0;
-                        al1 = q[u].y < kLog2AlphaMin ? 0.0f : al1;
-                        const float2 t2 = __fmul2_rn(T2, __ffma2_rn(make_float2(al0, al1), kMinusOne2, kOne2));
-                        done0 = done0 || t2.x < kTMin;
-                        done1 = done1 || t2.y < kTMin;
-                        const float2 w2 = __fmul2_rn(make_float2(done0 ? 0.0f : al0, done1 ? 0.0f : al1), T2);
+                        const float2 mq = make_float2(q[u].x >= kLog2AlphaMin ? 1.0f : 0.0f,
+                                                      q[u].y >= kLog2AlphaMin ? 1.0f : 0.0f);
+                        const float2 al = __fmul2_rn(make_float2(fminf(kAlphaMax, ex2_approx(q[u].x)),
+                                                                 fminf(kAlphaMax, ex2_approx(q[u].y))),
+                                                     mq);
+                        const float2 t2 = __fmul2_rn(T2, __ffma2_rn(al, kMinusOne2, kOne2));
+                        const float2 m = make_float2(t2.x >= kTMin ? 1.0f : 0.0f,
+                                                     t2.y >= kTMin ? 1.0f : 0.0f);
+                        const float2 w2 = __fmul2_rn(al, __fmul2_rn(T2, m));
                         const PairRec &pr = s_pair[jj[u]];
                         const float4 c_rg = pr.rg;
                         const float4 c_b = pr.bA;
                         cr2 = __ffma2_rn(w2, make_float2(c_rg.x, c_rg.y), cr2);
                         cg2 = __ffma2_rn(w2, make_float2(c_rg.z, c_rg.w), cg2);
                         cb2 = __ffma2_rn(w2, make_float2(c_b.x, c_b.y), cb2);
-                        T2.x = done0 ? T2.x : t2.x;
-                        T2.y = done1 ? T2.y : t2.y;
+                        T2 = __fmul2_rn(t2, m);
                     }
-                    if (done0 && done1) break;
+                    if (!(T2.x > 0.0f || T2.y > 0.0f)) break;
                 }
             }
         }
