@@ -159,7 +159,7 @@ __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
 void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
-    dfree(w.cut_off); dfree(w.vis_count); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.ranges);
+    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.ranges);
     dfree(w.hist); dfree(w.cams); dfree(w.work64);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
@@ -234,8 +234,6 @@ ngs_status ensure_work(ngs_ctx *c) {
     w.cams_cap = kMaxCamsPerCall;
     const int64_t nblk = (c->scene.n + cut_partition_nodes() - 1) / cut_partition_nodes();
     int64_t sw = std::max<int64_t>(nblk * kMaxCamsPerBatch, 1);
-    sw = std::max<int64_t>(sw, (c->scene.n + cutpre_partition_nodes() - 1) /
-                                   cutpre_partition_nodes() * kMaxCamsPerBatch);
     sw = std::max<int64_t>(sw, (std::max(w.rec_cap, w.pair_cap) + sort_partition() - 1) /
                                    sort_partition() * 256);
     sw = std::max<int64_t>(sw, (w.rec_cap + scan_partition() - 1) / scan_partition());
@@ -249,6 +247,11 @@ ngs_status ensure_work(ngs_ctx *c) {
     A(dalloc(&w.cut_ids, (size_t)w.cut_cap));
     A(dalloc(&w.cut_off, kMaxCamsPerBatch + 1));
     A(dalloc(&w.vis_count, kMaxCamsPerBatch));
+    w.part_cap = std::max<int64_t>(1, (c->scene.n + cutpre_partition_nodes() - 1) /
+                                          cutpre_partition_nodes() * kMaxCamsPerBatch);
+    A(dalloc(&w.part_list, (size_t)w.part_cap));
+    A(dalloc(&w.part_info, (size_t)w.part_cap));
+    A(dalloc(&w.part_pos, (size_t)w.part_cap));
     A(dalloc((unsigned char **)&w.rec, (size_t)w.rec_cap * sizeof(Rec32)));
     A(dalloc(&w.rect, (size_t)w.rec_cap));
     A(dalloc(&w.poff, (size_t)w.rec_cap));
@@ -372,12 +375,13 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st);
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
     uint32_t eo = 0;
-    launch_cutpre(c->scene, cams, nc, c->scene.n, w.rec, w.dkey[1], w.rect, w.vis_count,
-                  w.counters + CNT_CUT, w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->tile_w, c->tile_h,
+    launch_cutpre(c->scene, cams, nc, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
+                  w.counters, w.part_list, w.part_info, w.err, c->tile_w, c->tile_h,
                   c->block_cull ? 1 : 0, c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
-    launch_gather_keys(w.vis_count, nc, c->scene.n, w.dkey[1], w.dkey[0], w.didx[0], w.counters,
-                       w.rec_cap, w.err, c->num_sms * 2, st);
+    launch_gather_keys(w.vis_count, nc, c->scene, w.part_info, w.part_pos, w.part_list,
+                       w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.err,
+                       c->num_sms * 8, st);
     mark(c, sb_index, MK_PRE, st);
     SortHook dh{c, sb_index, MK_DHIST, st};
     SortArgs da{};
@@ -482,19 +486,20 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
         uint32_t eo = 0;
         const int64_t nblk = (c->scene.n + cutpre_partition_nodes() - 1) / cutpre_partition_nodes();
-        launch_cutpre(c->scene, cams, 1, c->scene.n, w.rec, w.dkey[1], w.rect, w.vis_count,
-                      w.counters + CNT_CUT, w.counters + TK_CUT, w.status, w.epoch, eo++, w.err, c->tile_w, c->tile_h,
-                      c->block_cull ? 1 : 0, (int)nblk, st);
+        launch_cutpre(c->scene, cams, 1, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
+                      w.counters, w.part_list, w.part_info, w.err, c->tile_w, c->tile_h,
+                      c->block_cull ? 1 : 0, (int)std::min<int64_t>(nblk, c->grid_pre), st);
+        eo++;
         mark(c, ci, MK_CUT, st);
         uint32_t n_cut = 0, n_vis = 0, n_pairs = 0;
         ngs_status s = read_u32(w.vis_count, &n_vis, st);
         if (s != NGS_OK) return s;
         if ((s = read_u32(w.counters + CNT_CUT, &n_cut, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
-        launch_gather_keys(w.vis_count, 1, c->scene.n, w.dkey[1], w.dkey[0], w.didx[0],
-                           w.counters, w.rec_cap, w.err,
-                           (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n_vis + 1023) / 1024,
-                                                                       4 * c->num_sms)), st);
+        launch_gather_keys(w.vis_count, 1, c->scene, w.part_info, w.part_pos, w.part_list,
+                           w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.err,
+                           (int)std::max<int64_t>(1, std::min<int64_t>(nblk / 8 + 1,
+                                                                       8 * c->num_sms)), st);
         mark(c, ci, MK_PRE, st);
         eo++;
         if ((s = check_err(c)) != NGS_OK) return s;

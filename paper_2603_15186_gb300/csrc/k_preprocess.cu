@@ -15,13 +15,18 @@
 // are the sort key and it decides the near-plane cull. The oracle evaluates
 // the same sequence, so keys and culls agree bit for bit. No float64 anywhere.
 //
-// Output is compacted in slot order (camera-major, then ascending node id) by
-// a one-pass chained scan, so the record index order breaks depth ties by
-// node id. HBM per cut Gaussian: 4 B id + 16 B position (always); quaternion
+// Output: each partition (block of nodes, camera) takes space for its visible
+// Gaussians with one atomic allocation and writes them there in node order;
+// its (offset, count) goes to a partition table. The dense depth-sort input is
+// then gathered in camera-major, node-id order through a scan of that table,
+// so depth ties are broken by node id whatever the allocation order was.
+// HBM per cut Gaussian: 4 B id + 16 B position (always); quaternion
 // 16 B and scale/opacity 16 B (f32) or 8 B (f16/bf16) for those in front of
 // the near plane; SH 192 B (f32) or 96 B for those with a non-empty rectangle;
 // written per visible one: record 48 B (f32) or 32 B, key 4 B, rect 16 B
 // (tile rectangle, camera index, node id).
+#include <algorithm>
+
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -356,14 +361,43 @@ __device__ __forceinline__ void store_rec(Rec16 *rec, int64_t i, const PreOut &o
                            __uint_as_float(*reinterpret_cast<const uint32_t *>(&b0)));
 }
 
-// Fused cut + preprocess. Partitions are (block of kPrePart nodes, camera) with
-// the camera varying fastest, so CTAs that run at the same time work on the same
-// node block for different cameras and share its attributes through L2. Each
-// camera has its own look-back chain over the node blocks, so camera c's
-// visible Gaussians land in node-id order in its region
-// [c * region, c * region + vis_count[c]) of the record, key and rect arrays.
-// Phase-B results of one partition, staged until the partition's output
-// offset is known (candidate j of the partition in slot j).
+// Live partitions: the (node block, camera) pairs that survive the block-level
+// cull, listed block-major with the camera varying fastest (within a warp;
+// warps append in any order), so that partitions running at the same time
+// work on the same node block and share its attributes through L2. Culled
+// partitions get an empty entry in the partition table.
+__global__ void k_live_parts(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams,
+                             int64_t nblk, uint32_t *__restrict__ part_list,
+                             uint2 *__restrict__ part_info, uint32_t *counters, int tile_w,
+                             int tile_h, int use_block_cull, const int *err) {
+    if (*err) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nparts = nblk * n_cams;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < nparts; t0 += stride) {
+        const int64_t t = t0 + threadIdx.x;
+        bool live = false;
+        if (t < nparts) {
+            const int64_t b = t / n_cams;
+            const int c = (int)(t - b * n_cams);
+            live = !(use_block_cull &&
+                     block_culled(sc.blk_lo[b], sc.blk_hi[b], cams[c], tile_w, tile_h));
+            if (!live) part_info[(int64_t)c * nblk + b] = make_uint2(0u, 0u);
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, live);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&counters[CNT_LIVE], (uint32_t)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (live) part_list[base + __popc(bal & lanemask_lt())] = (uint32_t)t;
+    }
+}
+
+// Fused cut + preprocess over the live partitions (block of kPrePart nodes,
+// camera), taken from an atomic ticket. Phase A applies the cut rule and the
+// conservative cull and compacts the candidates; phase B preprocesses them
+// densely, staging the results in shared memory until the partition knows
+// where its visible Gaussians go (one atomic allocation); they are written
+// there in node order.
 template <typename R>
 struct CutPreSmem {
     uint32_t cand[kPrePart];      // candidate node ids, node order
@@ -373,43 +407,37 @@ struct CutPreSmem {
     uint32_t vis[kPrePart];       // visible flag, then (rank | 1 << 31)
     uint32_t cnt[kPreItems * 8];
     uint32_t wsum[kPreThreads / 32];
-    uint32_t part, excl, ncand, sel, skip;
+    uint32_t part, ncand, sel;
+    unsigned long long off;
 };
 
 template <typename A, typename R>
 __global__ void __launch_bounds__(kPreThreads)
-k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t region,
-         R *__restrict__ rec, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
-         uint32_t *__restrict__ vis_count, uint32_t *cut_count, uint32_t *ticket,
-         uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, int tile_w,
-         int tile_h, int use_block_cull) {
+k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restrict__ rec,
+         int64_t rec_cap, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
+         uint32_t *__restrict__ vis_count, uint32_t *counters,
+         const uint32_t *__restrict__ part_list, uint2 *__restrict__ part_info, int *err,
+         int tile_w, int tile_h) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CutPreSmem<R> &S = *reinterpret_cast<CutPreSmem<R> *>(smem_raw);
     if (*err) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
-    const int64_t nparts = nblk * n_cams;
-    const uint32_t epoch = *epoch_ptr + epoch_off;
+    const uint32_t n_live = counters[CNT_LIVE];
+    unsigned long long *alloc = reinterpret_cast<unsigned long long *>(counters + CNT_ALLOC);
     const uint32_t lt = lanemask_lt();
     for (;;) {
         if (tid == 0) {
-            const uint32_t t = atomicAdd(ticket, 1u);
-            S.part = t;
+            const uint32_t i = atomicAdd(&counters[TK_PRE], 1u);
+            S.part = i < n_live ? part_list[i] : 0xffffffffu;
             S.sel = 0;
-            S.skip = 0;
-            if (use_block_cull && (int64_t)t < nparts) {
-                const int64_t bb = (int64_t)t / n_cams;
-                S.skip = block_culled(sc.blk_lo[bb], sc.blk_hi[bb], cams[(int)((int64_t)t - bb * n_cams)],
-                                      tile_w, tile_h) ? 1u : 0u;
-            }
         }
         __syncthreads();
+        if (S.part == 0xffffffffu) break;
         const int64_t part = S.part;
-        if (part >= nparts) break;
         const int64_t b = part / n_cams;
         const int c = (int)(part - b * n_cams);
         const DevCamera &cam = cams[c];
-        const bool skip = S.skip != 0;
         // phase A: cut rule and conservative cull; survivors compacted into
         // S.cand in node order
         uint32_t bal[kPreItems];
@@ -417,7 +445,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
 #pragma unroll
         for (int k = 0; k < kPreItems; ++k) {
             const int64_t node = b * kPrePart + k * kPreThreads + tid;
-            const bool sel = !skip && node < sc.n &&
+            const bool sel = node < sc.n &&
                              cut_selects(sc.box_lo, sc.box_hi, node, cam.pos[0], cam.pos[1],
                                          cam.pos[2], cam.fx, cam.tau);
             const bool cand = sel && precull<A>(sc, cam, (uint32_t)node, tile_w, tile_h);
@@ -444,7 +472,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
             if ((bal[k] >> lane) & 1u)
                 S.cand[S.cnt[k * 8 + warp] + __popc(bal[k] & lt)] =
                     (uint32_t)(b * kPrePart + k * kPreThreads + tid);
-        if (tid == 0) atomicAdd(cut_count, S.sel);
+        if (tid == 0 && S.sel) atomicAdd(&counters[CNT_CUT], S.sel);
         __syncthreads();
         // phase B: full preprocess, densely over the candidates, results staged
         const int ncand = (int)S.ncand;
@@ -490,24 +518,22 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
             r += f[k];
         }
         if (tid == 0) {
-            uint64_t *chain = status + (int64_t)c * nblk;
-            uint32_t prev = 0;
-            if (b == 0) {
-                publish(chain, pack_status(kFlagPrefix, epoch, total));
-            } else {
-                publish(chain + b, pack_status(kFlagAgg, epoch, total));
-                look_back(chain, b, 1, epoch, &prev, err);
-                publish(chain + b, pack_status(kFlagPrefix, epoch, prev + total));
+            unsigned long long off = 0;
+            if (total) {
+                off = atomicAdd(alloc, (unsigned long long)total);
+                atomicAdd(&vis_count[c], total);
+                if (off + total > (unsigned long long)rec_cap) latch_error(err, kErrCapacity);
             }
-            S.excl = prev;
-            if (b == nblk - 1) vis_count[c] = prev + total;
+            S.off = off;
+            part_info[(int64_t)c * nblk + b] =
+                make_uint2((uint32_t)min(off, (unsigned long long)rec_cap), total);
         }
         __syncthreads();
-        const int64_t base = (int64_t)c * region + S.excl;
+        const unsigned long long base = S.off;
         for (int j = tid; j < ncand; j += kPreThreads) {
             const uint32_t v = S.vis[j];
-            if (v) {
-                const int64_t pos = base + (v & 0x7fffffffu);
+            const unsigned long long pos = base + (v & 0x7fffffffu);
+            if (v && pos < (unsigned long long)rec_cap) {
                 rec[pos] = S.rec[j];
                 dkey[pos] = S.key[j];
                 rect[pos] = S.rect[j];
@@ -517,79 +543,121 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, int64_t re
     }
 }
 
-// Dense (key, record index) arrays for the depth sort: element i of the
-// concatenation of the per-camera regions, and the visible total.
-__global__ void k_gather_keys(const uint32_t *__restrict__ vis_count, int n_cams, int64_t region,
-                              const uint32_t *__restrict__ dkey_sparse,
-                              uint32_t *__restrict__ dkey, uint32_t *__restrict__ didx,
-                              uint32_t *counters, int64_t cap, int *err) {
-    __shared__ uint32_t s_off[kMaxCamsPerBatch + 1];
+// Dense depth-sort input, part 1: per camera (one CTA each), the position of
+// every partition's first record in the camera-major, node-order sequence;
+// block 0 also stores the visible total.
+__global__ void __launch_bounds__(1024)
+k_part_scan(const uint32_t *__restrict__ vis_count, int n_cams, int64_t nblk,
+            const uint2 *__restrict__ part_info, uint32_t *__restrict__ part_pos,
+            uint32_t *counters, int64_t cap, int *err) {
     __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_base, s_total;
     if (*err) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // exclusive scan of up to 1024 per-camera counts (blockDim = 1024)
-    const uint32_t v = tid < n_cams ? vis_count[tid] : 0u;
-    uint32_t incl = v;
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // exclusive scan of the (at most 1024) per-camera counts
+    auto block_scan = [&](uint32_t v, uint32_t &total) -> uint32_t {
+        uint32_t incl = v;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    uint32_t wb = 0;
-    for (int w = 0; w < warp; ++w) wb += s_w[w];
-    if (tid <= n_cams) s_off[tid] = wb + incl - v;
-    if (tid == n_cams - 1) s_off[n_cams] = wb + incl;
-    __syncthreads();
-    const uint32_t total = s_off[n_cams];
-    if (blockIdx.x == 0 && tid == 0) {
-        counters[CNT_VIS] = total;
-        if ((int64_t)total > cap) latch_error(err, kErrCapacity);
-    }
-    if ((int64_t)total > cap) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n_cams - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= (uint32_t)i) lo = mid; else hi = mid - 1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        const int64_t sp = (int64_t)lo * region + (i - s_off[lo]);
-        dkey[i] = dkey_sparse[sp];
-        didx[i] = (uint32_t)sp;
+        __syncthreads();
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        uint32_t wb = 0, tot = 0;
+        for (int w = 0; w < 32; ++w) {
+            if (w < warp) wb += s_w[w];
+            tot += s_w[w];
+        }
+        total = tot;
+        return wb + incl - v;
+    };
+    uint32_t tot;
+    const uint32_t ex = block_scan(tid < n_cams ? vis_count[tid] : 0u, tot);
+    if (tid == c) s_base = ex;
+    if (tid == 0) s_total = tot;
+    __syncthreads();
+    if (c == 0 && tid == 0) {
+        counters[CNT_VIS] = s_total;
+        if ((int64_t)s_total > cap) latch_error(err, kErrCapacity);
+    }
+    uint32_t carry = s_base;
+    for (int64_t b0 = 0; b0 < nblk; b0 += 1024) {
+        const int64_t b = b0 + tid;
+        const uint32_t n = b < nblk ? part_info[(int64_t)c * nblk + b].y : 0u;
+        uint32_t chunk;
+        const uint32_t e = block_scan(n, chunk);
+        if (b < nblk) part_pos[(int64_t)c * nblk + b] = carry + e;
+        carry += chunk;
     }
 }
 
-void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_t region,
-                   void *rec, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
-                   uint32_t *cut_count, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
-                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int use_block_cull,
-                   int grid, cudaStream_t st) {
+// Dense depth-sort input, part 2: one warp per live partition copies its keys
+// and writes their record indices at the partition's dense position.
+__global__ void k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
+                              const uint2 *__restrict__ part_info,
+                              const uint32_t *__restrict__ part_pos,
+                              const uint32_t *__restrict__ dkey_sparse,
+                              uint32_t *__restrict__ dkey, uint32_t *__restrict__ didx,
+                              const uint32_t *counters, int64_t cap, const int *err) {
+    if (*err) return;
+    const uint32_t n_live = counters[CNT_LIVE];
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_live; i += nw) {
+        const uint32_t t = part_list[i];
+        const uint32_t b = t / (uint32_t)n_cams, c = t - b * (uint32_t)n_cams;
+        const int64_t idx = (int64_t)c * nblk + b;
+        const uint2 info = part_info[idx];
+        const int64_t pos = part_pos[idx];
+        for (uint32_t k = lane; k < info.y; k += 32) {
+            if (pos + k < cap && (int64_t)info.x + k < cap) {
+                dkey[pos + k] = dkey_sparse[info.x + k];
+                didx[pos + k] = info.x + k;
+            }
+        }
+    }
+}
+
+void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
+                   int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
+                   uint32_t *counters, uint32_t *part_list, uint2 *part_info, int *err,
+                   int tile_w, int tile_h, int use_block_cull, int grid, cudaStream_t st) {
+    const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
+    cudaMemsetAsync(vis_count, 0, (size_t)n_cams * sizeof(uint32_t), st);
+    const int64_t nparts = nblk * n_cams;
+    const int lgrid = (int)std::min<int64_t>((nparts + 255) / 256, 8 * 1024);
+    k_live_parts<<<std::max(lgrid, 1), 256, 0, st>>>(sc, cams, n_cams, nblk, part_list, part_info,
+                                                     counters, tile_w, tile_h, use_block_cull, err);
     switch (sc.attr_dtype) {
     case NGS_F16:
         k_cutpre<__half, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
-            sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
-            ticket, status, epoch, epoch_off, err, tile_w, tile_h, use_block_cull);
+            sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
+            part_list, part_info, err, tile_w, tile_h);
         break;
     case NGS_BF16:
         k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
-            sc, cams, n_cams, region, (Rec16 *)rec, dkey_sparse, rect, vis_count, cut_count,
-            ticket, status, epoch, epoch_off, err, tile_w, tile_h, use_block_cull);
+            sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
+            part_list, part_info, err, tile_w, tile_h);
         break;
     default:
         k_cutpre<float, Rec32><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
-            sc, cams, n_cams, region, (Rec32 *)rec, dkey_sparse, rect, vis_count, cut_count,
-            ticket, status, epoch, epoch_off, err, tile_w, tile_h, use_block_cull);
+            sc, cams, n_cams, (Rec32 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
+            part_list, part_info, err, tile_w, tile_h);
         break;
     }
 }
 
-void launch_gather_keys(const uint32_t *vis_count, int n_cams, int64_t region,
+void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &sc,
+                        const uint2 *part_info, uint32_t *part_pos, const uint32_t *part_list,
                         const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,
                         uint32_t *counters, int64_t cap, int *err, int grid, cudaStream_t st) {
-    k_gather_keys<<<grid, 1024, 0, st>>>(vis_count, n_cams, region, dkey_sparse, dkey, didx,
-                                         counters, cap, err);
+    const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
+    k_part_scan<<<n_cams, 1024, 0, st>>>(vis_count, n_cams, nblk, part_info, part_pos, counters,
+                                         cap, err);
+    k_part_gather<<<grid, 256, 0, st>>>(part_list, n_cams, nblk, part_info, part_pos, dkey_sparse,
+                                        dkey, didx, counters, cap, err);
 }
 
 int cutpre_partition_nodes() { return kPrePart; }

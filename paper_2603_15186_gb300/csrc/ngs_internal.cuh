@@ -198,6 +198,12 @@ struct Work {
     uint32_t *cut_ids = nullptr;      int64_t cut_cap = 0;
     uint32_t *cut_off = nullptr;      // [cams + 1]
     uint32_t *vis_count = nullptr;    // [cams] visible Gaussians per camera
+    // cut+preprocess partition tables, [cams][node blocks]: live partition ids,
+    // (record offset, count), dense position of the first record
+    uint32_t *part_list = nullptr;
+    uint2 *part_info = nullptr;
+    uint32_t *part_pos = nullptr;
+    int64_t part_cap = 0;
     void *rec = nullptr;              int64_t rec_cap = 0;
     uint32_t *dkey[2] = {nullptr, nullptr};
     uint32_t *didx[2] = {nullptr, nullptr};
@@ -217,6 +223,8 @@ struct Work {
 enum : int {
     CNT_CUT = 0, CNT_VIS = 1, CNT_PAIRS = 2, TK_CUT = 3, TK_PRE = 4, TK_SCAN = 5, TK_DUP = 6,
     TK_SORT0 = 8,             // 8 .. 8 + 16: one ticket per sort pass
+    CNT_ALLOC = 24,           // 24, 25: 64-bit record allocation counter
+    CNT_LIVE = 26,            // live cut+preprocess partitions
     TK_COMPOSITE = 28, N_COUNTERS = 32
 };
 
@@ -231,17 +239,21 @@ void launch_cut(const SceneDev &sc, const DevCamera *cams, int n_cams, uint32_t 
                 int grid, cudaStream_t st);
 int cut_partition_nodes();
 
-// fused cut + preprocess: per camera c, visible Gaussians of the cut in node
-// order at [c * region, c * region + vis_count[c]) of rec / dkey_sparse / rect
-void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, int64_t region,
-                   void *rec, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
-                   uint32_t *cut_count, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
-                   uint32_t epoch_off, int *err, int tile_w, int tile_h, int use_block_cull,
-                   int grid, cudaStream_t st);
+// fused cut + preprocess of cameras [0, n_cams): the visible Gaussians of each
+// partition (block of cutpre_partition_nodes() nodes, camera) in node order at
+// an atomically allocated offset of rec / dkey_sparse / rect; (offset, count)
+// per partition in part_info[camera * nblk + block]; visible Gaussians per
+// camera in vis_count; counters[CNT_CUT], [CNT_LIVE], [CNT_ALLOC], [TK_PRE]
+void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
+                   int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
+                   uint32_t *counters, uint32_t *part_list, uint2 *part_info, int *err,
+                   int tile_w, int tile_h, int use_block_cull, int grid, cudaStream_t st);
 int cutpre_partition_nodes();
 void cutpre_init_attributes();
-// dense depth keys and sparse record indices for the sort; counters[CNT_VIS]
-void launch_gather_keys(const uint32_t *vis_count, int n_cams, int64_t region,
+// dense depth keys (camera-major, node order) and their record indices for the
+// sort; counters[CNT_VIS]
+void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &sc,
+                        const uint2 *part_info, uint32_t *part_pos, const uint32_t *part_list,
                         const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,
                         uint32_t *counters, int64_t cap, int *err, int grid, cudaStream_t st);
 
