@@ -24,6 +24,12 @@ constexpr int kScanPart = kScanThreads * kScanItems;
 
 int scan_partition() { return kScanPart; }
 
+// K4 works on chunks of kDupChunk consecutive pairs
+constexpr int kDupThreads = 256;
+constexpr int kDupChunk = 2048;
+constexpr int kDupWindow = 512;       // records staged at a time
+int64_t dup_chunks(int64_t pair_cap) { return pair_cap / kDupChunk + 1; }
+
 __device__ __forceinline__ uint32_t rect_area(const uint4 r) {
     const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
     return (x1 - x0 + 1u) * (y1 - y0 + 1u);
@@ -62,12 +68,15 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v[kScanItems], uint32_t 
 
 // Exclusive scan with one-pass decoupled look-back. Input element i is
 // in[i] (kGather = false) or area(rect[idx[i]]) (kGather = true).
+// With kGather, also chunk_first[c] = the input position whose output range
+// [out[i], out[i] + in_i) holds element c * kDupChunk (c < chunk_cap).
 template <bool kGather>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
        const uint32_t *__restrict__ idx, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
        uint32_t *total_out, int64_t total_cap, uint32_t *ticket, uint64_t *status,
-       const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+       const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, uint32_t *chunk_first,
+       int64_t chunk_cap) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_part, s_prev;
     if (*err) return;
@@ -82,12 +91,13 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
         const int64_t part = s_part;
         if (part >= nparts) break;
         const int64_t base = part * kScanPart + (int64_t)tid * kScanItems;
-        uint32_t v[kScanItems];
+        uint32_t v[kScanItems], a[kScanItems];
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) {
             const int64_t j = base + i;
             if (j < n) v[i] = kGather ? rect_area(rect[idx[j]]) : in[j];
             else v[i] = 0;
+            a[i] = v[i];
         }
         const uint32_t total = block_scan(v, s_warp);
         if (tid == 0) {
@@ -114,7 +124,16 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) {
             const int64_t j = base + i;
-            if (j < n) out[j] = prev + v[i];
+            if (j < n) {
+                const uint32_t lo = prev + v[i];
+                out[j] = lo;
+                if (kGather && a[i]) {
+                    const uint64_t hi = (uint64_t)lo + a[i];
+                    for (uint64_t c = ((uint64_t)lo + kDupChunk - 1) / kDupChunk;
+                         c * kDupChunk < hi && (int64_t)c < chunk_cap; ++c)
+                        chunk_first[c] = (uint32_t)j;
+                }
+            }
         }
         __syncthreads();
     }
@@ -124,35 +143,38 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, i
                      uint32_t *total, uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
                      uint32_t epoch_off, int *err, int grid, cudaStream_t st) {
     k_scan<false><<<grid, kScanThreads, 0, st>>>(in, nullptr, nullptr, out, n_dev, n_host, total,
-                                                 -1, ticket, status, epoch, epoch_off, err);
+                                                 -1, ticket, status, epoch, epoch_off, err,
+                                                 nullptr, 0);
 }
 
 void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         int grid, cudaStream_t st) {
+                         uint32_t *chunk_first, int grid, cudaStream_t st) {
     k_scan<true><<<grid, kScanThreads, 0, st>>>(nullptr, rect, sorted_idx, poff, n_vis, -1,
                                                 counters + CNT_PAIRS, pair_cap, ticket, status,
-                                                epoch, epoch_off, err);
+                                                epoch, epoch_off, err, chunk_first,
+                                                dup_chunks(pair_cap));
 }
 
-// K4: one CTA takes 256 consecutive records in depth order, and its threads
-// then walk the CTA's contiguous pair range, each pair finding its record by
-// binary search over the CTA's offsets in shared memory (so a Gaussian that
-// covers hundreds of tiles is spread over all threads of the CTA).
-constexpr int kDupThreads = 256;
-
+// K4: the pair array is cut into chunks of kDupChunk pairs, so every CTA
+// iteration writes the same number of pairs however many tiles a Gaussian
+// covers. A chunk starts at the record chunk_first[c] (from K3); its records
+// are staged kDupWindow at a time (offsets, rectangles, record ids, camera
+// tile bases), and each thread's pair finds its record by binary search over
+// the staged offsets. Tile-digit histograms of the radix passes that follow
+// are accumulated on the way.
 __global__ void __launch_bounds__(kDupThreads)
 k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_idx,
-            const uint32_t *__restrict__ poff, const uint32_t *n_vis_p,
-            const uint32_t *n_pairs_p, int64_t pair_cap, const DevCamera *__restrict__ cams,
-            uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval, uint32_t *hist, int passes,
-            int *err) {
+            const uint32_t *__restrict__ poff, const uint32_t *__restrict__ chunk_first,
+            const uint32_t *n_vis_p, const uint32_t *n_pairs_p, int64_t pair_cap,
+            const DevCamera *__restrict__ cams, uint32_t *__restrict__ pkey,
+            uint32_t *__restrict__ pval, uint32_t *hist, int passes, int *err) {
     __shared__ uint32_t s_h[3][256];       // digit counts of the tile keys, per radix pass
-    __shared__ uint32_t s_off[kDupThreads + 1];
-    __shared__ uint4 s_rect[kDupThreads];
-    __shared__ uint32_t s_idx[kDupThreads];
-    __shared__ uint2 s_cam[kDupThreads];   // (tile base, tiles_x) of each record's camera
+    __shared__ uint32_t s_off[kDupWindow + 1];
+    __shared__ uint4 s_rect[kDupWindow];
+    __shared__ uint32_t s_idx[kDupWindow];
+    __shared__ uint2 s_cam[kDupWindow];    // (tile base, tiles_x) of each record's camera
     if (*err) return;
     const uint32_t n_vis = *n_vis_p, n_pairs = *n_pairs_p;
     if ((int64_t)n_pairs > pair_cap) {
@@ -162,63 +184,71 @@ k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_
     const int tid = threadIdx.x, lane = tid & 31;
     if (hist)
         for (int i = tid; i < 3 * 256; i += kDupThreads) (&s_h[0][0])[i] = 0;
-    for (int64_t blk = blockIdx.x; blk * kDupThreads < n_vis; blk += gridDim.x) {
-        const int64_t first = blk * kDupThreads;
-        const int64_t rem = (int64_t)n_vis - first;
-        const int cnt = rem < kDupThreads ? (int)rem : kDupThreads;
-        if (tid < cnt) {
-            const uint32_t r = sorted_idx[first + tid];
-            s_idx[tid] = r;
-            const uint4 rr = rect[r];
-            s_rect[tid] = rr;
-            s_cam[tid] = make_uint2(cams[rr.z].tile_base, (uint32_t)cams[rr.z].tiles_x);
-            s_off[tid] = poff[first + tid];
-        }
-        if (tid == 0)
-            s_off[cnt] = (first + cnt < (int64_t)n_vis) ? poff[first + cnt] : n_pairs;
-        __syncthreads();
-        const uint32_t p0 = s_off[0], p1 = s_off[cnt];
-        // uniform trip count: every lane of a warp reaches the warp collectives
-        for (uint32_t base = p0; base < p1; base += kDupThreads) {
-            const uint32_t p = base + tid;
-            const bool valid = p < p1;
-            uint32_t key = 0;
-            if (valid) {
-                int lo = 0, hi = cnt - 1;   // last j with s_off[j] <= p
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
-                }
-                const uint4 r = s_rect[lo];
-                const uint32_t k = p - s_off[lo];
-                const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
-                const uint32_t w = x1 - x0 + 1u;
-                const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-                const uint2 cm = s_cam[lo];
-                key = cm.x + ty * cm.y + tx;
-                pkey[p] = key;
-                pval[p] = s_idx[lo];
+    const int64_t n_chunks = ((int64_t)n_pairs + kDupChunk - 1) / kDupChunk;
+    for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t p0 = (uint32_t)(ch * kDupChunk);
+        const uint32_t p1 = (uint32_t)min((int64_t)n_pairs, ch * kDupChunk + kDupChunk);
+        int64_t r0 = chunk_first[ch];
+        uint32_t q = p0;   // first pair of the chunk not yet written
+        while (q < p1) {
+            const int64_t rem = (int64_t)n_vis - r0;
+            const int cnt = rem < kDupWindow ? (int)rem : kDupWindow;
+            __syncthreads();
+            for (int j = tid; j < cnt; j += kDupThreads) {
+                const uint32_t r = sorted_idx[r0 + j];
+                s_idx[j] = r;
+                const uint4 rr = rect[r];
+                s_rect[j] = rr;
+                s_cam[j] = make_uint2(cams[rr.z].tile_base, (uint32_t)cams[rr.z].tiles_x);
+                s_off[j] = poff[r0 + j];
             }
-            if (hist) {
-                // neighbouring pairs mostly share their high digits: a warp whose
-                // valid lanes agree adds its count once
-                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-                if (vmask) {
-                    const int leader = __ffs(vmask) - 1;
-                    for (int q = 0; q < passes; ++q) {
-                        const uint32_t d = (key >> (8 * q)) & 255u;
-                        const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
-                        const bool same = __all_sync(0xffffffffu, !valid || d == dl);
-                        if (same) {
-                            if (lane == leader) atomicAdd(&s_h[q][d], (uint32_t)__popc(vmask));
-                        } else if (valid) {
-                            atomicAdd(&s_h[q][d], 1u);
+            if (tid == 0) s_off[cnt] = (r0 + cnt < (int64_t)n_vis) ? poff[r0 + cnt] : n_pairs;
+            __syncthreads();
+            const uint32_t q1 = min(p1, s_off[cnt]);
+            // uniform trip count: every lane of a warp reaches the warp collectives
+            for (uint32_t base = q; base < q1; base += kDupThreads) {
+                const uint32_t p = base + tid;
+                const bool valid = p < q1;
+                uint32_t key = 0;
+                if (valid) {
+                    int lo = 0, hi = cnt - 1;   // last j with s_off[j] <= p
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
+                    }
+                    const uint4 r = s_rect[lo];
+                    const uint32_t k = p - s_off[lo];
+                    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
+                    const uint32_t w = x1 - x0 + 1u;
+                    const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+                    const uint2 cm = s_cam[lo];
+                    key = cm.x + ty * cm.y + tx;
+                    pkey[p] = key;
+                    pval[p] = s_idx[lo];
+                }
+                if (hist) {
+                    // neighbouring pairs mostly share their high digits: a warp whose
+                    // valid lanes agree adds its count once
+                    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                    if (vmask) {
+                        const int leader = __ffs(vmask) - 1;
+                        for (int qd = 0; qd < passes; ++qd) {
+                            const uint32_t d = (key >> (8 * qd)) & 255u;
+                            const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+                            const bool same = __all_sync(0xffffffffu, !valid || d == dl);
+                            if (same) {
+                                if (lane == leader) atomicAdd(&s_h[qd][d], (uint32_t)__popc(vmask));
+                            } else if (valid) {
+                                atomicAdd(&s_h[qd][d], 1u);
+                            }
                         }
                     }
                 }
             }
+            q = q1;
+            r0 += cnt;
+            if (cnt == 0) break;
         }
-        __syncthreads();
     }
     if (hist) {
         __syncthreads();
@@ -230,12 +260,12 @@ k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_
 }
 
 void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
-                      const uint32_t *n_vis, const uint32_t *n_pairs, int64_t pair_cap,
-                      const DevCamera *cams, uint32_t *pkey, uint32_t *pval, uint32_t *hist,
-                      int passes, int *err, int grid, cudaStream_t st) {
-    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect, sorted_idx, poff, n_vis, n_pairs, pair_cap,
-                                              cams, pkey, pval, passes > 0 ? hist : nullptr,
-                                              passes, err);
+                      const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
+                      int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
+                      uint32_t *hist, int passes, int *err, int grid, cudaStream_t st) {
+    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect, sorted_idx, poff, chunk_first, n_vis, n_pairs,
+                                              pair_cap, cams, pkey, pval,
+                                              passes > 0 ? hist : nullptr, passes, err);
 }
 
 // K6: ranges[t] = [first, end) of tile t in the sorted pair keys (ranges of
