@@ -157,28 +157,47 @@ __device__ __forceinline__ bool cut_selects(const float4 *__restrict__ box_lo,
 
 // Decoupled look-back for one running sum: returns the exclusive prefix of
 // partition `part` over the chain whose words sit at status[j * stride]. The
-// caller has already published its own aggregate. Returns false (and latches
-// kErrTimeout) if a predecessor never publishes within the spin limit.
+// caller has already published its own aggregate. The words of the next
+// kLookBackWindow predecessors are requested together (one memory round trip
+// per window) and consumed in order until an inclusive prefix is found; a
+// window that reaches an unpublished word is requested again from there.
+// Returns false (and latches kErrTimeout) if a predecessor never publishes
+// within the spin limit.
+constexpr int kLookBackWindow = 8;
+
 __device__ __forceinline__ bool look_back(const uint64_t *status, int64_t part, int64_t stride,
                                           uint32_t epoch, uint32_t *excl, int *err) {
     uint32_t acc = 0;
     int64_t j = part - 1;
     uint32_t spins = 0;
+    const uint32_t ep = epoch & kEpochMask;
     while (j >= 0) {
-        const uint64_t w = peek(status + j * stride);
-        const uint32_t e = (uint32_t)(w >> 32) & kEpochMask;
-        const uint64_t flag = w & (3ull << 62);
-        if (e != (epoch & kEpochMask) || flag == 0) {
-            if (++spins > kSpinLimit) {
-                latch_error(err, kErrTimeout);
-                *excl = acc;
-                return false;
+        uint64_t w[kLookBackWindow];
+#pragma unroll
+        for (int k = 0; k < kLookBackWindow; ++k)
+            w[k] = j - k >= 0 ? peek(status + (j - k) * stride) : 0ull;
+        bool stalled = false;
+#pragma unroll
+        for (int k = 0; k < kLookBackWindow; ++k) {
+            if (stalled || j < 0) continue;
+            const uint32_t e = (uint32_t)(w[k] >> 32) & kEpochMask;
+            const uint64_t flag = w[k] & (3ull << 62);
+            if (e != ep || flag == 0) {
+                stalled = true;
+                continue;
             }
-            continue;
+            acc += (uint32_t)w[k];
+            if (flag == kFlagPrefix) {
+                *excl = acc;
+                return true;
+            }
+            --j;
         }
-        acc += (uint32_t)w;
-        if (flag == kFlagPrefix) break;
-        --j;
+        if (stalled && ++spins > kSpinLimit) {
+            latch_error(err, kErrTimeout);
+            *excl = acc;
+            return false;
+        }
     }
     *excl = acc;
     return true;
