@@ -65,6 +65,25 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def max_over_ranks(x, pg):
+    """The largest value of a per-rank float over all ranks (x itself without a
+    process group): the timed region of a multi-GPU run lasts as long as its
+    slowest rank."""
+    if not pg:
+        return float(x)
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_per_s(pixels_per_rank, steps, world, total_ms):
+    """Mpix/s of the whole job: every rank renders its own batch of
+    pixels_per_rank pixels per step (weak scaling)."""
+    return world * pixels_per_rank * steps / (total_ms * 1e3)
+
+
 def make_workload(args, rank):
     from scenegen import make_scene, mixed_batch_cameras
     scene = make_scene(args.leaves)
@@ -230,12 +249,9 @@ def run_ours(args, world, rank, local, pg):
     R.synchronize()
     total_ms = g0.elapsed_time(g1)
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, pg)
     ms_per_step = total_ms / args.steps
-    value = world * pixels * args.steps / (total_ms * 1e3)   # Mpix/s over all ranks
+    value = whole_job_mpix_per_s(pixels, args.steps, world, total_ms)
     stats = R.stats()
     kernels_per_step = stats["kernels"]
 

@@ -1,0 +1,164 @@
+"""GPU parity at the full workload sizes: the 1M-leaf floor (640x480 views,
+plain FP32), the 4M-leaf floor (1280x720 views with FP16 / BF16 attributes, and
+the 256-camera mixed-resolution batch in the configuration the benchmark times:
+batched, graph-captured, autotuned tile and staging depth), and the 8M-leaf
+two-wing floor served to many agents. The oracle renders sampled views whole;
+the rest of a batch is checked by properties that hold at any size (every
+image equals its camera rendered alone, and a graph replay gives the same
+bits).
+
+At these sizes a few percent of pixels meet a Gaussian whose alpha lies within
+float32 rounding of the 1/255 threshold (the oracle flags them); those pixels
+are held to a looser bound instead of the 2e-3 tolerance."""
+import numpy as np
+import pytest
+
+import oracle as O
+from scenegen import make_scene, mixed_batch_cameras, quantize_attributes, walk_cameras
+from tests.gpu_helpers import clear_tau, compare_cut, compare_image, compare_tile_lists
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FLAG_FRAC = 0.10          # flagged pixels allowed at full size
+FLAGGED_TOL = 0.05        # bound on flagged pixels (one threshold decision flipped)
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _check(img, ref):
+    emax, frac = compare_image(img, ref, max_flag_frac=FLAG_FRAC)
+    err = np.abs(np.asarray(img, np.float64) - ref.image)
+    assert float(err.max()) <= FLAGGED_TOL, f"flagged pixel off by {float(err.max()):.3e}"
+    mse = float(np.mean(err ** 2))
+    peak = float(ref.image.max())
+    psnr = 10.0 * np.log10(peak * peak / mse) if mse > 0 else np.inf
+    return emax, frac, psnr
+
+
+@pytest.fixture(scope="module")
+def floor4m():
+    return make_scene("floor4m")
+
+
+def test_floor1m_plain_fp32_views():
+    """1M leaves, 640x480, tau 0 / 3 / 6 px, the plain per-view FP32 path:
+    pixels within 2e-3, cuts bit-exact, one view's tile lists bit-exact."""
+    _need_gpu()
+    from paper_2603_15186_gb300 import Renderer
+    scene = make_scene("floor1m")
+    R = Renderer(device=0)
+    R.load_scene(scene)
+    R.set_mode("plain")
+    cams = walk_cameras(scene, 3, 41, 640, 480, fx=600.0, tau=0.0)
+    for c, tau in zip(cams, (0.0, 3.0, 6.0)):
+        c.tau = tau
+    cams = [clear_tau(scene, c) for c in cams]
+    imgs = [t.cpu().numpy() for t in R.render(cams)]
+    for cam, img in zip(cams, imgs):
+        ref = O.render(scene, cam)
+        assert ref.near.sum() == 0
+        _check(img, ref)
+    ids, off = R.select_cut(cams)
+    ids, off = ids.cpu().numpy(), off.cpu().numpy()
+    for i, cam in enumerate(cams):
+        compare_cut(ids[off[i]:off[i + 1]], scene, cam)
+    R.render([cams[1]])
+    ref = O.render(scene, cams[1])
+    rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
+    checked, _ = compare_tile_lists(rng, nodes, ref, (16, 16))
+    assert checked > 100_000
+    R.close()
+
+
+@pytest.mark.parametrize("dtype,poses", [("f16", 4), ("bf16", 1)])
+def test_floor4m_reduced_precision_720p(floor4m, dtype, poses):
+    """4M leaves, 1280x720, tau = 3 px, attributes stored in FP16 / BF16: the
+    oracle sees exactly the stored values."""
+    _need_gpu()
+    from paper_2603_15186_gb300 import Renderer
+    stored, deq = quantize_attributes(floor4m, dtype)
+    R = Renderer(device=0)
+    R.load_scene(floor4m, attr_dtype=dtype, stored=stored)
+    cams = [clear_tau(floor4m, c)
+            for c in walk_cameras(floor4m, poses, 51, 1280, 720, fx=1200.0, tau=3.0)]
+    imgs = [t.cpu().numpy() for t in R.render(cams)]
+    sa = O.SceneArrays(floor4m, overrides=deq)
+    for cam, img in zip(cams, imgs):
+        ref = O.render(sa, cam)
+        assert ref.near.sum() == 0
+        _, _, psnr = _check(img, ref)
+        assert psnr > 50.0, psnr
+    R.close()
+
+
+def test_floor4m_batch256_benchmark_configuration(floor4m):
+    """The benchmark's workload and launch configuration: 256 cameras of
+    mixed resolution and tau in one batched, graph-captured render with the
+    autotuned tile and staging depth. Three sampled cameras (one per
+    resolution) against the oracle; a graph replay and sixteen cameras
+    rendered alone give the same bits."""
+    _need_gpu()
+    from paper_2603_15186_gb300 import Renderer
+    stored, deq = quantize_attributes(floor4m, "f16")
+    R = Renderer(device=0)
+    R.load_scene(floor4m, attr_dtype="f16", stored=stored)
+    cams = mixed_batch_cameras(floor4m, 256, 1002)
+    sample = []
+    for res in (320, 640, 1280):
+        i = next(k for k, c in enumerate(cams) if c.width == res)
+        cams[i] = clear_tau(floor4m, cams[i])
+        sample.append(i)
+    R.autotune(cams, reps=1)
+    imgs = R.render(cams)
+    first = [t.cpu().numpy() for t in imgs]
+    again = [t.cpu().numpy() for t in R.render(cams)]
+    st = R.stats()
+    assert st["graph_replayed"] == 1 and st["sub_batches"] > 1
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)
+    sa = O.SceneArrays(floor4m, overrides=deq)
+    for i in sample:
+        ref = O.render(sa, cams[i])
+        assert ref.near.sum() == 0
+        _check(first[i], ref)
+    rng = np.random.default_rng(3)
+    for i in rng.choice(len(cams), 16, replace=False):
+        alone = R.render([cams[int(i)]])[0].cpu().numpy()
+        assert np.array_equal(alone, first[int(i)])
+    R.close()
+
+
+def test_floor8m_serving_sampled():
+    """8M leaves resident, requests from many agents at mixed resolutions
+    served by continuous batching: each served image equals its camera
+    rendered alone, and a sampled request matches the oracle."""
+    _need_gpu()
+    from paper_2603_15186_gb300 import Renderer, Server
+    scene = make_scene("floor8m")
+    stored, deq = quantize_attributes(scene, "f16")
+    R = Renderer(device=0)
+    R.load_scene(scene, attr_dtype="f16", stored=stored)
+    cams = mixed_batch_cameras(scene, 64, 88, n_walkers=64)
+    probe = next(k for k, c in enumerate(cams) if c.width == 320)
+    cams[probe] = clear_tau(scene, cams[probe])
+    S = Server(R, lanes=2, max_cams=32)
+    imgs = [torch.zeros((3, c.height, c.width), device="cuda") for c in cams]
+    for c, im in zip(cams, imgs):
+        S.submit(c, im)
+    S.wait_all()
+    st = S.stats()
+    S.stop()
+    assert st["completed"] == len(cams) and st["failed"] == 0
+    assert st["launches"] < st["submitted"]
+    for k in list(range(0, len(cams), 8)) + [probe]:
+        alone = R.render([cams[k]])[0]
+        assert torch.equal(alone, imgs[k]), k
+    ref = O.render(O.SceneArrays(scene, overrides=deq), cams[probe])
+    assert ref.near.sum() == 0
+    _check(imgs[probe].cpu().numpy(), ref)
+    R.close()
