@@ -48,6 +48,10 @@ def parse():
                     help="seconds of simulated agent load for the serving leg (0: skip)")
     ap.add_argument("--serving-scene", default="floor8m")
     ap.add_argument("--cpu-cams", type=int, default=3)
+    ap.add_argument("--record-capacity", type=int, default=1 << 27,
+                    help="record slots of the work buffers (smaller for profiling runs)")
+    ap.add_argument("--pair-capacity", type=int, default=(1 << 30) + (1 << 29),
+                    help="(tile, Gaussian) pair slots of the work buffers")
     return ap.parse_args()
 
 
@@ -206,7 +210,7 @@ def run_ours(args, world, rank, local, pg):
     tiles = sum(-(-c.width // tw) * -(-c.height // th) for c in cams)
 
     R = Renderer(device=local, tile=(tw, th), batch=args.batch, cut_capacity=1 << 27,
-                 record_capacity=1 << 27, pair_capacity=(1 << 30) + (1 << 29))
+                 record_capacity=args.record_capacity, pair_capacity=args.pair_capacity)
     R.load_scene(scene, attr_dtype="f16", stored=stored)
     R.set_mode("batched")
     R.set_stage_timing(not args.no_stage_timing)

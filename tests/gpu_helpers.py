@@ -76,3 +76,16 @@ def compare_tile_lists(gpu_ranges, gpu_nodes, ref, tile):
         assert g == o, f"tile {t}: lists differ (first mismatch at {next((i for i,(x,y) in enumerate(zip(g,o)) if x!=y), min(len(g),len(o)))})"
         checked += len(o)
     return checked, len(unc)
+
+
+def oracle_on_gpu_cut(R, cut_scene, scene, cam, tile=(16, 16)):
+    """Oracle render of the cut the GPU selects for ``cam``, once that cut is
+    checked to equal the oracle's on every decision away from the tau
+    threshold (where either choice is allowed). ``cut_scene`` holds the
+    hierarchy, ``scene`` the attributes the oracle renders (for example the
+    dequantised FP16 values). Large scenes nearly always have some node within
+    1e-5 of tau, so this replaces nudging tau at full size."""
+    ids, off = R.select_cut([cam])
+    gpu = ids[: int(off[1].item())].cpu().numpy()
+    compare_cut(gpu, cut_scene, cam)
+    return O.render(scene, cam, tile=tile, ids=gpu.astype(np.int32))

@@ -5,7 +5,9 @@ batched, graph-captured, autotuned tile and staging depth), and the 8M-leaf
 two-wing floor served to many agents. The oracle renders sampled views whole;
 the rest of a batch is checked by properties that hold at any size (every
 image equals its camera rendered alone, and a graph replay gives the same
-bits).
+bits). The oracle renders the cut the GPU selected once that cut is checked
+against the oracle's own (bit-exact away from the tau threshold), since a
+scene this large nearly always has some node within 1e-5 of tau.
 
 At these sizes a few percent of pixels meet a Gaussian whose alpha lies within
 float32 rounding of the 1/255 threshold (the oracle flags them); those pixels
@@ -15,7 +17,7 @@ import pytest
 
 import oracle as O
 from scenegen import make_scene, mixed_batch_cameras, quantize_attributes, walk_cameras
-from tests.gpu_helpers import clear_tau, compare_cut, compare_image, compare_tile_lists
+from tests.gpu_helpers import compare_cut, compare_image, compare_tile_lists, oracle_on_gpu_cut
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +42,11 @@ def _check(img, ref):
     return emax, frac, psnr
 
 
+def st_tile(R):
+    st = R.stats()
+    return st["tile_w"], st["tile_h"]
+
+
 @pytest.fixture(scope="module")
 def floor4m():
     return make_scene("floor4m")
@@ -57,18 +64,16 @@ def test_floor1m_plain_fp32_views():
     cams = walk_cameras(scene, 3, 41, 640, 480, fx=600.0, tau=0.0)
     for c, tau in zip(cams, (0.0, 3.0, 6.0)):
         c.tau = tau
-    cams = [clear_tau(scene, c) for c in cams]
     imgs = [t.cpu().numpy() for t in R.render(cams)]
-    for cam, img in zip(cams, imgs):
-        ref = O.render(scene, cam)
-        assert ref.near.sum() == 0
+    refs = [oracle_on_gpu_cut(R, scene, scene, cam) for cam in cams]
+    for img, ref in zip(imgs, refs):
         _check(img, ref)
     ids, off = R.select_cut(cams)
     ids, off = ids.cpu().numpy(), off.cpu().numpy()
     for i, cam in enumerate(cams):
         compare_cut(ids[off[i]:off[i + 1]], scene, cam)
     R.render([cams[1]])
-    ref = O.render(scene, cams[1])
+    ref = refs[1]
     rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
     checked, _ = compare_tile_lists(rng, nodes, ref, (16, 16))
     assert checked > 100_000
@@ -84,13 +89,11 @@ def test_floor4m_reduced_precision_720p(floor4m, dtype, poses):
     stored, deq = quantize_attributes(floor4m, dtype)
     R = Renderer(device=0)
     R.load_scene(floor4m, attr_dtype=dtype, stored=stored)
-    cams = [clear_tau(floor4m, c)
-            for c in walk_cameras(floor4m, poses, 51, 1280, 720, fx=1200.0, tau=3.0)]
+    cams = walk_cameras(floor4m, poses, 51, 1280, 720, fx=1200.0, tau=3.0)
     imgs = [t.cpu().numpy() for t in R.render(cams)]
     sa = O.SceneArrays(floor4m, overrides=deq)
     for cam, img in zip(cams, imgs):
-        ref = O.render(sa, cam)
-        assert ref.near.sum() == 0
+        ref = oracle_on_gpu_cut(R, floor4m, sa, cam)
         _, _, psnr = _check(img, ref)
         assert psnr > 50.0, psnr
     R.close()
@@ -108,11 +111,7 @@ def test_floor4m_batch256_benchmark_configuration(floor4m):
     R = Renderer(device=0)
     R.load_scene(floor4m, attr_dtype="f16", stored=stored)
     cams = mixed_batch_cameras(floor4m, 256, 1002)
-    sample = []
-    for res in (320, 640, 1280):
-        i = next(k for k, c in enumerate(cams) if c.width == res)
-        cams[i] = clear_tau(floor4m, cams[i])
-        sample.append(i)
+    sample = [next(k for k, c in enumerate(cams) if c.width == res) for res in (320, 640, 1280)]
     R.autotune(cams, reps=1)
     imgs = R.render(cams)
     first = [t.cpu().numpy() for t in imgs]
@@ -123,9 +122,7 @@ def test_floor4m_batch256_benchmark_configuration(floor4m):
         assert np.array_equal(a, b)
     sa = O.SceneArrays(floor4m, overrides=deq)
     for i in sample:
-        ref = O.render(sa, cams[i])
-        assert ref.near.sum() == 0
-        _check(first[i], ref)
+        _check(first[i], oracle_on_gpu_cut(R, floor4m, sa, cams[i], tile=tuple(st_tile(R))))
     rng = np.random.default_rng(3)
     for i in rng.choice(len(cams), 16, replace=False):
         alone = R.render([cams[int(i)]])[0].cpu().numpy()
@@ -145,7 +142,6 @@ def test_floor8m_serving_sampled():
     R.load_scene(scene, attr_dtype="f16", stored=stored)
     cams = mixed_batch_cameras(scene, 64, 88, n_walkers=64)
     probe = next(k for k, c in enumerate(cams) if c.width == 320)
-    cams[probe] = clear_tau(scene, cams[probe])
     S = Server(R, lanes=2, max_cams=32)
     imgs = [torch.zeros((3, c.height, c.width), device="cuda") for c in cams]
     for c, im in zip(cams, imgs):
@@ -158,7 +154,6 @@ def test_floor8m_serving_sampled():
     for k in list(range(0, len(cams), 8)) + [probe]:
         alone = R.render([cams[k]])[0]
         assert torch.equal(alone, imgs[k]), k
-    ref = O.render(O.SceneArrays(scene, overrides=deq), cams[probe])
-    assert ref.near.sum() == 0
+    ref = oracle_on_gpu_cut(R, scene, O.SceneArrays(scene, overrides=deq), cams[probe])
     _check(imgs[probe].cpu().numpy(), ref)
     R.close()
