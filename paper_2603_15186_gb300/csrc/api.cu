@@ -298,6 +298,11 @@ ngs_status epoch_guard(ngs_ctx *c, cudaStream_t st, uint64_t need) {
     return NGS_OK;
 }
 
+// tile shapes the compositing kernel is built for
+bool tile_supported(int w, int h) {
+    return (w == 8 && h == 8) || (w == 16 && h == 8) || (w == 16 && h == 16) || (w == 16 && h == 32);
+}
+
 bool camera_ok(const ngs_camera &k) {
     if (k.width <= 0 || k.height <= 0 || k.width > 32768 || k.height > 32768) return false;
     const float v[] = {k.pos[0], k.pos[1], k.pos[2], k.fx, k.fy, k.cx, k.cy, k.tau};
@@ -641,6 +646,7 @@ ngs_status render_common(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
     if (!c) return NGS_ERR_INVALID_ARG;
     if (!c->loaded) return NGS_ERR_NOT_LOADED;
     if (!cams || !images || n_cams <= 0 || n_cams > kMaxCamsPerCall) return NGS_ERR_INVALID_ARG;
+    if (!tile_supported(c->tile_w, c->tile_h)) return NGS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (!camera_ok(cams[i]) || !images[i]) return NGS_ERR_INVALID_ARG;
     ngs_status s = ensure_work(c);
@@ -750,8 +756,7 @@ NGS_API ngs_status ngs_create(const ngs_config *cfg, ngs_ctx **out) {
     if (c.record_capacity <= 0) c.record_capacity = (int64_t)1 << 26;
     if (c.pair_capacity <= 0) c.pair_capacity = (int64_t)1 << 29;
     if (c.max_tiles_per_batch <= 0) c.max_tiles_per_batch = 1 << 16;
-    const bool tile_ok = (c.tile_w == 16 && c.tile_h == 16) || (c.tile_w == 16 && c.tile_h == 8) ||
-                         (c.tile_w == 8 && c.tile_h == 8);
+    const bool tile_ok = tile_supported(c.tile_w, c.tile_h);
     if (!tile_ok || (c.batch != 64 && c.batch != 128 && c.batch != 256)) return NGS_ERR_INVALID_ARG;
     if (c.cut_capacity >= ((int64_t)1 << 31) || c.record_capacity >= ((int64_t)1 << 31) ||
         c.pair_capacity >= ((int64_t)1 << 31) || c.max_tiles_per_batch > (1 << 24))
@@ -808,7 +813,9 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
     case NGS_OPT_TILE_H: {
         int tw = opt == NGS_OPT_TILE_W ? (int)v : c->tile_w;
         int th = opt == NGS_OPT_TILE_H ? (int)v : c->tile_h;
-        if (!((tw == 16 || tw == 8) && (th == 16 || th == 8))) return NGS_ERR_INVALID_ARG;
+        // either dimension may be set first: an unsupported pair is held until
+        // the other dimension completes it, and a render rejects it
+        if (!(tw == 8 || tw == 16) || !(th == 8 || th == 16 || th == 32)) return NGS_ERR_INVALID_ARG;
         c->tile_w = tw; c->tile_h = th;
         drop_graph(c);
         return NGS_OK;
@@ -1061,7 +1068,7 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
                                 ngs_tune_result *out) {
     if (!c || !out || reps <= 0) return NGS_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
-    static const int kTiles[3][2] = {{8, 8}, {16, 8}, {16, 16}};
+    static const int kTiles[4][2] = {{8, 8}, {16, 8}, {16, 16}, {16, 32}};
     static const int kBatches[3] = {64, 128, 256};
     cudaStream_t st = (cudaStream_t)stream;
     const int mode = c->mode;
@@ -1075,7 +1082,7 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
     float best = 3.4e38f;
     int bt = 2, bb = 1;
     ngs_status s = NGS_OK;
-    for (int t = 0; t < 3 && s == NGS_OK; ++t)
+    for (int t = 0; t < 4 && s == NGS_OK; ++t)
         for (int b = 0; b < 3 && s == NGS_OK; ++b) {
             c->tile_w = kTiles[t][0];
             c->tile_h = kTiles[t][1];

@@ -378,6 +378,7 @@ static void set_attr_r() {
     set_attr<R, 8, 8, 64>(); set_attr<R, 8, 8, 128>(); set_attr<R, 8, 8, 256>();
     set_attr<R, 16, 8, 64>(); set_attr<R, 16, 8, 128>(); set_attr<R, 16, 8, 256>();
     set_attr<R, 16, 16, 64>(); set_attr<R, 16, 16, 128>(); set_attr<R, 16, 16, 256>();
+    set_attr<R, 16, 32, 64>(); set_attr<R, 16, 32, 128>(); set_attr<R, 16, 32, 256>();
 }
 
 void composite_init_attributes() {
@@ -418,6 +419,9 @@ static void launch_r(int tile_w, int tile_h, int batch, const DevCamera *cams, i
     else if (tile_w == 16 && tile_h == 8)
         launch_b<R, 16, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
                            grid, err, work64, st);
+    else if (tile_w == 16 && tile_h == 32)
+        launch_b<R, 16, 32>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
+                            grid, err, work64, st);
     else
         launch_b<R, 16, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
                             grid, err, work64, st);
@@ -453,6 +457,7 @@ template <typename R>
 static int occ_r(int tile_w, int tile_h, int batch) {
     if (tile_w == 8 && tile_h == 8) return occ_b<R, 8, 8>(batch);
     if (tile_w == 16 && tile_h == 8) return occ_b<R, 16, 8>(batch);
+    if (tile_w == 16 && tile_h == 32) return occ_b<R, 16, 32>(batch);
     return occ_b<R, 16, 16>(batch);
 }
 
