@@ -100,7 +100,8 @@ typedef struct ngs_ctx ngs_ctx;
  * NGS_ERR_CAPACITY and leaves the affected images undefined. */
 typedef struct {
     int32_t device;
-    int32_t tile_w, tile_h;          /* tile shape: 8x8, 16x8, 16x16 or 16x32 (default 16x16) */
+    int32_t tile_w, tile_h;          /* tile shape: 8x8, 16x8, 16x16, 16x32, 32x16 or 32x32
+                                        (default 16x16) */
     int32_t batch;                   /* records staged per compositing round: 64, 128, 256 (default 128) */
     int64_t cut_capacity;            /* default 2^27 */
     int64_t record_capacity;         /* default 2^26 */
@@ -116,8 +117,9 @@ typedef struct {
 enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
        NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7 };
-/* NGS_OPT_TILE_W / NGS_OPT_TILE_H: tile width 8 or 16, height 8, 16 or 32;
- * a render accepts the shapes 8x8, 16x8, 16x16 and 16x32 (INVALID_ARG else).
+/* NGS_OPT_TILE_W / NGS_OPT_TILE_H: tile width 8, 16 or 32, height 8, 16 or 32;
+ * a render accepts the shapes 8x8, 16x8, 16x16, 16x32, 32x16 and 32x32
+ * (INVALID_ARG else).
  * Every shape gives the same pixels.
  * NGS_OPT_BLOCK_CULL (default 1): skip, per camera, node blocks that provably
  * hold no visible Gaussian; 0 tests every node (same images, slower). */
@@ -184,15 +186,16 @@ NGS_API ngs_status ngs_synchronize(ngs_ctx *ctx, void *stream);
 /* Result of ngs_autotune: the chosen tile shape and staging batch, and the
  * measured milliseconds of one render of the given cameras for every
  * candidate (index = tile index * 3 + batch index over tiles {8x8, 16x8,
- * 16x16, 16x32} and batches {64, 128, 256}). */
+ * 16x16, 16x32, 32x16, 32x32} and batches {64, 128, 256}). */
 typedef struct {
     int32_t tile_w, tile_h, batch;
     int32_t reserved;
-    float ms[12];
+    float ms[18];
 } ngs_tune_result;
 
 /* Autotuner of the batched path: renders `cams` (into d_images) with every
- * tile shape {8x8, 16x8, 16x16, 16x32} and compositing batch {64, 128, 256}, each
+ * tile shape {8x8, 16x8, 16x16, 16x32, 32x16, 32x32} and compositing batch
+ * {64, 128, 256}, each
  * captured in its CUDA graph, warmed up and timed over `reps` replays with
  * CUDA events on `stream`, then keeps the fastest setting in the context.
  * All candidates give bit-identical images. Synchronous. */

@@ -58,7 +58,7 @@ class Config(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
-                ("reserved", C.c_int32), ("ms", C.c_float * 12)]
+                ("reserved", C.c_int32), ("ms", C.c_float * 18)]
 
 
 class ServerConfig(C.Structure):

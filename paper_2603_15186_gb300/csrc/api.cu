@@ -300,7 +300,8 @@ ngs_status epoch_guard(ngs_ctx *c, cudaStream_t st, uint64_t need) {
 
 // tile shapes the compositing kernel is built for
 bool tile_supported(int w, int h) {
-    return (w == 8 && h == 8) || (w == 16 && h == 8) || (w == 16 && h == 16) || (w == 16 && h == 32);
+    return (w == 8 && h == 8) || (w == 16 && h == 8) || (w == 16 && h == 16) ||
+           (w == 16 && h == 32) || (w == 32 && h == 16) || (w == 32 && h == 32);
 }
 
 bool camera_ok(const ngs_camera &k) {
@@ -815,7 +816,8 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         int th = opt == NGS_OPT_TILE_H ? (int)v : c->tile_h;
         // either dimension may be set first: an unsupported pair is held until
         // the other dimension completes it, and a render rejects it
-        if (!(tw == 8 || tw == 16) || !(th == 8 || th == 16 || th == 32)) return NGS_ERR_INVALID_ARG;
+        if (!(tw == 8 || tw == 16 || tw == 32) || !(th == 8 || th == 16 || th == 32))
+            return NGS_ERR_INVALID_ARG;
         c->tile_w = tw; c->tile_h = th;
         drop_graph(c);
         return NGS_OK;
@@ -1068,7 +1070,7 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
                                 ngs_tune_result *out) {
     if (!c || !out || reps <= 0) return NGS_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
-    static const int kTiles[4][2] = {{8, 8}, {16, 8}, {16, 16}, {16, 32}};
+    static const int kTiles[6][2] = {{8, 8}, {16, 8}, {16, 16}, {16, 32}, {32, 16}, {32, 32}};
     static const int kBatches[3] = {64, 128, 256};
     cudaStream_t st = (cudaStream_t)stream;
     const int mode = c->mode;
@@ -1082,7 +1084,7 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
     float best = 3.4e38f;
     int bt = 2, bb = 1;
     ngs_status s = NGS_OK;
-    for (int t = 0; t < 4 && s == NGS_OK; ++t)
+    for (int t = 0; t < 6 && s == NGS_OK; ++t)
         for (int b = 0; b < 3 && s == NGS_OK; ++b) {
             c->tile_w = kTiles[t][0];
             c->tile_h = kTiles[t][1];

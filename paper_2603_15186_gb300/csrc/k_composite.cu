@@ -93,21 +93,29 @@ struct PairRec {
     float4 bA;
 };
 
+// A warp renders a WBW x BH block (64 pixels, two per thread) of the tile:
+// 8x8 in 8-wide tiles, 16x4 otherwise; 32-wide tiles hold two blocks side by
+// side. NCB 16-pixel column blocks per tile row (one for 8 and 16 wide tiles).
 template <typename R, int TW, int TH, int BATCH>
 struct CompLayout {
-    static constexpr int BH = 64 / TW;                 // rows of a warp's block
-    static constexpr int NW = TH / BH;                 // warps per tile
+    static constexpr int WBW = TW < 16 ? TW : 16;      // width of a warp's block
+    static constexpr int BH = 64 / WBW;                // rows of a warp's block
+    static constexpr int NWX = TW / WBW;               // warp blocks across the tile
+    static constexpr int NW = NWX * (TH / BH);         // warps per tile
     static constexpr int NT = 32 * NW;                 // threads: two pixels each
     static constexpr int NRP = TH / 2;                 // row pairs per tile
+    static constexpr int NCB = TW < 16 ? 1 : TW / 16;  // 16-pixel column blocks
+    static constexpr int NCOEF = NRP * NCB;            // coefficient sets per record
     static constexpr int kListStride = BATCH + 4;      // u32 entries per warp list
     static constexpr size_t rec_off = 0;
     static constexpr size_t coef_off = rec_off + (size_t)BATCH * sizeof(R);
-    static constexpr size_t pair_off = coef_off + (size_t)(BATCH + 1) * NRP * sizeof(float4);
+    static constexpr size_t pair_off = coef_off + (size_t)(BATCH + 1) * NCOEF * sizeof(float4);
     static constexpr size_t box_off = pair_off + (size_t)(BATCH + 1) * sizeof(PairRec);
     static constexpr size_t list_off = box_off + (size_t)BATCH * sizeof(float4);
     static constexpr size_t bytes = list_off + (size_t)NW * kListStride * sizeof(uint32_t);
-    static_assert(TW == 8 || TW == 16, "tile width 8 or 16");
+    static_assert(TW == 8 || TW == 16 || TW == 32, "tile width 8, 16 or 32");
     static_assert(TH % BH == 0, "tile of whole warp blocks");
+    static_assert(NT <= 1024, "at most 1024 threads");
     static_assert(BATCH % 4 == 0, "lists padded to groups of four");
 };
 
@@ -120,13 +128,15 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
             unsigned long long *work64) {
     using Lay = CompLayout<R, TW, TH, BATCH>;
-    constexpr int NT = Lay::NT, NRP = Lay::NRP, BH = Lay::BH;
+    constexpr int NT = Lay::NT, BH = Lay::BH, WBW = Lay::WBW, NWX = Lay::NWX;
+    constexpr int NCB = Lay::NCB, NCOEF = Lay::NCOEF;
     constexpr int kPer = (BATCH + NT - 1) / NT;   // records gathered per thread per round
     __shared__ uint32_t s_wsum[Lay::NW];
     // dynamic shared memory, per round: the tile's kept records; per (record,
-    // pair of tile rows r, r + 1) the exponent as a quadratic in the pixel's
-    // column offset lx within its 16-pixel column block, q = (A lx + a1) lx + a0,
-    // stored (a1_r, a1_r+1, a0_r, a0_r+1); the records' PairRec; their reach
+    // pair of tile rows r, r + 1, 16-pixel column block) the exponent as a
+    // quadratic in the pixel's column offset lx within its column block,
+    // q = (A lx + a1) lx + a0, stored (a1_r, a1_r+1, a0_r, a0_r+1) at
+    // (record * NRP + row pair) * NCB + block; the records' PairRec; their reach
     // boxes; one record list per warp. Index BATCH holds a sentinel record
     // (q = -inf everywhere).
     extern __shared__ float4 smem_dyn[];
@@ -139,13 +149,14 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
     __shared__ uint32_t s_tile;
     if (*err) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // warp -> TW x BH pixel block of the tile; thread -> the pixels (lx, ly)
+    // warp -> WBW x BH pixel block of the tile; thread -> the pixels (lx, ly)
     // and (lx, ly + 1)
-    const int lx = lane % TW, by = warp * BH, ly = by + 2 * (lane / TW);
-    const int rp = ly >> 1;
+    const int bx = (warp % NWX) * WBW, by = (warp / NWX) * BH;
+    const int lx = bx + lane % WBW, ly = by + 2 * (lane / WBW);
+    const int coef_slot = (ly >> 1) * NCB + (TW < 16 ? 0 : lx >> 4);
     uint32_t *my_list = s_list + warp * Lay::kListStride;
     const float inf = __int_as_float(0x7f800000);
-    if (tid < NRP) s_coef[BATCH * NRP + tid] = make_float4(0.0f, 0.0f, -inf, -inf);
+    if (tid < NCOEF) s_coef[BATCH * NCOEF + tid] = make_float4(0.0f, 0.0f, -inf, -inf);
     if (tid == 0) {
         s_pair[BATCH].rg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         s_pair[BATCH].bA = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -180,6 +191,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         // also where it overhangs the image)
         const float tile_x0c = (float)x0 + 0.5f, tile_x1c = (float)(x0 + TW) - 0.5f;
         const float tile_y0c = (float)y0 + 0.5f, tile_y1c = (float)(y0 + TH) - 0.5f;
+        const float blk_x0c = (float)(x0 + bx) + 0.5f, blk_x1c = blk_x0c + (float)(WBW - 1);
         const float blk_y0c = (float)(y0 + by) + 0.5f, blk_y1c = blk_y0c + (float)(BH - 1);
         const float lxf = (float)(px & 15);
         const float2 lx2 = make_float2(lxf, lxf);
@@ -265,7 +277,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     bool hit = false;
                     if (j < (int)nk) {
                         const float4 b = s_box[j];
-                        hit = b.y >= tile_x0c && b.x <= tile_x1c && b.w >= blk_y0c && b.z <= blk_y1c;
+                        hit = b.y >= blk_x0c && b.x <= blk_x1c && b.w >= blk_y0c && b.z <= blk_y1c;
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, hit);
                     if (hit) my_list[len + __popc(bal & lanemask_lt())] = (uint32_t)j;
@@ -273,11 +285,12 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                 }
                 if (lane < ((4 - (len & 3)) & 3)) my_list[len + lane] = (uint32_t)BATCH;
             }
-            for (int e = tid; e < (int)nk * NRP; e += NT) {
-                const int j = e / NRP, p = e - j * NRP;
+            for (int e = tid; e < (int)nk * NCOEF; e += NT) {
+                const int j = e / NCOEF, rem = e - j * NCOEF;
+                const int p = rem / NCB, cb = rem - p * NCB;
                 const R &rr = s_rec[j];
                 const float A = rr.a.z, B = rr.a.w, C = rr.b.x, L = rr.b.y;
-                const float dxt = __fsub_rn(xref, rr.a.x);
+                const float dxt = __fsub_rn(xref + (float)(16 * cb), rr.a.x);
                 const float axb = __fadd_rn(A, A);
                 float a1[2], a0[2];
 #pragma unroll
@@ -287,7 +300,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     a1[h] = __fmaf_rn(axb, dxt, bdy);
                     a0[h] = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt, __fmaf_rn(C, __fmul_rn(dy, dy), L));
                 }
-                s_coef[j * NRP + p] = make_float4(a1[0], a1[1], a0[0], a0[1]);
+                s_coef[j * NCOEF + rem] = make_float4(a1[0], a1[1], a0[0], a0[1]);
             }
             __syncthreads();
             if (T2.x > 0.0f || T2.y > 0.0f) {
@@ -309,7 +322,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     float2 q[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float4 cf = s_coef[jj[u] * NRP + rp];
+                        const float4 cf = s_coef[jj[u] * NCOEF + coef_slot];
                         const float4 bA = s_pair[jj[u]].bA;
                         const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
                         q[u] = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
@@ -379,6 +392,8 @@ static void set_attr_r() {
     set_attr<R, 16, 8, 64>(); set_attr<R, 16, 8, 128>(); set_attr<R, 16, 8, 256>();
     set_attr<R, 16, 16, 64>(); set_attr<R, 16, 16, 128>(); set_attr<R, 16, 16, 256>();
     set_attr<R, 16, 32, 64>(); set_attr<R, 16, 32, 128>(); set_attr<R, 16, 32, 256>();
+    set_attr<R, 32, 16, 64>(); set_attr<R, 32, 16, 128>(); set_attr<R, 32, 16, 256>();
+    set_attr<R, 32, 32, 64>(); set_attr<R, 32, 32, 128>(); set_attr<R, 32, 32, 256>();
 }
 
 void composite_init_attributes() {
@@ -422,6 +437,12 @@ static void launch_r(int tile_w, int tile_h, int batch, const DevCamera *cams, i
     else if (tile_w == 16 && tile_h == 32)
         launch_b<R, 16, 32>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
                             grid, err, work64, st);
+    else if (tile_w == 32 && tile_h == 16)
+        launch_b<R, 32, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
+                            grid, err, work64, st);
+    else if (tile_w == 32 && tile_h == 32)
+        launch_b<R, 32, 32>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
+                            grid, err, work64, st);
     else
         launch_b<R, 16, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
                             grid, err, work64, st);
@@ -458,6 +479,8 @@ static int occ_r(int tile_w, int tile_h, int batch) {
     if (tile_w == 8 && tile_h == 8) return occ_b<R, 8, 8>(batch);
     if (tile_w == 16 && tile_h == 8) return occ_b<R, 16, 8>(batch);
     if (tile_w == 16 && tile_h == 32) return occ_b<R, 16, 32>(batch);
+    if (tile_w == 32 && tile_h == 16) return occ_b<R, 32, 16>(batch);
+    if (tile_w == 32 && tile_h == 32) return occ_b<R, 32, 32>(batch);
     return occ_b<R, 16, 16>(batch);
 }
 

@@ -158,7 +158,8 @@ class Renderer:
         res = _lib.TuneResult()
         check(self.L.ngs_autotune(self.h, arr, len(cams), ptrs, int(reps), _stream_ptr(stream),
                                   C.byref(res)), "ngs_autotune")
-        names = [f"{tw}x{th}/{b}" for tw, th in ((8, 8), (16, 8), (16, 16), (16, 32))
+        names = [f"{tw}x{th}/{b}" for tw, th in ((8, 8), (16, 8), (16, 16), (16, 32), (32, 16),
+                                                  (32, 32))
                  for b in (64, 128, 256)]
         return {"tile": (res.tile_w, res.tile_h), "batch": res.batch,
                 "ms": dict(zip(names, [round(x, 3) for x in res.ms]))}

@@ -166,7 +166,7 @@ def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
     base = [t.cpu().numpy() for t in R.render(cams)]
     again = [t.cpu().numpy() for t in R.render(cams)]   # replays the captured graph
     assert R.stats()["graph_replayed"] == 1
-    for tile in [(8, 8), (16, 8), (16, 32)]:
+    for tile in [(8, 8), (16, 8), (16, 32), (32, 16), (32, 32)]:
         for batch in [64, 256]:
             R.set_tile(*tile)
             R.set_batch(batch)
@@ -208,8 +208,9 @@ def test_autotune_keeps_pixels(R, small_floor):
     R.set_batch(128)
     base = [t.cpu().numpy() for t in R.render(cams)]
     res = R.autotune(cams, reps=1)
-    assert res["tile"] in [(8, 8), (16, 8), (16, 16), (16, 32)] and res["batch"] in (64, 128, 256)
-    assert all(v > 0 for v in res["ms"].values()) and len(res["ms"]) == 12
+    assert res["tile"] in [(8, 8), (16, 8), (16, 16), (16, 32), (32, 16), (32, 32)]
+    assert res["batch"] in (64, 128, 256)
+    assert all(v > 0 for v in res["ms"].values()) and len(res["ms"]) == 18
     out = [t.cpu().numpy() for t in R.render(cams)]
     st = R.stats()
     assert (st["tile_w"], st["tile_h"], st["batch"]) == (*res["tile"], res["batch"])
@@ -295,7 +296,7 @@ def test_unsupported_tile_shape_rejected(R, small_floor):
     from paper_2603_15186_gb300 import NgsError
     R.load_scene(small_floor)
     cam = walk_cameras(small_floor, 1, 5, 64, 48, fx=60.0, tau=0.0)[0]
-    R.set_tile(8, 16)            # both dimensions are valid alone, the pair is not built
+    R.set_tile(8, 32)            # both dimensions are valid alone, the pair is not built
     with pytest.raises(NgsError) as e:
         R.render([cam])
     assert e.value.status == 1
