@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--cams", type=int, default=256)
     ap.add_argument("--leaves", default="floor4m")
     ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--cta", default="0x0", help="compositing block (0x0: the tile)")
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -48,9 +49,9 @@ def parse():
                     help="seconds of simulated agent load for the serving leg (0: skip)")
     ap.add_argument("--serving-scene", default="floor8m")
     ap.add_argument("--cpu-cams", type=int, default=3)
-    ap.add_argument("--record-capacity", type=int, default=1 << 27,
+    ap.add_argument("--record-capacity", type=int, default=1 << 29,
                     help="record slots of the work buffers (smaller for profiling runs)")
-    ap.add_argument("--pair-capacity", type=int, default=(1 << 30) + (1 << 29),
+    ap.add_argument("--pair-capacity", type=int, default=(1 << 31) - (1 << 24),
                     help="(tile, Gaussian) pair slots of the work buffers")
     return ap.parse_args()
 
@@ -101,7 +102,8 @@ def config_dict(args, scene, cams, world):
             "nodes": int(scene.n_nodes), "cameras_per_step": len(cams),
             "resolutions": "320x240:640x480:1280x720 = 1:2:1", "tau_px": "U[2,8]",
             "mpix_per_step": round(pix / 1e6, 4), "attr_storage": "f16 sh/scale/opacity",
-            "tile": args.tile, "smem_batch": args.batch, "cuda_graph": True,
+            "tile": args.tile, "composite_block": args.cta, "smem_batch": args.batch,
+            "cuda_graph": True,
             "l2": "inputs exceed L2 (scene ~0.6 GB, pair buffers GBs)",
             "parallelism": f"replicas{world}"}
 
@@ -237,6 +239,7 @@ def run_ours(args, world, rank, local, pg):
     R = Renderer(device=local, tile=(tw, th), batch=args.batch, cut_capacity=1 << 27,
                  record_capacity=args.record_capacity, pair_capacity=args.pair_capacity)
     R.load_scene(scene, attr_dtype="f16", stored=stored)
+    R.set_cta(*(int(x) for x in args.cta.split("x")))
     R.set_mode("batched")
     R.set_stage_timing(not args.no_stage_timing)
     imgs = R.new_images(cams)
@@ -246,6 +249,7 @@ def run_ours(args, world, rank, local, pg):
         tune = R.autotune(cams, imgs, reps=2)
         tw, th = tune["tile"]
         args.tile, args.batch = f"{tw}x{th}", tune["batch"]
+        args.cta = "{}x{}".format(*tune["cta"])
         tiles = sum(-(-c.width // tw) * -(-c.height // th) for c in cams)
     for _ in range(max(args.warmup, 3)):
         R.render(cams, imgs)
@@ -364,6 +368,7 @@ def run_ours(args, world, rank, local, pg):
         P = Renderer(device=local, tile=(tw, th), batch=args.batch, cut_capacity=1 << 23,
                      record_capacity=1 << 23, pair_capacity=1 << 27)
         P.load_scene(scene, attr_dtype="f32")
+        P.set_cta(*(int(x) for x in args.cta.split("x")))
         P.set_mode("plain")
         plain_imgs = P.new_images(cams)
         P.render(cams[:8], plain_imgs[:8])

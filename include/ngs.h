@@ -116,11 +116,18 @@ typedef struct {
  * to the host between stages, no graph. Both compute identical pixels. */
 enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
-       NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7 };
+       NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7,
+       NGS_OPT_CTA_W = 8, NGS_OPT_CTA_H = 9 };
 /* NGS_OPT_TILE_W / NGS_OPT_TILE_H: tile width 8, 16 or 32, height 8, 16 or 32;
  * a render accepts the shapes 8x8, 16x8, 16x16, 16x32, 32x16 and 32x32
  * (INVALID_ARG else).
  * Every shape gives the same pixels.
+ * NGS_OPT_CTA_W / NGS_OPT_CTA_H (default 0 = the tile): the pixel block one
+ * compositing CTA covers. A tile may be composited as equal blocks of a
+ * supported shape that divides it (e.g. a 32x32 tile as four 16x16 blocks):
+ * binning and sorting work on the large tiles (fewer pairs), each block walks
+ * its tile's list and skips the Gaussians that cannot reach it. A shape that
+ * does not divide the tile is rejected at render (INVALID_ARG). Same pixels.
  * NGS_OPT_BLOCK_CULL (default 1): skip, per camera, node blocks that provably
  * hold no visible Gaussian; 0 tests every node (same images, slower). */
 
@@ -134,6 +141,7 @@ typedef struct {
     int32_t graph_replayed;  /* 1 if the last render replayed a captured graph */
     int32_t tile_w, tile_h, batch, mode;
     int32_t kernels;         /* kernel launches of the last render */
+    int32_t cta_w, cta_h;    /* compositing block of the last render */
     int32_t reserved;
 } ngs_stats;
 
@@ -183,22 +191,27 @@ NGS_API ngs_status ngs_selftest_wait_timeout(ngs_ctx *ctx, void *stream);
 /* Waits for the stream and returns (then clears) any latched device error. */
 NGS_API ngs_status ngs_synchronize(ngs_ctx *ctx, void *stream);
 
-/* Result of ngs_autotune: the chosen tile shape and staging batch, and the
- * measured milliseconds of one render of the given cameras for every
- * candidate (index = tile index * 3 + batch index over tiles {8x8, 16x8,
- * 16x16, 16x32, 32x16, 32x32} and batches {64, 128, 256}). */
+/* Candidates of ngs_autotune, as (binning tile / compositing block):
+ *   0 8x8/8x8      1 16x8/16x8     2 16x16/16x16   3 16x32/16x32
+ *   4 32x16/32x16  5 32x32/32x32   6 16x16/16x8    7 16x32/16x16
+ *   8 32x16/16x16  9 32x32/16x16  10 32x32/32x16  11 32x32/16x8
+ * each with the compositing batches {64, 128, 256}. */
+#define NGS_TUNE_SHAPES 12
+
+/* Result of ngs_autotune: the chosen tile shape, compositing block and staging
+ * batch, and the measured milliseconds of one render of the given cameras for
+ * every candidate (index = shape index * 3 + batch index). */
 typedef struct {
-    int32_t tile_w, tile_h, batch;
+    int32_t tile_w, tile_h, cta_w, cta_h, batch;
     int32_t reserved;
-    float ms[18];
+    float ms[NGS_TUNE_SHAPES * 3];
 } ngs_tune_result;
 
 /* Autotuner of the batched path: renders `cams` (into d_images) with every
- * tile shape {8x8, 16x8, 16x16, 16x32, 32x16, 32x32} and compositing batch
- * {64, 128, 256}, each
- * captured in its CUDA graph, warmed up and timed over `reps` replays with
- * CUDA events on `stream`, then keeps the fastest setting in the context.
- * All candidates give bit-identical images. Synchronous. */
+ * candidate shape and compositing batch, each captured in its CUDA graph,
+ * warmed up and timed over `reps` replays with CUDA events on `stream`, then
+ * keeps the fastest setting in the context. All candidates give bit-identical
+ * images. Synchronous. */
 NGS_API ngs_status ngs_autotune(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                                 float *const *d_images, int32_t reps, void *stream,
                                 ngs_tune_result *out);

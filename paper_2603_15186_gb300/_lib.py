@@ -13,6 +13,13 @@ NGS_MODE_BATCHED, NGS_MODE_PLAIN = 0, 1
 NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H, NGS_OPT_BATCH, NGS_OPT_GRAPH = 1, 2, 3, 4, 5
 NGS_OPT_STAGE_TIMING = 6
 NGS_OPT_BLOCK_CULL = 7
+NGS_OPT_CTA_W, NGS_OPT_CTA_H = 8, 9
+# (binning tile, compositing block) candidates of ngs_autotune, in its order
+TUNE_SHAPES = [((8, 8), (8, 8)), ((16, 8), (16, 8)), ((16, 16), (16, 16)), ((16, 32), (16, 32)),
+               ((32, 16), (32, 16)), ((32, 32), (32, 32)), ((16, 16), (16, 8)),
+               ((16, 32), (16, 16)), ((32, 16), (16, 16)), ((32, 32), (16, 16)),
+               ((32, 32), (32, 16)), ((32, 32), (16, 8))]
+TUNE_BATCHES = [64, 128, 256]
 STAGES = ["cut_preprocess", "gather_keys", "depth_hist", "depth_pass0", "depth_pass1", "depth_pass2",
           "depth_pass3", "pair_offsets", "duplicate", "tile_hist", "tile_pass0", "tile_pass1",
           "tile_pass2", "ranges", "composite"]
@@ -57,8 +64,9 @@ class Config(C.Structure):
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
-                ("reserved", C.c_int32), ("ms", C.c_float * 18)]
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("cta_w", C.c_int32),
+                ("cta_h", C.c_int32), ("batch", C.c_int32), ("reserved", C.c_int32),
+                ("ms", C.c_float * (3 * len(TUNE_SHAPES)))]
 
 
 class ServerConfig(C.Structure):
@@ -80,7 +88,7 @@ class Stats(C.Structure):
                 ("evaluations", C.c_int64), ("sub_batches", C.c_int32),
                 ("graph_replayed", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("batch", C.c_int32), ("mode", C.c_int32), ("kernels", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("cta_w", C.c_int32), ("cta_h", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None

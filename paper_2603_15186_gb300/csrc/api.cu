@@ -20,6 +20,7 @@ namespace {
 constexpr uint32_t kEpochStride = 32;   // epoch values reserved per sub-batch
 constexpr int kMaxCamsPerBatch = 1024;
 constexpr int kMaxCamsPerCall = 1 << 16;
+constexpr int kTuneShapes = NGS_TUNE_SHAPES;
 
 struct SubBatch {
     int c0, c1;          // cameras [c0, c1)
@@ -65,6 +66,7 @@ struct ngs_ctx {
     ngs_config cfg{};
     int mode = NGS_MODE_BATCHED;
     int tile_w = 16, tile_h = 16, batch = 128;
+    int cta_w = 0, cta_h = 0;          // block one compositing CTA covers (0: the tile)
     bool use_graph = true;
     bool block_cull = true;
     SceneDev scene;
@@ -304,6 +306,15 @@ bool tile_supported(int w, int h) {
            (w == 16 && h == 32) || (w == 32 && h == 16) || (w == 32 && h == 32);
 }
 
+// block one compositing CTA covers: the tile itself, or a compiled shape that
+// splits the tile into equal blocks
+int cta_w_of(const ngs_ctx *c) { return c->cta_w > 0 ? c->cta_w : c->tile_w; }
+int cta_h_of(const ngs_ctx *c) { return c->cta_h > 0 ? c->cta_h : c->tile_h; }
+bool split_supported(const ngs_ctx *c) {
+    const int w = cta_w_of(c), h = cta_h_of(c);
+    return tile_supported(w, h) && c->tile_w % w == 0 && c->tile_h % h == 0;
+}
+
 bool camera_ok(const ngs_camera &k) {
     if (k.width <= 0 || k.height <= 0 || k.width > 32768 || k.height > 32768) return false;
     const float v[] = {k.pos[0], k.pos[1], k.pos[2], k.fx, k.fy, k.cx, k.cy, k.tau};
@@ -337,13 +348,16 @@ int bits_for(uint32_t n) {
 
 // Splits cameras into sub-batches: at most kMaxCamsPerBatch cameras, at most
 // max_tiles tiles (one camera alone may exceed it), cut and record bounds
-// (every camera's cut holds at most n nodes) and an estimate of the pairs.
+// (a camera's cut is an antichain of the tree, so it holds at most as many
+// nodes as the tree has leaves) and an estimate of the pairs.
 std::vector<SubBatch> plan(ngs_ctx *c, std::vector<DevCamera> &cams, int max_cams_per_batch) {
     std::vector<SubBatch> out;
-    const int64_t n = c->scene.n;
+    const int64_t per_cam = c->scene.n_leaves > 0 ? c->scene.n_leaves : c->scene.n;
     const int64_t max_tiles = c->cfg.max_tiles_per_batch;
-    // each camera of a sub-batch owns a region of n record slots
-    const int64_t cams_by_cut = std::max<int64_t>(1, c->w.rec_cap / std::max<int64_t>(n, 1));
+    // the visible Gaussians of a sub-batch (at most per_cam per camera) share
+    // the record slots
+    const int64_t cams_by_cut =
+        std::max<int64_t>(1, c->w.rec_cap / std::max<int64_t>(per_cam, 1));
     int i = 0;
     const int N = (int)cams.size();
     while (i < N) {
@@ -432,11 +446,12 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     if (sb.tile_passes == 0) mark(c, sb_index, MK_THIST, st);
     launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, c->grid_ranges, st, w.err);
     mark(c, sb_index, MK_RANGES, st);
-    const int cgrid = std::min<int64_t>(
-        sb.n_tiles, (int64_t)c->num_sms *
-                        std::max(1, composite_blocks_per_sm(c->scene.attr_dtype, c->tile_w,
-                                                            c->tile_h, c->batch)));
-    launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, c->batch, true, cams, nc,
+    const int cw = cta_w_of(c), ch = cta_h_of(c);
+    const int64_t items = (int64_t)sb.n_tiles * (c->tile_w / cw) * (c->tile_h / ch);
+    const int cgrid = (int)std::min<int64_t>(
+        items, (int64_t)c->num_sms *
+                   std::max(1, composite_blocks_per_sm(c->scene.attr_dtype, cw, ch, c->batch)));
+    launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, cw, ch, c->batch, true, cams, nc,
                      sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
                      std::max(cgrid, 1), w.err, w.work64, st);
     mark(c, sb_index, MK_COMPOSITE, st);
@@ -564,9 +579,12 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         if (sb.tile_passes == 0) mark(c, ci, MK_THIST, st);
         launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, grng, st, w.err);
         mark(c, ci, MK_RANGES, st);
-        launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, c->batch, false, cams, 1,
-                         sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
-                         (int)std::max<uint32_t>(sb.n_tiles, 1), w.err, w.work64, st);
+        const int cw = cta_w_of(c), ch = cta_h_of(c);
+        const uint32_t items = sb.n_tiles * (uint32_t)((c->tile_w / cw) * (c->tile_h / ch));
+        launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, cw, ch, c->batch, false,
+                         cams, 1, sb.n_tiles, w.ranges, w.pval[psel], w.rec,
+                         w.counters + TK_COMPOSITE, (int)std::max<uint32_t>(items, 1), w.err,
+                         w.work64, st);
         mark(c, ci, MK_COMPOSITE, st);
         CK(cudaGetLastError());
         c->kernels_per_render += kernels_of(sb, false);
@@ -591,6 +609,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     key.reserve(8 + 3 * n_cams);
     key.push_back(n_cams); key.push_back(c->tile_w); key.push_back(c->tile_h);
     key.push_back(c->batch); key.push_back((int64_t)c->scene_version);
+    key.push_back(cta_w_of(c)); key.push_back(cta_h_of(c));
     for (int i = 0; i < n_cams; ++i) {
         key.push_back(c->host_cams[i].width);
         key.push_back(c->host_cams[i].height);
@@ -647,7 +666,7 @@ ngs_status render_common(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
     if (!c) return NGS_ERR_INVALID_ARG;
     if (!c->loaded) return NGS_ERR_NOT_LOADED;
     if (!cams || !images || n_cams <= 0 || n_cams > kMaxCamsPerCall) return NGS_ERR_INVALID_ARG;
-    if (!tile_supported(c->tile_w, c->tile_h)) return NGS_ERR_INVALID_ARG;
+    if (!tile_supported(c->tile_w, c->tile_h) || !split_supported(c)) return NGS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (!camera_ok(cams[i]) || !images[i]) return NGS_ERR_INVALID_ARG;
     ngs_status s = ensure_work(c);
@@ -665,6 +684,7 @@ ngs_status render_common(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
     }
     c->stats.tile_w = c->tile_w; c->stats.tile_h = c->tile_h;
     c->stats.batch = c->batch; c->stats.mode = c->mode;
+    c->stats.cta_w = cta_w_of(c); c->stats.cta_h = cta_h_of(c);
     return c->mode == NGS_MODE_PLAIN ? render_plain(c, n_cams, st) : render_batched(c, n_cams, st);
 }
 
@@ -724,6 +744,7 @@ ngs_status ngs::lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pa
     l->loaded = true;
     l->scene_version = parent->scene_version;
     l->tile_w = parent->tile_w; l->tile_h = parent->tile_h; l->batch = parent->batch;
+    l->cta_w = parent->cta_w; l->cta_h = parent->cta_h;
     l->use_graph = false;   // every launch has a different camera mix
     l->block_cull = parent->block_cull;
     return NGS_OK;
@@ -819,6 +840,15 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         if (!(tw == 8 || tw == 16 || tw == 32) || !(th == 8 || th == 16 || th == 32))
             return NGS_ERR_INVALID_ARG;
         c->tile_w = tw; c->tile_h = th;
+        drop_graph(c);
+        return NGS_OK;
+    }
+    case NGS_OPT_CTA_W:
+    case NGS_OPT_CTA_H: {
+        // 0 restores "the whole tile"; other shapes are checked at render
+        // against the tile shape in force then
+        if (!(v == 0 || v == 8 || v == 16 || v == 32)) return NGS_ERR_INVALID_ARG;
+        (opt == NGS_OPT_CTA_W ? c->cta_w : c->cta_h) = (int)v;
         drop_graph(c);
         return NGS_OK;
     }
@@ -936,6 +966,8 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *c, const ngs_gaussians *g, const ngs_
     CK(cudaMemcpy(d.blk_hi, bhi.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
     d.nblk = nb;
     d.n = n;
+    d.n_leaves = 0;
+    for (int64_t i = 0; i < n; ++i) d.n_leaves += h->child_count[i] == 0 ? 1 : 0;
     d.attr_dtype = g->attr_dtype;
     c->loaded = true;
     ++c->scene_version;
@@ -1070,7 +1102,11 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
                                 ngs_tune_result *out) {
     if (!c || !out || reps <= 0) return NGS_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
-    static const int kTiles[6][2] = {{8, 8}, {16, 8}, {16, 16}, {16, 32}, {32, 16}, {32, 32}};
+    // (binning tile, compositing block) candidates, as listed in ngs.h
+    static const int kShapes[kTuneShapes][4] = {
+        {8, 8, 8, 8},     {16, 8, 16, 8},   {16, 16, 16, 16}, {16, 32, 16, 32},
+        {32, 16, 32, 16}, {32, 32, 32, 32}, {16, 16, 16, 8},  {16, 32, 16, 16},
+        {32, 16, 16, 16}, {32, 32, 16, 16}, {32, 32, 32, 16}, {32, 32, 16, 8}};
     static const int kBatches[3] = {64, 128, 256};
     cudaStream_t st = (cudaStream_t)stream;
     const int mode = c->mode;
@@ -1084,10 +1120,12 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
     float best = 3.4e38f;
     int bt = 2, bb = 1;
     ngs_status s = NGS_OK;
-    for (int t = 0; t < 6 && s == NGS_OK; ++t)
+    for (int t = 0; t < kTuneShapes && s == NGS_OK; ++t)
         for (int b = 0; b < 3 && s == NGS_OK; ++b) {
-            c->tile_w = kTiles[t][0];
-            c->tile_h = kTiles[t][1];
+            c->tile_w = kShapes[t][0];
+            c->tile_h = kShapes[t][1];
+            c->cta_w = kShapes[t][2];
+            c->cta_h = kShapes[t][3];
             c->batch = kBatches[b];
             drop_graph(c);
             // capture + one warm-up replay, then the timed replays
@@ -1105,8 +1143,10 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->tile_w = kTiles[bt][0];
-    c->tile_h = kTiles[bt][1];
+    c->tile_w = kShapes[bt][0];
+    c->tile_h = kShapes[bt][1];
+    c->cta_w = kShapes[bt][2];
+    c->cta_h = kShapes[bt][3];
     c->batch = kBatches[bb];
     c->mode = mode;
     c->use_graph = graph;
@@ -1114,6 +1154,8 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
     drop_graph(c);
     out->tile_w = c->tile_w;
     out->tile_h = c->tile_h;
+    out->cta_w = c->cta_w;
+    out->cta_h = c->cta_h;
     out->batch = c->batch;
     out->reserved = 0;
     return s;

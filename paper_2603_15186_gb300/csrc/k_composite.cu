@@ -21,9 +21,17 @@
 // pixel's value depends only on its own Gaussian sequence: the same bits for any
 // tile shape, batch size, camera batch or launch form.
 //
-// Launch forms: one CTA per tile (grid = tiles), or persistent CTAs that take
-// tiles from an atomic ticket (batched renders, where one launch covers the
-// tiles of many cameras).
+// A CTA covers a TW x TH block of pixels: a whole binning tile, or one of the
+// sub_x x sub_y equal blocks a binning tile is split into (work item = tile *
+// sub_x * sub_y + block, row-major within the tile). Each block walks its
+// tile's whole list and keeps only the records that can reach it, so large
+// binning tiles (few pairs to sort) can be composited by small CTAs (few warps
+// waiting on one another at the staging barriers, early exit per block). The
+// pixels do not depend on the split either.
+//
+// Launch forms: one CTA per work item (grid = items), or persistent CTAs that
+// take items from an atomic ticket (batched renders, where one launch covers
+// the tiles of many cameras).
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -126,7 +134,7 @@ __global__ void __launch_bounds__(CompLayout<R, TW, TH, BATCH>::NT)
 k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
             const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
-            unsigned long long *work64) {
+            unsigned long long *work64, int sub_x, int sub_y) {
     using Lay = CompLayout<R, TW, TH, BATCH>;
     constexpr int NT = Lay::NT, BH = Lay::BH, WBW = Lay::WBW, NWX = Lay::NWX;
     constexpr int NCB = Lay::NCB, NCOEF = Lay::NCOEF;
@@ -163,14 +171,18 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
     }
     const float2 kOne2 = make_float2(1.0f, 1.0f), kMinusOne2 = make_float2(-1.0f, -1.0f);
     unsigned long long evals = 0, staged = 0;
-    uint32_t tile = blockIdx.x;
+    const uint32_t nsub = (uint32_t)(sub_x * sub_y);
+    const uint32_t n_items = n_tiles * nsub;
+    uint32_t item = blockIdx.x;
     for (;;) {
         if (persistent) {
             if (tid == 0) s_tile = atomicAdd(ticket, 1u);
             __syncthreads();
-            tile = s_tile;
+            item = s_tile;
         }
-        if (tile >= n_tiles) break;
+        if (item >= n_items) break;
+        const uint32_t tile = nsub == 1 ? item : item / nsub;
+        const int sub = (int)(item - tile * nsub);
         int lo = 0, hi = n_cams - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -179,7 +191,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         const DevCamera &cam = cams[lo];
         const uint32_t local = tile - cam.tile_base;
         const int tx = (int)(local % (uint32_t)cam.tiles_x), ty = (int)(local / (uint32_t)cam.tiles_x);
-        const int x0 = tx * TW, y0 = ty * TH;
+        const int x0 = (tx * sub_x + sub % sub_x) * TW, y0 = (ty * sub_y + sub / sub_x) * TH;
         const int px = x0 + lx, py = y0 + ly;
         const bool in0 = px < cam.width && py < cam.height;
         const bool in1 = px < cam.width && py + 1 < cam.height;
@@ -401,63 +413,55 @@ void composite_init_attributes() {
     set_attr_r<Rec16>();
 }
 
+struct CompLaunch {
+    const DevCamera *cams;
+    int n_cams;
+    uint32_t n_tiles;
+    const uint2 *ranges;
+    const uint32_t *pval;
+    const void *rec;
+    uint32_t *ticket;
+    int persistent, grid;
+    const int *err;
+    unsigned long long *work64;
+    int sub_x, sub_y;
+    cudaStream_t st;
+};
+
+template <typename R, int TW, int TH, int BATCH>
+static void launch_one(const CompLaunch &a) {
+    k_composite<R, TW, TH, BATCH>
+        <<<a.grid, CompLayout<R, TW, TH, BATCH>::NT, comp_smem<R, TW, TH, BATCH>(), a.st>>>(
+            a.cams, a.n_cams, a.n_tiles, a.ranges, a.pval, (const R *)a.rec, a.ticket,
+            a.persistent, a.err, a.work64, a.sub_x, a.sub_y);
+}
+
 template <typename R, int TW, int TH>
-static void launch_b(int batch, const DevCamera *cams, int n_cams, uint32_t n_tiles,
-                     const uint2 *ranges, const uint32_t *pval, const void *rec, uint32_t *ticket,
-                     int persistent, int grid, const int *err, unsigned long long *work64,
-                     cudaStream_t st) {
-    const R *r = (const R *)rec;
-    switch (batch) {
-    case 64:
-        k_composite<R, TW, TH, 64><<<grid, (CompLayout<R, TW, TH, 64>::NT), comp_smem<R, TW, TH, 64>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
-                                                             r, ticket, persistent, err, work64);
-        break;
-    case 256:
-        k_composite<R, TW, TH, 256><<<grid, (CompLayout<R, TW, TH, 64>::NT), comp_smem<R, TW, TH, 256>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
-                                                              r, ticket, persistent, err, work64);
-        break;
-    default:
-        k_composite<R, TW, TH, 128><<<grid, (CompLayout<R, TW, TH, 64>::NT), comp_smem<R, TW, TH, 128>(), st>>>(cams, n_cams, n_tiles, ranges, pval,
-                                                              r, ticket, persistent, err, work64);
-        break;
-    }
+static void launch_b(int batch, const CompLaunch &a) {
+    if (batch == 64) launch_one<R, TW, TH, 64>(a);
+    else if (batch == 256) launch_one<R, TW, TH, 256>(a);
+    else launch_one<R, TW, TH, 128>(a);
 }
 
 template <typename R>
-static void launch_r(int tile_w, int tile_h, int batch, const DevCamera *cams, int n_cams,
-                     uint32_t n_tiles, const uint2 *ranges, const uint32_t *pval, const void *rec,
-                     uint32_t *ticket, int persistent, int grid, const int *err,
-                     unsigned long long *work64, cudaStream_t st) {
-    if (tile_w == 8 && tile_h == 8)
-        launch_b<R, 8, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent, grid,
-                          err, work64, st);
-    else if (tile_w == 16 && tile_h == 8)
-        launch_b<R, 16, 8>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                           grid, err, work64, st);
-    else if (tile_w == 16 && tile_h == 32)
-        launch_b<R, 16, 32>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                            grid, err, work64, st);
-    else if (tile_w == 32 && tile_h == 16)
-        launch_b<R, 32, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                            grid, err, work64, st);
-    else if (tile_w == 32 && tile_h == 32)
-        launch_b<R, 32, 32>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                            grid, err, work64, st);
-    else
-        launch_b<R, 16, 16>(batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent,
-                            grid, err, work64, st);
+static void launch_r(int w, int h, int batch, const CompLaunch &a) {
+    if (w == 8 && h == 8) launch_b<R, 8, 8>(batch, a);
+    else if (w == 16 && h == 8) launch_b<R, 16, 8>(batch, a);
+    else if (w == 16 && h == 32) launch_b<R, 16, 32>(batch, a);
+    else if (w == 32 && h == 16) launch_b<R, 32, 16>(batch, a);
+    else if (w == 32 && h == 32) launch_b<R, 32, 32>(batch, a);
+    else launch_b<R, 16, 16>(batch, a);
 }
 
-void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool persistent,
-                      const DevCamera *cams, int n_cams, uint32_t n_tiles, const uint2 *ranges,
-                      const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
-                      const int *err, unsigned long long *work64, cudaStream_t st) {
-    if (attr_dtype == NGS_F32)
-        launch_r<Rec32>(tile_w, tile_h, batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket,
-                        persistent ? 1 : 0, grid, err, work64, st);
-    else
-        launch_r<Rec16>(tile_w, tile_h, batch, cams, n_cams, n_tiles, ranges, pval, rec, ticket,
-                        persistent ? 1 : 0, grid, err, work64, st);
+void launch_composite(int attr_dtype, int tile_w, int tile_h, int cta_w, int cta_h, int batch,
+                      bool persistent, const DevCamera *cams, int n_cams, uint32_t n_tiles,
+                      const uint2 *ranges, const uint32_t *pval, const void *rec,
+                      uint32_t *ticket, int grid, const int *err, unsigned long long *work64,
+                      cudaStream_t st) {
+    const CompLaunch a{cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent ? 1 : 0,
+                       grid, err, work64, tile_w / cta_w, tile_h / cta_h, st};
+    if (attr_dtype == NGS_F32) launch_r<Rec32>(cta_w, cta_h, batch, a);
+    else launch_r<Rec16>(cta_w, cta_h, batch, a);
 }
 
 template <typename R, int TW, int TH, int BATCH>

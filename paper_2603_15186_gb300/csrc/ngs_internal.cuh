@@ -83,6 +83,9 @@ struct __align__(16) Rec16 {
 
 struct SceneDev {
     int64_t n = 0;
+    // nodes without children: a cut is an antichain of the tree, so no camera
+    // selects more Gaussians than this
+    int64_t n_leaves = 0;
     int32_t attr_dtype = NGS_F32;
     float4 *box_lo = nullptr, *box_hi = nullptr, *pos4 = nullptr, *quat = nullptr;
     void *sop = nullptr;     // [n][4] of attr type
@@ -330,10 +333,13 @@ void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges,
                    cudaStream_t st, const int *err);
 
 // compositing of tiles [0, n_tiles) of a sub-batch
-void launch_composite(int attr_dtype, int tile_w, int tile_h, int batch, bool persistent,
-                      const DevCamera *cams, int n_cams, uint32_t n_tiles, const uint2 *ranges,
-                      const uint32_t *pval, const void *rec, uint32_t *ticket, int grid,
-                      const int *err, unsigned long long *work64, cudaStream_t st);
+// tile_w x tile_h: binning tile; cta_w x cta_h: the block one CTA composites
+// (equal to the tile, or a compiled shape dividing it)
+void launch_composite(int attr_dtype, int tile_w, int tile_h, int cta_w, int cta_h, int batch,
+                      bool persistent, const DevCamera *cams, int n_cams, uint32_t n_tiles,
+                      const uint2 *ranges, const uint32_t *pval, const void *rec,
+                      uint32_t *ticket, int grid, const int *err, unsigned long long *work64,
+                      cudaStream_t st);
 int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch);
 void composite_init_attributes();
 

@@ -85,6 +85,11 @@ class Renderer:
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_TILE_W, int(w)), "tile_w")
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_TILE_H, int(h)), "tile_h")
 
+    def set_cta(self, w: int, h: int):
+        """Pixel block of one compositing CTA (0, 0: the whole tile)."""
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_CTA_W, int(w)), "cta_w")
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_CTA_H, int(h)), "cta_h")
+
     def set_batch(self, b: int):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_BATCH, int(b)), "batch")
 
@@ -150,7 +155,8 @@ class Renderer:
         return images
 
     def autotune(self, cams, images: Optional[list] = None, reps: int = 3, stream=None) -> dict:
-        """Times every tile shape x staging batch on ``cams`` and keeps the fastest."""
+        """Times every (tile, compositing block) shape x staging batch on ``cams``
+        and keeps the fastest."""
         if images is None:
             images = self.new_images(cams)
         arr = camera_array(cams)
@@ -158,11 +164,10 @@ class Renderer:
         res = _lib.TuneResult()
         check(self.L.ngs_autotune(self.h, arr, len(cams), ptrs, int(reps), _stream_ptr(stream),
                                   C.byref(res)), "ngs_autotune")
-        names = [f"{tw}x{th}/{b}" for tw, th in ((8, 8), (16, 8), (16, 16), (16, 32), (32, 16),
-                                                  (32, 32))
-                 for b in (64, 128, 256)]
-        return {"tile": (res.tile_w, res.tile_h), "batch": res.batch,
-                "ms": dict(zip(names, [round(x, 3) for x in res.ms]))}
+        names = [f"{t[0]}x{t[1]}:{k[0]}x{k[1]}/{b}" for t, k in _lib.TUNE_SHAPES
+                 for b in _lib.TUNE_BATCHES]
+        return {"tile": (res.tile_w, res.tile_h), "cta": (res.cta_w, res.cta_h),
+                "batch": res.batch, "ms": dict(zip(names, [round(x, 3) for x in res.ms]))}
 
     def render_host(self, cams, out: Optional[List[np.ndarray]] = None, stream=None):
         """Renders and copies every image into host arrays [3, H, W] float32."""

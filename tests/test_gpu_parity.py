@@ -175,6 +175,21 @@ def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
                 assert np.array_equal(a, b), (tile, batch)
     for a, b in zip(base, again):
         assert np.array_equal(a, b)
+    # large binning tiles composited as smaller blocks, batched and plain
+    for tile, cta in [((32, 32), (16, 16)), ((32, 32), (16, 8)), ((32, 16), (16, 16)),
+                      ((16, 16), (8, 8)), ((16, 32), (16, 16))]:
+        R.set_tile(*tile)
+        R.set_cta(*cta)
+        R.set_batch(128)
+        for mode in ("batched", "plain"):
+            R.set_mode(mode)
+            out = [t.cpu().numpy() for t in R.render(cams)]
+            st = R.stats()
+            assert (st["cta_w"], st["cta_h"]) == cta
+            for a, b in zip(base, out):
+                assert np.array_equal(a, b), (tile, cta, mode)
+        R.set_mode("batched")
+    R.set_cta(0, 0)
     # alone vs in a batch
     R.set_tile(16, 16)
     R.set_batch(128)
@@ -208,15 +223,18 @@ def test_autotune_keeps_pixels(R, small_floor):
     R.set_batch(128)
     base = [t.cpu().numpy() for t in R.render(cams)]
     res = R.autotune(cams, reps=1)
-    assert res["tile"] in [(8, 8), (16, 8), (16, 16), (16, 32), (32, 16), (32, 32)]
+    from paper_2603_15186_gb300 import _lib
+    assert (res["tile"], res["cta"]) in _lib.TUNE_SHAPES
     assert res["batch"] in (64, 128, 256)
-    assert all(v > 0 for v in res["ms"].values()) and len(res["ms"]) == 18
+    assert all(v > 0 for v in res["ms"].values()) and len(res["ms"]) == 3 * len(_lib.TUNE_SHAPES)
     out = [t.cpu().numpy() for t in R.render(cams)]
     st = R.stats()
     assert (st["tile_w"], st["tile_h"], st["batch"]) == (*res["tile"], res["batch"])
+    assert (st["cta_w"], st["cta_h"]) == res["cta"]
     for a, b in zip(base, out):
         assert np.array_equal(a, b)
     R.set_tile(16, 16)
+    R.set_cta(0, 0)
     R.set_batch(128)
 
 
@@ -303,4 +321,11 @@ def test_unsupported_tile_shape_rejected(R, small_floor):
     R.set_tile(16, 32)
     img = R.render([cam])[0].cpu().numpy()
     R.set_tile(16, 16)
+    assert np.array_equal(img, R.render([cam])[0].cpu().numpy())
+    # a compositing block that does not divide the tile
+    R.set_cta(32, 16)
+    with pytest.raises(NgsError) as e:
+        R.render([cam])
+    assert e.value.status == 1
+    R.set_cta(0, 0)
     assert np.array_equal(img, R.render([cam])[0].cpu().numpy())
