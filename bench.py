@@ -49,6 +49,8 @@ def parse():
                     help="seconds of simulated agent load for the serving leg (0: skip)")
     ap.add_argument("--serving-scene", default="floor8m")
     ap.add_argument("--cpu-cams", type=int, default=3)
+    ap.add_argument("--pairs-per-pixel", type=int, default=0,
+                    help="planner estimate of pairs per pixel (0: the library's default)")
     ap.add_argument("--record-capacity", type=int, default=1 << 29,
                     help="record slots of the work buffers (smaller for profiling runs)")
     ap.add_argument("--pair-capacity", type=int, default=(1 << 31) - (1 << 24),
@@ -240,6 +242,8 @@ def run_ours(args, world, rank, local, pg):
                  record_capacity=args.record_capacity, pair_capacity=args.pair_capacity)
     R.load_scene(scene, attr_dtype="f16", stored=stored)
     R.set_cta(*(int(x) for x in args.cta.split("x")))
+    if args.pairs_per_pixel:
+        R.set_pairs_per_pixel(args.pairs_per_pixel)
     R.set_mode("batched")
     R.set_stage_timing(not args.no_stage_timing)
     imgs = R.new_images(cams)

@@ -852,6 +852,10 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         drop_graph(c);
         return NGS_OK;
     }
+    case NGS_OPT_PAIRS_PER_PIXEL:
+        if (v < 1 || v > 4096) return NGS_ERR_INVALID_ARG;
+        c->pairs_per_pixel = (double)v;
+        return NGS_OK;
     case NGS_OPT_BATCH:
         if (v != 64 && v != 128 && v != 256) return NGS_ERR_INVALID_ARG;
         c->batch = (int)v;

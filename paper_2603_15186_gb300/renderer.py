@@ -90,6 +90,11 @@ class Renderer:
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_CTA_W, int(w)), "cta_w")
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_CTA_H, int(h)), "cta_h")
 
+    def set_pairs_per_pixel(self, v: int):
+        """The sub-batch planner's estimate of (tile, Gaussian) pairs per pixel."""
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_PAIRS_PER_PIXEL, int(v)),
+              "pairs_per_pixel")
+
     def set_batch(self, b: int):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_BATCH, int(b)), "batch")
 
