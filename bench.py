@@ -209,12 +209,14 @@ def stage_bytes(st, n_nodes, n_cams, pixels, tiles, attr="f16"):
         "cut_preprocess": st["sub_batches"] * n_nodes * 32 + V * (rec + 4 + 16),
         "gather_keys": 12 * V,
         "depth_hist": 4 * V,
-        "depth_pass0": 16 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 16 * V,
+        # the last depth pass writes values only; the last tile pass writes
+        # values and each tile's range (8 B per tile) instead of keys
+        "depth_pass0": 16 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 12 * V,
         "pair_offsets": 24 * V,
         "duplicate": 24 * V + 8 * P,
         "tile_hist": 4 * P,
-        "tile_pass0": 16 * P, "tile_pass1": 16 * P, "tile_pass2": 16 * P,
-        "ranges": 4 * P + 8 * tiles,
+        "tile_pass0": 16 * P, "tile_pass1": 12 * P + 8 * tiles, "tile_pass2": 0,
+        "ranges": 8 * tiles,
         "composite": 12 * pixels + st["records_staged"] * (4 + rec),
     }
 

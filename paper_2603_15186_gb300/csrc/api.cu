@@ -413,6 +413,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     da.hist = w.hist; da.tickets = w.counters + TK_SORT0; da.status = w.status;
     da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
     da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
+    da.skip_last_keys = true;   // later stages read the record order only
     launch_sort(da, c->grid_sort32, st);
     eo += 4;
     const int dsel = 4 & 1;  // four passes: the result is back in buffer 0
@@ -438,13 +439,15 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
         pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
         pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
         pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
+        pa.ranges = w.ranges;   // the last pass records the tile ranges
         launch_sort(pa, c->grid_sort32, st);
         eo += sb.tile_passes;
         psel = sb.tile_passes & 1;
     }
     for (int k = MK_THIST + 1 + sb.tile_passes; k < MK_RANGES; ++k) mark(c, sb_index, k, st);
     if (sb.tile_passes == 0) mark(c, sb_index, MK_THIST, st);
-    launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, c->grid_ranges, st, w.err);
+    if (sb.tile_passes == 0)
+        launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, c->grid_ranges, st, w.err);
     mark(c, sb_index, MK_RANGES, st);
     const int cw = cta_w_of(c), ch = cta_h_of(c);
     const int64_t items = (int64_t)sb.n_tiles * (c->tile_w / cw) * (c->tile_h / ch);
@@ -460,10 +463,12 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
 }
 
 int kernels_of(const SubBatch &sb, bool batched) {
-    // bump, cut, preprocess, depth sort (histogram, digit scan, 4 passes), pair
-    // offsets, duplicate, tile sort (histogram, digit scan, passes), ranges,
-    // composite, and in the batched path the stats copy
-    return 3 + 6 + 2 + (sb.tile_passes > 0 ? 2 + sb.tile_passes : 0) + 2 + (batched ? 1 : 0);
+    // epoch bump, live partitions, fused cut + preprocess, partition scan and
+    // gather; depth sort (histogram, digit scan, 4 passes); pair offsets,
+    // duplication; tile sort (digit scan and passes, the last one writing the
+    // tile ranges) or, with a single tile, the ranges kernel; compositing; and
+    // in the batched path the stats copy
+    return 5 + 6 + 2 + (sb.tile_passes > 0 ? 1 + sb.tile_passes : 1) + 1 + (batched ? 1 : 0);
 }
 
 ngs_status read_u32(const uint32_t *d, uint32_t *h, cudaStream_t st) {
@@ -536,6 +541,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
         SortHook dh{c, ci, MK_DHIST, st};
         da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
+    da.skip_last_keys = true;   // later stages read the record order only
         launch_sort(da, std::min(gsort_v, c->grid_sort32), st);
         eo += 4;
         const int gscan = std::max<int64_t>(1, ((int64_t)n_vis + scan_partition() - 1) /
@@ -569,6 +575,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
             pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
             pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
             pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
+            pa.ranges = w.ranges;   // the last pass records the tile ranges
             launch_sort(pa, std::min(gsort_p, c->grid_sort32), st);
             eo += sb.tile_passes;
             psel = sb.tile_passes & 1;
@@ -577,7 +584,8 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
                                                                  (int64_t)c->num_sms * 16));
         for (int k = MK_THIST + 1 + sb.tile_passes; k < MK_RANGES; ++k) mark(c, ci, k, st);
         if (sb.tile_passes == 0) mark(c, ci, MK_THIST, st);
-        launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, grng, st, w.err);
+        if (sb.tile_passes == 0)
+            launch_ranges(w.pkey[psel], w.counters + CNT_PAIRS, w.ranges, grng, st, w.err);
         mark(c, ci, MK_RANGES, st);
         const int cw = cta_w_of(c), ch = cta_h_of(c);
         const uint32_t items = sb.n_tiles * (uint32_t)((c->tile_w / cw) * (c->tile_h / ch));
@@ -1201,6 +1209,7 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     CK(cudaMemcpy(&npairs, w.counters + CNT_PAIRS, 4, cudaMemcpyDeviceToHost));
     const int psel = sb.tile_passes & 1;
     int64_t lo = INT64_MAX, hi = 0;
+    for (int64_t t = 0; t < nt; ++t) rg[t].x = ~rg[t].x;   // stored as ~first
     for (int64_t t = 0; t < nt; ++t)
         if (rg[t].y > rg[t].x) { lo = std::min<int64_t>(lo, rg[t].x); hi = std::max<int64_t>(hi, rg[t].y); }
     if (lo == INT64_MAX) lo = hi = 0;

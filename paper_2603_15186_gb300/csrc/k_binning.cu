@@ -268,8 +268,11 @@ void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint3
                                               passes > 0 ? hist : nullptr, passes, err);
 }
 
-// K6: ranges[t] = [first, end) of tile t in the sorted pair keys (ranges of
-// tiles without pairs stay as zeroed beforehand).
+// K6: ranges[t] = [first, end) of tile t in the sorted pair keys, stored as
+// (~first, end) so that a zeroed entry reads as an empty range (first =
+// 0xffffffff > end = 0) for tiles without pairs. The last pass of the tile
+// sort writes the same encoding while it scatters (k_onesweep, kOut = 2); this
+// kernel covers sub-batches of a single tile, which need no tile sort.
 __global__ void k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *n_pairs_p,
                          uint2 *__restrict__ ranges, const int *err) {
     if (*err) return;
@@ -277,7 +280,7 @@ __global__ void k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *n_pa
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = pkey[i];
-        if (i == 0 || pkey[i - 1] != k) ranges[k].x = (uint32_t)i;
+        if (i == 0 || pkey[i - 1] != k) ranges[k].x = ~(uint32_t)i;
         if (i == n - 1 || pkey[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
     }
 }

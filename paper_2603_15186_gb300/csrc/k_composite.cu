@@ -207,7 +207,8 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         const float blk_y0c = (float)(y0 + by) + 0.5f, blk_y1c = blk_y0c + (float)(BH - 1);
         const float lxf = (float)(px & 15);
         const float2 lx2 = make_float2(lxf, lxf);
-        const uint2 rg = ranges[tile];
+        const uint2 rgs = ranges[tile];
+        const uint2 rg = make_uint2(~rgs.x, rgs.y);   // stored as (~first, end)
         // T = 0 marks a finished pixel (also one outside the image)
         float2 T2 = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
         float2 cr2 = make_float2(0.0f, 0.0f), cg2 = cr2, cb2 = cr2;

@@ -105,12 +105,20 @@ struct SortSmem {
     uint32_t part;
 };
 
-template <typename K, bool kIdentity>
+// kOut: 0 writes keys and values; 1 values only (last pass of a sort whose
+// keys are not needed afterwards); 2 values only, plus the [first, end) range
+// of every key in the sorted output (last pass of the tile sort, 32-bit keys):
+// within a partition equal keys are adjacent in the staged order and land on
+// consecutive output positions, so each run of equal keys contributes its
+// first and end position with one atomicMax each (first stored as ~first), and
+// the runs a key has in several partitions combine to its global range.
+template <typename K, bool kIdentity, int kOut>
 __global__ void __launch_bounds__(kOsThreads, 2)
 k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
            uint32_t *__restrict__ vout, const uint32_t *n_dev, int64_t n_host, int shift,
            uint32_t mask, const uint32_t *__restrict__ digit_base, uint64_t *status,
-           uint32_t *ticket, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+           uint32_t *ticket, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err,
+           uint2 *__restrict__ ranges) {
     constexpr int ITEMS = SortShape<K>::kItems;
     constexpr int PART = SortSmem<K>::kPart;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,8 +220,13 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             const K k = S.keys[j];
             const uint32_t d = digit_of(k, shift, mask);
             const int64_t g = (int64_t)S.gstart[d] + (j - S.dstart[d]);
-            kout[g] = k;
+            if (kOut == 0) kout[g] = k;
             vout[g] = S.vals[j];
+            if (kOut == 2) {
+                const uint32_t t = (uint32_t)k;
+                if (j == 0 || S.keys[j - 1] != k) atomicMax(&ranges[t].x, ~(uint32_t)g);
+                if (j + 1 == cnt || S.keys[j + 1] != k) atomicMax(&ranges[t].y, (uint32_t)g + 1u);
+            }
         }
         __syncthreads();
     }
@@ -223,15 +236,36 @@ size_t sort_smem_bytes(int key_bytes) {
     return key_bytes == 8 ? sizeof(SortSmem<uint64_t>) : sizeof(SortSmem<uint32_t>);
 }
 
+template <typename K>
+static void set_sort_attr() {
+    const int b = (int)sizeof(SortSmem<K>);
+    cudaFuncSetAttribute(k_onesweep<K, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(k_onesweep<K, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(k_onesweep<K, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(k_onesweep<K, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
 void sort_init_attributes() {
-    cudaFuncSetAttribute(k_onesweep<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    set_sort_attr<uint32_t>();
+    set_sort_attr<uint64_t>();
+    cudaFuncSetAttribute(k_onesweep<uint32_t, false, 2>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(SortSmem<uint32_t>));
-    cudaFuncSetAttribute(k_onesweep<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SortSmem<uint32_t>));
-    cudaFuncSetAttribute(k_onesweep<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SortSmem<uint64_t>));
-    cudaFuncSetAttribute(k_onesweep<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SortSmem<uint64_t>));
+}
+
+template <typename K, bool kIdentity>
+static void launch_pass(int out, int grid, size_t smem, cudaStream_t st, const K *kin,
+                        const uint32_t *vin, K *kout, uint32_t *vout, const SortArgs &a, int sh,
+                        uint32_t mask, int p) {
+    const uint32_t *base = a.hist + p * kRadix;
+    if (out == 1)
+        k_onesweep<K, kIdentity, 1><<<grid, kOsThreads, smem, st>>>(
+            kin, vin, kout, vout, a.n_dev, a.n_host, sh, mask, base, a.status, a.tickets + p,
+            a.epoch, a.epoch_off + p, a.err, nullptr);
+    else
+        k_onesweep<K, kIdentity, 0><<<grid, kOsThreads, smem, st>>>(
+            kin, vin, kout, vout, a.n_dev, a.n_host, sh, mask, base, a.status, a.tickets + p,
+            a.epoch, a.epoch_off + p, a.err, nullptr);
 }
 
 template <typename K>
@@ -250,16 +284,20 @@ static void launch_sort_t(const SortArgs &a, int grid, cudaStream_t st) {
         const int sh = a.begin_bit + 8 * p;
         const int bits = std::min(8, a.end_bit - sh);
         const uint32_t mask = (1u << bits) - 1u;
-        if (p == 0 && a.vals_identity)
-            k_onesweep<K, true><<<grid, kOsThreads, smem, st>>>(
-                (const K *)a.keys[src], nullptr, (K *)a.keys[dst], a.vals[dst], a.n_dev, a.n_host,
-                sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch, a.epoch_off + p,
-                a.err);
-        else
-            k_onesweep<K, false><<<grid, kOsThreads, smem, st>>>(
-                (const K *)a.keys[src], a.vals[src], (K *)a.keys[dst], a.vals[dst], a.n_dev,
+        const bool last = p == passes - 1;
+        const K *kin = (const K *)a.keys[src];
+        K *kout = (K *)a.keys[dst];
+        if (last && a.ranges && sizeof(K) == 4 && !(p == 0 && a.vals_identity))
+            k_onesweep<uint32_t, false, 2><<<grid, kOsThreads, smem, st>>>(
+                (const uint32_t *)kin, a.vals[src], (uint32_t *)kout, a.vals[dst], a.n_dev,
                 a.n_host, sh, mask, a.hist + p * kRadix, a.status, a.tickets + p, a.epoch,
-                a.epoch_off + p, a.err);
+                a.epoch_off + p, a.err, a.ranges);
+        else if (p == 0 && a.vals_identity)
+            launch_pass<K, true>(last && a.skip_last_keys ? 1 : 0, grid, smem, st, kin, nullptr,
+                                 kout, a.vals[dst], a, sh, mask, p);
+        else
+            launch_pass<K, false>(last && a.skip_last_keys ? 1 : 0, grid, smem, st, kin,
+                                  a.vals[src], kout, a.vals[dst], a, sh, mask, p);
         if (a.hook) a.hook(a.hook_user, p + 1);
     }
 }

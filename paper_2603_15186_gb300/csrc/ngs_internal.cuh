@@ -294,6 +294,12 @@ struct SortArgs {
     bool vals_identity;       // first pass takes value = input index
     bool hist_ready;          // hist already holds the digit counts (no upsweep)
     uint32_t *hist;           // [passes][256]
+    // last pass: skip_last_keys writes the values only (the sorted keys are
+    // not needed afterwards); a non-null ranges (32-bit tile keys only) also
+    // records every key's [first, end) there, encoded as in k_ranges (x holds
+    // ~first, so zeroed entries mean "no pairs"), and implies skip_last_keys
+    bool skip_last_keys;
+    uint2 *ranges;
     uint32_t *tickets;        // one per pass
     uint64_t *status;
     const uint32_t *epoch;
