@@ -161,7 +161,7 @@ __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
 void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
-    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
+    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.group_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
     dfree(w.hist); dfree(w.cams); dfree(w.work64);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
@@ -252,6 +252,7 @@ ngs_status ensure_work(ngs_ctx *c) {
     w.part_cap = std::max<int64_t>(1, (c->scene.n + cutpre_partition_nodes() - 1) /
                                           cutpre_partition_nodes() * kMaxCamsPerBatch);
     A(dalloc(&w.part_list, (size_t)w.part_cap));
+    A(dalloc(&w.group_list, (size_t)w.part_cap));
     A(dalloc(&w.part_info, (size_t)w.part_cap));
     A(dalloc(&w.part_pos, (size_t)w.part_cap));
     A(dalloc((unsigned char **)&w.rec, (size_t)w.rec_cap * sizeof(Rec32)));
@@ -397,7 +398,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
     uint32_t eo = 0;
     launch_cutpre(c->scene, cams, nc, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
-                  w.counters, w.part_list, w.part_info, w.err, c->tile_w, c->tile_h,
+                  w.counters, w.part_list, w.group_list, w.part_info, w.err, c->tile_w, c->tile_h,
                   c->block_cull ? 1 : 0, c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
     launch_gather_keys(w.vis_count, nc, c->scene, w.part_info, w.part_pos, w.part_list,
@@ -514,7 +515,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         uint32_t eo = 0;
         const int64_t nblk = (c->scene.n + cutpre_partition_nodes() - 1) / cutpre_partition_nodes();
         launch_cutpre(c->scene, cams, 1, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
-                      w.counters, w.part_list, w.part_info, w.err, c->tile_w, c->tile_h,
+                      w.counters, w.part_list, w.group_list, w.part_info, w.err, c->tile_w, c->tile_h,
                       c->block_cull ? 1 : 0, (int)std::min<int64_t>(nblk, c->grid_pre), st);
         eo++;
         mark(c, ci, MK_CUT, st);

@@ -142,12 +142,28 @@ struct PreOut {
     uint4 rect;
 };
 
+// Camera fields the phase-A tests read, staged in shared memory per group.
+struct CamLite {
+    float R[9];
+    float pos[3];
+    float fx, fy, cx, cy, tau;
+    int32_t tiles_x, tiles_y;
+    float pad;
+};
+
+// Camera-independent inputs of the conservative cull of one node: its
+// position word (mean + load-time flags), K = 2 ln(255 o) and the largest
+// scale.
+struct NodeCull {
+    float4 p;
+    float K, smax;
+};
+
 // Cheap conservative test (phase A of the fused kernel): false only for a
 // Gaussian that cannot touch any tile of the camera.
-template <typename A>
-__device__ __forceinline__ bool precull(const SceneDev &sc, const DevCamera &cam, uint32_t node,
-                                        int tile_w, int tile_h) {
-    const float4 p = sc.pos4[node];
+__device__ __forceinline__ bool precull(const CamLite &cam, const NodeCull &nd, int tile_w,
+                                        int tile_h) {
+    const float4 p = nd.p;
     if (__float_as_uint(p.w) & kNodeCullOpacity) return false;
     const float dx = __fsub_rn(p.x, cam.pos[0]);
     const float dy = __fsub_rn(p.y, cam.pos[1]);
@@ -165,10 +181,7 @@ __device__ __forceinline__ bool precull(const SceneDev &sc, const DevCamera &cam
     // than the float32 slack can have no tile.
     const float tx = __fmaf_rn(cam.R[0], dx, __fmaf_rn(cam.R[1], dy, __fmul_rn(cam.R[2], dz)));
     const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
-    float so[4];
-    Attr<A>::load4(sc.sop, node, so);
-    const float K = 2.0f * logf(255.0f * so[3]);
-    const float smax = expf(fmaxf(fmaxf(so[0], so[1]), so[2]));
+    const float K = nd.K, smax = nd.smax;
     const float iz = 1.0f / tz32;
     const float ax = cam.fx * iz, bx = -cam.fx * tx * iz * iz;
     const float ay = cam.fy * iz, by = -cam.fy * ty * iz * iz;
@@ -362,42 +375,61 @@ __device__ __forceinline__ void store_rec(Rec16 *rec, int64_t i, const PreOut &o
 }
 
 // Live partitions: the (node block, camera) pairs that survive the block-level
-// cull, listed block-major with the camera varying fastest (within a warp;
-// warps append in any order), so that partitions running at the same time
-// work on the same node block and share its attributes through L2. Culled
-// partitions get an empty entry in the partition table.
+// cull, appended to part_list, and grouped: a group is a run of up to
+// kGroupCams live partitions of the same node block (one half-warp's chunk of
+// cameras), recorded as (first entry, count) in group_list. Groups come out
+// block-major, so groups running at the same time mostly read the same node
+// block through L2. Culled partitions get an empty entry in the partition
+// table.
+constexpr int kGroupCams = 16;
+
 __global__ void k_live_parts(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams,
                              int64_t nblk, uint32_t *__restrict__ part_list,
-                             uint2 *__restrict__ part_info, uint32_t *counters, int tile_w,
-                             int tile_h, int use_block_cull, const int *err) {
+                             uint2 *__restrict__ group_list, uint2 *__restrict__ part_info,
+                             uint32_t *counters, int tile_w, int tile_h, int use_block_cull,
+                             const int *err) {
     if (*err) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t nparts = nblk * n_cams;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < nparts; t0 += stride) {
-        const int64_t t = t0 + threadIdx.x;
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const int64_t nch = (n_cams + kGroupCams - 1) / kGroupCams;
+    const int64_t nq = nblk * nch;   // (block, chunk of kGroupCams cameras)
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q0 = 2 * (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); q0 < nq;
+         q0 += 2 * warps) {
+        const int64_t q = q0 + half;
         bool live = false;
-        if (t < nparts) {
-            const int64_t b = t / n_cams;
-            const int c = (int)(t - b * n_cams);
-            live = !(use_block_cull &&
-                     block_culled(sc.blk_lo[b], sc.blk_hi[b], cams[c], tile_w, tile_h));
-            if (!live) part_info[(int64_t)c * nblk + b] = make_uint2(0u, 0u);
+        uint32_t t = 0;
+        if (q < nq) {
+            const int64_t b = q / nch;
+            const int c = (int)(q - b * nch) * kGroupCams + hl;
+            if (c < n_cams) {
+                t = (uint32_t)(b * n_cams + c);
+                live = !(use_block_cull &&
+                         block_culled(sc.blk_lo[b], sc.blk_hi[b], cams[c], tile_w, tile_h));
+                if (!live) part_info[(int64_t)c * nblk + b] = make_uint2(0u, 0u);
+            }
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, live);
-        uint32_t base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&counters[CNT_LIVE], (uint32_t)__popc(bal));
+        const uint32_t n_lo = __popc(bal & 0xffffu), n_hi = __popc(bal >> 16);
+        uint32_t base = 0, gbase = 0;
+        if (lane == 0 && bal) {
+            base = atomicAdd(&counters[CNT_LIVE], (uint32_t)__popc(bal));
+            gbase = atomicAdd(&counters[CNT_GROUPS], (n_lo ? 1u : 0u) + (n_hi ? 1u : 0u));
+            if (n_lo) group_list[gbase++] = make_uint2(base, n_lo);
+            if (n_hi) group_list[gbase] = make_uint2(base + n_lo, n_hi);
+        }
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (live) part_list[base + __popc(bal & lanemask_lt())] = (uint32_t)t;
+        if (live) part_list[base + __popc(bal & lanemask_lt())] = t;
     }
 }
 
-// Fused cut + preprocess over the live partitions (block of kPrePart nodes,
-// camera), taken from an atomic ticket. Phase A applies the cut rule and the
-// conservative cull and compacts the candidates; phase B preprocesses them
-// densely, staging the results in shared memory until the partition knows
-// where its visible Gaussians go (one atomic allocation); they are written
-// there in node order.
+// Fused cut + preprocess over groups of live partitions (one node block and up
+// to kGroupCams cameras), taken from an atomic ticket. Phase A loads each
+// node's box, parent box, position and scale/opacity once for the whole group
+// and applies the cut rule and the conservative cull for every camera of it;
+// then, per camera, the candidates are compacted in node order and phase B
+// preprocesses them densely, staging the results in shared memory until the
+// partition knows where its visible Gaussians go (one atomic allocation); they
+// are written there in node order.
 template <typename R>
 struct CutPreSmem {
     uint32_t cand[kPrePart];      // candidate node ids, node order
@@ -405,9 +437,13 @@ struct CutPreSmem {
     uint32_t key[kPrePart];
     uint4 rect[kPrePart];
     uint32_t vis[kPrePart];       // visible flag, then (rank | 1 << 31)
+    uint32_t balw[kGroupCams][kPreItems * 8];   // candidate ballot per (camera, item, warp)
     uint32_t cnt[kPreItems * 8];
+    uint32_t sel[kGroupCams];
+    CamLite cam[kGroupCams];
+    uint32_t gcam[kGroupCams];
     uint32_t wsum[kPreThreads / 32];
-    uint32_t part, ncand, sel;
+    uint32_t goff, gcnt, ncand;
     unsigned long long off;
 };
 
@@ -416,130 +452,173 @@ __global__ void __launch_bounds__(kPreThreads)
 k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restrict__ rec,
          int64_t rec_cap, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
          uint32_t *__restrict__ vis_count, uint32_t *counters,
-         const uint32_t *__restrict__ part_list, uint2 *__restrict__ part_info, int *err,
-         int tile_w, int tile_h) {
+         const uint32_t *__restrict__ part_list, const uint2 *__restrict__ group_list,
+         uint2 *__restrict__ part_info, int *err, int tile_w, int tile_h) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CutPreSmem<R> &S = *reinterpret_cast<CutPreSmem<R> *>(smem_raw);
     if (*err) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
-    const uint32_t n_live = counters[CNT_LIVE];
+    const uint32_t n_groups = counters[CNT_GROUPS];
     unsigned long long *alloc = reinterpret_cast<unsigned long long *>(counters + CNT_ALLOC);
     const uint32_t lt = lanemask_lt();
     for (;;) {
         if (tid == 0) {
             const uint32_t i = atomicAdd(&counters[TK_PRE], 1u);
-            S.part = i < n_live ? part_list[i] : 0xffffffffu;
-            S.sel = 0;
+            const uint2 g = i < n_groups ? group_list[i] : make_uint2(0u, 0u);
+            S.goff = g.x;
+            S.gcnt = g.y;
         }
         __syncthreads();
-        if (S.part == 0xffffffffu) break;
-        const int64_t part = S.part;
-        const int64_t b = part / n_cams;
-        const int c = (int)(part - b * n_cams);
-        const DevCamera &cam = cams[c];
-        // phase A: cut rule and conservative cull; survivors compacted into
-        // S.cand in node order
-        uint32_t bal[kPreItems];
-        uint32_t nsel = 0;
-#pragma unroll
+        const int gcnt = (int)S.gcnt;
+        if (gcnt == 0) break;
+        const uint32_t goff = S.goff;
+        const int64_t b = part_list[goff] / (uint32_t)n_cams;
+        if (tid < gcnt) {
+            const int c = (int)(part_list[goff + tid] - b * n_cams);
+            const DevCamera &d = cams[c];
+            CamLite &l = S.cam[tid];
+            for (int k = 0; k < 9; ++k) l.R[k] = d.R[k];
+            l.pos[0] = d.pos[0]; l.pos[1] = d.pos[1]; l.pos[2] = d.pos[2];
+            l.fx = d.fx; l.fy = d.fy; l.cx = d.cx; l.cy = d.cy; l.tau = d.tau;
+            l.tiles_x = d.tiles_x; l.tiles_y = d.tiles_y;
+            S.gcam[tid] = (uint32_t)c;
+            S.sel[tid] = 0;
+        }
+        __syncthreads();
+        // phase A: per node, one set of loads for every camera of the group
+#pragma unroll 1
         for (int k = 0; k < kPreItems; ++k) {
             const int64_t node = b * kPrePart + k * kPreThreads + tid;
-            const bool sel = node < sc.n &&
-                             cut_selects(sc.box_lo, sc.box_hi, node, cam.pos[0], cam.pos[1],
-                                         cam.pos[2], cam.fx, cam.tau);
-            const bool cand = sel && precull<A>(sc, cam, (uint32_t)node, tile_w, tile_h);
-            nsel += __popc(__ballot_sync(0xffffffffu, sel));
-            bal[k] = __ballot_sync(0xffffffffu, cand);
-            if (lane == 0) S.cnt[k * 8 + warp] = __popc(bal[k]);
+            const bool valid = node < sc.n;
+            float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo, plo = lo, phi = lo;
+            NodeCull nd;
+            nd.p = lo;
+            float so[4] = {1.f, 1.f, 1.f, 1.f};
+            if (valid) {
+                lo = sc.box_lo[node];
+                hi = sc.box_hi[node];
+                nd.p = sc.pos4[node];
+                Attr<A>::load4(sc.sop, node, so);
+            }
+            const int par = __float_as_int(lo.w);
+            const bool leaf = __float_as_int(hi.w) == 0;
+            if (valid && par >= 0) {
+                plo = sc.box_lo[par];
+                phi = sc.box_hi[par];
+            }
+            nd.K = 2.0f * logf(255.0f * so[3]);
+            nd.smax = expf(fmaxf(fmaxf(so[0], so[1]), so[2]));
+            for (int i = 0; i < gcnt; ++i) {
+                const CamLite &cam = S.cam[i];
+                const bool sel =
+                    valid &&
+                    (leaf || granularity(lo, hi, cam.pos[0], cam.pos[1], cam.pos[2], cam.fx) <=
+                                 cam.tau) &&
+                    (par < 0 || granularity(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
+                                            cam.fx) > cam.tau);
+                const bool cand = sel && precull(cam, nd, tile_w, tile_h);
+                const uint32_t nsel = __popc(__ballot_sync(0xffffffffu, sel));
+                const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+                if (lane == 0) {
+                    S.balw[i][k * 8 + warp] = bal;
+                    if (nsel) atomicAdd(&S.sel[i], nsel);
+                }
+            }
         }
-        if (lane == 0) atomicAdd(&S.sel, nsel);
         __syncthreads();
-        if (warp == 0) {
-            const uint32_t v = lane < kPreItems * 8 ? S.cnt[lane] : 0u;
-            uint32_t incl = v;
+        for (int i = 0; i < gcnt; ++i) {
+            const int c = (int)S.gcam[i];
+            const DevCamera &cam = cams[c];
+            // candidates of camera i compacted into S.cand in node order
+            if (warp == 0) {
+                const uint32_t v = lane < kPreItems * 8 ? __popc(S.balw[i][lane]) : 0u;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (lane < kPreItems * 8) S.cnt[lane] = incl - v;
+                if (lane == 31) S.ncand = incl;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kPreItems; ++k) {
+                const uint32_t bal = S.balw[i][k * 8 + warp];
+                if ((bal >> lane) & 1u)
+                    S.cand[S.cnt[k * 8 + warp] + __popc(bal & lt)] =
+                        (uint32_t)(b * kPrePart + k * kPreThreads + tid);
+            }
+            if (tid == 0 && S.sel[i]) atomicAdd(&counters[CNT_CUT], S.sel[i]);
+            __syncthreads();
+            // phase B: full preprocess, densely over the candidates, results staged
+            const int ncand = (int)S.ncand;
+            for (int j = tid; j < ncand; j += kPreThreads) {
+                PreOut o;
+                const bool vis = preprocess_one<A>(sc, cam, S.cand[j], tile_w, tile_h, o);
+                S.vis[j] = vis ? 1u : 0u;
+                if (vis) {
+                    store_rec(S.rec, j, o);
+                    S.key[j] = o.key;
+                    o.rect.z = (uint32_t)c;
+                    S.rect[j] = o.rect;
+                }
+            }
+            __syncthreads();
+            // ranks of the visible candidates (thread t owns slots 4t .. 4t + 3)
+            uint32_t f[kPreItems], run = 0;
+#pragma unroll
+            for (int k = 0; k < kPreItems; ++k) {
+                const int j = tid * kPreItems + k;
+                f[k] = j < ncand ? S.vis[j] : 0u;
+                run += f[k];
+            }
+            uint32_t incl = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
-            if (lane < kPreItems * 8) S.cnt[lane] = incl - v;
-            if (lane == 31) S.ncand = incl;
-        }
-        __syncthreads();
+            if (lane == 31) S.wsum[warp] = incl;
+            __syncthreads();
+            uint32_t wb = 0, total = 0;
 #pragma unroll
-        for (int k = 0; k < kPreItems; ++k)
-            if ((bal[k] >> lane) & 1u)
-                S.cand[S.cnt[k * 8 + warp] + __popc(bal[k] & lt)] =
-                    (uint32_t)(b * kPrePart + k * kPreThreads + tid);
-        if (tid == 0 && S.sel) atomicAdd(&counters[CNT_CUT], S.sel);
-        __syncthreads();
-        // phase B: full preprocess, densely over the candidates, results staged
-        const int ncand = (int)S.ncand;
-        for (int j = tid; j < ncand; j += kPreThreads) {
-            PreOut o;
-            const bool vis = preprocess_one<A>(sc, cam, S.cand[j], tile_w, tile_h, o);
-            S.vis[j] = vis ? 1u : 0u;
-            if (vis) {
-                store_rec(S.rec, j, o);
-                S.key[j] = o.key;
-                o.rect.z = (uint32_t)c;
-                S.rect[j] = o.rect;
+            for (int w = 0; w < kPreThreads / 32; ++w) {
+                if (w < warp) wb += S.wsum[w];
+                total += S.wsum[w];
             }
-        }
-        __syncthreads();
-        // ranks of the visible candidates (thread t owns slots 4t .. 4t + 3)
-        uint32_t f[kPreItems], run = 0;
+            uint32_t r = wb + incl - run;
 #pragma unroll
-        for (int k = 0; k < kPreItems; ++k) {
-            const int j = tid * kPreItems + k;
-            f[k] = j < ncand ? S.vis[j] : 0u;
-            run += f[k];
-        }
-        uint32_t incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) S.wsum[warp] = incl;
-        __syncthreads();
-        uint32_t wb = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < kPreThreads / 32; ++w) {
-            if (w < warp) wb += S.wsum[w];
-            total += S.wsum[w];
-        }
-        uint32_t r = wb + incl - run;
-#pragma unroll
-        for (int k = 0; k < kPreItems; ++k) {
-            const int j = tid * kPreItems + k;
-            if (j < ncand) S.vis[j] = f[k] ? (r | 0x80000000u) : 0u;
-            r += f[k];
-        }
-        if (tid == 0) {
-            unsigned long long off = 0;
-            if (total) {
-                off = atomicAdd(alloc, (unsigned long long)total);
-                atomicAdd(&vis_count[c], total);
-                if (off + total > (unsigned long long)rec_cap) latch_error(err, kErrCapacity);
+            for (int k = 0; k < kPreItems; ++k) {
+                const int j = tid * kPreItems + k;
+                if (j < ncand) S.vis[j] = f[k] ? (r | 0x80000000u) : 0u;
+                r += f[k];
             }
-            S.off = off;
-            part_info[(int64_t)c * nblk + b] =
-                make_uint2((uint32_t)min(off, (unsigned long long)rec_cap), total);
-        }
-        __syncthreads();
-        const unsigned long long base = S.off;
-        for (int j = tid; j < ncand; j += kPreThreads) {
-            const uint32_t v = S.vis[j];
-            const unsigned long long pos = base + (v & 0x7fffffffu);
-            if (v && pos < (unsigned long long)rec_cap) {
-                rec[pos] = S.rec[j];
-                dkey[pos] = S.key[j];
-                rect[pos] = S.rect[j];
+            if (tid == 0) {
+                unsigned long long off = 0;
+                if (total) {
+                    off = atomicAdd(alloc, (unsigned long long)total);
+                    atomicAdd(&vis_count[c], total);
+                    if (off + total > (unsigned long long)rec_cap) latch_error(err, kErrCapacity);
+                }
+                S.off = off;
+                part_info[(int64_t)c * nblk + b] =
+                    make_uint2((uint32_t)min(off, (unsigned long long)rec_cap), total);
             }
+            __syncthreads();
+            const unsigned long long base = S.off;
+            for (int j = tid; j < ncand; j += kPreThreads) {
+                const uint32_t v = S.vis[j];
+                const unsigned long long pos = base + (v & 0x7fffffffu);
+                if (v && pos < (unsigned long long)rec_cap) {
+                    rec[pos] = S.rec[j];
+                    dkey[pos] = S.key[j];
+                    rect[pos] = S.rect[j];
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -622,29 +701,32 @@ __global__ void k_part_gather(const uint32_t *__restrict__ part_list, int n_cams
 
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
                    int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
-                   uint32_t *counters, uint32_t *part_list, uint2 *part_info, int *err,
-                   int tile_w, int tile_h, int use_block_cull, int grid, cudaStream_t st) {
+                   uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
+                   int *err, int tile_w, int tile_h, int use_block_cull, int grid,
+                   cudaStream_t st) {
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
     cudaMemsetAsync(vis_count, 0, (size_t)n_cams * sizeof(uint32_t), st);
-    const int64_t nparts = nblk * n_cams;
-    const int lgrid = (int)std::min<int64_t>((nparts + 255) / 256, 8 * 1024);
-    k_live_parts<<<std::max(lgrid, 1), 256, 0, st>>>(sc, cams, n_cams, nblk, part_list, part_info,
-                                                     counters, tile_w, tile_h, use_block_cull, err);
+    const int64_t nq = nblk * ((n_cams + kGroupCams - 1) / kGroupCams);
+    // 8 warps per CTA, two (block, camera chunk) items per warp and iteration
+    const int lgrid = (int)std::min<int64_t>((nq + 15) / 16, 8 * 1024);
+    k_live_parts<<<std::max(lgrid, 1), 256, 0, st>>>(sc, cams, n_cams, nblk, part_list,
+                                                     group_list, part_info, counters, tile_w,
+                                                     tile_h, use_block_cull, err);
     switch (sc.attr_dtype) {
     case NGS_F16:
         k_cutpre<__half, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-            part_list, part_info, err, tile_w, tile_h);
+            part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     case NGS_BF16:
         k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-            part_list, part_info, err, tile_w, tile_h);
+            part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     default:
         k_cutpre<float, Rec32><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
             sc, cams, n_cams, (Rec32 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-            part_list, part_info, err, tile_w, tile_h);
+            part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     }
 }

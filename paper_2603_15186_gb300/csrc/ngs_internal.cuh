@@ -223,6 +223,7 @@ struct Work {
     // cut+preprocess partition tables, [cams][node blocks]: live partition ids,
     // (record offset, count), dense position of the first record
     uint32_t *part_list = nullptr;
+    uint2 *group_list = nullptr;
     uint2 *part_info = nullptr;
     uint32_t *part_pos = nullptr;
     int64_t part_cap = 0;
@@ -248,6 +249,7 @@ enum : int {
     TK_SORT0 = 8,             // 8 .. 8 + 16: one ticket per sort pass
     CNT_ALLOC = 24,           // 24, 25: 64-bit record allocation counter
     CNT_LIVE = 26,            // live cut+preprocess partitions
+    CNT_GROUPS = 27,          // groups of live partitions (same node block)
     TK_COMPOSITE = 28, N_COUNTERS = 32
 };
 
@@ -266,11 +268,13 @@ int cut_partition_nodes();
 // partition (block of cutpre_partition_nodes() nodes, camera) in node order at
 // an atomically allocated offset of rec / dkey_sparse / rect; (offset, count)
 // per partition in part_info[camera * nblk + block]; visible Gaussians per
-// camera in vis_count; counters[CNT_CUT], [CNT_LIVE], [CNT_ALLOC], [TK_PRE]
+// camera in vis_count; counters[CNT_CUT], [CNT_LIVE], [CNT_GROUPS],
+// [CNT_ALLOC], [TK_PRE]. part_list and group_list hold part_cap entries.
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
                    int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
-                   uint32_t *counters, uint32_t *part_list, uint2 *part_info, int *err,
-                   int tile_w, int tile_h, int use_block_cull, int grid, cudaStream_t st);
+                   uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
+                   int *err, int tile_w, int tile_h, int use_block_cull, int grid,
+                   cudaStream_t st);
 int cutpre_partition_nodes();
 void cutpre_init_attributes();
 // dense depth keys (camera-major, node order) and their record indices for the
