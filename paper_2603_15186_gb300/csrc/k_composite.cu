@@ -317,6 +317,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             }
             __syncthreads();
             if (T2.x > 0.0f || T2.y > 0.0f) {
+                uint32_t live_groups = 0;   // groups of four, counted per live pixel
                 // both pixels in packed (f32x2) arithmetic, every step the same
                 // rounded operation per pixel as a scalar evaluation:
                 //   q = (A lx + a1) lx + a0; alpha = min(0.99, 2^q), 0 if
@@ -340,7 +341,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                         const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
                         q[u] = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
                     }
-                    evals += (T2.x > 0.0f ? 4u : 0u) + (T2.y > 0.0f ? 4u : 0u);
+                    live_groups += (T2.x > 0.0f ? 1u : 0u) + (T2.y > 0.0f ? 1u : 0u);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const float2 mq = make_float2(q[u].x >= kLog2AlphaMin ? 1.0f : 0.0f,
@@ -362,6 +363,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     }
                     if (!(T2.x > 0.0f || T2.y > 0.0f)) break;
                 }
+                evals += 4ull * live_groups;
             }
         }
         const int64_t plane = (int64_t)cam.width * cam.height;
