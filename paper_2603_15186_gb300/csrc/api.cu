@@ -402,7 +402,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
                   c->block_cull ? 1 : 0, c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
     launch_gather_keys(w.vis_count, nc, c->scene, w.part_info, w.part_pos, w.part_list,
-                       w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.err,
+                       w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.hist, w.err,
                        c->num_sms * 8, st);
     mark(c, sb_index, MK_PRE, st);
     SortHook dh{c, sb_index, MK_DHIST, st};
@@ -415,6 +415,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
     da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
     da.skip_last_keys = true;   // later stages read the record order only
+    da.hist_ready = true;       // counted by the key gather
     launch_sort(da, c->grid_sort32, st);
     eo += 4;
     const int dsel = 4 & 1;  // four passes: the result is back in buffer 0
@@ -465,11 +466,11 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
 
 int kernels_of(const SubBatch &sb, bool batched) {
     // epoch bump, live partitions, fused cut + preprocess, partition scan and
-    // gather; depth sort (histogram, digit scan, 4 passes); pair offsets,
-    // duplication; tile sort (digit scan and passes, the last one writing the
-    // tile ranges) or, with a single tile, the ranges kernel; compositing; and
-    // in the batched path the stats copy
-    return 5 + 6 + 2 + (sb.tile_passes > 0 ? 1 + sb.tile_passes : 1) + 1 + (batched ? 1 : 0);
+    // key gather (which also counts the depth histograms); depth sort (digit
+    // scan, 4 passes); pair offsets, duplication; tile sort (digit scan and
+    // passes, the last one writing the tile ranges) or, with a single tile,
+    // the ranges kernel; compositing; and in the batched path the stats copy
+    return 5 + 5 + 2 + (sb.tile_passes > 0 ? 1 + sb.tile_passes : 1) + 1 + (batched ? 1 : 0);
 }
 
 ngs_status read_u32(const uint32_t *d, uint32_t *h, cudaStream_t st) {
@@ -525,7 +526,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         if ((s = read_u32(w.counters + CNT_CUT, &n_cut, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
         launch_gather_keys(w.vis_count, 1, c->scene, w.part_info, w.part_pos, w.part_list,
-                           w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.err,
+                           w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.hist, w.err,
                            (int)std::max<int64_t>(1, std::min<int64_t>(nblk / 8 + 1,
                                                                        8 * c->num_sms)), st);
         mark(c, ci, MK_PRE, st);
@@ -542,7 +543,8 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         da.epoch = w.epoch; da.epoch_off = eo; da.err = w.err;
         SortHook dh{c, ci, MK_DHIST, st};
         da.hook = c->timing ? sort_hook : nullptr; da.hook_user = &dh;
-    da.skip_last_keys = true;   // later stages read the record order only
+        da.skip_last_keys = true;   // later stages read the record order only
+        da.hist_ready = true;       // counted by the key gather
         launch_sort(da, std::min(gsort_v, c->grid_sort32), st);
         eo += 4;
         const int gscan = std::max<int64_t>(1, ((int64_t)n_vis + scan_partition() - 1) /

@@ -673,29 +673,61 @@ k_part_scan(const uint32_t *__restrict__ vis_count, int n_cams, int64_t nblk,
 }
 
 // Dense depth-sort input, part 2: one warp per live partition copies its keys
-// and writes their record indices at the partition's dense position.
-__global__ void k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
-                              const uint2 *__restrict__ part_info,
-                              const uint32_t *__restrict__ part_pos,
-                              const uint32_t *__restrict__ dkey_sparse,
-                              uint32_t *__restrict__ dkey, uint32_t *__restrict__ didx,
-                              const uint32_t *counters, int64_t cap, const int *err) {
+// and writes their record indices at the partition's dense position. On the
+// way it counts the digit histograms of the four 8-bit passes of the depth
+// sort into hist[4][256] (zeroed beforehand): positive float depths share
+// their high digits, so a warp whose keys agree on a digit adds its count once
+// instead of contending on one shared-memory counter.
+__global__ void __launch_bounds__(256)
+k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
+              const uint2 *__restrict__ part_info, const uint32_t *__restrict__ part_pos,
+              const uint32_t *__restrict__ dkey_sparse, uint32_t *__restrict__ dkey,
+              uint32_t *__restrict__ didx, const uint32_t *counters, int64_t cap,
+              uint32_t *hist, const int *err) {
+    __shared__ uint32_t s_h[4][256];
     if (*err) return;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 4 * 256; i += blockDim.x) (&s_h[0][0])[i] = 0;
+    __syncthreads();
     const uint32_t n_live = counters[CNT_LIVE];
-    const int lane = threadIdx.x & 31;
+    const int lane = tid & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_live; i += nw) {
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + tid) >> 5; i < n_live; i += nw) {
         const uint32_t t = part_list[i];
         const uint32_t b = t / (uint32_t)n_cams, c = t - b * (uint32_t)n_cams;
         const int64_t idx = (int64_t)c * nblk + b;
         const uint2 info = part_info[idx];
         const int64_t pos = part_pos[idx];
-        for (uint32_t k = lane; k < info.y; k += 32) {
-            if (pos + k < cap && (int64_t)info.x + k < cap) {
-                dkey[pos + k] = dkey_sparse[info.x + k];
+        // uniform trip count: every lane reaches the warp collectives
+        for (uint32_t k0 = 0; k0 < info.y; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const bool valid = k < info.y && pos + k < cap && (int64_t)info.x + k < cap;
+            uint32_t key = 0;
+            if (valid) {
+                key = dkey_sparse[info.x + k];
+                dkey[pos + k] = key;
                 didx[pos + k] = info.x + k;
             }
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            if (vmask) {
+                const int leader = __ffs(vmask) - 1;
+#pragma unroll
+                for (int qd = 0; qd < 4; ++qd) {
+                    const uint32_t d = (key >> (8 * qd)) & 255u;
+                    const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+                    if (__all_sync(0xffffffffu, !valid || d == dl)) {
+                        if (lane == leader) atomicAdd(&s_h[qd][d], (uint32_t)__popc(vmask));
+                    } else if (valid) {
+                        atomicAdd(&s_h[qd][d], 1u);
+                    }
+                }
+            }
         }
+    }
+    __syncthreads();
+    for (int i = tid; i < 4 * 256; i += blockDim.x) {
+        const uint32_t v = (&s_h[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
     }
 }
 
@@ -734,12 +766,14 @@ void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *
 void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &sc,
                         const uint2 *part_info, uint32_t *part_pos, const uint32_t *part_list,
                         const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,
-                        uint32_t *counters, int64_t cap, int *err, int grid, cudaStream_t st) {
+                        uint32_t *counters, int64_t cap, uint32_t *hist, int *err, int grid,
+                        cudaStream_t st) {
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
     k_part_scan<<<n_cams, 1024, 0, st>>>(vis_count, n_cams, nblk, part_info, part_pos, counters,
                                          cap, err);
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4 * 256, st);
     k_part_gather<<<grid, 256, 0, st>>>(part_list, n_cams, nblk, part_info, part_pos, dkey_sparse,
-                                        dkey, didx, counters, cap, err);
+                                        dkey, didx, counters, cap, hist, err);
 }
 
 int cutpre_partition_nodes() { return kPrePart; }

@@ -278,11 +278,12 @@ void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *
 int cutpre_partition_nodes();
 void cutpre_init_attributes();
 // dense depth keys (camera-major, node order) and their record indices for the
-// sort; counters[CNT_VIS]
+// sort, and the depth sort's digit histograms in hist[4][256]; counters[CNT_VIS]
 void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &sc,
                         const uint2 *part_info, uint32_t *part_pos, const uint32_t *part_list,
                         const uint32_t *dkey_sparse, uint32_t *dkey, uint32_t *didx,
-                        uint32_t *counters, int64_t cap, int *err, int grid, cudaStream_t st);
+                        uint32_t *counters, int64_t cap, uint32_t *hist, int *err, int grid,
+                        cudaStream_t st);
 
 // radix sort (onesweep) of (uint32 | uint64 key, uint32 value) pairs; n from
 // device memory (*n_dev) or host (n_host >= 0). Result lands in buffer
