@@ -15,11 +15,13 @@
 // are the sort key and it decides the near-plane cull. The oracle evaluates
 // the same sequence, so keys and culls agree bit for bit. No float64 anywhere.
 //
-// Output: each partition (block of nodes, camera) takes space for its visible
-// Gaussians with one atomic allocation and writes them there in node order;
-// its (offset, count) goes to a partition table. The dense depth-sort input is
-// then gathered in camera-major, node-id order through a scan of that table,
-// so depth ties are broken by node id whatever the allocation order was.
+// Output: each partition (block of nodes, camera) takes one slot per candidate
+// (a Gaussian that passed the cut and the conservative cull) with one atomic
+// allocation; visible ones are written to their slots in node order, the
+// others leave a hole; (first slot, visible and candidate counts) go to a
+// partition table. The dense depth-sort input is then gathered in
+// camera-major, node-id order through a scan of that table, so depth ties are
+// broken by node id whatever the allocation order was.
 // HBM per cut Gaussian: 4 B id + 16 B position (always); quaternion
 // 16 B and scale/opacity 16 B (f32) or 8 B (f16/bf16) for those in front of
 // the near plane; SH 192 B (f32) or 96 B for those with a non-empty rectangle;
@@ -34,7 +36,6 @@ namespace ngs {
 constexpr int kPreThreads = 256;
 constexpr int kPreItems = 4;                          // phase-A nodes per thread
 constexpr int kPrePart = kPreThreads * kPreItems;     // nodes per partition
-constexpr int kMaxCamsPerBatch = 1024;
 
 
 template <typename A> struct Attr;
@@ -423,29 +424,33 @@ __global__ void k_live_parts(SceneDev sc, const DevCamera *__restrict__ cams, in
 }
 
 // Fused cut + preprocess over groups of live partitions (one node block and up
-// to kGroupCams cameras), taken from an atomic ticket. Phase A loads each
-// node's box, parent box, position and scale/opacity once for the whole group
-// and applies the cut rule and the conservative cull for every camera of it;
-// then, per camera, the candidates are compacted in node order and phase B
-// preprocesses them densely, staging the results in shared memory until the
-// partition knows where its visible Gaussians go (one atomic allocation); they
-// are written there in node order.
+// to kGroupCams cameras), taken from an atomic ticket.
+//  - Phase A loads each node's box, parent box, position and scale/opacity
+//    once for the whole group and applies the cut rule and the conservative
+//    cull for every camera of it (one ballot per camera, item and warp).
+//  - The (node, camera) candidates of the group are listed node-major, and
+//    each partition takes output space for its candidates with one atomic; a
+//    candidate's slot is its rank among its camera's candidates in node order.
+//  - Phase B preprocesses the list densely (neighbouring entries mostly share a
+//    node, so its attributes are read once into L1) and writes each result
+//    straight to its slot; a candidate that turns out invisible leaves its
+//    slot with the key kKeyHole, which the key gather skips.
+//  - Per partition: (first slot, visible | candidates << 16) in part_info.
+constexpr uint32_t kKeyHole = 0xffffffffu;   // a NaN pattern: never a depth key
+
 template <typename R>
 struct CutPreSmem {
-    uint32_t cand[kPrePart];      // candidate node ids, node order
-    R rec[kPrePart];
-    uint32_t key[kPrePart];
-    uint4 rect[kPrePart];
-    uint32_t vis[kPrePart];       // visible flag, then (rank | 1 << 31)
+    uint16_t ent[kGroupCams * kPrePart];        // node-major candidates: node << 4 | camera
     uint32_t balw[kGroupCams][kPreItems * 8];   // candidate ballot per (camera, item, warp)
-    uint32_t cnt[kPreItems * 8];
-    uint32_t sel[kGroupCams];
+    uint32_t cex[kGroupCams][kPreItems * 8];    // candidates of the camera before (item, warp)
+    unsigned long long off[kGroupCams];         // first slot of each camera's partition
+    uint32_t ncand[kGroupCams], nvis[kGroupCams], sel[kGroupCams];
     CamLite cam[kGroupCams];
     uint32_t gcam[kGroupCams];
     uint32_t wsum[kPreThreads / 32];
-    uint32_t goff, gcnt, ncand;
-    unsigned long long off;
+    uint32_t goff, gcnt;
 };
+static_assert(kGroupCams <= 16 && kPrePart <= 4096, "entries pack node and camera in 16 bits");
 
 template <typename A, typename R>
 __global__ void __launch_bounds__(kPreThreads)
@@ -461,7 +466,6 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
     const uint32_t n_groups = counters[CNT_GROUPS];
     unsigned long long *alloc = reinterpret_cast<unsigned long long *>(counters + CNT_ALLOC);
-    const uint32_t lt = lanemask_lt();
     for (;;) {
         if (tid == 0) {
             const uint32_t i = atomicAdd(&counters[TK_PRE], 1u);
@@ -484,9 +488,12 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             l.tiles_x = d.tiles_x; l.tiles_y = d.tiles_y;
             S.gcam[tid] = (uint32_t)c;
             S.sel[tid] = 0;
+            S.nvis[tid] = 0;
         }
         __syncthreads();
-        // phase A: per node, one set of loads for every camera of the group
+        // phase A: per node, one set of loads for every camera of the group;
+        // mask[k]: the cameras for which node k of this thread is a candidate
+        uint32_t mask[kPreItems];
 #pragma unroll 1
         for (int k = 0; k < kPreItems; ++k) {
             const int64_t node = b * kPrePart + k * kPreThreads + tid;
@@ -509,6 +516,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             }
             nd.K = 2.0f * logf(255.0f * so[3]);
             nd.smax = expf(fmaxf(fmaxf(so[0], so[1]), so[2]));
+            uint32_t m = 0;
             for (int i = 0; i < gcnt; ++i) {
                 const CamLite &cam = S.cam[i];
                 const bool sel =
@@ -518,6 +526,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
                     (par < 0 || granularity(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
                                             cam.fx) > cam.tau);
                 const bool cand = sel && precull(cam, nd, tile_w, tile_h);
+                m |= cand ? 1u << i : 0u;
                 const uint32_t nsel = __popc(__ballot_sync(0xffffffffu, sel));
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
                 if (lane == 0) {
@@ -525,56 +534,37 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
                     if (nsel) atomicAdd(&S.sel[i], nsel);
                 }
             }
+            mask[k] = m;
         }
         __syncthreads();
-        for (int i = 0; i < gcnt; ++i) {
-            const int c = (int)S.gcam[i];
-            const DevCamera &cam = cams[c];
-            // candidates of camera i compacted into S.cand in node order
-            if (warp == 0) {
-                const uint32_t v = lane < kPreItems * 8 ? __popc(S.balw[i][lane]) : 0u;
-                uint32_t incl = v;
+        // per camera: candidates before each (item, warp) in node order, and
+        // the partition's output space
+        for (int i = warp; i < gcnt; i += kPreThreads / 32) {
+            const uint32_t v = lane < kPreItems * 8 ? __popc(S.balw[i][lane]) : 0u;
+            uint32_t incl = v;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane < kPreItems * 8) S.cex[i][lane] = incl - v;
+            if (lane == 31) {
+                S.ncand[i] = incl;
+                unsigned long long off = 0;
+                if (incl) {
+                    off = atomicAdd(alloc, (unsigned long long)incl);
+                    if (off + incl > (unsigned long long)rec_cap) latch_error(err, kErrCapacity);
                 }
-                if (lane < kPreItems * 8) S.cnt[lane] = incl - v;
-                if (lane == 31) S.ncand = incl;
+                S.off[i] = off;
             }
-            __syncthreads();
+        }
+        // node-major entry list: node v = k * kPreThreads + tid has popc(mask[k])
+        // entries, one per candidate camera in camera order
+        uint32_t base = 0;
 #pragma unroll
-            for (int k = 0; k < kPreItems; ++k) {
-                const uint32_t bal = S.balw[i][k * 8 + warp];
-                if ((bal >> lane) & 1u)
-                    S.cand[S.cnt[k * 8 + warp] + __popc(bal & lt)] =
-                        (uint32_t)(b * kPrePart + k * kPreThreads + tid);
-            }
-            if (tid == 0 && S.sel[i]) atomicAdd(&counters[CNT_CUT], S.sel[i]);
-            __syncthreads();
-            // phase B: full preprocess, densely over the candidates, results staged
-            const int ncand = (int)S.ncand;
-            for (int j = tid; j < ncand; j += kPreThreads) {
-                PreOut o;
-                const bool vis = preprocess_one<A>(sc, cam, S.cand[j], tile_w, tile_h, o);
-                S.vis[j] = vis ? 1u : 0u;
-                if (vis) {
-                    store_rec(S.rec, j, o);
-                    S.key[j] = o.key;
-                    o.rect.z = (uint32_t)c;
-                    S.rect[j] = o.rect;
-                }
-            }
-            __syncthreads();
-            // ranks of the visible candidates (thread t owns slots 4t .. 4t + 3)
-            uint32_t f[kPreItems], run = 0;
-#pragma unroll
-            for (int k = 0; k < kPreItems; ++k) {
-                const int j = tid * kPreItems + k;
-                f[k] = j < ncand ? S.vis[j] : 0u;
-                run += f[k];
-            }
-            uint32_t incl = run;
+        for (int k = 0; k < kPreItems; ++k) {
+            const uint32_t v = __popc(mask[k]);
+            uint32_t incl = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -582,43 +572,54 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             }
             if (lane == 31) S.wsum[warp] = incl;
             __syncthreads();
-            uint32_t wb = 0, total = 0;
+            uint32_t wb = 0, tot = 0;
 #pragma unroll
             for (int w = 0; w < kPreThreads / 32; ++w) {
                 if (w < warp) wb += S.wsum[w];
-                total += S.wsum[w];
+                tot += S.wsum[w];
             }
-            uint32_t r = wb + incl - run;
-#pragma unroll
-            for (int k = 0; k < kPreItems; ++k) {
-                const int j = tid * kPreItems + k;
-                if (j < ncand) S.vis[j] = f[k] ? (r | 0x80000000u) : 0u;
-                r += f[k];
-            }
-            if (tid == 0) {
-                unsigned long long off = 0;
-                if (total) {
-                    off = atomicAdd(alloc, (unsigned long long)total);
-                    atomicAdd(&vis_count[c], total);
-                    if (off + total > (unsigned long long)rec_cap) latch_error(err, kErrCapacity);
-                }
-                S.off = off;
-                part_info[(int64_t)c * nblk + b] =
-                    make_uint2((uint32_t)min(off, (unsigned long long)rec_cap), total);
-            }
-            __syncthreads();
-            const unsigned long long base = S.off;
-            for (int j = tid; j < ncand; j += kPreThreads) {
-                const uint32_t v = S.vis[j];
-                const unsigned long long pos = base + (v & 0x7fffffffu);
-                if (v && pos < (unsigned long long)rec_cap) {
-                    rec[pos] = S.rec[j];
-                    dkey[pos] = S.key[j];
-                    rect[pos] = S.rect[j];
-                }
-            }
-            __syncthreads();
+            uint32_t e = base + wb + incl - v;
+            const uint32_t nodev = (uint32_t)(k * kPreThreads + tid);
+            for (uint32_t mm = mask[k]; mm; mm &= mm - 1)
+                S.ent[e++] = (uint16_t)((nodev << 4) | (uint32_t)(__ffs(mm) - 1));
+            base += tot;
+            __syncthreads();   // S.wsum is reused by the next item
         }
+        const int nent = (int)base;
+        // phase B: preprocess every (node, camera) candidate straight into its slot
+        for (int e = tid; e < nent; e += kPreThreads) {
+            const uint32_t en = S.ent[e];
+            const int i = (int)(en & 15u);
+            const uint32_t v = en >> 4;
+            const int k = (int)(v / kPreThreads), w = (int)((v % kPreThreads) >> 5),
+                      l = (int)(v & 31u);
+            const uint32_t rank = S.cex[i][k * 8 + w] + __popc(S.balw[i][k * 8 + w] & ((1u << l) - 1u));
+            const unsigned long long pos = S.off[i] + rank;
+            if (pos >= (unsigned long long)rec_cap) continue;   // capacity already latched
+            const int c = (int)S.gcam[i];
+            PreOut o;
+            const uint32_t node = (uint32_t)(b * kPrePart + v);
+            if (preprocess_one<A>(sc, cams[c], node, tile_w, tile_h, o)) {
+                store_rec(rec, (int64_t)pos, o);
+                dkey[pos] = o.key;
+                o.rect.z = (uint32_t)c;
+                rect[pos] = o.rect;
+                atomicAdd(&S.nvis[i], 1u);
+            } else {
+                dkey[pos] = kKeyHole;
+            }
+        }
+        __syncthreads();
+        if (tid < gcnt) {
+            const int c = (int)S.gcam[tid];
+            const uint32_t nv = S.nvis[tid];
+            part_info[(int64_t)c * nblk + b] =
+                make_uint2((uint32_t)min(S.off[tid], (unsigned long long)rec_cap),
+                           nv | (S.ncand[tid] << 16));
+            if (nv) atomicAdd(&vis_count[c], nv);
+            if (S.sel[tid]) atomicAdd(&counters[CNT_CUT], S.sel[tid]);
+        }
+        __syncthreads();
     }
 }
 
@@ -664,7 +665,7 @@ k_part_scan(const uint32_t *__restrict__ vis_count, int n_cams, int64_t nblk,
     uint32_t carry = s_base;
     for (int64_t b0 = 0; b0 < nblk; b0 += 1024) {
         const int64_t b = b0 + tid;
-        const uint32_t n = b < nblk ? part_info[(int64_t)c * nblk + b].y : 0u;
+        const uint32_t n = b < nblk ? part_info[(int64_t)c * nblk + b].y & 0xffffu : 0u;
         uint32_t chunk;
         const uint32_t e = block_scan(n, chunk);
         if (b < nblk) part_pos[(int64_t)c * nblk + b] = carry + e;
@@ -672,8 +673,9 @@ k_part_scan(const uint32_t *__restrict__ vis_count, int n_cams, int64_t nblk,
     }
 }
 
-// Dense depth-sort input, part 2: one warp per live partition copies its keys
-// and writes their record indices at the partition's dense position. On the
+// Dense depth-sort input, part 2: one warp per live partition copies the keys
+// of its visible Gaussians (skipping holes) and writes their record indices at
+// the partition's dense position. On the
 // way it counts the digit histograms of the four 8-bit passes of the depth
 // sort into hist[4][256] (zeroed beforehand): positive float depths share
 // their high digits, so a warp whose keys agree on a digit adds its count once
@@ -697,17 +699,24 @@ k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
         const uint32_t b = t / (uint32_t)n_cams, c = t - b * (uint32_t)n_cams;
         const int64_t idx = (int64_t)c * nblk + b;
         const uint2 info = part_info[idx];
-        const int64_t pos = part_pos[idx];
-        // uniform trip count: every lane reaches the warp collectives
-        for (uint32_t k0 = 0; k0 < info.y; k0 += 32) {
+        const uint32_t ncand = info.y >> 16;
+        int64_t pos = part_pos[idx];
+        // the partition's slots hold its candidates in node order; the visible
+        // ones are packed to their dense positions, holes are skipped. Uniform
+        // trip count: every lane reaches the warp collectives
+        for (uint32_t k0 = 0; k0 < ncand; k0 += 32) {
             const uint32_t k = k0 + lane;
-            const bool valid = k < info.y && pos + k < cap && (int64_t)info.x + k < cap;
-            uint32_t key = 0;
+            uint32_t key = kKeyHole;
+            if (k < ncand && (int64_t)info.x + k < cap) key = dkey_sparse[info.x + k];
+            const bool vis = key != kKeyHole;
+            const uint32_t vb = __ballot_sync(0xffffffffu, vis);
+            const int64_t dst = pos + __popc(vb & lanemask_lt());
+            const bool valid = vis && dst < cap;
             if (valid) {
-                key = dkey_sparse[info.x + k];
-                dkey[pos + k] = key;
-                didx[pos + k] = info.x + k;
+                dkey[dst] = key;
+                didx[dst] = info.x + k;
             }
+            pos += __popc(vb);
             const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
             if (vmask) {
                 const int leader = __ffs(vmask) - 1;

@@ -264,10 +264,11 @@ void launch_cut(const SceneDev &sc, const DevCamera *cams, int n_cams, uint32_t 
                 int grid, cudaStream_t st);
 int cut_partition_nodes();
 
-// fused cut + preprocess of cameras [0, n_cams): the visible Gaussians of each
+// fused cut + preprocess of cameras [0, n_cams): the candidates of each
 // partition (block of cutpre_partition_nodes() nodes, camera) in node order at
-// an atomically allocated offset of rec / dkey_sparse / rect; (offset, count)
-// per partition in part_info[camera * nblk + block]; visible Gaussians per
+// an atomically allocated offset of rec / dkey_sparse / rect, invisible ones
+// as holes (key 0xffffffff); (offset, visible | candidates << 16) per
+// partition in part_info[camera * nblk + block]; visible Gaussians per
 // camera in vis_count; counters[CNT_CUT], [CNT_LIVE], [CNT_GROUPS],
 // [CNT_ALLOC], [TK_PRE]. part_list and group_list hold part_cap entries.
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
