@@ -169,14 +169,16 @@ def measured_peaks():
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the launches of one timed step of this workload at 16x16 tiles, batch
-# 128) from the ncu capture summarised in profiles/traffic_batch256_floor4m_f16.md.
-# Each figure is tied to the sources of the kernel it was taken on (sha256 of
-# the files, concatenated, first 16 hex digits) and reads null once they change.
+# over the launches of one timed step of this workload at 32x32 tiles in 16x16
+# compositing blocks, batch 128) from the ncu capture summarised in
+# profiles/traffic_batch256_floor4m_f16.md. Each figure is tied to the sources
+# of the kernel it was taken on (sha256 of the files, concatenated, first 16 hex
+# digits) and reads null once they change.
 MEASURED_TRAFFIC = {
-    "onesweep": (664_364_000, ("k_sort.cu", "ngs_internal.cuh"), "79247cf1c8ff3266"),
-    "composite": (212_884_573, ("k_composite.cu", "ngs_internal.cuh"), "6fb40aed0e440d90"),
-    "cut_preprocess": (1_339_416_413, ("k_preprocess.cu", "ngs_internal.cuh"), "6bd8640bd4f8cb45"),
+    "onesweep": (1_272_517_304, ("k_sort.cu", "ngs_internal.cuh"), "1e035c0eb913455c"),
+    "composite": (606_189_226, ("k_composite.cu", "ngs_internal.cuh"), "5a35f6db8af31a7c"),
+    "cut_preprocess": (4_084_315_306, ("k_preprocess.cu", "ngs_internal.cuh"), "5de46d2496810877"),
+    "duplicate": (5_286_151_082, ("k_binning.cu", "ngs_internal.cuh"), "ae191bb90f7d2793"),
 }
 
 
