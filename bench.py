@@ -214,8 +214,11 @@ def stage_bytes(st, n_nodes, n_cams, pixels, tiles, attr="f16"):
         # the last depth pass writes values only; the last tile pass writes
         # values and each tile's range (8 B per tile) instead of keys
         "depth_pass0": 16 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 12 * V,
-        "pair_offsets": 24 * V,
-        "duplicate": 24 * V + 8 * P,
+        # pair offsets: index, gathered rect and offset per Gaussian, plus the
+        # rect written in depth order for the pair emission, which reads it
+        # and the offset back sequentially
+        "pair_offsets": 40 * V,
+        "duplicate": 20 * V + 8 * P,
         "tile_hist": 4 * P,
         "tile_pass0": 16 * P, "tile_pass1": 12 * P + 8 * tiles, "tile_pass2": 0,
         "ranges": 8 * tiles,

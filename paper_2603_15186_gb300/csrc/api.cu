@@ -161,7 +161,7 @@ __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
 void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
-    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.group_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
+    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.group_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.rect_sorted); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
     dfree(w.hist); dfree(w.cams); dfree(w.work64);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
@@ -257,6 +257,7 @@ ngs_status ensure_work(ngs_ctx *c) {
     A(dalloc(&w.part_pos, (size_t)w.part_cap));
     A(dalloc((unsigned char **)&w.rec, (size_t)w.rec_cap * sizeof(Rec32)));
     A(dalloc(&w.rect, (size_t)w.rec_cap));
+    A(dalloc(&w.rect_sorted, (size_t)w.rec_cap));
     A(dalloc(&w.poff, (size_t)w.rec_cap));
     A(dalloc(&w.chunk_first, (size_t)dup_chunks(w.pair_cap)));
     for (int i = 0; i < 2; ++i) {
@@ -421,10 +422,10 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     const int dsel = 4 & 1;  // four passes: the result is back in buffer 0
     launch_pair_offsets(w.rect, w.didx[dsel], w.counters + CNT_VIS, w.poff, w.counters,
                         w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
-                        w.chunk_first, c->grid_scan, st);
+                        w.chunk_first, w.rect_sorted, c->grid_scan, st);
     mark(c, sb_index, MK_POFF, st);
     cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st);
-    launch_duplicate(w.rect, w.didx[dsel], w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
+    launch_duplicate(w.rect_sorted, w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
                      w.pair_cap, cams, w.pkey[0], w.pval[0], w.hist, sb.tile_passes, w.err,
                      c->grid_dup, st);
     mark(c, sb_index, MK_DUP, st);
@@ -551,7 +552,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
                                                    scan_partition());
         launch_pair_offsets(w.rect, w.didx[0], w.counters + CNT_VIS, w.poff, w.counters,
                             w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
-                            w.chunk_first, gscan, st);
+                            w.chunk_first, w.rect_sorted, gscan, st);
         mark(c, ci, MK_POFF, st);
         if ((s = read_u32(w.counters + CNT_PAIRS, &n_pairs, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
@@ -559,7 +560,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         const int gdup = (int)std::max<int64_t>(
             1, std::min<int64_t>(((int64_t)n_pairs + 2047) / 2048, 8 * (int64_t)c->num_sms));
         CK(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st));
-        launch_duplicate(w.rect, w.didx[0], w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
+        launch_duplicate(w.rect_sorted, w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
                          w.pair_cap, cams, w.pkey[0], w.pval[0], w.hist, sb.tile_passes, w.err,
                          gdup, st);
         mark(c, ci, MK_DUP, st);

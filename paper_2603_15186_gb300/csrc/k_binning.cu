@@ -69,14 +69,16 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v[kScanItems], uint32_t 
 // Exclusive scan with one-pass decoupled look-back. Input element i is
 // in[i] (kGather = false) or area(rect[idx[i]]) (kGather = true).
 // With kGather, also chunk_first[c] = the input position whose output range
-// [out[i], out[i] + in_i) holds element c * kDupChunk (c < chunk_cap).
+// [out[i], out[i] + in_i) holds element c * kDupChunk (c < chunk_cap), and
+// rect_out[i] = rect[idx[i]] with idx[i] in w: the one gather of the rects in
+// depth order, so that the pair emission reads them sequentially.
 template <bool kGather>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
        const uint32_t *__restrict__ idx, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
        uint32_t *total_out, int64_t total_cap, uint32_t *ticket, uint64_t *status,
        const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, uint32_t *chunk_first,
-       int64_t chunk_cap) {
+       int64_t chunk_cap, uint4 *__restrict__ rect_out) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_part, s_prev;
     if (*err) return;
@@ -95,8 +97,19 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) {
             const int64_t j = base + i;
-            if (j < n) v[i] = kGather ? rect_area(rect[idx[j]]) : in[j];
-            else v[i] = 0;
+            if (j < n) {
+                if (kGather) {
+                    const uint32_t r = idx[j];
+                    uint4 rr = rect[r];
+                    v[i] = rect_area(rr);
+                    rr.w = r;
+                    rect_out[j] = rr;
+                } else {
+                    v[i] = in[j];
+                }
+            } else {
+                v[i] = 0;
+            }
             a[i] = v[i];
         }
         const uint32_t total = block_scan(v, s_warp);
@@ -144,17 +157,17 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, i
                      uint32_t epoch_off, int *err, int grid, cudaStream_t st) {
     k_scan<false><<<grid, kScanThreads, 0, st>>>(in, nullptr, nullptr, out, n_dev, n_host, total,
                                                  -1, ticket, status, epoch, epoch_off, err,
-                                                 nullptr, 0);
+                                                 nullptr, 0, nullptr);
 }
 
 void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         uint32_t *chunk_first, int grid, cudaStream_t st) {
+                         uint32_t *chunk_first, uint4 *rect_sorted, int grid, cudaStream_t st) {
     k_scan<true><<<grid, kScanThreads, 0, st>>>(nullptr, rect, sorted_idx, poff, n_vis, -1,
                                                 counters + CNT_PAIRS, pair_cap, ticket, status,
                                                 epoch, epoch_off, err, chunk_first,
-                                                dup_chunks(pair_cap));
+                                                dup_chunks(pair_cap), rect_sorted);
 }
 
 // K4: the pair array is cut into chunks of kDupChunk pairs, so every CTA
@@ -165,7 +178,7 @@ void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const ui
 // the staged offsets. Tile-digit histograms of the radix passes that follow
 // are accumulated on the way.
 __global__ void __launch_bounds__(kDupThreads)
-k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_idx,
+k_duplicate(const uint4 *__restrict__ rect_sorted,
             const uint32_t *__restrict__ poff, const uint32_t *__restrict__ chunk_first,
             const uint32_t *n_vis_p, const uint32_t *n_pairs_p, int64_t pair_cap,
             const DevCamera *__restrict__ cams, uint32_t *__restrict__ pkey,
@@ -195,9 +208,8 @@ k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_
             const int cnt = rem < kDupWindow ? (int)rem : kDupWindow;
             __syncthreads();
             for (int j = tid; j < cnt; j += kDupThreads) {
-                const uint32_t r = sorted_idx[r0 + j];
-                s_idx[j] = r;
-                const uint4 rr = rect[r];
+                const uint4 rr = rect_sorted[r0 + j];   // record index in w
+                s_idx[j] = rr.w;
                 s_rect[j] = rr;
                 s_cam[j] = make_uint2(cams[rr.z].tile_base, (uint32_t)cams[rr.z].tiles_x);
                 s_off[j] = poff[r0 + j];
@@ -259,11 +271,11 @@ k_duplicate(const uint4 *__restrict__ rect, const uint32_t *__restrict__ sorted_
     }
 }
 
-void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
+void launch_duplicate(const uint4 *rect_sorted, const uint32_t *poff,
                       const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
                       int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
                       uint32_t *hist, int passes, int *err, int grid, cudaStream_t st) {
-    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect, sorted_idx, poff, chunk_first, n_vis, n_pairs,
+    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect_sorted, poff, chunk_first, n_vis, n_pairs,
                                               pair_cap, cams, pkey, pval,
                                               passes > 0 ? hist : nullptr, passes, err);
 }

@@ -231,6 +231,7 @@ struct Work {
     uint32_t *dkey[2] = {nullptr, nullptr};
     uint32_t *didx[2] = {nullptr, nullptr};
     uint4 *rect = nullptr;            // x0|y0<<16, x1|y1<<16, camera index, node id
+    uint4 *rect_sorted = nullptr;     // the visible rects in depth order, record index in w
     uint32_t *poff = nullptr;         // pair offsets per sorted record
     uint32_t *chunk_first = nullptr;  // first sorted record of each pair chunk
     uint32_t *pkey[2] = {nullptr, nullptr};
@@ -329,15 +330,17 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, i
 int scan_partition();
 
 // binning: tiles-touched scan over depth order (also the first record of every
-// pair chunk, chunk_first[dup_chunks(pair_cap)]), then pair emission
+// pair chunk, chunk_first[dup_chunks(pair_cap)], and the rects in depth order,
+// record index in w, in rect_sorted), then pair emission
 void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         uint32_t *chunk_first, int grid, cudaStream_t st);
+                         uint32_t *chunk_first, uint4 *rect_sorted, int grid, cudaStream_t st);
 int64_t dup_chunks(int64_t pair_cap);
-// emits the pairs and, if hist is given, adds the digit counts of their tile
-// keys for `passes` 8-bit radix passes to hist (zeroed by the caller)
-void launch_duplicate(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *poff,
+// emits the pairs from the depth-ordered rects and, if hist is given, adds the
+// digit counts of their tile keys for `passes` 8-bit radix passes to hist
+// (zeroed by the caller)
+void launch_duplicate(const uint4 *rect_sorted, const uint32_t *poff,
                       const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
                       int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
                       uint32_t *hist, int passes, int *err, int grid, cudaStream_t st);
