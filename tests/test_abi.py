@@ -66,19 +66,33 @@ int main(void) {
          sizeof(ngs_hierarchy), sizeof(ngs_config), sizeof(ngs_stats));
   printf("%zu %zu %zu %zu\n", offsetof(ngs_camera, tau), offsetof(ngs_gaussians, attr_dtype),
          offsetof(ngs_config, max_tiles_per_batch), offsetof(ngs_stats, mode));
+  printf("%zu %zu %zu %zu %zu %d\n", sizeof(ngs_tune_result), offsetof(ngs_tune_result, ms),
+         offsetof(ngs_tune_result, batch), offsetof(ngs_stats, cta_w), sizeof(ngs_server_config),
+         NGS_TUNE_SHAPES);
+  printf("%d %d %d %d %d %d %d %d %d %d\n", NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H,
+         NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL, NGS_OPT_CTA_W,
+         NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL);
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, t, o = subprocess.run([str(exe)], capture_output=True, text=True,
+                                check=True).stdout.split("\n")[:4]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [C.sizeof(_lib.Camera), C.sizeof(_lib.Gaussians), C.sizeof(_lib.Hierarchy),
                      C.sizeof(_lib.Config), C.sizeof(_lib.Stats)]
     assert offs == [_lib.Camera.tau.offset, _lib.Gaussians.attr_dtype.offset,
                     _lib.Config.max_tiles_per_batch.offset, _lib.Stats.mode.offset]
+    assert [int(x) for x in t.split()] == [
+        C.sizeof(_lib.TuneResult), _lib.TuneResult.ms.offset, _lib.TuneResult.batch.offset,
+        _lib.Stats.cta_w.offset, C.sizeof(_lib.ServerConfig), len(_lib.TUNE_SHAPES)]
+    assert [int(x) for x in o.split()] == [
+        _lib.NGS_OPT_MODE, _lib.NGS_OPT_TILE_W, _lib.NGS_OPT_TILE_H, _lib.NGS_OPT_BATCH,
+        _lib.NGS_OPT_GRAPH, _lib.NGS_OPT_STAGE_TIMING, _lib.NGS_OPT_BLOCK_CULL,
+        _lib.NGS_OPT_CTA_W, _lib.NGS_OPT_CTA_H, _lib.NGS_OPT_PAIRS_PER_PIXEL]
 
 
 def test_renderer_fails_loudly_without_gpu():

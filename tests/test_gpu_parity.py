@@ -216,6 +216,29 @@ def test_block_cull_is_conservative(R, small_floor, box10k):
             assert np.array_equal(a, b)
 
 
+def test_planner_estimate_changes_sub_batches_not_pixels(small_floor):
+    """The planner's pairs-per-pixel estimate decides how cameras are grouped
+    into sub-batches (with a pair buffer of 2^22 slots, 48 pairs per pixel fit
+    about 87k pixels per sub-batch, 4 fit about 1 Mpix); the images do not
+    depend on it."""
+    from paper_2603_15186_gb300 import Renderer
+    r = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22, pair_capacity=1 << 22)
+    r.load_scene(small_floor)
+    cams = _floor_cams(small_floor)
+    out, subs = [], []
+    for ppp in (48, 4):
+        r.set_pairs_per_pixel(ppp)
+        out.append([t.cpu().numpy() for t in r.render(cams)])
+        subs.append(r.stats()["sub_batches"])
+    assert subs[0] > subs[1] >= 1, subs
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    from paper_2603_15186_gb300 import NgsError
+    with pytest.raises(NgsError):
+        r.set_pairs_per_pixel(0)
+    r.close()
+
+
 def test_autotune_keeps_pixels(R, small_floor):
     R.load_scene(small_floor)
     cams = _floor_cams(small_floor)
