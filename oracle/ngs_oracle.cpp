@@ -21,6 +21,14 @@
 //   4. composite : per pixel, front-to-back alpha blending over its tile's list.
 //   5. brute force: per pixel over every visible Gaussian in depth order, no
 //                  tiles, as an independent check of 3-4.
+//   Optional level-of-detail blending (Sec. III-B: transitions between levels
+//   are interpolated): a selected node n with parent p is rendered with its
+//   attributes moved toward p's, parent weight
+//       v = 1 - clamp((s(p) - tau) / (s(p) - s(n)), 0, 1)
+//   (v = 0 for the root, when s(p) is infinite or s(p) <= s(n)): mean
+//   mu_n + v (mu_p - mu_n), covariance, opacity and SH likewise. v is 0 where
+//   tau has just reached s(n) from below (n itself) and 1 where tau is about
+//   to reach s(p) (n has become its parent); a leaf finer than tau keeps v = 0.
 // Every floating-point step is float64 except where a step's result decides an
 // integer that the renderer must reproduce exactly: the near-plane cull and the
 // depth sort key use the float32 view depth computed by one fixed sequence of
@@ -71,6 +79,8 @@ static const double kAlphaMax = 0.99;
 static const double kTMin = 1e-4;
 static const double kRectMargin = 1.0 / 64.0;   // pixels added to the support radius
 
+void orc_cov3d(const float *quat, const float *log_scale, double *out);
+
 // ---------------------------------------------------------------------------
 // 1. cut
 // ---------------------------------------------------------------------------
@@ -88,6 +98,58 @@ static double granularity(const orc_scene *sc, const orc_camera *cam, int64_t n)
     }
     if (d2 == 0.0) return INFINITY;
     return cam->fx * ext / std::sqrt(d2);
+}
+
+// The granularity in the renderer's precision (float32, one IEEE operation per
+// step, no contraction), used only for the blend weight, so that the blended
+// mean, and with it the float32 depth key, is the same bit pattern on both
+// sides.
+float orc_granularity_f32(const orc_scene *sc, const orc_camera *cam, int64_t n) {
+    const float px = (float)cam->pos[0], py = (float)cam->pos[1], pz = (float)cam->pos[2];
+    const float *lo = sc->aabb_min + 3 * n, *hi = sc->aabb_max + 3 * n;
+    const float gx = std::fmax(std::fmax(lo[0] - px, 0.0f), px - hi[0]);
+    const float gy = std::fmax(std::fmax(lo[1] - py, 0.0f), py - hi[1]);
+    const float gz = std::fmax(std::fmax(lo[2] - pz, 0.0f), pz - hi[2]);
+    const float d2 = std::fma(gx, gx, std::fma(gy, gy, gz * gz));
+    const float ext = std::fmax(std::fmax(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+    if (d2 == 0.0f) return INFINITY;
+    return ((float)cam->fx * ext) / std::sqrt(d2);
+}
+
+// Parent weight of the level-of-detail blend (float32, as the renderer).
+float orc_blend_parent_weight(float s_n, float s_p, float tau) {
+    if (!(s_p < INFINITY)) return 0.0f;
+    const float den = s_p - s_n;
+    if (!(den > 0.0f)) return 0.0f;
+    const float w = std::fmin(std::fmax((s_p - tau) / den, 0.0f), 1.0f);
+    return 1.0f - w;
+}
+
+// Attributes of node g as rendered: its own, or, with blend, moved toward its
+// parent's by the parent weight v. mu: float32 (it decides the depth key);
+// Sigma: 3x3 row-major; sh: [16][3]. Returns v.
+double orc_blend_gaussian(const orc_scene *sc, const orc_camera *cam, int64_t g, int32_t blend,
+                          float *mu, double *Sigma, double *opac, double *sh) {
+    float v = 0.0f;
+    const int32_t par = sc->parent[g];
+    if (blend && par >= 0)
+        v = orc_blend_parent_weight(orc_granularity_f32(sc, cam, g),
+                                    orc_granularity_f32(sc, cam, par), (float)cam->tau);
+    orc_cov3d(sc->quat + 4 * g, sc->log_scale + 3 * g, Sigma);
+    *opac = sc->opacity[g];
+    for (int k = 0; k < 3; ++k) mu[k] = sc->pos[3 * g + k];
+    for (int k = 0; k < 48; ++k) sh[k] = sc->sh[48 * g + k];
+    if (v > 0.0f) {
+        double Sp[9];
+        orc_cov3d(sc->quat + 4 * par, sc->log_scale + 3 * par, Sp);
+        const double vd = v;
+        for (int k = 0; k < 3; ++k)
+            mu[k] = std::fma(v, sc->pos[3 * par + k] - mu[k], mu[k]);
+        for (int k = 0; k < 9; ++k) Sigma[k] += vd * (Sp[k] - Sigma[k]);
+        *opac += vd * ((double)sc->opacity[par] - *opac);
+        for (int k = 0; k < 48; ++k) sh[k] += vd * ((double)sc->sh[48 * par + k] - sh[k]);
+    }
+    return v;
 }
 
 // Writes the selected node ids (ascending) and returns their count. If
@@ -190,9 +252,11 @@ float orc_depth_f32(const float *mu, const orc_camera *cam) {
 // For each cut slot i (node ids[i]) fills out[i*PC_NCOLS + col], depth_key[i]
 // (float32 bits of the rounded depth) and rect[i*4..] = (x0, y0, x1, y1), the
 // inclusive tile range. Invisible slots get PC_VISIBLE = 0 and rect (0,0,-1,-1).
+// With blend, each node is rendered with its level-of-detail blended
+// attributes (orc_blend_gaussian).
 void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *ids, int64_t n,
-                    int32_t tile_w, int32_t tile_h, double *out, uint32_t *depth_key,
-                    int32_t *rect) {
+                    int32_t tile_w, int32_t tile_h, int32_t blend, double *out,
+                    uint32_t *depth_key, int32_t *rect) {
     const int32_t tiles_x = (cam->width + tile_w - 1) / tile_w;
     const int32_t tiles_y = (cam->height + tile_h - 1) / tile_h;
     #pragma omp parallel for schedule(static)
@@ -203,10 +267,11 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         rc[0] = 0; rc[1] = 0; rc[2] = -1; rc[3] = -1;
         depth_key[i] = 0xFFFFFFFFu;
         const int64_t g = ids[i];
-        const float *mu = sc->pos + 3 * g;
+        float mu[3];
+        double S[9], opac, shg[48];
+        orc_blend_gaussian(sc, cam, g, blend, mu, S, &opac, shg);
         const float z32 = orc_depth_f32(mu, cam);
         if (!(z32 > (float)kNear)) continue;
-        const double opac = sc->opacity[g];
         if (255.0 * opac < 1.0) continue;
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = (double)mu[k] - cam->pos[k];
@@ -223,8 +288,6 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
                 for (int k = 0; k < 3; ++k) acc += J[3 * r + k] * cam->R[3 * k + c];
                 T[3 * r + c] = acc;
             }
-        double S[9];
-        orc_cov3d(sc->quat + 4 * g, sc->log_scale + 3 * g, S);
         double TS[6];
         for (int r = 0; r < 2; ++r)
             for (int c = 0; c < 3; ++c) {
@@ -264,11 +327,10 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         for (int k = 0; k < 3; ++k) dir[k] = d[k] / nd;
         double Y[16];
         orc_sh_basis(dir, Y);
-        const float *shg = sc->sh + 48 * g;
         double rgb[3];
         for (int ch = 0; ch < 3; ++ch) {
             double acc = 0.0;
-            for (int k = 0; k < 16; ++k) acc += Y[k] * (double)shg[3 * k + ch];
+            for (int k = 0; k < 16; ++k) acc += Y[k] * shg[3 * k + ch];
             rgb[ch] = std::max(0.0, acc + 0.5);
         }
         o[PC_VISIBLE] = 1.0;

@@ -5,7 +5,11 @@ Each function follows one step of the render path as the C++ source states it:
 and SH colour of 3DGS, Sec. III-A), ``bin_pairs`` ((tile, depth) keys and a
 stable sort), ``composite_tiled`` (front-to-back blending) and
 ``render_bruteforce`` (per-pixel blending over every visible Gaussian, no
-tiles). ``render`` chains them for one camera.
+tiles). ``render`` chains them for one camera. With ``blend``, preprocess
+renders each cut node with its level-of-detail blended attributes
+(``blend_gaussian``: moved toward its parent's by the parent weight
+``blend_parent_weight`` of the granularities, Sec. III-B's interpolated
+transitions).
 """
 from __future__ import annotations
 
@@ -50,7 +54,14 @@ def lib():
             L.orc_select_cut.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), vp, vp, vp]
             L.orc_preprocess.restype = None
             L.orc_preprocess.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), vp, i64, i32, i32,
-                                         vp, vp, vp]
+                                         i32, vp, vp, vp]
+            L.orc_granularity_f32.restype = C.c_float
+            L.orc_granularity_f32.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), i64]
+            L.orc_blend_parent_weight.restype = C.c_float
+            L.orc_blend_parent_weight.argtypes = [C.c_float, C.c_float, C.c_float]
+            L.orc_blend_gaussian.restype = C.c_double
+            L.orc_blend_gaussian.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), i64, i32, vp,
+                                             vp, vp, vp]
             L.orc_count_pairs.restype = i64
             L.orc_count_pairs.argtypes = [vp, i64]
             L.orc_bin_pairs.restype = None
@@ -129,9 +140,10 @@ def select_cut(scene, cam, with_s: bool = False):
     return out + (s,) if with_s else out
 
 
-def preprocess(scene, cam, ids, tile=(16, 16)):
+def preprocess(scene, cam, ids, tile=(16, 16), blend=False):
     """Per cut slot: float64 table (columns PC.*), float32 depth-key bits and
-    the inclusive tile rectangle (x0, y0, x1, y1)."""
+    the inclusive tile rectangle (x0, y0, x1, y1). ``blend``: level-of-detail
+    blended attributes."""
     sa = _as_scene(scene)
     ids = np.ascontiguousarray(ids, dtype=np.int32)
     n = len(ids)
@@ -140,7 +152,7 @@ def preprocess(scene, cam, ids, tile=(16, 16)):
     rect = np.empty((n, 4), dtype=np.int32)
     cc = camera_struct(cam)
     lib().orc_preprocess(C.byref(sa.c), C.byref(cc), _p(ids), n, int(tile[0]), int(tile[1]),
-                         _p(pre), _p(key), _p(rect))
+                         1 if blend else 0, _p(pre), _p(key), _p(rect))
     return pre, key, rect
 
 
@@ -193,14 +205,15 @@ def render_bruteforce(pre, key, pixels=None, cam=None):
     return out, flags
 
 
-def render(scene, cam, tile=(16, 16), ids=None):
-    """Full tiled render of one camera. Returns a namespace with the cut, the
-    preprocess table, sorted pairs, ranges, the image and its flags."""
+def render(scene, cam, tile=(16, 16), ids=None, blend=False):
+    """Full tiled render of one camera (``blend``: level-of-detail blending).
+    Returns a namespace with the cut, the preprocess table, sorted pairs,
+    ranges, the image and its flags."""
     sa = _as_scene(scene)
     near = None
     if ids is None:
         ids, near = select_cut(sa, cam)
-    pre, key, rect = preprocess(sa, cam, ids, tile)
+    pre, key, rect = preprocess(sa, cam, ids, tile, blend)
     keys, vals, ranges = bin_pairs(rect, key, cam, tile)
     img, flags = composite_tiled(pre, vals, ranges, cam, tile)
     return SimpleNamespace(ids=ids, near=near, pre=pre, key=key, rect=rect, keys=keys, vals=vals,
@@ -233,10 +246,36 @@ def depth_f32(mu, cam):
     return lib().orc_depth_f32(_p(mu), C.byref(cc))
 
 
+def granularity_f32(scene, cam, node):
+    """s(node) in the renderer's float32 operation sequence."""
+    sa = _as_scene(scene)
+    cc = camera_struct(cam)
+    return float(lib().orc_granularity_f32(C.byref(sa.c), C.byref(cc), int(node)))
+
+
+def blend_parent_weight(s_n, s_p, tau):
+    """Parent weight v of the level-of-detail blend (float32)."""
+    return float(lib().orc_blend_parent_weight(float(s_n), float(s_p), float(tau)))
+
+
+def blend_gaussian(scene, cam, node, blend=True):
+    """(v, mu float32 [3], Sigma [3, 3], opacity, sh [16, 3]) of a node as rendered."""
+    sa = _as_scene(scene)
+    cc = camera_struct(cam)
+    mu = np.empty(3, dtype=np.float32)
+    S = np.empty((3, 3), dtype=np.float64)
+    op = np.empty(1, dtype=np.float64)
+    sh = np.empty((16, 3), dtype=np.float64)
+    v = lib().orc_blend_gaussian(C.byref(sa.c), C.byref(cc), int(node), 1 if blend else 0,
+                                 _p(mu), _p(S), _p(op), _p(sh))
+    return float(v), mu, S, float(op[0]), sh
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
 __all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bin_pairs",
            "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "depth_f32",
-           "tiles_xy", "num_threads", "lib"]
+           "tiles_xy", "num_threads", "lib", "granularity_f32", "blend_parent_weight",
+           "blend_gaussian"]

@@ -124,6 +124,88 @@ def test_cut_hand_worked_tree():
     assert O.select_cut(t, cam)[0].tolist() == [1, 2]
 
 
+def test_blend_weight_hand_worked_tree():
+    """Parent weights of the level-of-detail blend on the hand-worked tree."""
+    g, t = _golden_cut()
+    for tau, want in g["blend_parent_weight"].items():
+        cam = Camera(pos=np.array(g["camera_pos"], np.float32), R_wc=np.eye(3, dtype=np.float32),
+                     fx=g["fx"], fy=g["fx"], cx=8, cy=8, width=16, height=16, tau=float(tau))
+        got = [O.blend_gaussian(t, cam, n)[0] for n in range(3)]
+        np.testing.assert_allclose(got, want, atol=1e-6, err_msg=tau)
+    # camera inside the root box: s(parent) = inf, leaves are never blended
+    cam = Camera(pos=np.array([0.5, 0.5, 0.5], np.float32), R_wc=np.eye(3, dtype=np.float32),
+                 fx=g["fx"], fy=g["fx"], cx=8, cy=8, width=16, height=16, tau=15.0)
+    assert [O.blend_gaussian(t, cam, n)[0] for n in range(3)] == [0.0, 0.0, 0.0]
+    # the weight formula's edge cases
+    assert O.blend_parent_weight(10.0, math.inf, 5.0) == 0.0
+    assert O.blend_parent_weight(10.0, 10.0, 5.0) == 0.0      # s(p) <= s(n)
+    assert O.blend_parent_weight(10.0, 20.0, 25.0) == 1.0     # tau beyond s(p): clamped
+
+
+def test_blend_interpolates_attributes():
+    """At parent weight v the rendered Gaussian is the node's attributes moved
+    by v toward the parent's: mean (float32, one fused step), covariance from
+    scipy's rotation, opacity and SH, each linear in v."""
+    g, t = _golden_cut()
+    rng = np.random.default_rng(12)
+    t.pos = rng.normal(0.5, 0.3, (3, 3)).astype(np.float32)
+    t.quat = rng.normal(size=(3, 4)).astype(np.float32)
+    t.log_scale = rng.normal(-3.0, 0.5, (3, 3)).astype(np.float32)
+    t.opacity = rng.uniform(0.1, 0.9, 3).astype(np.float32)
+    t.sh = rng.normal(0, 0.3, (3, 16, 3)).astype(np.float32)
+
+    def sigma(i):
+        q = t.quat[i].astype(np.float64)
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        return R @ np.diag(np.exp(2.0 * t.log_scale[i].astype(np.float64))) @ R.T
+
+    for tau, want in g["blend_parent_weight"].items():
+        cam = Camera(pos=np.array(g["camera_pos"], np.float32), R_wc=np.eye(3, dtype=np.float32),
+                     fx=g["fx"], fy=g["fx"], cx=8, cy=8, width=16, height=16, tau=float(tau))
+        for n in (1, 2):
+            v, mu, S, op, sh = O.blend_gaussian(t, cam, n)
+            assert abs(v - want[n]) <= 1e-6
+            # float32 mean: the float32 difference, then one rounding of
+            # v * difference + mean (the float64 product of two float32 values is
+            # exact)
+            diff = (t.pos[0] - t.pos[n]).astype(np.float32)
+            mu_want = (np.float64(np.float32(v)) * diff.astype(np.float64) +
+                       t.pos[n].astype(np.float64)).astype(np.float32)
+            np.testing.assert_allclose(mu, mu_want, rtol=0, atol=1.2e-7)
+            np.testing.assert_allclose(S, sigma(n) + v * (sigma(0) - sigma(n)), rtol=1e-12, atol=1e-15)
+            assert op == pytest.approx(t.opacity[n] + v * (t.opacity[0] - t.opacity[n]), abs=1e-15)
+            np.testing.assert_allclose(sh, t.sh[n] + v * (t.sh[0].astype(np.float64) - t.sh[n]),
+                                       rtol=0, atol=1e-15)
+        # without blending every node keeps its own attributes
+        v, mu, S, op, sh = O.blend_gaussian(t, cam, 1, blend=False)
+        assert v == 0.0 and np.array_equal(mu, t.pos[1]) and op == np.float64(t.opacity[1])
+        np.testing.assert_allclose(S, sigma(1), rtol=1e-12, atol=1e-15)
+
+
+def test_granularity_f32_close_to_float64(box10k):
+    cam = camera_c0(4.0)
+    _, _, s64 = O.select_cut(box10k, cam, with_s=True)
+    sa = O.SceneArrays(box10k)
+    for n in range(0, box10k.n_nodes, 97):
+        s32 = O.granularity_f32(sa, cam, n)
+        if math.isinf(s64[n]):
+            assert math.isinf(s32)
+        else:
+            assert abs(s32 - s64[n]) <= 1e-6 * s64[n], n
+
+
+def test_blend_at_tau_zero_is_the_plain_render(box10k):
+    """At tau = 0 every cut node is a leaf finer than tau (parent weight 0),
+    so the blended render is the plain one, bit for bit."""
+    cam = camera_c0(0.0)
+    a = O.render(box10k, cam)
+    b = O.render(box10k, cam, blend=True)
+    assert np.array_equal(a.image, b.image) and np.array_equal(a.vals, b.vals)
+    c = O.render(box10k, camera_c0(10.0), blend=True)
+    d = O.render(box10k, camera_c0(10.0))
+    assert not np.array_equal(c.image, d.image)   # nodes in transition move toward parents
+
+
 def _check_antichain_cover(s, ids):
     sel = np.zeros(s.n_nodes, bool)
     sel[ids] = True
