@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stage-timing", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-blend", action="store_true",
+                    help="skip the level-of-detail blending leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="seconds of simulated agent load for the serving leg (0: skip)")
     ap.add_argument("--serving-scene", default="floor8m")
@@ -445,6 +447,37 @@ def run_ours(args, world, rank, local, pg):
         out["parity_vs_oracle"] = {"max_abs_err": max(errs), "tolerance": 2e-3,
                                    "flagged_pixel_frac": max(flagged),
                                    "views": [int(i) for i in order]}
+    # level-of-detail blending (each cut node moved toward its parent), same
+    # batch, same launch configuration
+    if not args.no_blend:
+        R.set_stage_timing(False)
+        R.set_lod_blend(True)
+        for _ in range(max(args.warmup, 3)):
+            R.render(cams, imgs)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            R.render(cams, imgs, stream=stream, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        R.synchronize()
+        bms = a.elapsed_time(b) / args.steps
+        bst = R.stats()
+        blend = {"value": round(world * pixels / (bms * 1e3), 2), "unit": "Mpix/s",
+                 "ms_per_step": round(bms, 3), "visible_total": bst["visible_total"],
+                 "pair_total": bst["pair_total"],
+                 "note": "block and per-Gaussian pre-culls off while blending"}
+        if rank == 0 and not args.no_cpu:
+            errs = []
+            for i in order:
+                ref = O.render(sa, cams[i], tile=(tw, th), blend=True)
+                got = imgs[i].cpu().numpy().astype(np.float64)
+                ok = ref.flags == 0
+                errs.append(float(np.abs(got - ref.image)[:, ok].max()))
+            blend["max_abs_err_vs_oracle"] = max(errs)
+        out["lod_blend"] = blend
+        R.set_lod_blend(False)
     R.close()
     if args.serving_seconds > 0:
         out["serving"] = run_serving(args, local)

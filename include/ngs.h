@@ -117,7 +117,8 @@ typedef struct {
 enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
        NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7,
-       NGS_OPT_CTA_W = 8, NGS_OPT_CTA_H = 9, NGS_OPT_PAIRS_PER_PIXEL = 10 };
+       NGS_OPT_CTA_W = 8, NGS_OPT_CTA_H = 9, NGS_OPT_PAIRS_PER_PIXEL = 10,
+       NGS_OPT_LOD_BLEND = 11 };
 /* NGS_OPT_TILE_W / NGS_OPT_TILE_H: tile width 8, 16 or 32, height 8, 16 or 32;
  * a render accepts the shapes 8x8, 16x8, 16x16, 16x32, 32x16 and 32x32
  * (INVALID_ARG else).
@@ -128,6 +129,16 @@ enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH =
  * binning and sorting work on the large tiles (fewer pairs), each block walks
  * its tile's list and skips the Gaussians that cannot reach it. A shape that
  * does not divide the tile is rejected at render (INVALID_ARG). Same pixels.
+ * NGS_OPT_LOD_BLEND (default 0): level-of-detail blending (Sec. III-B: the
+ * transitions between levels are interpolated). A selected node n other than
+ * the root is rendered with its attributes moved toward its parent p's by the
+ * parent weight v = 1 - clamp((s(p) - tau) / (s(p) - s(n)), 0, 1) (0 where s(p)
+ * is infinite or s(p) <= s(n)): mean mu_n + v (mu_p - mu_n), and likewise the
+ * 3D covariance, the opacity and the SH coefficients. v and the mean are
+ * evaluated in float32 by a fixed IEEE operation sequence. v = 0 for every
+ * node at tau = 0, where the images equal the plain ones bit for bit. The
+ * block and per-Gaussian pre-culls are off while it is on (a blended Gaussian
+ * is not bounded by its node's own position and scale).
  * NGS_OPT_PAIRS_PER_PIXEL (1..4096, default 48): the planner's estimate of
  * (tile, Gaussian) pairs per pixel, used to fit sub-batches into
  * pair_capacity; it is raised automatically to 1.25x the largest density a

@@ -69,6 +69,7 @@ struct ngs_ctx {
     int cta_w = 0, cta_h = 0;          // block one compositing CTA covers (0: the tile)
     bool use_graph = true;
     bool block_cull = true;
+    bool lod_blend = false;            // level-of-detail blending toward parents
     SceneDev scene;
     bool loaded = false;
     bool owns_scene = true;           // false for serving lanes sharing a scene
@@ -400,7 +401,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     uint32_t eo = 0;
     launch_cutpre(c->scene, cams, nc, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
                   w.counters, w.part_list, w.group_list, w.part_info, w.err, c->tile_w, c->tile_h,
-                  c->block_cull ? 1 : 0, c->grid_pre, st);
+                  c->block_cull ? 1 : 0, c->lod_blend ? 1 : 0, c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
     launch_gather_keys(w.vis_count, nc, c->scene, w.part_info, w.part_pos, w.part_list,
                        w.dkey[1], w.dkey[0], w.didx[0], w.counters, w.rec_cap, w.hist, w.err,
@@ -518,7 +519,8 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         const int64_t nblk = (c->scene.n + cutpre_partition_nodes() - 1) / cutpre_partition_nodes();
         launch_cutpre(c->scene, cams, 1, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
                       w.counters, w.part_list, w.group_list, w.part_info, w.err, c->tile_w, c->tile_h,
-                      c->block_cull ? 1 : 0, (int)std::min<int64_t>(nblk, c->grid_pre), st);
+                      c->block_cull ? 1 : 0, c->lod_blend ? 1 : 0,
+                      (int)std::min<int64_t>(nblk, c->grid_pre), st);
         eo++;
         mark(c, ci, MK_CUT, st);
         uint32_t n_cut = 0, n_vis = 0, n_pairs = 0;
@@ -622,6 +624,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     key.push_back(n_cams); key.push_back(c->tile_w); key.push_back(c->tile_h);
     key.push_back(c->batch); key.push_back((int64_t)c->scene_version);
     key.push_back(cta_w_of(c)); key.push_back(cta_h_of(c));
+    key.push_back(c->lod_blend ? 1 : 0);
     for (int i = 0; i < n_cams; ++i) {
         key.push_back(c->host_cams[i].width);
         key.push_back(c->host_cams[i].height);
@@ -759,6 +762,7 @@ ngs_status ngs::lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pa
     l->cta_w = parent->cta_w; l->cta_h = parent->cta_h;
     l->use_graph = false;   // every launch has a different camera mix
     l->block_cull = parent->block_cull;
+    l->lod_blend = parent->lod_blend;
     return NGS_OK;
 }
 
@@ -883,6 +887,10 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         return NGS_OK;
     case NGS_OPT_BLOCK_CULL:
         c->block_cull = v != 0;
+        drop_graph(c);
+        return NGS_OK;
+    case NGS_OPT_LOD_BLEND:
+        c->lod_blend = v != 0;
         drop_graph(c);
         return NGS_OK;
     }

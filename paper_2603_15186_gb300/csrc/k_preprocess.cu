@@ -44,6 +44,18 @@ template <> struct Attr<float> {
         const float4 t = reinterpret_cast<const float4 *>(p)[i];
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
+    // rows i and j side by side: f(h, row i value, row j value)
+    template <typename F>
+    static __device__ __forceinline__ void stream_sh2(const void *p, int64_t i, int64_t j, F f) {
+        const float4 *a = reinterpret_cast<const float4 *>(p) + i * 12;
+        const float4 *b = reinterpret_cast<const float4 *>(p) + j * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float4 t = a[k], u = b[k];
+            f(4 * k, t.x, u.x); f(4 * k + 1, t.y, u.y); f(4 * k + 2, t.z, u.z);
+            f(4 * k + 3, t.w, u.w);
+        }
+    }
     template <int kUnused, typename F>
     static __device__ __forceinline__ void stream_sh(const void *p, int64_t i, F f) {
         const float4 *s = reinterpret_cast<const float4 *>(p) + i * 12;
@@ -60,6 +72,22 @@ template <> struct Attr<__half> {
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    template <typename F>
+    static __device__ __forceinline__ void stream_sh2(const void *p, int64_t i, int64_t j, F f) {
+        const uint4 *a = reinterpret_cast<const uint4 *>(p) + i * 6;
+        const uint4 *b = reinterpret_cast<const uint4 *>(p) + j * 6;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const uint4 t = a[k], u = b[k];
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w}, x[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 va = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
+                const float2 vb = __half22float2(*reinterpret_cast<const __half2 *>(&x[q]));
+                f(8 * k + 2 * q, va.x, vb.x); f(8 * k + 2 * q + 1, va.y, vb.y);
+            }
+        }
     }
     template <int kUnused, typename F>
     static __device__ __forceinline__ void stream_sh(const void *p, int64_t i, F f) {
@@ -86,6 +114,21 @@ template <> struct Attr<__nv_bfloat16> {
         const float2 a = bf2(t.x), b = bf2(t.y);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
+    template <typename F>
+    static __device__ __forceinline__ void stream_sh2(const void *p, int64_t i, int64_t j, F f) {
+        const uint4 *a = reinterpret_cast<const uint4 *>(p) + i * 6;
+        const uint4 *b = reinterpret_cast<const uint4 *>(p) + j * 6;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const uint4 t = a[k], u = b[k];
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w}, x[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 va = bf2(w[q]), vb = bf2(x[q]);
+                f(8 * k + 2 * q, va.x, vb.x); f(8 * k + 2 * q + 1, va.y, vb.y);
+            }
+        }
+    }
     template <int kUnused, typename F>
     static __device__ __forceinline__ void stream_sh(const void *p, int64_t i, F f) {
         const uint4 *s = reinterpret_cast<const uint4 *>(p) + i * 6;
@@ -107,11 +150,8 @@ template <> struct Attr<__nv_bfloat16> {
 // sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0) folded with
 // the polynomial coefficients. The 48 coefficients are streamed from memory
 // in storage order (coefficient-major), each channel accumulating k = 0..15.
-template <typename A>
-__device__ __forceinline__ void sh_colour(const void *sh, int64_t node, float x, float y,
-                                          float z, float rgb[3]) {
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
     const float xx = x * x, yy = y * y, zz = z * z;
-    float Y[16];
     Y[0] = 0.28209479177387814f;
     Y[1] = -0.48860251190291992f * y;
     Y[2] = 0.48860251190291992f * z;
@@ -128,6 +168,13 @@ __device__ __forceinline__ void sh_colour(const void *sh, int64_t node, float x,
     Y[13] = -0.45704579946446572f * x * (4.0f * zz - xx - yy);
     Y[14] = 1.4453057213202769f * z * (xx - yy);
     Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+template <typename A>
+__device__ __forceinline__ void sh_colour(const void *sh, int64_t node, float x, float y,
+                                          float z, float rgb[3]) {
+    float Y[16];
+    sh_basis(x, y, z, Y);
     float acc[3] = {0.5f, 0.5f, 0.5f};
     Attr<A>::template stream_sh<3>(sh, node, [&](int h, float v) {
         acc[h % 3] = __fmaf_rn(Y[h / 3], v, acc[h % 3]);
@@ -135,6 +182,58 @@ __device__ __forceinline__ void sh_colour(const void *sh, int64_t node, float x,
     rgb[0] = fmaxf(acc[0], 0.0f);
     rgb[1] = fmaxf(acc[1], 0.0f);
     rgb[2] = fmaxf(acc[2], 0.0f);
+}
+
+// The same with the coefficients of `node` moved toward those of `par` by v.
+template <typename A>
+__device__ __forceinline__ void sh_colour_blend(const void *sh, int64_t node, int64_t par,
+                                                float v, float x, float y, float z,
+                                                float rgb[3]) {
+    float Y[16];
+    sh_basis(x, y, z, Y);
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    Attr<A>::stream_sh2(sh, node, par, [&](int h, float cn, float cp) {
+        acc[h % 3] = __fmaf_rn(Y[h / 3], __fmaf_rn(v, __fsub_rn(cp, cn), cn), acc[h % 3]);
+    });
+    rgb[0] = fmaxf(acc[0], 0.0f);
+    rgb[1] = fmaxf(acc[1], 0.0f);
+    rgb[2] = fmaxf(acc[2], 0.0f);
+}
+
+// Parent weight of the level-of-detail blend (Sec. III-B: transitions between
+// levels are interpolated): v = 1 - clamp((s(p) - tau) / (s(p) - s(n)), 0, 1),
+// 0 when s(p) is infinite or s(p) <= s(n). Every step one IEEE float32
+// operation, the same sequence as the oracle's, so the blended mean and the
+// depth key derived from it agree bit for bit.
+__device__ __forceinline__ float blend_parent_weight(float s_n, float s_p, float tau) {
+    if (!(s_p < __int_as_float(0x7f800000))) return 0.0f;
+    const float den = __fsub_rn(s_p, s_n);
+    if (!(den > 0.0f)) return 0.0f;
+    const float w = fminf(fmaxf(__fdiv_rn(__fsub_rn(s_p, tau), den), 0.0f), 1.0f);
+    return __fsub_rn(1.0f, w);
+}
+
+// Sigma = R(q) S^2 R(q)^T from a quaternion (w, x, y, z, normalised here) and
+// log-scales; upper triangle S00, S01, S02, S11, S12, S22.
+__device__ __forceinline__ void cov3d(const float4 q4, const float ls[3], float S[6]) {
+    const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
+    const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z),
+                R02 = 2.f * (x * z + w * y);
+    const float R10 = 2.f * (x * y + w * z), R11 = 1.f - 2.f * (x * x + z * z),
+                R12 = 2.f * (y * z - w * x);
+    const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x),
+                R22 = 1.f - 2.f * (x * x + y * y);
+    const float s0 = expf(ls[0]), s1 = expf(ls[1]), s2 = expf(ls[2]);
+    const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+    const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+    const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+    S[0] = M00 * M00 + M01 * M01 + M02 * M02;
+    S[1] = M00 * M10 + M01 * M11 + M02 * M12;
+    S[2] = M00 * M20 + M01 * M21 + M02 * M22;
+    S[3] = M10 * M10 + M11 * M11 + M12 * M12;
+    S[4] = M10 * M20 + M11 * M21 + M12 * M22;
+    S[5] = M20 * M20 + M21 * M21 + M22 * M22;
 }
 
 struct PreOut {
@@ -269,11 +368,35 @@ __device__ __forceinline__ bool block_culled(const float4 lo, const float4 hi,
 
 // Full preprocess of a Gaussian that passed precull (phase B); returns whether
 // it is visible (in front of the near plane and touching at least one tile).
-template <typename A>
+// kBlend: the node is rendered with its level-of-detail blended attributes
+// (moved toward its parent's by blend_parent_weight): mean and opacity in one
+// fused step each, covariance and SH coefficients element by element.
+template <typename A, bool kBlend = false>
 __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCamera &cam,
                                                uint32_t node, int tile_w, int tile_h,
                                                PreOut &o) {
-    const float4 p = sc.pos4[node];
+    float4 p = sc.pos4[node];
+    float vb = 0.0f;   // parent weight of the blend
+    int par = -1;
+    if (kBlend) {
+        const float4 lo = sc.box_lo[node], hi = sc.box_hi[node];
+        par = __float_as_int(lo.w);
+        if (par >= 0)
+            vb = blend_parent_weight(
+                granularity(lo, hi, cam.pos[0], cam.pos[1], cam.pos[2], cam.fx),
+                granularity(sc.box_lo[par], sc.box_hi[par], cam.pos[0], cam.pos[1], cam.pos[2],
+                            cam.fx),
+                cam.tau);
+    }
+    const bool mix = kBlend && vb > 0.0f;
+    float sp[4];
+    if (mix) {
+        const float4 pp = sc.pos4[par];
+        p.x = __fmaf_rn(vb, __fsub_rn(pp.x, p.x), p.x);
+        p.y = __fmaf_rn(vb, __fsub_rn(pp.y, p.y), p.y);
+        p.z = __fmaf_rn(vb, __fsub_rn(pp.z, p.z), p.z);
+        Attr<A>::load4(sc.sop, par, sp);
+    }
     const float dx = __fsub_rn(p.x, cam.pos[0]);
     const float dy = __fsub_rn(p.y, cam.pos[1]);
     const float dz = __fsub_rn(p.z, cam.pos[2]);
@@ -281,7 +404,10 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
     float so[4];
     Attr<A>::load4(sc.sop, node, so);
-    const float opac = so[3];
+    float opac = so[3];
+    if (mix) opac = __fmaf_rn(vb, __fsub_rn(sp[3], opac), opac);
+    // without blending, nodes with 255 o < 1 never get here (load-time flag)
+    if (kBlend && !(255.0f * opac >= 1.0f)) return false;
     const float K = 2.0f * logf(255.0f * opac);
     // view depth in the fixed float32 operation sequence that the near-plane
     // cull and the sort key use
@@ -302,12 +428,22 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
     const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
     const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
-    const float S00 = M00 * M00 + M01 * M01 + M02 * M02;
-    const float S01 = M00 * M10 + M01 * M11 + M02 * M12;
-    const float S02 = M00 * M20 + M01 * M21 + M02 * M22;
-    const float S11 = M10 * M10 + M11 * M11 + M12 * M12;
-    const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
-    const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
+    float S00 = M00 * M00 + M01 * M01 + M02 * M02;
+    float S01 = M00 * M10 + M01 * M11 + M02 * M12;
+    float S02 = M00 * M20 + M01 * M21 + M02 * M22;
+    float S11 = M10 * M10 + M11 * M11 + M12 * M12;
+    float S12 = M10 * M20 + M11 * M21 + M12 * M22;
+    float S22 = M20 * M20 + M21 * M21 + M22 * M22;
+    if (mix) {
+        float Sp[6];
+        cov3d(sc.quat[par], sp, Sp);
+        S00 = __fmaf_rn(vb, __fsub_rn(Sp[0], S00), S00);
+        S01 = __fmaf_rn(vb, __fsub_rn(Sp[1], S01), S01);
+        S02 = __fmaf_rn(vb, __fsub_rn(Sp[2], S02), S02);
+        S11 = __fmaf_rn(vb, __fsub_rn(Sp[3], S11), S11);
+        S12 = __fmaf_rn(vb, __fsub_rn(Sp[4], S12), S12);
+        S22 = __fmaf_rn(vb, __fsub_rn(Sp[5], S22), S22);
+    }
 
     // T = J W (2x3): rows (fx/z) W0 - (fx x/z^2) W2 and (fy/z) W1 - (fy y/z^2) W2
     const float iz = 1.0f / tz;
@@ -346,7 +482,8 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     // colour seen along camera -> mean
     const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
     float rgb[3];
-    sh_colour<A>(sc.sh, node, dx * inv, dy * inv, dz * inv, rgb);
+    if (mix) sh_colour_blend<A>(sc.sh, node, par, vb, dx * inv, dy * inv, dz * inv, rgb);
+    else sh_colour<A>(sc.sh, node, dx * inv, dy * inv, dz * inv, rgb);
 
     o.x = u;
     o.y = v;
@@ -452,7 +589,7 @@ struct CutPreSmem {
 };
 static_assert(kGroupCams <= 16 && kPrePart <= 4096, "entries pack node and camera in 16 bits");
 
-template <typename A, typename R>
+template <typename A, typename R, bool kBlend>
 __global__ void __launch_bounds__(kPreThreads)
 k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restrict__ rec,
          int64_t rec_cap, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
@@ -525,7 +662,9 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
                                  cam.tau) &&
                     (par < 0 || granularity(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
                                             cam.fx) > cam.tau);
-                const bool cand = sel && precull(cam, nd, tile_w, tile_h);
+                // a blended Gaussian is not bounded by its node's own position
+                // and scale: with blending every selected node is a candidate
+                const bool cand = sel && (kBlend || precull(cam, nd, tile_w, tile_h));
                 m |= cand ? 1u << i : 0u;
                 const uint32_t nsel = __popc(__ballot_sync(0xffffffffu, sel));
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
@@ -599,7 +738,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             const int c = (int)S.gcam[i];
             PreOut o;
             const uint32_t node = (uint32_t)(b * kPrePart + v);
-            if (preprocess_one<A>(sc, cams[c], node, tile_w, tile_h, o)) {
+            if (preprocess_one<A, kBlend>(sc, cams[c], node, tile_w, tile_h, o)) {
                 store_rec(rec, (int64_t)pos, o);
                 dkey[pos] = o.key;
                 o.rect.z = (uint32_t)c;
@@ -740,36 +879,55 @@ k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
     }
 }
 
-void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
-                   int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
-                   uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
-                   int *err, int tile_w, int tile_h, int use_block_cull, int grid,
-                   cudaStream_t st) {
-    const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
-    cudaMemsetAsync(vis_count, 0, (size_t)n_cams * sizeof(uint32_t), st);
-    const int64_t nq = nblk * ((n_cams + kGroupCams - 1) / kGroupCams);
-    // 8 warps per CTA, two (block, camera chunk) items per warp and iteration
-    const int lgrid = (int)std::min<int64_t>((nq + 15) / 16, 8 * 1024);
-    k_live_parts<<<std::max(lgrid, 1), 256, 0, st>>>(sc, cams, n_cams, nblk, part_list,
-                                                     group_list, part_info, counters, tile_w,
-                                                     tile_h, use_block_cull, err);
+template <bool kBlend>
+static void launch_cutpre_t(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
+                            int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect,
+                            uint32_t *vis_count, uint32_t *counters, uint32_t *part_list,
+                            uint2 *group_list, uint2 *part_info, int *err, int tile_w, int tile_h,
+                            int grid, cudaStream_t st) {
     switch (sc.attr_dtype) {
     case NGS_F16:
-        k_cutpre<__half, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
+        k_cutpre<__half, Rec16, kBlend><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
             sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
             part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     case NGS_BF16:
-        k_cutpre<__nv_bfloat16, Rec16><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
-            sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-            part_list, group_list, part_info, err, tile_w, tile_h);
+        k_cutpre<__nv_bfloat16, Rec16, kBlend>
+            <<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
+                sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
+                part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     default:
-        k_cutpre<float, Rec32><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
+        k_cutpre<float, Rec32, kBlend><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
             sc, cams, n_cams, (Rec32 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
             part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     }
+}
+
+void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
+                   int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
+                   uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
+                   int *err, int tile_w, int tile_h, int use_block_cull, int blend, int grid,
+                   cudaStream_t st) {
+    const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
+    cudaMemsetAsync(vis_count, 0, (size_t)n_cams * sizeof(uint32_t), st);
+    const int64_t nq = nblk * ((n_cams + kGroupCams - 1) / kGroupCams);
+    // 8 warps per CTA, two (block, camera chunk) items per warp and iteration.
+    // The block cull bounds a block's own Gaussians; blended ones may lie
+    // outside it, so blending tests every block.
+    const int lgrid = (int)std::min<int64_t>((nq + 15) / 16, 8 * 1024);
+    k_live_parts<<<std::max(lgrid, 1), 256, 0, st>>>(sc, cams, n_cams, nblk, part_list,
+                                                     group_list, part_info, counters, tile_w,
+                                                     tile_h, use_block_cull && !blend, err);
+    if (blend)
+        launch_cutpre_t<true>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, vis_count,
+                              counters, part_list, group_list, part_info, err, tile_w, tile_h,
+                              grid, st);
+    else
+        launch_cutpre_t<false>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, vis_count,
+                               counters, part_list, group_list, part_info, err, tile_w, tile_h,
+                               grid, st);
 }
 
 void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &sc,
@@ -787,14 +945,22 @@ void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &s
 
 int cutpre_partition_nodes() { return kPrePart; }
 
-void cutpre_init_attributes() {
-    cudaFuncSetAttribute(k_cutpre<float, Rec32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <bool kBlend>
+static void cutpre_attr() {
+    cudaFuncSetAttribute(k_cutpre<float, Rec32, kBlend>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(CutPreSmem<Rec32>));
-    cudaFuncSetAttribute(k_cutpre<__half, Rec16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(CutPreSmem<Rec16>));
-    cudaFuncSetAttribute(k_cutpre<__nv_bfloat16, Rec16>,
+    cudaFuncSetAttribute(k_cutpre<__half, Rec16, kBlend>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(CutPreSmem<Rec16>));
+    cudaFuncSetAttribute(k_cutpre<__nv_bfloat16, Rec16, kBlend>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(CutPreSmem<Rec16>));
+}
+
+void cutpre_init_attributes() {
+    cutpre_attr<false>();
+    cutpre_attr<true>();
 }
 
 }  // namespace ngs

@@ -272,10 +272,11 @@ int cut_partition_nodes();
 // partition in part_info[camera * nblk + block]; visible Gaussians per
 // camera in vis_count; counters[CNT_CUT], [CNT_LIVE], [CNT_GROUPS],
 // [CNT_ALLOC], [TK_PRE]. part_list and group_list hold part_cap entries.
+// blend: level-of-detail blending of every node toward its parent.
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
                    int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
                    uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
-                   int *err, int tile_w, int tile_h, int use_block_cull, int grid,
+                   int *err, int tile_w, int tile_h, int use_block_cull, int blend, int grid,
                    cudaStream_t st);
 int cutpre_partition_nodes();
 void cutpre_init_attributes();

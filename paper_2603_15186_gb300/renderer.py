@@ -104,6 +104,10 @@ class Renderer:
     def set_block_cull(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_BLOCK_CULL, 1 if on else 0), "block cull")
 
+    def set_lod_blend(self, on: bool):
+        """Level-of-detail blending of every cut node toward its parent."""
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_LOD_BLEND, 1 if on else 0), "lod blend")
+
     def set_stage_timing(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_STAGE_TIMING, 1 if on else 0),
               "stage timing")

@@ -69,9 +69,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %d\n", sizeof(ngs_tune_result), offsetof(ngs_tune_result, ms),
          offsetof(ngs_tune_result, batch), offsetof(ngs_stats, cta_w), sizeof(ngs_server_config),
          NGS_TUNE_SHAPES);
-  printf("%d %d %d %d %d %d %d %d %d %d\n", NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H,
+  printf("%d %d %d %d %d %d %d %d %d %d %d\n", NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H,
          NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL, NGS_OPT_CTA_W,
-         NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL);
+         NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL, NGS_OPT_LOD_BLEND);
   return 0;
 }
 """)
@@ -92,7 +92,8 @@ int main(void) {
     assert [int(x) for x in o.split()] == [
         _lib.NGS_OPT_MODE, _lib.NGS_OPT_TILE_W, _lib.NGS_OPT_TILE_H, _lib.NGS_OPT_BATCH,
         _lib.NGS_OPT_GRAPH, _lib.NGS_OPT_STAGE_TIMING, _lib.NGS_OPT_BLOCK_CULL,
-        _lib.NGS_OPT_CTA_W, _lib.NGS_OPT_CTA_H, _lib.NGS_OPT_PAIRS_PER_PIXEL]
+        _lib.NGS_OPT_CTA_W, _lib.NGS_OPT_CTA_H, _lib.NGS_OPT_PAIRS_PER_PIXEL,
+        _lib.NGS_OPT_LOD_BLEND]
 
 
 def test_renderer_fails_loudly_without_gpu():

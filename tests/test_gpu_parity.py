@@ -158,6 +158,49 @@ def test_render_batch_matches_oracle_and_plain(R, small_floor):
     R.set_mode("batched")
 
 
+def test_lod_blend_matches_oracle(R, small_floor):
+    """Level-of-detail blending (each cut node moved toward its parent by its
+    granularity position): images against the oracle's blended render, the
+    same bits batched and plain and for another tile shape, tile lists
+    against the oracle's, and at tau = 0 the plain render bit for bit."""
+    R.load_scene(small_floor)
+    cams = _floor_cams(small_floor)
+    extra = walk_cameras(small_floor, 2, 78, 160, 120, fx=150.0, tau=20.0)[1]
+    cams.append(clear_tau(small_floor, extra))
+    R.set_tile(16, 16)
+    R.set_mode("batched")
+    plain_imgs = [t.cpu().numpy() for t in R.render(cams)]
+    R.set_lod_blend(True)
+    try:
+        imgs = [t.cpu().numpy() for t in R.render(cams)]
+        changed = 0
+        for cam, img, pimg in zip(cams, imgs, plain_imgs):
+            ref = O.render(small_floor, cam, blend=True)
+            compare_image(img, ref)
+            if cam.tau == 0.0:
+                assert np.array_equal(img, pimg)
+            else:
+                changed += int(not np.array_equal(img, pimg))
+        assert changed >= 2
+        R.set_mode("plain")
+        for a, b in zip(imgs, [t.cpu().numpy() for t in R.render(cams)]):
+            assert np.array_equal(a, b)
+        R.render([cams[2]])
+        ref = O.render(small_floor, cams[2], blend=True)
+        rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
+        compare_tile_lists(rng, nodes, ref, (16, 16))
+        R.set_mode("batched")
+        R.set_tile(32, 32)
+        R.set_cta(16, 16)
+        for a, b in zip(imgs, [t.cpu().numpy() for t in R.render(cams)]):
+            assert np.array_equal(a, b)
+    finally:
+        R.set_lod_blend(False)
+        R.set_mode("batched")
+        R.set_tile(16, 16)
+        R.set_cta(0, 0)
+
+
 def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
     R.load_scene(small_floor)
     cams = _floor_cams(small_floor)
