@@ -467,7 +467,7 @@ def run_ours(args, world, rank, local, pg):
         blend = {"value": round(world * pixels / (bms * 1e3), 2), "unit": "Mpix/s",
                  "ms_per_step": round(bms, 3), "visible_total": bst["visible_total"],
                  "pair_total": bst["pair_total"],
-                 "note": "block and per-Gaussian pre-culls off while blending"}
+                 "note": "pre-culls bound the node-parent segment while blending"}
         if rank == 0 and not args.no_cpu:
             errs = []
             for i in order:

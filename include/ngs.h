@@ -136,9 +136,10 @@ enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH =
  * is infinite or s(p) <= s(n)): mean mu_n + v (mu_p - mu_n), and likewise the
  * 3D covariance, the opacity and the SH coefficients. v and the mean are
  * evaluated in float32 by a fixed IEEE operation sequence. v = 0 for every
- * node at tau = 0, where the images equal the plain ones bit for bit. The
- * block and per-Gaussian pre-culls are off while it is on (a blended Gaussian
- * is not bounded by its node's own position and scale).
+ * node at tau = 0, where the images equal the plain ones bit for bit. While it
+ * is on, the pre-culls bound the segment from a node's mean to its parent's
+ * with the larger scale and opacity of the two (a blended Gaussian lies
+ * within those bounds).
  * NGS_OPT_PAIRS_PER_PIXEL (1..4096, default 48): the planner's estimate of
  * (tile, Gaussian) pairs per pixel, used to fit sub-batches into
  * pair_capacity; it is raised automatically to 1.25x the largest density a

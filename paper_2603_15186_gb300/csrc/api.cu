@@ -179,7 +179,7 @@ void free_scene(ngs_ctx *c) {
     SceneDev &s = c->scene;
     if (c->owns_scene) {
         dfree(s.box_lo); dfree(s.box_hi); dfree(s.pos4); dfree(s.quat); dfree(s.sop); dfree(s.sh);
-        dfree(s.blk_lo); dfree(s.blk_hi);
+        dfree(s.blk_lo); dfree(s.blk_hi); dfree(s.blk_lo_b); dfree(s.blk_hi_b);
     }
     c->scene = SceneDev();
     c->loaded = false;
@@ -941,39 +941,52 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *c, const ngs_gaussians *g, const ngs_
     // per-block bounds for the block-level cull of the fused cut + preprocess
     const int64_t bs = cutpre_partition_nodes();
     const int64_t nb = (n + bs - 1) / bs;
-    std::vector<float4> blo(nb), bhi(nb);
+    std::vector<float4> blo(nb), bhi(nb), blo_b(nb), bhi_b(nb);
+    auto log_scale_of = [&](int64_t i, int k) -> double {
+        if (g->attr_dtype == NGS_F32) return ((const float *)g->log_scale)[3 * i + k];
+        const uint16_t hv = ((const uint16_t *)g->log_scale)[3 * i + k];
+        return g->attr_dtype == NGS_F16 ? half_to_float(hv) : bf16_to_float(hv);
+    };
+    auto opacity_of = [&](int64_t i) -> double {
+        if (g->attr_dtype == NGS_F32) return ((const float *)g->opacity)[i];
+        const uint16_t hv = ((const uint16_t *)g->opacity)[i];
+        return g->attr_dtype == NGS_F16 ? half_to_float(hv) : bf16_to_float(hv);
+    };
     for (int64_t b = 0; b < nb; ++b) {
-        float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-        double smax = 0.0, kmax = 0.0;
+        // own: the block's nodes; both: the block's nodes and their parents
+        float mn[2][3], mx[2][3];
+        double smax[2] = {0.0, 0.0}, kmax[2] = {0.0, 0.0};
+        for (int w = 0; w < 2; ++w)
+            for (int k = 0; k < 3; ++k) { mn[w][k] = INFINITY; mx[w][k] = -INFINITY; }
         for (int64_t i = b * bs; i < std::min(n, (b + 1) * bs); ++i) {
-            for (int k = 0; k < 3; ++k) {
-                mn[k] = std::min(mn[k], g->pos[3 * i + k]);
-                mx[k] = std::max(mx[k], g->pos[3 * i + k]);
-            }
-            double ls[3], o;
-            for (int k = 0; k < 3; ++k) {
-                if (g->attr_dtype == NGS_F32) ls[k] = ((const float *)g->log_scale)[3 * i + k];
-                else {
-                    const uint16_t h = ((const uint16_t *)g->log_scale)[3 * i + k];
-                    ls[k] = g->attr_dtype == NGS_F16 ? half_to_float(h) : bf16_to_float(h);
+            const int64_t par = h->parent[i];
+            for (int src = 0; src < 2; ++src) {
+                const int64_t j = src == 0 ? i : par;
+                if (j < 0) continue;
+                for (int w = src; w < 2; ++w) {
+                    for (int k = 0; k < 3; ++k) {
+                        mn[w][k] = std::min(mn[w][k], g->pos[3 * j + k]);
+                        mx[w][k] = std::max(mx[w][k], g->pos[3 * j + k]);
+                    }
+                    const double ls = std::max(log_scale_of(j, 0),
+                                               std::max(log_scale_of(j, 1), log_scale_of(j, 2)));
+                    smax[w] = std::max(smax[w], std::exp(ls));
+                    const double o = opacity_of(j);
+                    if (255.0 * o >= 1.0) kmax[w] = std::max(kmax[w], 2.0 * std::log(255.0 * o));
                 }
             }
-            if (g->attr_dtype == NGS_F32) o = ((const float *)g->opacity)[i];
-            else {
-                const uint16_t h = ((const uint16_t *)g->opacity)[i];
-                o = g->attr_dtype == NGS_F16 ? half_to_float(h) : bf16_to_float(h);
-            }
-            smax = std::max(smax, std::exp(std::max(ls[0], std::max(ls[1], ls[2]))));
-            if (255.0 * o >= 1.0) kmax = std::max(kmax, 2.0 * std::log(255.0 * o));
         }
-        blo[b] = make_float4(mn[0], mn[1], mn[2], (float)(smax * (1.0 + 1e-5)));
-        bhi[b] = make_float4(mx[0], mx[1], mx[2], (float)(kmax * (1.0 + 1e-5) + 1e-6));
+        blo[b] = make_float4(mn[0][0], mn[0][1], mn[0][2], (float)(smax[0] * (1.0 + 1e-5)));
+        bhi[b] = make_float4(mx[0][0], mx[0][1], mx[0][2], (float)(kmax[0] * (1.0 + 1e-5) + 1e-6));
+        blo_b[b] = make_float4(mn[1][0], mn[1][1], mn[1][2], (float)(smax[1] * (1.0 + 1e-5)));
+        bhi_b[b] = make_float4(mx[1][0], mx[1][1], mx[1][2], (float)(kmax[1] * (1.0 + 1e-5) + 1e-6));
     }
     SceneDev &d = c->scene;
     ngs_status st = NGS_OK;
     auto A = [&](ngs_status x) { if (st == NGS_OK) st = x; };
     A(dalloc(&d.box_lo, n)); A(dalloc(&d.box_hi, n)); A(dalloc(&d.pos4, n)); A(dalloc(&d.quat, n));
     A(dalloc(&d.blk_lo, nb)); A(dalloc(&d.blk_hi, nb));
+    A(dalloc(&d.blk_lo_b, nb)); A(dalloc(&d.blk_hi_b, nb));
     A(dalloc((unsigned char **)&d.sop, (size_t)n * 4 * esz));
     A(dalloc((unsigned char **)&d.sh, (size_t)n * 48 * esz));
     if (st != NGS_OK) {
@@ -988,6 +1001,8 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *c, const ngs_gaussians *g, const ngs_
     CK(cudaMemcpy(d.sh, g->sh, (size_t)n * 48 * esz, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.blk_lo, blo.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.blk_hi, bhi.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.blk_lo_b, blo_b.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.blk_hi_b, bhi_b.data(), nb * sizeof(float4), cudaMemcpyHostToDevice));
     d.nblk = nb;
     d.n = n;
     d.n_leaves = 0;

@@ -308,8 +308,9 @@ __device__ __forceinline__ bool precull(const CamLite &cam, const NodeCull &nd, 
 // are bounded over the 8 corners; the support half-width is bounded with the
 // smallest depth and the largest |T0|^2 = (fx / z)^2 |W0 - r W2|^2 over the r
 // range (convex in r); every bound carries slack well above float32 error.
-__device__ __forceinline__ bool block_culled(const float4 lo, const float4 hi,
-                                             const DevCamera &cam, int tile_w, int tile_h) {
+template <typename Cam>
+__device__ __forceinline__ bool block_culled(const float4 lo, const float4 hi, const Cam &cam,
+                                             int tile_w, int tile_h) {
     float tzmin = INFINITY, tzmax = -INFINITY, dmax = 0.0f;
     float t[8][3];
 #pragma unroll
@@ -525,7 +526,11 @@ __global__ void k_live_parts(SceneDev sc, const DevCamera *__restrict__ cams, in
                              int64_t nblk, uint32_t *__restrict__ part_list,
                              uint2 *__restrict__ group_list, uint2 *__restrict__ part_info,
                              uint32_t *counters, int tile_w, int tile_h, int use_block_cull,
-                             const int *err) {
+                             int blend, const int *err) {
+    // with level-of-detail blending a node's Gaussian may move toward its
+    // parent: the bounds then cover the block's nodes and their parents
+    const float4 *__restrict__ blo = blend ? sc.blk_lo_b : sc.blk_lo;
+    const float4 *__restrict__ bhi = blend ? sc.blk_hi_b : sc.blk_hi;
     if (*err) return;
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int64_t nch = (n_cams + kGroupCams - 1) / kGroupCams;
@@ -541,8 +546,7 @@ __global__ void k_live_parts(SceneDev sc, const DevCamera *__restrict__ cams, in
             const int c = (int)(q - b * nch) * kGroupCams + hl;
             if (c < n_cams) {
                 t = (uint32_t)(b * n_cams + c);
-                live = !(use_block_cull &&
-                         block_culled(sc.blk_lo[b], sc.blk_hi[b], cams[c], tile_w, tile_h));
+                live = !(use_block_cull && block_culled(blo[b], bhi[b], cams[c], tile_w, tile_h));
                 if (!live) part_info[(int64_t)c * nblk + b] = make_uint2(0u, 0u);
             }
         }
@@ -590,7 +594,7 @@ struct CutPreSmem {
 static_assert(kGroupCams <= 16 && kPrePart <= 4096, "entries pack node and camera in 16 bits");
 
 template <typename A, typename R, bool kBlend>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, kBlend ? 3 : 0)
 k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restrict__ rec,
          int64_t rec_cap, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
          uint32_t *__restrict__ vis_count, uint32_t *counters,
@@ -653,6 +657,30 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             }
             nd.K = 2.0f * logf(255.0f * so[3]);
             nd.smax = expf(fmaxf(fmaxf(so[0], so[1]), so[2]));
+            // blending: the Gaussian's mean lies on the segment from the node's
+            // mean to its parent's, its scale and opacity below the larger of
+            // the two; the box of that segment with those bounds is tested
+            // like a block of means (conservative)
+            float4 seg_lo = nd.p, seg_hi = nd.p;
+            bool seg_dead = false;
+            if (kBlend) {
+                float K = 255.0f * so[3] >= 1.0f ? nd.K : -INFINITY;
+                float smax = nd.smax;
+                if (valid && par >= 0) {
+                    const float4 pp = sc.pos4[par];
+                    float sq[4];
+                    Attr<A>::load4(sc.sop, par, sq);
+                    seg_lo = make_float4(fminf(nd.p.x, pp.x), fminf(nd.p.y, pp.y),
+                                         fminf(nd.p.z, pp.z), 0.f);
+                    seg_hi = make_float4(fmaxf(nd.p.x, pp.x), fmaxf(nd.p.y, pp.y),
+                                         fmaxf(nd.p.z, pp.z), 0.f);
+                    if (255.0f * sq[3] >= 1.0f) K = fmaxf(K, 2.0f * logf(255.0f * sq[3]));
+                    smax = fmaxf(smax, expf(fmaxf(fmaxf(sq[0], sq[1]), sq[2])));
+                }
+                seg_dead = !(K >= 0.0f);   // opacity below 1/255 at both ends
+                seg_lo.w = smax * (1.0f + 1e-5f);
+                seg_hi.w = K * (1.0f + 1e-5f) + 1e-6f;
+            }
             uint32_t m = 0;
             for (int i = 0; i < gcnt; ++i) {
                 const CamLite &cam = S.cam[i];
@@ -662,9 +690,9 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
                                  cam.tau) &&
                     (par < 0 || granularity(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
                                             cam.fx) > cam.tau);
-                // a blended Gaussian is not bounded by its node's own position
-                // and scale: with blending every selected node is a candidate
-                const bool cand = sel && (kBlend || precull(cam, nd, tile_w, tile_h));
+                const bool cand =
+                    sel && (kBlend ? !seg_dead && !block_culled(seg_lo, seg_hi, cam, tile_w, tile_h)
+                                   : precull(cam, nd, tile_w, tile_h));
                 m |= cand ? 1u << i : 0u;
                 const uint32_t nsel = __popc(__ballot_sync(0xffffffffu, sel));
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
@@ -913,13 +941,11 @@ void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
     cudaMemsetAsync(vis_count, 0, (size_t)n_cams * sizeof(uint32_t), st);
     const int64_t nq = nblk * ((n_cams + kGroupCams - 1) / kGroupCams);
-    // 8 warps per CTA, two (block, camera chunk) items per warp and iteration.
-    // The block cull bounds a block's own Gaussians; blended ones may lie
-    // outside it, so blending tests every block.
+    // 8 warps per CTA, two (block, camera chunk) items per warp and iteration
     const int lgrid = (int)std::min<int64_t>((nq + 15) / 16, 8 * 1024);
     k_live_parts<<<std::max(lgrid, 1), 256, 0, st>>>(sc, cams, n_cams, nblk, part_list,
                                                      group_list, part_info, counters, tile_w,
-                                                     tile_h, use_block_cull && !blend, err);
+                                                     tile_h, use_block_cull, blend, err);
     if (blend)
         launch_cutpre_t<true>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, vis_count,
                               counters, part_list, group_list, part_info, err, tile_w, tile_h,

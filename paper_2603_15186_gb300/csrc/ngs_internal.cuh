@@ -93,6 +93,9 @@ struct SceneDev {
     // per block of cutpre_partition_nodes() consecutive nodes: box of the means
     // (xyz) with the largest scale (lo.w) and the largest 2 ln(255 o) (hi.w)
     float4 *blk_lo = nullptr, *blk_hi = nullptr;
+    // the same bounds over the block's nodes and their parents: every
+    // level-of-detail blend of a node with its parent lies within them
+    float4 *blk_lo_b = nullptr, *blk_hi_b = nullptr;
     int64_t nblk = 0;
 };
 

@@ -241,12 +241,17 @@ def test_pixels_independent_of_tile_shape_batch_and_graph(R, small_floor):
         assert np.array_equal(alone, base[i])
 
 
-def test_block_cull_is_conservative(R, small_floor, box10k):
+@pytest.mark.parametrize("blend", [False, True])
+def test_block_cull_is_conservative(R, small_floor, box10k, blend):
     """Skipping node blocks that provably hold no visible Gaussian changes
-    nothing: same visible Gaussians, same pairs, same image bits."""
-    for scene, cams in [(small_floor, _floor_cams(small_floor)),
-                        (box10k, [camera_c0(0.0), look_camera((-3.0, 2.0, 1.5), 0.3, 64, 48, fx=60.0)])]:
+    nothing: same visible Gaussians, same pairs, same image bits; with
+    level-of-detail blending too (bounds over the nodes and their parents)."""
+    extra = walk_cameras(small_floor, 2, 78, 160, 120, fx=150.0, tau=20.0)[1]
+    for scene, cams in [(small_floor, _floor_cams(small_floor) + [extra]),
+                        (box10k, [camera_c0(0.0), camera_c0(10.0),
+                                  look_camera((-3.0, 2.0, 1.5), 0.3, 64, 48, fx=60.0, tau=6.0)])]:
         R.load_scene(scene)
+        R.set_lod_blend(blend)
         outs, work = [], []
         for on in (True, False):
             R.set_block_cull(on)
@@ -254,6 +259,7 @@ def test_block_cull_is_conservative(R, small_floor, box10k):
             st = R.stats()
             work.append((st["visible_total"], st["pair_total"]))
         R.set_block_cull(True)
+        R.set_lod_blend(False)
         assert work[0] == work[1]
         for a, b in zip(*outs):
             assert np.array_equal(a, b)
