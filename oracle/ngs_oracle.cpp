@@ -465,6 +465,109 @@ void orc_render_bruteforce(const double *pre, const uint32_t *depth_key, int64_t
     }
 }
 
+// ---------------------------------------------------------------------------
+// 6. GS-slice occupancy (Sec. III-C, Eqs. for G3D, Sigma3D^-1, G2D, alpha/beta,
+//    lambda and mu(z); derivation in the supplementary section)
+// ---------------------------------------------------------------------------
+//
+// A horizontal plane at height z cuts the 3D Gaussian
+// G3D(x) = exp(-1/2 (x - mu)^T Sigma^-1 (x - mu)), Sigma^-1 = [[cxx cxy cxz],
+// [cxy cyy cyz], [cxz cyz czz]], in the 2D Gaussian
+//   G2D(x, z) = exp(-1/2 lambda (z - mu_z)^2) exp(-1/2 [x - mu(z)]^T C [x - mu(z)])
+// with C = [[cxx cxy], [cxy cyy]], (alpha, beta) solving C (alpha, beta)^T =
+// (cxz, cyz)^T, lambda = czz - alpha^2 cxx - beta^2 cyy - 2 alpha beta cxy and
+// mu(z) = (mu_x, mu_y) - (z - mu_z) (alpha, beta). (Readings: the second
+// exponent carries the factor -1/2, as the derivation implies; the printed
+// "(y' + beta y')" is (y' + beta z').)
+
+// The slice of one Gaussian: out[0..9] = alpha, beta, lambda, C (cxx, cxy, cyy),
+// and Sigma^-1 (cxz, cyz, czz), from Sigma^-1 = R S^-2 R^T.
+void orc_slice_params(const float *quat, const float *log_scale, double *out) {
+    double w = quat[0], x = quat[1], y = quat[2], z = quat[3];
+    const double nq = std::sqrt(w * w + x * x + y * y + z * z);
+    w /= nq; x /= nq; y /= nq; z /= nq;
+    const double R[9] = {
+        1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y),
+        2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x),
+        2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)};
+    double is2[3];
+    for (int k = 0; k < 3; ++k) is2[k] = std::exp(-2.0 * (double)log_scale[k]);
+    double c[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * is2[k] * R[3 * j + k];
+            c[3 * i + j] = acc;
+        }
+    const double cxx = c[0], cxy = c[1], cxz = c[2], cyy = c[4], cyz = c[5], czz = c[8];
+    const double det = cxx * cyy - cxy * cxy;
+    const double alpha = (cxz * cyy - cyz * cxy) / det;
+    const double beta = (cyz * cxx - cxz * cxy) / det;
+    const double lambda = czz - alpha * alpha * cxx - beta * beta * cyy - 2.0 * alpha * beta * cxy;
+    const double o[9] = {alpha, beta, lambda, cxx, cxy, cyy, cxz, cyz, czz};
+    for (int k = 0; k < 9; ++k) out[k] = o[k];
+}
+
+// Slice value of Gaussian g at (x, y) on the plane at height z:
+// o G2D(x, z) (before the 0.99 cap and the 1/255 cut-off).
+double orc_slice_value(const orc_scene *sc, int64_t g, double x, double y, double z) {
+    double p[9];
+    orc_slice_params(sc->quat + 4 * g, sc->log_scale + 3 * g, p);
+    const double zp = z - sc->pos[3 * g + 2];
+    const double mx = sc->pos[3 * g] - zp * p[0], my = sc->pos[3 * g + 1] - zp * p[1];
+    const double dx = x - mx, dy = y - my;
+    const double q2 = p[3] * dx * dx + 2.0 * p[4] * dx * dy + p[5] * dy * dy;
+    return sc->opacity[g] * std::exp(-0.5 * p[2] * zp * zp) * std::exp(-0.5 * q2);
+}
+
+// Occupancy grid of the leaves (child_count 0): value[k][j][i] = the largest
+// a = min(0.99, o G2D(c_ij, z_k)) over the leaves with a >= 1/255 (0 if none),
+// c_ij = (x0 + (i + 1/2) cell, y0 + (j + 1/2) cell), z_k = z0 + k dz;
+// occ = value >= threshold. Each slice is visited over the cells of the bounding
+// box of its support ellipse (exactly where a >= 1/255), widened by 1e-9 m.
+void orc_slice_occupancy(const orc_scene *sc, double x0, double y0, double cell, int32_t nx,
+                         int32_t ny, double z0, double dz, int32_t nz, double threshold,
+                         double *value, uint8_t *occ) {
+    const int64_t plane = (int64_t)nx * ny;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t k = 0; k < nz; ++k) {
+        double *vk = value + k * plane;
+        for (int64_t c = 0; c < plane; ++c) vk[c] = 0.0;
+        const double z = z0 + k * dz;
+        for (int64_t g = 0; g < sc->n; ++g) {
+            if (sc->child_count[g] != 0) continue;
+            const double o = sc->opacity[g];
+            if (255.0 * o < 1.0) continue;
+            const double K = 2.0 * std::log(255.0 * o);   // a >= 1/255 <=> exponent sum <= K
+            double p[9];
+            orc_slice_params(sc->quat + 4 * g, sc->log_scale + 3 * g, p);
+            const double zp = z - sc->pos[3 * g + 2];
+            const double rem = K - p[2] * zp * zp;
+            if (rem < 0.0) continue;
+            const double det = p[3] * p[5] - p[4] * p[4];
+            const double hx = std::sqrt(rem * p[5] / det) + 1e-9;
+            const double hy = std::sqrt(rem * p[3] / det) + 1e-9;
+            const double mx = sc->pos[3 * g] - zp * p[0], my = sc->pos[3 * g + 1] - zp * p[1];
+            // cells whose centre lies in [m - h, m + h]
+            const int64_t i0 = std::max<int64_t>(0, (int64_t)std::ceil((mx - hx - x0) / cell - 0.5));
+            const int64_t i1 = std::min<int64_t>(nx - 1, (int64_t)std::floor((mx + hx - x0) / cell - 0.5));
+            const int64_t j0 = std::max<int64_t>(0, (int64_t)std::ceil((my - hy - y0) / cell - 0.5));
+            const int64_t j1 = std::min<int64_t>(ny - 1, (int64_t)std::floor((my + hy - y0) / cell - 0.5));
+            for (int64_t j = j0; j <= j1; ++j)
+                for (int64_t i = i0; i <= i1; ++i) {
+                    const double dx = x0 + (i + 0.5) * cell - mx, dy = y0 + (j + 0.5) * cell - my;
+                    const double q2 = p[3] * dx * dx + 2.0 * p[4] * dx * dy + p[5] * dy * dy;
+                    const double a = o * std::exp(-0.5 * (p[2] * zp * zp + q2));
+                    if (a < kAlphaMin) continue;
+                    const double v = std::min(kAlphaMax, a);
+                    if (v > vk[j * nx + i]) vk[j * nx + i] = v;
+                }
+        }
+        if (occ)
+            for (int64_t c = 0; c < plane; ++c) occ[k * plane + c] = vk[c] >= threshold ? 1 : 0;
+    }
+}
+
 int32_t orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -77,6 +77,15 @@ def lib():
             L.orc_depth_f32.restype = C.c_float
             L.orc_depth_f32.argtypes = [vp, C.POINTER(_Camera)]
             L.orc_num_threads.restype = i32
+            L.orc_slice_params.restype = None
+            L.orc_slice_params.argtypes = [vp, vp, vp]
+            L.orc_slice_value.restype = C.c_double
+            L.orc_slice_value.argtypes = [C.POINTER(_Scene), i64, C.c_double, C.c_double,
+                                          C.c_double]
+            L.orc_slice_occupancy.restype = None
+            L.orc_slice_occupancy.argtypes = [C.POINTER(_Scene), C.c_double, C.c_double,
+                                              C.c_double, i32, i32, C.c_double, C.c_double, i32,
+                                              C.c_double, vp, vp]
             _lib = L
     return _lib
 
@@ -271,6 +280,36 @@ def blend_gaussian(scene, cam, node, blend=True):
     return float(v), mu, S, float(op[0]), sh
 
 
+def slice_params(quat, log_scale):
+    """(alpha, beta, lambda, cxx, cxy, cyy, cxz, cyz, czz) of the GS slice of a
+    Gaussian (Sec. III-C)."""
+    q = np.ascontiguousarray(quat, dtype=np.float32)
+    ls = np.ascontiguousarray(log_scale, dtype=np.float32)
+    out = np.empty(9, dtype=np.float64)
+    lib().orc_slice_params(_p(q), _p(ls), _p(out))
+    return out
+
+
+def slice_value(scene, g, x, y, z):
+    """o G2D((x, y), z) of Gaussian g (no cap, no cut-off)."""
+    sa = _as_scene(scene)
+    return float(lib().orc_slice_value(C.byref(sa.c), int(g), float(x), float(y), float(z)))
+
+
+def slice_occupancy(scene, grid):
+    """Per plane and cell the largest slice value of the leaves (float64
+    [nz, ny, nx]) and the occupancy mask at grid.threshold (uint8).
+    ``grid``: x0, y0, cell, nx, ny, z0, dz, nz, threshold."""
+    sa = _as_scene(scene)
+    g = grid
+    val = np.empty((g.nz, g.ny, g.nx), dtype=np.float64)
+    occ = np.empty((g.nz, g.ny, g.nx), dtype=np.uint8)
+    lib().orc_slice_occupancy(C.byref(sa.c), float(g.x0), float(g.y0), float(g.cell), int(g.nx),
+                              int(g.ny), float(g.z0), float(g.dz), int(g.nz), float(g.threshold),
+                              _p(val), _p(occ))
+    return val, occ
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())
 
@@ -278,4 +317,4 @@ def num_threads() -> int:
 __all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bin_pairs",
            "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "depth_f32",
            "tiles_xy", "num_threads", "lib", "granularity_f32", "blend_parent_weight",
-           "blend_gaussian"]
+           "blend_gaussian", "slice_params", "slice_value", "slice_occupancy"]

@@ -512,3 +512,82 @@ def test_binning_sort_matches_numpy_stable_sort(small_floor):
     cnt = np.bincount(tiles, minlength=tx * ty)
     assert np.array_equal(ranges[:, 1] - ranges[:, 0], cnt)
     assert len(keys) > 1000
+
+
+# ---------------------------------------------------------------------------
+# GS-slice occupancy (Sec. III-C)
+# ---------------------------------------------------------------------------
+
+def _sigma_scipy(quat, log_scale):
+    q = np.asarray(quat, np.float64)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    return R @ np.diag(np.exp(2.0 * np.asarray(log_scale, np.float64))) @ R.T
+
+
+def test_slice_axis_aligned_closed_form():
+    """An axis-aligned Gaussian slices without shift (alpha = beta = 0), with
+    lambda = 1 / sigma_z^2 and C = diag(1 / sigma_x^2, 1 / sigma_y^2)."""
+    ls = np.array([-3.0, -2.5, -2.0], np.float32)
+    p = O.slice_params([1, 0, 0, 0], ls)
+    s2 = np.exp(2.0 * ls.astype(np.float64))
+    np.testing.assert_allclose(p[:2], [0.0, 0.0], atol=1e-9)
+    np.testing.assert_allclose(p[2], 1.0 / s2[2], rtol=1e-12)
+    np.testing.assert_allclose(p[3:6], [1.0 / s2[0], 0.0, 1.0 / s2[1]], rtol=1e-12, atol=1e-9)
+
+
+def test_slice_is_the_3d_gaussian_on_the_plane():
+    """The slice identity: o G2D((x, y), z) = o G3D((x, y, z)) for any point;
+    lambda is the Schur complement 1 / Sigma_zz and mu(z) the conditional mean
+    mu_xy + Sigma_xy,z (z - mu_z) / Sigma_zz (Sigma from scipy's rotation)."""
+    rng = np.random.default_rng(21)
+    n = 40
+    t = _Tree(n, np.zeros((n, 3)), np.ones((n, 3)), [-1] + [0] * (n - 1), [n - 1] + [0] * (n - 1))
+    t.pos = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    t.quat = rng.normal(size=(n, 4)).astype(np.float32)
+    t.log_scale = rng.normal(-3.0, 0.6, (n, 3)).astype(np.float32)
+    t.opacity = rng.uniform(0.05, 0.95, n).astype(np.float32)
+    for g in range(n):
+        S = _sigma_scipy(t.quat[g], t.log_scale[g])
+        Si = np.linalg.inv(S)
+        p = O.slice_params(t.quat[g], t.log_scale[g])
+        assert p[2] == pytest.approx(1.0 / S[2, 2], rel=1e-9)
+        np.testing.assert_allclose(p[:2], -S[:2, 2] / S[2, 2], rtol=1e-9, atol=1e-12)
+        for _ in range(5):
+            x = t.pos[g].astype(np.float64) + rng.normal(0, 0.05, 3)
+            d = x - t.pos[g]
+            want = float(t.opacity[g]) * math.exp(-0.5 * d @ Si @ d)
+            got = O.slice_value(t, g, x[0], x[1], x[2])
+            assert got == pytest.approx(want, rel=1e-9, abs=1e-300)
+
+
+def test_slice_occupancy_against_brute_force():
+    """Per plane and cell, the oracle's occupancy value equals the brute-force
+    maximum over every leaf of min(0.99, o G3D) (values below 1/255 dropped),
+    with G3D from scipy's covariance; the mask is value >= threshold."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(5)
+    pos = np.column_stack([rng.uniform(0, 1.0, 60), rng.uniform(0, 0.8, 60),
+                           rng.uniform(0, 0.6, 60)])
+    s = _scene_from_leaves(pos, quat=rng.normal(size=(60, 4)),
+                           log_scale=rng.normal(-2.8, 0.4, (60, 3)),
+                           opacity=rng.uniform(0.02, 0.99, 60))
+    grid = SimpleNamespace(x0=-0.05, y0=0.02, cell=0.04, nx=29, ny=21, z0=0.03, dz=0.1, nz=6,
+                           threshold=0.3)
+    val, occ = O.slice_occupancy(s, grid)
+    leaves = np.flatnonzero(s.child_count == 0)
+    xs = grid.x0 + (np.arange(grid.nx) + 0.5) * grid.cell
+    ys = grid.y0 + (np.arange(grid.ny) + 0.5) * grid.cell
+    X, Y = np.meshgrid(xs, ys)
+    for k in range(grid.nz):
+        z = grid.z0 + k * grid.dz
+        want = np.zeros((grid.ny, grid.nx))
+        for g in leaves:
+            Si = np.linalg.inv(_sigma_scipy(s.quat[g], s.log_scale[g]))
+            mu = s.pos[g].astype(np.float64)
+            d = np.stack([X - mu[0], Y - mu[1], np.full_like(X, z - mu[2])], -1)
+            a = np.float64(s.opacity[g]) * np.exp(-0.5 * np.einsum("...i,ij,...j->...", d, Si, d))
+            a = np.where(a >= 1.0 / 255.0, np.minimum(a, 0.99), 0.0)
+            want = np.maximum(want, a)
+        np.testing.assert_allclose(val[k], want, rtol=1e-9, atol=1e-12)
+        assert np.array_equal(occ[k], (val[k] >= grid.threshold).astype(np.uint8))
+    assert (val > 0).mean() > 0.2 and occ.any()
