@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-blend", action="store_true",
                     help="skip the level-of-detail blending leg")
+    ap.add_argument("--no-slice", action="store_true",
+                    help="skip the GS-slice occupancy leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="seconds of simulated agent load for the serving leg (0: skip)")
     ap.add_argument("--serving-scene", default="floor8m")
@@ -478,11 +480,66 @@ def run_ours(args, world, rank, local, pg):
             blend["max_abs_err_vs_oracle"] = max(errs)
         out["lod_blend"] = blend
         R.set_lod_blend(False)
+    if not args.no_slice:
+        out["gs_slice"] = run_slice(args, R, scene, stored, deq, rank, stream)
     R.close()
     if args.serving_seconds > 0:
         out["serving"] = run_serving(args, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GS-slice occupancy leg: the floor's leaves cut by planes every 10 cm
+# ---------------------------------------------------------------------------
+
+def slice_grid(scene, cell=0.05, z0=0.05, dz=0.1, nz=13, threshold=0.5):
+    """Cells of `cell` metres over the scene's box, planes every 10 cm from
+    5 cm to 1.25 m (the robot's height range)."""
+    from types import SimpleNamespace
+    lo, hi = scene.aabb_min[0], scene.aabb_max[0]
+    return SimpleNamespace(x0=float(lo[0]), y0=float(lo[1]), cell=cell,
+                           nx=int(np.ceil((hi[0] - lo[0]) / cell)),
+                           ny=int(np.ceil((hi[1] - lo[1]) / cell)), z0=z0, dz=dz, nz=nz,
+                           threshold=threshold)
+
+
+def run_slice(args, R, scene, stored, deq, rank, stream):
+    import torch
+    import oracle as O
+    g = slice_grid(scene)
+    val, occ = R.slice_occupancy(g, stream=stream)
+    for _ in range(2):
+        R.slice_occupancy(g, val, occ, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 3)
+    a.record(stream)
+    for _ in range(reps):
+        R.slice_occupancy(g, val, occ, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    evals = R.stats()["evaluations"]
+    leaves = int(scene.n_leaves)
+    outd = {"grid": f"{g.nx}x{g.ny} cells of {g.cell} m, {g.nz} planes {g.z0}..{g.z0 + (g.nz - 1) * g.dz:.2f} m",
+            "leaves": leaves, "ms": round(ms, 3),
+            "leaf_planes_per_s": round(leaves * g.nz / (ms * 1e-3) / 1e9, 3), "unit": "G/s",
+            "cell_evaluations_per_s": round(evals / (ms * 1e-3) / 1e9, 2),
+            "cell_evaluations": int(evals), "occupied_frac": float(occ.float().mean().item())}
+    if rank == 0 and not args.no_cpu:
+        t = time.time()
+        want, wocc = O.slice_occupancy(O.SceneArrays(scene, overrides=deq), g)
+        outd["oracle_s"] = round(time.time() - t, 2)
+        outd["oracle_cores"] = O.num_threads()
+        got = val.cpu().numpy().astype(np.float64)
+        exempt = (np.minimum(got, want) <= 1.0 / 255.0 + 1e-3) & (np.abs(got - want) > 1e-3)
+        outd["max_abs_err_vs_oracle"] = float(np.abs(got - want)[~exempt].max())
+        outd["cutoff_exempt_frac"] = float(exempt.mean())
+        near = np.abs(want - g.threshold) <= 1e-3
+        outd["mask_mismatch_away_from_threshold"] = int(
+            (occ.cpu().numpy()[~near] != wocc[~near]).sum())
+    return outd
 
 
 # ---------------------------------------------------------------------------

@@ -254,6 +254,33 @@ NGS_API ngs_status ngs_stage_times(ngs_ctx *ctx, double *ms, int32_t n);
 NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *ctx, int32_t cam, int64_t *h_ranges,
                                         int32_t *h_nodes, int64_t cap, int64_t *n_pairs);
 
+/* GS-slice occupancy (Sec. III-C: the scene's Gaussians cut by horizontal
+ * planes give the floor-level occupancy used for collision checks). Plane k
+ * lies at height z0 + k dz; cell (i, j) of a plane spans [x0 + i cell, x0 +
+ * (i + 1) cell) x [y0 + j cell, y0 + (j + 1) cell). */
+typedef struct {
+    float x0, y0, cell;
+    int32_t nx, ny;
+    float z0, dz;
+    int32_t nz;
+    float threshold;      /* a cell is occupied where its value >= threshold */
+} ngs_slice_grid;
+
+/* Cuts every leaf Gaussian of the loaded scene by the grid's planes. A plane at
+ * height z cuts G3D(x) = exp(-1/2 (x - mu)^T Sigma^-1 (x - mu)) in the 2D
+ * Gaussian exp(-1/2 lambda (z - mu_z)^2) exp(-1/2 [x - mu(z)]^T C [x - mu(z)]),
+ * C the xy block of Sigma^-1, (alpha, beta) = C^-1 (c_xz, c_yz), mu(z) = mu_xy -
+ * (z - mu_z) (alpha, beta), lambda = c_zz - alpha^2 c_xx - beta^2 c_yy -
+ * 2 alpha beta c_xy. d_value [nz][ny][nx] (device float32, caller-owned)
+ * receives per cell the largest min(0.99, o G2D(cell centre, z)) over the
+ * leaves for which that value is >= 1/255 (0 if none); d_occ (device uint8,
+ * same shape, may be NULL) receives value >= threshold. Asynchronous on
+ * `stream`. NGS_ERR_INVALID_ARG for a non-positive size, cell or dz, a
+ * non-finite field, or nx * ny * nz >= 2^31; NGS_ERR_NOT_LOADED without a
+ * scene. */
+NGS_API ngs_status ngs_slice_occupancy(ngs_ctx *ctx, const ngs_slice_grid *grid, float *d_value,
+                                       uint8_t *d_occ, void *stream);
+
 /* Stable LSD radix sort (onesweep: one histogram pass, then one chained-scan
  * scatter pass per 8-bit digit) of n (key, value) pairs by key bits
  * [begin_bit, end_bit). d_keys/d_vals: device arrays sorted in place; keys are

@@ -32,7 +32,7 @@ EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_l
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
            "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune", "ngs_server_start",
            "ngs_server_submit", "ngs_server_poll", "ngs_server_wait_all", "ngs_server_stats",
-           "ngs_server_stop", "ngs_selftest_wait_timeout"]
+           "ngs_server_stop", "ngs_selftest_wait_timeout", "ngs_slice_occupancy"]
 
 
 class NgsError(RuntimeError):
@@ -69,6 +69,12 @@ class TuneResult(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("cta_w", C.c_int32),
                 ("cta_h", C.c_int32), ("batch", C.c_int32), ("reserved", C.c_int32),
                 ("ms", C.c_float * (3 * len(TUNE_SHAPES)))]
+
+
+class SliceGrid(C.Structure):
+    _fields_ = [("x0", C.c_float), ("y0", C.c_float), ("cell", C.c_float), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("z0", C.c_float), ("dz", C.c_float), ("nz", C.c_int32),
+                ("threshold", C.c_float)]
 
 
 class ServerConfig(C.Structure):
@@ -137,6 +143,8 @@ def load(build_if_missing: bool = True):
     L.ngs_sort_pairs.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp]
     L.ngs_sort_pairs_static.restype = i32
     L.ngs_sort_pairs_static.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    L.ngs_slice_occupancy.restype = i32
+    L.ngs_slice_occupancy.argtypes = [vp, C.POINTER(SliceGrid), vp, vp, vp]
     L.ngs_autotune.restype = i32
     L.ngs_autotune.argtypes = [vp, C.POINTER(Camera), i32, C.POINTER(vp), i32, vp,
                                C.POINTER(TuneResult)]

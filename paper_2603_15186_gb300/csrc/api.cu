@@ -1260,6 +1260,28 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     return NGS_OK;
 }
 
+NGS_API ngs_status ngs_slice_occupancy(ngs_ctx *c, const ngs_slice_grid *grid, float *d_value,
+                                       uint8_t *d_occ, void *stream) {
+    if (!c || !grid || !d_value) return NGS_ERR_INVALID_ARG;
+    if (!c->loaded) return NGS_ERR_NOT_LOADED;
+    const ngs_slice_grid &g = *grid;
+    const float f[] = {g.x0, g.y0, g.cell, g.z0, g.dz, g.threshold};
+    for (float v : f)
+        if (!std::isfinite(v)) return NGS_ERR_INVALID_ARG;
+    if (g.nx <= 0 || g.ny <= 0 || g.nz <= 0 || !(g.cell > 0.0f) || !(g.dz > 0.0f))
+        return NGS_ERR_INVALID_ARG;
+    if ((int64_t)g.nx * g.ny * g.nz >= ((int64_t)1 << 31)) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    SliceGrid sg{g.x0, g.y0, g.cell, g.nx, g.ny, g.z0, g.dz, g.nz, g.threshold};
+    ngs_status es = ensure_work(c);
+    if (es != NGS_OK) return es;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(c->w.work64, 0, 2 * sizeof(unsigned long long), st));
+    launch_slice(c->scene, sg, d_value, d_occ, c->w.work64 + 1, c->num_sms, st);
+    CK(cudaGetLastError());
+    return NGS_OK;
+}
+
 NGS_API ngs_status ngs_sort_pairs(ngs_ctx *c, void *d_keys, uint32_t *d_vals, int64_t n,
                                   int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
                                   void *stream) {

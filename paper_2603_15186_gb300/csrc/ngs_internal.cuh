@@ -352,6 +352,18 @@ void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges,
                    cudaStream_t st, const int *err);
 
 // compositing of tiles [0, n_tiles) of a sub-batch
+// GS-slice occupancy grid (see include/ngs.h, ngs_slice_grid)
+struct SliceGrid {
+    float x0, y0, cell;
+    int32_t nx, ny;
+    float z0, dz;
+    int32_t nz;
+    float threshold;
+};
+// value: [nz][ny][nx] float32, zeroed here; occ (optional): the mask
+void launch_slice(const SceneDev &sc, const SliceGrid &g, float *value, uint8_t *occ,
+                  unsigned long long *work, int num_sms, cudaStream_t st);
+
 // tile_w x tile_h: binning tile; cta_w x cta_h: the block one CTA composites
 // (equal to the tile, or a compiled shape dividing it)
 void launch_composite(int attr_dtype, int tile_w, int tile_h, int cta_w, int cta_h, int batch,

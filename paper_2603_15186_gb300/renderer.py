@@ -201,6 +201,25 @@ class Renderer:
         check(self.L.ngs_last_stats(self.h, C.byref(s)), "ngs_last_stats")
         return {k: getattr(s, k) for k, _ in _lib.Stats._fields_}
 
+    def slice_occupancy(self, grid, value=None, occ=None, stream=None):
+        """GS-slice occupancy of the loaded scene's leaves. ``grid``: any object
+        with x0, y0, cell, nx, ny, z0, dz, nz, threshold. Returns (value float32
+        CUDA tensor [nz, ny, nx], occupancy uint8 tensor of the same shape)."""
+        torch = _torch()
+        shape = (int(grid.nz), int(grid.ny), int(grid.nx))
+        dev = f"cuda:{self.device}"
+        if value is None:
+            value = torch.empty(shape, dtype=torch.float32, device=dev)
+        if occ is None:
+            occ = torch.empty(shape, dtype=torch.uint8, device=dev)
+        g = _lib.SliceGrid(float(grid.x0), float(grid.y0), float(grid.cell), int(grid.nx),
+                           int(grid.ny), float(grid.z0), float(grid.dz), int(grid.nz),
+                           float(grid.threshold))
+        check(self.L.ngs_slice_occupancy(self.h, C.byref(g), C.c_void_p(value.data_ptr()),
+                                         C.c_void_p(occ.data_ptr()), _stream_ptr(stream)),
+              "ngs_slice_occupancy")
+        return value, occ
+
     def select_cut(self, cams, cap: Optional[int] = None, stream=None):
         """Per-camera LOD cuts: (ids int32 CUDA tensor, offsets int64 CUDA tensor)."""
         torch = _torch()

@@ -66,9 +66,9 @@ int main(void) {
          sizeof(ngs_hierarchy), sizeof(ngs_config), sizeof(ngs_stats));
   printf("%zu %zu %zu %zu\n", offsetof(ngs_camera, tau), offsetof(ngs_gaussians, attr_dtype),
          offsetof(ngs_config, max_tiles_per_batch), offsetof(ngs_stats, mode));
-  printf("%zu %zu %zu %zu %zu %d\n", sizeof(ngs_tune_result), offsetof(ngs_tune_result, ms),
+  printf("%zu %zu %zu %zu %zu %d %zu %zu\n", sizeof(ngs_tune_result), offsetof(ngs_tune_result, ms),
          offsetof(ngs_tune_result, batch), offsetof(ngs_stats, cta_w), sizeof(ngs_server_config),
-         NGS_TUNE_SHAPES);
+         NGS_TUNE_SHAPES, sizeof(ngs_slice_grid), offsetof(ngs_slice_grid, threshold));
   printf("%d %d %d %d %d %d %d %d %d %d %d\n", NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H,
          NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL, NGS_OPT_CTA_W,
          NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL, NGS_OPT_LOD_BLEND);
@@ -88,7 +88,8 @@ int main(void) {
                     _lib.Config.max_tiles_per_batch.offset, _lib.Stats.mode.offset]
     assert [int(x) for x in t.split()] == [
         C.sizeof(_lib.TuneResult), _lib.TuneResult.ms.offset, _lib.TuneResult.batch.offset,
-        _lib.Stats.cta_w.offset, C.sizeof(_lib.ServerConfig), len(_lib.TUNE_SHAPES)]
+        _lib.Stats.cta_w.offset, C.sizeof(_lib.ServerConfig), len(_lib.TUNE_SHAPES),
+        C.sizeof(_lib.SliceGrid), _lib.SliceGrid.threshold.offset]
     assert [int(x) for x in o.split()] == [
         _lib.NGS_OPT_MODE, _lib.NGS_OPT_TILE_W, _lib.NGS_OPT_TILE_H, _lib.NGS_OPT_BATCH,
         _lib.NGS_OPT_GRAPH, _lib.NGS_OPT_STAGE_TIMING, _lib.NGS_OPT_BLOCK_CULL,

@@ -310,6 +310,44 @@ def test_autotune_keeps_pixels(R, small_floor):
     R.set_batch(128)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_slice_occupancy_matches_oracle(R, small_floor, dtype):
+    """GS-slice occupancy of every leaf against the oracle: per plane and cell
+    the largest capped slice value within 1e-3 (cells whose value sits at the
+    1/255 cut-off on either side excepted, under 1% of them), and the
+    occupancy mask equal away from the threshold."""
+    from types import SimpleNamespace
+    if dtype == "f32":
+        R.load_scene(small_floor)
+        ref_scene = small_floor
+    else:
+        stored, deq = quantize_attributes(small_floor, dtype)
+        R.load_scene(small_floor, attr_dtype=dtype, stored=stored)
+        ref_scene = O.SceneArrays(small_floor, overrides=deq)
+    lo, hi = small_floor.aabb_min[0], small_floor.aabb_max[0]
+    grid = SimpleNamespace(x0=float(lo[0]) - 0.013, y0=float(lo[1]) + 0.007, cell=0.04,
+                           nx=int((hi[0] - lo[0]) / 0.04) + 2, ny=int((hi[1] - lo[1]) / 0.04) + 1,
+                           z0=0.05, dz=0.1, nz=13, threshold=0.5)
+    val, occ = R.slice_occupancy(grid)
+    torch.cuda.synchronize()
+    got, gocc = val.cpu().numpy().astype(np.float64), occ.cpu().numpy()
+    want, wocc = O.slice_occupancy(ref_scene, grid)
+    cut = 1.0 / 255.0 + 1e-3
+    exempt = (np.minimum(got, want) <= cut) & (np.abs(got - want) > 1e-3)
+    assert exempt.mean() < 0.01
+    assert np.abs(got - want)[~exempt].max() <= 1e-3
+    near = np.abs(want - grid.threshold) <= 1e-3
+    assert np.array_equal(gocc[~near], wocc[~near])
+    assert wocc.any() and (want > 0).mean() > 0.05
+    # a grid beside the scene holds nothing; sizes are checked
+    far = SimpleNamespace(**{**vars(grid), "x0": float(hi[0]) + 5.0, "nz": 1})
+    v2, o2 = R.slice_occupancy(far)
+    assert float(v2.max()) == 0.0 and int(o2.max()) == 0
+    from paper_2603_15186_gb300 import NgsError
+    with pytest.raises(NgsError):
+        R.slice_occupancy(SimpleNamespace(**{**vars(grid), "nx": 0}))
+
+
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 def test_reduced_precision_attributes(R, small_floor, dtype):
     stored, deq = quantize_attributes(small_floor, dtype)
