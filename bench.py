@@ -37,8 +37,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cams", type=int, default=256)
     ap.add_argument("--leaves", default="floor4m")
-    ap.add_argument("--tile", default="16x16")
-    ap.add_argument("--cta", default="0x0", help="compositing block (0x0: the tile)")
+    ap.add_argument("--tile", default="32x32", help="binning tile (the autotuner's pick by default)")
+    ap.add_argument("--cta", default="16x16", help="compositing block (0x0: the tile)")
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
