@@ -103,7 +103,8 @@ struct PairRec {
 
 // A warp renders a WBW x BH block (64 pixels, two per thread) of the tile:
 // 8x8 in 8-wide tiles, 16x4 otherwise; 32-wide tiles hold two blocks side by
-// side. NCB 16-pixel column blocks per tile row (one for 8 and 16 wide tiles).
+// side. A warp block lies in one 16-pixel column block and holds NRPW row
+// pairs, for which the warp computes its records' coefficient sets.
 template <typename R, int TW, int TH, int BATCH>
 struct CompLayout {
     static constexpr int WBW = TW < 16 ? TW : 16;      // width of a warp's block
@@ -111,13 +112,12 @@ struct CompLayout {
     static constexpr int NWX = TW / WBW;               // warp blocks across the tile
     static constexpr int NW = NWX * (TH / BH);         // warps per tile
     static constexpr int NT = 32 * NW;                 // threads: two pixels each
-    static constexpr int NRP = TH / 2;                 // row pairs per tile
-    static constexpr int NCB = TW < 16 ? 1 : TW / 16;  // 16-pixel column blocks
-    static constexpr int NCOEF = NRP * NCB;            // coefficient sets per record
+    static constexpr int NRPW = BH / 2;                // row pairs per warp block
     static constexpr int kListStride = BATCH + 4;      // u32 entries per warp list
     static constexpr size_t rec_off = 0;
     static constexpr size_t coef_off = rec_off + (size_t)BATCH * sizeof(R);
-    static constexpr size_t pair_off = coef_off + (size_t)(BATCH + 1) * NCOEF * sizeof(float4);
+    static constexpr size_t pair_off =
+        coef_off + (size_t)NW * kListStride * NRPW * sizeof(float4);
     static constexpr size_t box_off = pair_off + (size_t)(BATCH + 1) * sizeof(PairRec);
     static constexpr size_t list_off = box_off + (size_t)BATCH * sizeof(float4);
     static constexpr size_t bytes = list_off + (size_t)NW * kListStride * sizeof(uint32_t);
@@ -137,16 +137,17 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             unsigned long long *work64, int sub_x, int sub_y) {
     using Lay = CompLayout<R, TW, TH, BATCH>;
     constexpr int NT = Lay::NT, BH = Lay::BH, WBW = Lay::WBW, NWX = Lay::NWX;
-    constexpr int NCB = Lay::NCB, NCOEF = Lay::NCOEF;
+    constexpr int NRPW = Lay::NRPW;
     constexpr int kPer = (BATCH + NT - 1) / NT;   // records gathered per thread per round
     __shared__ uint32_t s_wsum[Lay::NW];
-    // dynamic shared memory, per round: the tile's kept records; per (record,
-    // pair of tile rows r, r + 1, 16-pixel column block) the exponent as a
-    // quadratic in the pixel's column offset lx within its column block,
-    // q = (A lx + a1) lx + a0, stored (a1_r, a1_r+1, a0_r, a0_r+1) at
-    // (record * NRP + row pair) * NCB + block; the records' PairRec; their reach
-    // boxes; one record list per warp. Index BATCH holds a sentinel record
-    // (q = -inf everywhere).
+    // dynamic shared memory, per round: the tile's kept records; per warp, for
+    // each entry of its record list and each pair of rows r, r + 1 of its pixel
+    // block, the exponent as a quadratic in the pixel's column offset lx within
+    // its 16-pixel column block, q = (A lx + a1) lx + a0, stored (a1_r,
+    // a1_r+1, a0_r, a0_r+1) at (warp * list stride + entry) * NRPW + row pair;
+    // the records' PairRec; their reach boxes; one record list per warp. Record
+    // index BATCH is a sentinel (zero colour; its coefficient sets hold
+    // q = -inf).
     extern __shared__ float4 smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(smem_dyn);
     R *s_rec = reinterpret_cast<R *>(sm + Lay::rec_off);
@@ -161,10 +162,11 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
     // and (lx, ly + 1)
     const int bx = (warp % NWX) * WBW, by = (warp / NWX) * BH;
     const int lx = bx + lane % WBW, ly = by + 2 * (lane / WBW);
-    const int coef_slot = (ly >> 1) * NCB + (TW < 16 ? 0 : lx >> 4);
+    const int rp = lane / WBW;                        // the lane's row pair in its block
+    const int wcb = TW < 16 ? 0 : bx >> 4;            // the warp's 16-pixel column block
     uint32_t *my_list = s_list + warp * Lay::kListStride;
+    float4 *my_coef = s_coef + (size_t)warp * Lay::kListStride * NRPW;
     const float inf = __int_as_float(0x7f800000);
-    if (tid < NCOEF) s_coef[BATCH * NCOEF + tid] = make_float4(0.0f, 0.0f, -inf, -inf);
     if (tid == 0) {
         s_pair[BATCH].rg = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         s_pair[BATCH].bA = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -298,24 +300,34 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                 }
                 if (lane < ((4 - (len & 3)) & 3)) my_list[len + lane] = (uint32_t)BATCH;
             }
-            for (int e = tid; e < (int)nk * NCOEF; e += NT) {
-                const int j = e / NCOEF, rem = e - j * NCOEF;
-                const int p = rem / NCB, cb = rem - p * NCB;
-                const R &rr = s_rec[j];
-                const float A = rr.a.z, B = rr.a.w, C = rr.b.x, L = rr.b.y;
-                const float dxt = __fsub_rn(xref + (float)(16 * cb), rr.a.x);
-                const float axb = __fadd_rn(A, A);
-                float a1[2], a0[2];
+            // the warp's coefficient sets for its own list entries and row
+            // pairs (padding entries get the sentinel's q = -inf)
+            if (warp_live) {
+                const int len4w = (len + 3) & ~3;
+                for (int e = lane; e < len4w * NRPW; e += 32) {
+                    const int i = e / NRPW, r = e - i * NRPW;
+                    float4 cfv = make_float4(0.0f, 0.0f, -inf, -inf);
+                    if (i < len) {
+                        const R &rr = s_rec[my_list[i]];
+                        const float A = rr.a.z, B = rr.a.w, C = rr.b.x, L = rr.b.y;
+                        const float dxt = __fsub_rn(xref + (float)(16 * wcb), rr.a.x);
+                        const float axb = __fadd_rn(A, A);
+                        const int p = (by >> 1) + r;
+                        float a1[2], a0[2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float dy = __fsub_rn((float)(y0 + 2 * p + h) + 0.5f, rr.a.y);
-                    const float bdy = __fmul_rn(B, dy);
-                    a1[h] = __fmaf_rn(axb, dxt, bdy);
-                    a0[h] = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt, __fmaf_rn(C, __fmul_rn(dy, dy), L));
+                        for (int h = 0; h < 2; ++h) {
+                            const float dy = __fsub_rn((float)(y0 + 2 * p + h) + 0.5f, rr.a.y);
+                            const float bdy = __fmul_rn(B, dy);
+                            a1[h] = __fmaf_rn(axb, dxt, bdy);
+                            a0[h] = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt,
+                                              __fmaf_rn(C, __fmul_rn(dy, dy), L));
+                        }
+                        cfv = make_float4(a1[0], a1[1], a0[0], a0[1]);
+                    }
+                    my_coef[e] = cfv;
                 }
-                s_coef[j * NCOEF + rem] = make_float4(a1[0], a1[1], a0[0], a0[1]);
+                __syncwarp();
             }
-            __syncthreads();
             if (T2.x > 0.0f || T2.y > 0.0f) {
                 uint32_t live_groups = 0;   // groups of four, counted per live pixel
                 // both pixels in packed (f32x2) arithmetic, every step the same
@@ -336,7 +348,7 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     float2 q[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float4 cf = s_coef[jj[u] * NCOEF + coef_slot];
+                        const float4 cf = my_coef[(i + u) * NRPW + rp];
                         const float4 bA = s_pair[jj[u]].bA;
                         const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
                         q[u] = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
