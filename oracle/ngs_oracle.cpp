@@ -568,6 +568,86 @@ void orc_slice_occupancy(const orc_scene *sc, double x0, double y0, double cell,
     }
 }
 
+// ---------------------------------------------------------------------------
+// 7. Navigable map, shortest-path distance fields and paths (Sec. III-C: the
+//    slices give the navigable area for collision checks and path planning;
+//    Sec. IV-A: trajectories from a shortest-path planner)
+// ---------------------------------------------------------------------------
+//
+// blocked(i, j): some plane k in [k_lo, k_hi] (the robot's height range) is
+// occupied at a cell within Chebyshev distance `inflate` of (i, j) (the robot's
+// footprint). Distance field of a goal: breadth-first 4-connected steps over
+// free cells (UINT32_MAX where unreachable, blocked, or when the goal itself is
+// blocked). A path from a start cell descends the field one step at a time,
+// taking the first neighbour in the order (+x, -x, +y, -y) whose distance is
+// one less, until the goal.
+
+static const uint32_t kUnreached = 0xFFFFFFFFu;
+
+void orc_nav_blocked(const uint8_t *occ, int32_t nx, int32_t ny, int32_t k_lo, int32_t k_hi,
+                     int32_t inflate, uint8_t *blocked) {
+    const int64_t plane = (int64_t)nx * ny;
+    std::vector<uint8_t> any(plane, 0);
+    for (int32_t k = k_lo; k <= k_hi; ++k)
+        for (int64_t c = 0; c < plane; ++c) any[c] |= occ[k * plane + c];
+    for (int32_t j = 0; j < ny; ++j)
+        for (int32_t i = 0; i < nx; ++i) {
+            uint8_t b = 0;
+            for (int32_t dj = -inflate; dj <= inflate && !b; ++dj)
+                for (int32_t di = -inflate; di <= inflate && !b; ++di) {
+                    const int32_t a = i + di, c = j + dj;
+                    if (a >= 0 && a < nx && c >= 0 && c < ny && any[(int64_t)c * nx + a]) b = 1;
+                }
+            blocked[(int64_t)j * nx + i] = b;
+        }
+}
+
+void orc_nav_field(const uint8_t *blocked, int32_t nx, int32_t ny, int32_t gi, int32_t gj,
+                   uint32_t *dist) {
+    const int64_t plane = (int64_t)nx * ny;
+    for (int64_t c = 0; c < plane; ++c) dist[c] = kUnreached;
+    if (gi < 0 || gi >= nx || gj < 0 || gj >= ny || blocked[(int64_t)gj * nx + gi]) return;
+    std::vector<int64_t> q;
+    q.reserve(plane);
+    dist[(int64_t)gj * nx + gi] = 0;
+    q.push_back((int64_t)gj * nx + gi);
+    for (size_t h = 0; h < q.size(); ++h) {
+        const int64_t c = q[h];
+        const int32_t i = (int32_t)(c % nx), j = (int32_t)(c / nx);
+        const int32_t ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
+        for (int e = 0; e < 4; ++e) {
+            if (ni[e] < 0 || ni[e] >= nx || nj[e] < 0 || nj[e] >= ny) continue;
+            const int64_t n = (int64_t)nj[e] * nx + ni[e];
+            if (blocked[n] || dist[n] != kUnreached) continue;
+            dist[n] = dist[c] + 1;
+            q.push_back(n);
+        }
+    }
+}
+
+// Writes the path's cells (i, j) from the start to the goal into path
+// [max_len][2]; returns its length (0 if the start is unreachable; at most
+// max_len cells are written).
+int32_t orc_nav_path(const uint32_t *dist, int32_t nx, int32_t ny, int32_t si, int32_t sj,
+                     int32_t max_len, int32_t *path) {
+    if (si < 0 || si >= nx || sj < 0 || sj >= ny) return 0;
+    uint32_t d = dist[(int64_t)sj * nx + si];
+    if (d == kUnreached) return 0;
+    int32_t i = si, j = sj, len = 0;
+    for (;;) {
+        if (len < max_len) { path[2 * len] = i; path[2 * len + 1] = j; }
+        ++len;
+        if (d == 0 || len >= max_len) break;
+        const int32_t ni[4] = {i + 1, i - 1, i, i}, nj[4] = {j, j, j + 1, j - 1};
+        for (int e = 0; e < 4; ++e) {
+            if (ni[e] < 0 || ni[e] >= nx || nj[e] < 0 || nj[e] >= ny) continue;
+            if (dist[(int64_t)nj[e] * nx + ni[e]] == d - 1) { i = ni[e]; j = nj[e]; break; }
+        }
+        --d;
+    }
+    return std::min(len, max_len);
+}
+
 int32_t orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

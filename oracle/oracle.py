@@ -82,6 +82,12 @@ def lib():
             L.orc_slice_value.restype = C.c_double
             L.orc_slice_value.argtypes = [C.POINTER(_Scene), i64, C.c_double, C.c_double,
                                           C.c_double]
+            L.orc_nav_blocked.restype = None
+            L.orc_nav_blocked.argtypes = [vp, i32, i32, i32, i32, i32, vp]
+            L.orc_nav_field.restype = None
+            L.orc_nav_field.argtypes = [vp, i32, i32, i32, i32, vp]
+            L.orc_nav_path.restype = i32
+            L.orc_nav_path.argtypes = [vp, i32, i32, i32, i32, i32, vp]
             L.orc_slice_occupancy.restype = None
             L.orc_slice_occupancy.argtypes = [C.POINTER(_Scene), C.c_double, C.c_double,
                                               C.c_double, i32, i32, C.c_double, C.c_double, i32,
@@ -310,6 +316,35 @@ def slice_occupancy(scene, grid):
     return val, occ
 
 
+def nav_blocked(occ, k_lo, k_hi, inflate):
+    """Blocked cells [ny, nx] (uint8): some plane in [k_lo, k_hi] occupied
+    within Chebyshev distance ``inflate``."""
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    nz, ny, nx = occ.shape
+    out = np.empty((ny, nx), dtype=np.uint8)
+    lib().orc_nav_blocked(_p(occ), nx, ny, int(k_lo), int(k_hi), int(inflate), _p(out))
+    return out
+
+
+def nav_field(blocked, goal):
+    """4-connected breadth-first distances (uint32, 0xffffffff unreachable)
+    from goal = (i, j) over the free cells."""
+    blocked = np.ascontiguousarray(blocked, dtype=np.uint8)
+    ny, nx = blocked.shape
+    out = np.empty((ny, nx), dtype=np.uint32)
+    lib().orc_nav_field(_p(blocked), nx, ny, int(goal[0]), int(goal[1]), _p(out))
+    return out
+
+
+def nav_path(dist, start, max_len):
+    """Shortest path (cells (i, j), start first) descending the field."""
+    dist = np.ascontiguousarray(dist, dtype=np.uint32)
+    ny, nx = dist.shape
+    path = np.zeros((max_len, 2), dtype=np.int32)
+    n = lib().orc_nav_path(_p(dist), nx, ny, int(start[0]), int(start[1]), int(max_len), _p(path))
+    return path[:n].copy()
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())
 
@@ -317,4 +352,5 @@ def num_threads() -> int:
 __all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bin_pairs",
            "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "depth_f32",
            "tiles_xy", "num_threads", "lib", "granularity_f32", "blend_parent_weight",
-           "blend_gaussian", "slice_params", "slice_value", "slice_occupancy"]
+           "blend_gaussian", "slice_params", "slice_value", "slice_occupancy", "nav_blocked",
+           "nav_field", "nav_path"]

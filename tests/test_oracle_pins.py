@@ -591,3 +591,70 @@ def test_slice_occupancy_against_brute_force():
         np.testing.assert_allclose(val[k], want, rtol=1e-9, atol=1e-12)
         assert np.array_equal(occ[k], (val[k] >= grid.threshold).astype(np.uint8))
     assert (val > 0).mean() > 0.2 and occ.any()
+
+
+# ---------------------------------------------------------------------------
+# navigable map, distance fields, shortest paths
+# ---------------------------------------------------------------------------
+
+def test_nav_hand_worked_detour():
+    with open(os.path.join(GOLDEN, "nav_detour_grid.json")) as f:
+        g = json.load(f)
+    b = np.array(g["blocked"], np.uint8)
+    d = O.nav_field(b, g["goal"]).astype(np.int64)
+    d[d == 0xFFFFFFFF] = -1
+    assert d.tolist() == g["dist"]
+    assert O.nav_path(O.nav_field(b, g["goal"]), g["path_from"], 64).tolist() == g["path"]
+
+
+def test_nav_field_free_grid_is_manhattan_and_matches_scipy():
+    """Without obstacles the field is the Manhattan distance; with random
+    obstacles it equals scipy's unweighted shortest paths on the grid graph."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import shortest_path
+    ny, nx = 23, 31
+    d = O.nav_field(np.zeros((ny, nx), np.uint8), (7, 11)).astype(np.int64)
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    assert np.array_equal(d, np.abs(ii - 7) + np.abs(jj - 11))
+    rng = np.random.default_rng(8)
+    b = (rng.random((ny, nx)) < 0.28).astype(np.uint8)
+    b[11, 7] = 0
+    idx = np.arange(ny * nx).reshape(ny, nx)
+    rows, cols = [], []
+    for (dj, di) in ((0, 1), (1, 0)):
+        a = idx[: ny - dj, : nx - di]
+        c = idx[dj:, di:]
+        ok = (b[: ny - dj, : nx - di] == 0) & (b[dj:, di:] == 0)
+        rows += list(a[ok]); cols += list(c[ok])
+    G = coo_matrix((np.ones(len(rows)), (rows, cols)), shape=(ny * nx, ny * nx))
+    ref = shortest_path(G, directed=False, unweighted=True, indices=idx[11, 7])
+    got = O.nav_field(b, (7, 11)).astype(np.float64).ravel()
+    got[got == 0xFFFFFFFF] = np.inf
+    ref[b.ravel() == 1] = np.inf
+    assert np.array_equal(got, ref)
+
+
+def test_nav_paths_descend_the_field():
+    rng = np.random.default_rng(9)
+    b = (rng.random((40, 50)) < 0.2).astype(np.uint8)
+    b[20, 25] = 0
+    d = O.nav_field(b, (25, 20))
+    for _ in range(30):
+        s = (int(rng.integers(50)), int(rng.integers(40)))
+        p = O.nav_path(d, s, 500)
+        if d[s[1], s[0]] == 0xFFFFFFFF:
+            assert len(p) == 0
+            continue
+        assert len(p) == int(d[s[1], s[0]]) + 1 and tuple(p[0]) == s and tuple(p[-1]) == (25, 20)
+        steps = np.abs(np.diff(p, axis=0)).sum(1)
+        assert np.all(steps == 1) and not b[p[:, 1], p[:, 0]].any()
+        assert np.array_equal(d[p[:, 1], p[:, 0]], np.arange(len(p))[::-1])
+
+
+def test_nav_blocked_against_numpy_dilation():
+    from scipy.ndimage import binary_dilation
+    rng = np.random.default_rng(10)
+    occ = (rng.random((6, 30, 40)) < 0.02).astype(np.uint8)
+    got = O.nav_blocked(occ, 1, 4, 2)
+    want = binary_dilation(occ[1:5].any(0), structure=np.ones((5, 5), bool))
+    assert np.array_equal(got.astype(bool), want)
