@@ -540,7 +540,53 @@ def run_slice(args, R, scene, stored, deq, rank, stream):
         near = np.abs(want - g.threshold) <= 1e-3
         outd["mask_mismatch_away_from_threshold"] = int(
             (occ.cpu().numpy()[~near] != wocc[~near]).sum())
+    outd["navigation"] = run_nav(args, R, g, occ, rank, stream)
     return outd
+
+
+def run_nav(args, R, g, occ, rank, stream):
+    """Navigable map for a robot between planes 1 and 9 (0.15..0.85 m) with a
+    10 cm footprint (2 cells), breadth-first distance fields of 9 goals (the
+    paper's 9 annotated landmarks) and shortest paths for 64 agents."""
+    import torch
+    import oracle as O
+    rng = np.random.default_rng(77)
+    blocked, _ = R.nav_fields(occ, [(0, 0)], 1, 9, 2, stream=stream)
+    free = np.argwhere(blocked.cpu().numpy() == 0)
+    goals = [tuple(int(v) for v in free[k][::-1]) for k in rng.choice(len(free), 9, replace=False)]
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        blocked, dist = R.nav_fields(occ, goals, 1, 9, 2, stream=stream)
+        times.append(time.perf_counter() - t)
+    starts = [(int(free[k][1]), int(free[k][0]), int(rng.integers(9)))
+              for k in rng.choice(len(free), 64, replace=False)]
+    R.nav_paths(dist, starts, 4096, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    paths, lens = R.nav_paths(dist, starts, 4096, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    dist_h = dist.cpu().numpy().view(np.uint32)
+    out = {"grid": f"{g.nx}x{g.ny}", "goals": len(goals), "agents": len(starts),
+           "fields_ms": round(1e3 * min(times), 3), "paths_ms": round(a.elapsed_time(b), 3),
+           "reachable_frac": float((dist_h[0] < 0xFFFFFFFF).mean()),
+           "mean_path_cells": float(lens.float().mean().item())}
+    if rank == 0 and not args.no_cpu:
+        occ_h = occ.cpu().numpy()
+        t = time.time()
+        b_ref = O.nav_blocked(occ_h, 1, 9, 2)
+        refs = [O.nav_field(b_ref, q) for q in goals]
+        out["oracle_fields_s"] = round(time.time() - t, 3)
+        ph, lh = paths.cpu().numpy(), lens.cpu().numpy()
+        same_paths = all(np.array_equal(ph[k, :lh[k]], O.nav_path(refs[s_[2]], s_[:2], 4096))
+                         for k, s_ in enumerate(starts))
+        out["bit_exact_vs_oracle"] = bool(
+            np.array_equal(blocked.cpu().numpy(), b_ref) and
+            all(np.array_equal(dist_h[q], refs[q]) for q in range(len(goals))) and same_paths)
+    return out
 
 
 # ---------------------------------------------------------------------------

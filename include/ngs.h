@@ -281,6 +281,33 @@ typedef struct {
 NGS_API ngs_status ngs_slice_occupancy(ngs_ctx *ctx, const ngs_slice_grid *grid, float *d_value,
                                        uint8_t *d_occ, void *stream);
 
+/* Navigation on the slice occupancy (Sec. III-C: navigable areas for
+ * collision checks and path planning; Sec. IV-A: expert trajectories from a
+ * shortest-path planner). d_occ: device uint8 [nz][ny][nx] (e.g. the d_occ of
+ * ngs_slice_occupancy). d_blocked (device uint8 [ny][nx]) receives 1 where some
+ * plane k_lo..k_hi (the robot's height range) is occupied within Chebyshev
+ * distance `inflate` cells (the robot's footprint; 0..64). For each goal g
+ * (host int32 [n_goals][2] = cell (i, j)), d_dist + g * ny * nx (device uint32)
+ * receives the 4-connected breadth-first step count from the goal over the
+ * free cells, 0xffffffff where unreachable (also everywhere when the goal is
+ * blocked or outside the grid). Synchronous: returns once the fields are
+ * complete. The context keeps a scratch buffer for it (two frontier queues of
+ * ny * nx entries per goal), grown on demand. */
+NGS_API ngs_status ngs_nav_fields(ngs_ctx *ctx, const uint8_t *d_occ, int32_t nx, int32_t ny,
+                                  int32_t nz, int32_t k_lo, int32_t k_hi, int32_t inflate,
+                                  const int32_t *goals, int32_t n_goals, uint8_t *d_blocked,
+                                  uint32_t *d_dist, void *stream);
+
+/* Shortest paths for n agents: d_starts (device int32 [n][3]) = start cell
+ * (i, j) and goal index. Each path descends its goal's field from the start,
+ * taking the first neighbour in the order (+x, -x, +y, -y) whose distance is
+ * one less; d_paths (device int32 [n][max_len][2]) receives its cells from the
+ * start to the goal and d_len [n] their number (0 when the start is unreachable;
+ * at most max_len). Asynchronous on `stream`. */
+NGS_API ngs_status ngs_nav_paths(ngs_ctx *ctx, const uint32_t *d_dist, int32_t nx, int32_t ny,
+                                 int32_t n_goals, const int32_t *d_starts, int32_t n,
+                                 int32_t max_len, int32_t *d_paths, int32_t *d_len, void *stream);
+
 /* Stable LSD radix sort (onesweep: one histogram pass, then one chained-scan
  * scatter pass per 8-bit digit) of n (key, value) pairs by key bits
  * [begin_bit, end_bit). d_keys/d_vals: device arrays sorted in place; keys are

@@ -32,7 +32,8 @@ EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_l
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
            "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune", "ngs_server_start",
            "ngs_server_submit", "ngs_server_poll", "ngs_server_wait_all", "ngs_server_stats",
-           "ngs_server_stop", "ngs_selftest_wait_timeout", "ngs_slice_occupancy"]
+           "ngs_server_stop", "ngs_selftest_wait_timeout", "ngs_slice_occupancy",
+           "ngs_nav_fields", "ngs_nav_paths"]
 
 
 class NgsError(RuntimeError):
@@ -143,6 +144,10 @@ def load(build_if_missing: bool = True):
     L.ngs_sort_pairs.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp]
     L.ngs_sort_pairs_static.restype = i32
     L.ngs_sort_pairs_static.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    L.ngs_nav_fields.restype = i32
+    L.ngs_nav_fields.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, vp, i32, vp, vp, vp]
+    L.ngs_nav_paths.restype = i32
+    L.ngs_nav_paths.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, vp, vp, vp]
     L.ngs_slice_occupancy.restype = i32
     L.ngs_slice_occupancy.argtypes = [vp, C.POINTER(SliceGrid), vp, vp, vp]
     L.ngs_autotune.restype = i32

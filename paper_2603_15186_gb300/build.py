@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libngs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "k_cut.cu", "k_preprocess.cu", "k_sort.cu", "k_binning.cu",
-           "k_composite.cu", "k_slice.cu", "sort_static.cu", "server.cu"]
+           "k_composite.cu", "k_slice.cu", "k_nav.cu", "sort_static.cu", "server.cu"]
 
 
 def nvcc() -> str:

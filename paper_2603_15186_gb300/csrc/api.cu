@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ngs_internal.cuh"
+#include "nav.h"
 
 using namespace ngs;
 
@@ -105,6 +106,10 @@ struct ngs_ctx {
     std::vector<cudaEvent_t> ev;
     int ev_groups = 0;
     int kernels_per_render = 0;
+
+    // navigation scratch (occupied-any map, goals, frontier queues), grown on demand
+    unsigned char *nav_tmp = nullptr;
+    size_t nav_tmp_bytes = 0;
 
     // standalone sort/scan scratch
     void *sort_tmp_keys = nullptr;
@@ -829,6 +834,7 @@ NGS_API ngs_status ngs_destroy(ngs_ctx *c) {
     if (!c) return NGS_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    if (c->nav_tmp) dfree(c->nav_tmp);
     drop_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -1278,6 +1284,58 @@ NGS_API ngs_status ngs_slice_occupancy(ngs_ctx *c, const ngs_slice_grid *grid, f
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(c->w.work64, 0, 2 * sizeof(unsigned long long), st));
     launch_slice(c->scene, sg, d_value, d_occ, c->w.work64 + 1, c->num_sms, st);
+    CK(cudaGetLastError());
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_nav_fields(ngs_ctx *c, const uint8_t *d_occ, int32_t nx, int32_t ny,
+                                  int32_t nz, int32_t k_lo, int32_t k_hi, int32_t inflate,
+                                  const int32_t *goals, int32_t n_goals, uint8_t *d_blocked,
+                                  uint32_t *d_dist, void *stream) {
+    if (!c || !d_occ || !goals || !d_blocked || !d_dist) return NGS_ERR_INVALID_ARG;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || n_goals <= 0 || n_goals > 4096) return NGS_ERR_INVALID_ARG;
+    if (k_lo < 0 || k_hi >= nz || k_lo > k_hi || inflate < 0 || inflate > 64)
+        return NGS_ERR_INVALID_ARG;
+    const int64_t plane = (int64_t)nx * ny;
+    if (plane >= ((int64_t)1 << 30) || plane * n_goals >= ((int64_t)1 << 31))
+        return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const size_t a_bytes = ((size_t)plane + 255) & ~(size_t)255;
+    const size_t g_bytes = ((size_t)n_goals * sizeof(int2) + 255) & ~(size_t)255;
+    const size_t need = a_bytes + g_bytes + (size_t)n_goals * 2 * plane * sizeof(uint32_t);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (need > c->nav_tmp_bytes) {
+        CK(cudaStreamSynchronize(st));
+        if (c->nav_tmp) dfree(c->nav_tmp);
+        c->nav_tmp = nullptr;
+        c->nav_tmp_bytes = 0;
+        ngs_status s = dalloc(&c->nav_tmp, need);
+        if (s != NGS_OK) return s;
+        c->nav_tmp_bytes = need;
+    }
+    std::vector<int2> hg((size_t)n_goals);
+    for (int32_t g = 0; g < n_goals; ++g) hg[g] = make_int2(goals[2 * g], goals[2 * g + 1]);
+    int2 *dg = reinterpret_cast<int2 *>(c->nav_tmp + a_bytes);
+    CK(cudaMemcpyAsync(dg, hg.data(), (size_t)n_goals * sizeof(int2), cudaMemcpyHostToDevice, st));
+    const int e = launch_nav_fields(d_occ, nx, ny, k_lo, k_hi, inflate, dg, n_goals, c->nav_tmp,
+                                    reinterpret_cast<uint32_t *>(c->nav_tmp + a_bytes + g_bytes),
+                                    d_blocked, d_dist, c->num_sms, st);
+    if (e != 0) {
+        std::fprintf(stderr, "ngs: nav fields: %s\n", cudaGetErrorString((cudaError_t)e));
+        return NGS_ERR_CUDA;
+    }
+    return NGS_OK;
+}
+
+NGS_API ngs_status ngs_nav_paths(ngs_ctx *c, const uint32_t *d_dist, int32_t nx, int32_t ny,
+                                 int32_t n_goals, const int32_t *d_starts, int32_t n,
+                                 int32_t max_len, int32_t *d_paths, int32_t *d_len, void *stream) {
+    if (!c || !d_dist || (n > 0 && (!d_starts || !d_paths || !d_len))) return NGS_ERR_INVALID_ARG;
+    if (nx <= 0 || ny <= 0 || n_goals <= 0 || n < 0 || max_len <= 0) return NGS_ERR_INVALID_ARG;
+    if ((int64_t)n * max_len >= ((int64_t)1 << 31)) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    launch_nav_paths(d_dist, nx, ny, n_goals, reinterpret_cast<const int3 *>(d_starts), n, max_len,
+                     reinterpret_cast<int2 *>(d_paths), d_len, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return NGS_OK;
 }

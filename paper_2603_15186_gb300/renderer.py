@@ -220,6 +220,36 @@ class Renderer:
               "ngs_slice_occupancy")
         return value, occ
 
+    def nav_fields(self, occ, goals, k_lo: int, k_hi: int, inflate: int, stream=None):
+        """Blocked map (uint8 [ny, nx]) and one breadth-first distance field per
+        goal (int64 view of uint32 [n_goals, ny, nx]) from an occupancy tensor
+        [nz, ny, nx] on the device; ``goals``: (i, j) cells."""
+        torch = _torch()
+        nz, ny, nx = (int(v) for v in occ.shape)
+        g = np.ascontiguousarray(np.asarray(goals, dtype=np.int32).reshape(-1, 2))
+        blocked = torch.empty((ny, nx), dtype=torch.uint8, device=occ.device)
+        dist = torch.empty((len(g), ny, nx), dtype=torch.int32, device=occ.device)
+        check(self.L.ngs_nav_fields(self.h, C.c_void_p(occ.data_ptr()), nx, ny, nz, int(k_lo),
+                                    int(k_hi), int(inflate), g.ctypes.data_as(C.c_void_p), len(g),
+                                    C.c_void_p(blocked.data_ptr()), C.c_void_p(dist.data_ptr()),
+                                    _stream_ptr(stream)), "ngs_nav_fields")
+        return blocked, dist
+
+    def nav_paths(self, dist, starts, max_len: int, stream=None):
+        """Paths (int32 [n, max_len, 2]) and lengths (int32 [n]) for starts
+        (i, j, goal index) descending the fields ``dist`` [n_goals, ny, nx]."""
+        torch = _torch()
+        n_goals, ny, nx = (int(v) for v in dist.shape)
+        s = torch.as_tensor(np.asarray(starts, dtype=np.int32).reshape(-1, 3), device=dist.device)
+        n = int(s.shape[0])
+        paths = torch.zeros((n, int(max_len), 2), dtype=torch.int32, device=dist.device)
+        lens = torch.zeros(n, dtype=torch.int32, device=dist.device)
+        check(self.L.ngs_nav_paths(self.h, C.c_void_p(dist.data_ptr()), nx, ny, n_goals,
+                                   C.c_void_p(s.data_ptr()), n, int(max_len),
+                                   C.c_void_p(paths.data_ptr()), C.c_void_p(lens.data_ptr()),
+                                   _stream_ptr(stream)), "ngs_nav_paths")
+        return paths, lens
+
     def select_cut(self, cams, cap: Optional[int] = None, stream=None):
         """Per-camera LOD cuts: (ids int32 CUDA tensor, offsets int64 CUDA tensor)."""
         torch = _torch()

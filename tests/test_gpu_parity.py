@@ -348,6 +348,41 @@ def test_slice_occupancy_matches_oracle(R, small_floor, dtype):
         R.slice_occupancy(SimpleNamespace(**{**vars(grid), "nx": 0}))
 
 
+def test_nav_fields_and_paths_match_oracle(R, small_floor):
+    """Blocked map, breadth-first distance fields and agent paths on the GPU's
+    slice occupancy of the small floor, bit for bit against the oracle on the
+    same occupancy (integer results: no tolerance)."""
+    from types import SimpleNamespace
+    R.load_scene(small_floor)
+    lo, hi = small_floor.aabb_min[0], small_floor.aabb_max[0]
+    grid = SimpleNamespace(x0=float(lo[0]), y0=float(lo[1]), cell=0.05,
+                           nx=int((hi[0] - lo[0]) / 0.05) + 1, ny=int((hi[1] - lo[1]) / 0.05) + 1,
+                           z0=0.05, dz=0.1, nz=13, threshold=0.5)
+    _, occ = R.slice_occupancy(grid)
+    occ_h = occ.cpu().numpy()
+    rng = np.random.default_rng(31)
+    b_ref = O.nav_blocked(occ_h, 1, 9, 2)
+    free = np.argwhere(b_ref == 0)
+    goals = [tuple(int(v) for v in free[k][::-1]) for k in rng.choice(len(free), 5, replace=False)]
+    goals.append((-1, 3))                                  # outside the grid: nothing reachable
+    blocked, dist = R.nav_fields(occ, goals, 1, 9, 2)
+    torch.cuda.synchronize()
+    assert np.array_equal(blocked.cpu().numpy(), b_ref)
+    dist_h = dist.cpu().numpy().view(np.uint32)
+    refs = [O.nav_field(b_ref, g) for g in goals]
+    for g in range(len(goals)):
+        assert np.array_equal(dist_h[g], refs[g]), g
+    assert np.all(dist_h[-1] == 0xFFFFFFFF) and (dist_h[0] < 0xFFFFFFFF).mean() > 0.3
+    starts = [(int(rng.integers(grid.nx)), int(rng.integers(grid.ny)), int(rng.integers(len(goals))))
+              for _ in range(200)]
+    paths, lens = R.nav_paths(dist, starts, 600)
+    paths, lens = paths.cpu().numpy(), lens.cpu().numpy()
+    for a, (i, j, g) in enumerate(starts):
+        ref = O.nav_path(refs[g], (i, j), 600)
+        assert lens[a] == len(ref) and np.array_equal(paths[a, :lens[a]], ref), a
+    assert (lens > 1).sum() > 50
+
+
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 def test_reduced_precision_attributes(R, small_floor, dtype):
     stored, deq = quantize_attributes(small_floor, dtype)
