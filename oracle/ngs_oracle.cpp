@@ -29,6 +29,10 @@
 //   mu_n + v (mu_p - mu_n), covariance, opacity and SH likewise. v is 0 where
 //   tau has just reached s(n) from below (n itself) and 1 where tau is about
 //   to reach s(p) (n has become its parent); a leaf finer than tau keeps v = 0.
+//   Frustum-culled and shared cuts (Sec. III-B: the selection of levels is
+//   made per view, dynamically): the cut can drop the nodes whose box lies
+//   outside one of the five planes of a camera's view volume, and one cut can
+//   serve a group of cameras (the deepest of the members' choices per path).
 // Every floating-point step is float64 except where a step's result decides an
 // integer that the renderer must reproduce exactly: the near-plane cull and the
 // depth sort key use the float32 view depth computed by one fixed sequence of
@@ -646,6 +650,118 @@ int32_t orc_nav_path(const uint32_t *dist, int32_t nx, int32_t ny, int32_t si, i
         --d;
     }
     return std::min(len, max_len);
+}
+
+// ---------------------------------------------------------------------------
+// 8. Frustum-culled and shared cuts (Sec. III-B: Gaussians are taken from the
+//    tree's levels per view, dynamically)
+// ---------------------------------------------------------------------------
+//
+// View volume of a camera with a guard band of g pixels:
+//     {x : t_z >= 0.2, -g <= u <= W + g, -g <= v <= H + g},
+// t = R (x - pos), u = fx t_x / t_z + cx, v = fy t_y / t_z + cy. Where t_z > 0
+// it is the intersection of five half-spaces m_k . t + b_k >= 0:
+//     near   m = (0, 0, 1), b = -0.2
+//     left   m = (fx, 0, cx + g)          right  m = (-fx, 0, W + g - cx)
+//     top    m = (0, fy, cy + g)          bottom m = (0, -fy, H + g - cy)
+// (u >= -g  <=>  fx t_x + (cx + g) t_z >= 0, and so on). In world terms
+// P_k(x) = a_k . (x - pos) + b_k with a_k = R^T m_k. A node is culled when its
+// box lies wholly outside one half-space: max over the box of P_k < 0, the
+// maximum of a linear function over a box being the sum over the axes of the
+// larger of its values at the two faces. Boxes nest, so a culled node's
+// subtree is culled.
+//
+// Shared cut of a group G of cameras (cull on or off): n is fine enough for G
+// when every member c culls n (cull on) or has s_c(n) <= tau_c; n is selected
+// iff (leaf or fine(n)) and (root or not fine(parent)) and, with the cull on,
+// some member keeps n. "fine" only grows towards the leaves (boxes nest, so
+// s_c shrinks and culls spread downwards), so the selection is an antichain;
+// on each root-to-leaf path it is the deepest of the members' own choices.
+
+static void frustum_planes(const orc_camera *cam, double guard, double a[5][3], double b[5]) {
+    const double W = cam->width, H = cam->height;
+    const double m[5][3] = {{0.0, 0.0, 1.0},
+                            {cam->fx, 0.0, cam->cx + guard},
+                            {-cam->fx, 0.0, W + guard - cam->cx},
+                            {0.0, cam->fy, cam->cy + guard},
+                            {0.0, -cam->fy, H + guard - cam->cy}};
+    for (int k = 0; k < 5; ++k) {
+        for (int i = 0; i < 3; ++i)
+            a[k][i] = m[k][0] * cam->R[i] + m[k][1] * cam->R[3 + i] + m[k][2] * cam->R[6 + i];
+        b[k] = k == 0 ? -kNear : 0.0;
+    }
+}
+
+// Bit 0: culled; bit 1: a plane's value lies within 1e-5 of its scale
+// (sum_i |a_ki| max(|lo_i - p_i|, |hi_i - p_i|) + |b_k|) and no plane culls the
+// box by more than that, so the float32 renderer may decide either way.
+static int frustum_state(const orc_scene *sc, const orc_camera *cam, const double a[5][3],
+                         const double b[5], int64_t n) {
+    bool culled = false, sure_cull = false, unsure = false;
+    for (int k = 0; k < 5; ++k) {
+        double mx = b[k], scale = std::fabs(b[k]);
+        for (int i = 0; i < 3; ++i) {
+            const double dl = (double)sc->aabb_min[3 * n + i] - cam->pos[i];
+            const double dh = (double)sc->aabb_max[3 * n + i] - cam->pos[i];
+            mx += std::max(a[k][i] * dl, a[k][i] * dh);
+            scale += std::fabs(a[k][i]) * std::max(std::fabs(dl), std::fabs(dh));
+        }
+        if (mx < 0.0) culled = true;
+        if (mx < -1e-5 * scale) sure_cull = true;
+        if (std::fabs(mx) <= 1e-5 * scale) unsure = true;
+    }
+    return (culled ? 1 : 0) | (unsure && !sure_cull ? 2 : 0);
+}
+
+void orc_frustum_state(const orc_scene *sc, const orc_camera *cam, double guard, uint8_t *out) {
+    double a[5][3], b[5];
+    frustum_planes(cam, guard, a, b);
+    for (int64_t n = 0; n < sc->n; ++n) out[n] = (uint8_t)frustum_state(sc, cam, a, b, n);
+}
+
+// Group g is cams[group_begin[g] .. group_begin[g + 1]). Writes the groups'
+// cuts (ascending ids, group after group) to ids_out and their offsets to
+// offsets_out[0 .. n_groups]; returns the total. near_out (optional,
+// [n_groups][n]): 1 where, for some member, s(n) or s(parent) lies within
+// 1e-5 relative of tau, or the cull of n or of its parent is unsure.
+int64_t orc_select_cut_shared(const orc_scene *sc, const orc_camera *cams,
+                              const int32_t *group_begin, int32_t n_groups, int32_t frustum,
+                              double guard, int32_t *ids_out, int64_t *offsets_out,
+                              uint8_t *near_out) {
+    const int64_t n = sc->n;
+    std::vector<uint8_t> fine(n), seen(n), unsure(n);
+    int64_t cnt = 0;
+    for (int32_t g = 0; g < n_groups; ++g) {
+        offsets_out[g] = cnt;
+        std::fill(fine.begin(), fine.end(), 1);
+        std::fill(seen.begin(), seen.end(), frustum ? 0 : 1);
+        std::fill(unsure.begin(), unsure.end(), 0);
+        for (int32_t c = group_begin[g]; c < group_begin[g + 1]; ++c) {
+            const orc_camera *cam = &cams[c];
+            double a[5][3], b[5];
+            frustum_planes(cam, guard, a, b);
+            for (int64_t i = 0; i < n; ++i) {
+                const double s = granularity(sc, cam, i);
+                bool culled = false;
+                if (frustum) {
+                    const int st = frustum_state(sc, cam, a, b, i);
+                    culled = st & 1;
+                    if (st & 2) unsure[i] = 1;
+                }
+                if (!culled) seen[i] = 1;
+                if (!culled && !(s <= cam->tau)) fine[i] = 0;
+                if (std::fabs(s - cam->tau) <= 1e-5 * cam->tau) unsure[i] = 1;
+            }
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            const bool leaf = sc->child_count[i] == 0;
+            const int32_t par = sc->parent[i];
+            if ((leaf || fine[i]) && (par < 0 || !fine[par]) && seen[i]) ids_out[cnt++] = (int32_t)i;
+            if (near_out) near_out[(int64_t)g * n + i] = (unsure[i] || (par >= 0 && unsure[par])) ? 1 : 0;
+        }
+    }
+    offsets_out[n_groups] = cnt;
+    return cnt;
 }
 
 int32_t orc_num_threads(void) {

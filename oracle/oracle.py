@@ -9,7 +9,9 @@ tiles). ``render`` chains them for one camera. With ``blend``, preprocess
 renders each cut node with its level-of-detail blended attributes
 (``blend_gaussian``: moved toward its parent's by the parent weight
 ``blend_parent_weight`` of the granularities, Sec. III-B's interpolated
-transitions).
+transitions). ``frustum_state`` and ``select_cut_shared`` give the cut's
+variants: nodes culled against the five planes of a camera's view volume, and
+one cut for a group of cameras (Sec. III-B's per-view, dynamic selection).
 """
 from __future__ import annotations
 
@@ -92,6 +94,12 @@ def lib():
             L.orc_slice_occupancy.argtypes = [C.POINTER(_Scene), C.c_double, C.c_double,
                                               C.c_double, i32, i32, C.c_double, C.c_double, i32,
                                               C.c_double, vp, vp]
+            L.orc_frustum_state.restype = None
+            L.orc_frustum_state.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), C.c_double,
+                                            vp]
+            L.orc_select_cut_shared.restype = i64
+            L.orc_select_cut_shared.argtypes = [C.POINTER(_Scene), vp, vp, i32, i32, C.c_double,
+                                                vp, vp, vp]
             _lib = L
     return _lib
 
@@ -153,6 +161,34 @@ def select_cut(scene, cam, with_s: bool = False):
                              _p(s) if with_s else None)
     out = (ids[:k].copy(), near)
     return out + (s,) if with_s else out
+
+
+def frustum_state(scene, cam, guard: float = 0.0):
+    """Frustum cull of every node's box for a view volume widened by ``guard``
+    pixels: (culled bool[M], unsure bool[M]); unsure marks a plane value
+    within 1e-5 of its scale that no other plane overrides."""
+    sa = _as_scene(scene)
+    out = np.empty(sa.n, dtype=np.uint8)
+    lib().orc_frustum_state(C.byref(sa.c), C.byref(camera_struct(cam)), float(guard), _p(out))
+    return (out & 1).astype(bool), (out & 2).astype(bool)
+
+
+def select_cut_shared(scene, cams, group_begin, frustum: bool = True, guard: float = 0.0):
+    """One cut per group of cameras, group g = cams[group_begin[g]:group_begin[g+1]],
+    optionally frustum-culled: (ids int32 concatenated group after group,
+    offsets int64[n_groups + 1], near uint8[n_groups, M])."""
+    sa = _as_scene(scene)
+    gb = np.ascontiguousarray(group_begin, dtype=np.int32)
+    ng = len(gb) - 1
+    assert ng >= 1 and gb[0] == 0 and gb[-1] == len(cams) and np.all(np.diff(gb) >= 1)
+    carr = (_Camera * len(cams))(*[camera_struct(c) for c in cams])
+    ids = np.empty(max(ng * sa.n, 1), dtype=np.int32)
+    off = np.empty(ng + 1, dtype=np.int64)
+    near = np.empty((ng, sa.n), dtype=np.uint8)
+    k = lib().orc_select_cut_shared(C.byref(sa.c), C.cast(carr, C.c_void_p), _p(gb), ng,
+                                    1 if frustum else 0, float(guard), _p(ids), _p(off),
+                                    _p(near))
+    return ids[:k].copy(), off, near
 
 
 def preprocess(scene, cam, ids, tile=(16, 16), blend=False):
@@ -353,4 +389,4 @@ __all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bi
            "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "depth_f32",
            "tiles_xy", "num_threads", "lib", "granularity_f32", "blend_parent_weight",
            "blend_gaussian", "slice_params", "slice_value", "slice_occupancy", "nav_blocked",
-           "nav_field", "nav_path"]
+           "nav_field", "nav_path", "frustum_state", "select_cut_shared"]

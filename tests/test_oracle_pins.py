@@ -258,6 +258,232 @@ def test_cut_coarsens_with_tau(box10k):
 
 
 # ---------------------------------------------------------------------------
+# frustum-culled and shared cuts
+# ---------------------------------------------------------------------------
+
+def _boxes(lo, hi):
+    n = len(lo)
+    return _Tree(n, lo, hi, [-1] * n, [0] * n)
+
+
+def _camera_at_origin(R, guard_note=None):
+    return Camera(pos=np.zeros(3, np.float32), R_wc=np.asarray(R, np.float32), fx=100.0,
+                  fy=100.0, cx=50.0, cy=50.0, width=100, height=100, tau=0.0)
+
+
+def test_frustum_hand_worked_boxes():
+    """R = I, fx = fy = 100, cx = cy = 50, 100x100: the view volume is z >= 0.2,
+    -z/2 <= x <= z/2, -z/2 <= y <= z/2 (worked by hand per box below); the same
+    boxes rotated into the frame of a camera looking along +x give the same
+    answers (camera x = -world y, camera y = -world z, camera z = world x)."""
+    boxes = [  # lo, hi, culled at guard 0, culled at guard 400
+        ((-1, -1, 4), (1, 1, 6), False, False),       # straight ahead
+        ((-1, -1, -6), (1, 1, -4), True, True),       # behind the camera
+        ((-10, -1, 4), (-5, 1, 6), True, False),      # left: 100(-5) + 50(6) < 0; corner u = -33.3
+        ((-10, -1, 4), (-2, 1, 6), False, False),     # reaches in: corner (-2, ., 6) has u = 16.7
+        ((5, -1, 4), (10, 1, 6), True, False),        # right: -100(5) + 50(6) < 0
+        ((-1, 5, 4), (1, 10, 6), True, False),        # below the image: -100(5) + 50(6) < 0
+        ((-1, -10, 4), (1, -5, 6), True, False),      # above the image
+        ((-1, -1, -1), (1, 1, 0.1), True, True),      # in front of the camera but before z = 0.2
+        ((-1, -1, -1), (1, 1, 0.3), False, False),    # crosses z = 0.2
+    ]
+    lo = np.array([b[0] for b in boxes], np.float32)
+    hi = np.array([b[1] for b in boxes], np.float32)
+    want0 = [b[2] for b in boxes]
+    want400 = [b[3] for b in boxes]
+    cam = _camera_at_origin(np.eye(3))
+    c0, u0 = O.frustum_state(_boxes(lo, hi), cam, 0.0)
+    c4, u4 = O.frustum_state(_boxes(lo, hi), cam, 400.0)
+    assert c0.tolist() == want0 and c4.tolist() == want400
+    assert not u0.any() and not u4.any()
+    # camera looking along +x (yaw 0, level): t = (-y, -z, x); box (lo, hi) in
+    # the camera frame becomes the world box below
+    wlo = np.stack([lo[:, 2], -hi[:, 0], -hi[:, 1]], 1)
+    whi = np.stack([hi[:, 2], -lo[:, 0], -lo[:, 1]], 1)
+    camx = _camera_at_origin(yaw_rotation(0.0))
+    cx, _ = O.frustum_state(_boxes(wlo, whi), camx, 0.0)
+    assert cx.tolist() == want0
+    # a box whose left-plane maximum is exactly 0 (100(-3) + 50(6)) is kept, and unsure
+    c, u = O.frustum_state(_boxes([(-10, -1, 4)], [(-3, 1, 6)]), cam, 0.0)
+    assert c.tolist() == [False] and u.tolist() == [True]
+
+
+@pytest.mark.parametrize("guard", [0.0, 10.0])
+def test_frustum_is_exact_for_an_axis_aligned_camera(guard):
+    """With R = I the view volume's cross-section at depth z is the rectangle
+    [(-g - cx) z / fx, (W + g - cx) z / fx] x [(-g - cy) z / fy, (H + g - cy) z / fy],
+    which only grows with z: a box meets the volume iff the point of its far
+    face (z = hi.z >= 0.2) closest to that rectangle's centre projects inside.
+    The cull must be exactly that (off-centre principal point, W != H, fx != fy)."""
+    rng = np.random.default_rng(11)
+    cam = Camera(pos=np.zeros(3, np.float32), R_wc=np.eye(3, dtype=np.float32), fx=120.0,
+                 fy=90.0, cx=70.0, cy=40.0, width=160, height=100, tau=0.0)
+    c = rng.uniform([-8, -8, -2], [8, 8, 10], (4000, 3))
+    h = rng.uniform(0.05, 2.0, (4000, 3))
+    lo, hi = (c - h).astype(np.float32), (c + h).astype(np.float32)
+    culled, unsure = O.frustum_state(_boxes(lo, hi), cam, guard)
+    z = hi[:, 2].astype(np.float64)
+    zz = np.maximum(z, 0.2)
+    xc = ((-guard - cam.cx) + (cam.width + guard - cam.cx)) / 2 * zz / cam.fx
+    yc = ((-guard - cam.cy) + (cam.height + guard - cam.cy)) / 2 * zz / cam.fy
+    w = np.stack([np.clip(xc, lo[:, 0], hi[:, 0]), np.clip(yc, lo[:, 1], hi[:, 1]), z], 1)
+    meets = _inside_view(cam, w, guard + 1e-9)
+    assert np.array_equal(culled[~unsure], ~meets[~unsure])
+    assert 0.2 < culled.mean() < 0.8 and unsure.sum() <= 2
+
+
+def _inside_view(cam, pts, guard):
+    t = (pts - cam.pos.astype(np.float64)) @ cam.R_wc.astype(np.float64).T
+    ok = t[..., 2] >= 0.2
+    z = np.where(ok, t[..., 2], 1.0)
+    u = cam.fx * t[..., 0] / z + cam.cx
+    v = cam.fy * t[..., 1] / z + cam.cy
+    return ok & (u >= -guard) & (u <= cam.width + guard) & (v >= -guard) & (v <= cam.height + guard)
+
+
+@pytest.mark.parametrize("guard", [0.0, 24.0])
+def test_frustum_cull_agrees_with_projection(box10k, guard):
+    """No sampled point (8 corners + 24 random points) of a culled box projects
+    inside the view; a box with such a point is never culled. Culls nest down
+    the tree."""
+    s = box10k
+    rng = np.random.default_rng(3)
+    cams = [camera_c0(0.0), look_camera((-3.0, 2.0, 1.5), 0.3, 64, 48, fx=60.0),
+            look_camera((2.0, 2.0, 1.5), 2.0, 80, 60, fx=50.0, pitch=-0.4),
+            look_camera((6.0, -1.0, 4.0), 2.5, 96, 96, fx=90.0, pitch=-0.6)]
+    lo = s.aabb_min.astype(np.float64)
+    hi = s.aabb_max.astype(np.float64)
+    corners = np.stack([np.stack([(hi if (k >> a) & 1 else lo)[:, a] for a in range(3)], 1)
+                        for k in range(8)], 1)
+    rand = lo[:, None] + rng.random((len(lo), 24, 3)) * (hi - lo)[:, None]
+    pts = np.concatenate([corners, rand], 1)
+    n_culled = []
+    for cam in cams:
+        culled, unsure = O.frustum_state(s, cam, guard)
+        inside = _inside_view(cam, pts, guard).any(1)
+        assert not np.any(culled & inside & ~unsure)
+        assert unsure.sum() < 0.001 * len(culled)
+        kids = np.arange(1, s.n_nodes)
+        assert np.all(culled[kids] | ~culled[s.parent[kids]])
+        n_culled.append(int(culled.sum()))
+    assert min(n_culled) < s.n_nodes // 2 and max(n_culled) > s.n_nodes // 2, n_culled
+
+
+def _leaf_paths(s):
+    """[leaves, depth] node ids root first, padded with -1 after the leaf."""
+    leaves = np.flatnonzero(s.child_count == 0)
+    chains = [leaves.astype(np.int64)]
+    while np.any(chains[-1] >= 0):
+        prev = chains[-1]
+        chains.append(np.where(prev >= 0, s.parent[np.maximum(prev, 0)], -1))
+    chains = np.stack(chains[:-1], 1)[:, ::-1]          # root first, -1 padding in front
+    out = np.full_like(chains, -1)
+    for i, row in enumerate(chains):
+        r = row[row >= 0]
+        out[i, :len(r)] = r
+    return out
+
+
+def _group_cams():
+    return [look_camera((0.5, 0.6, 1.2), 0.2, 64, 48, fx=60.0, tau=6.0),
+            look_camera((1.2, 0.9, 1.2), 1.4, 64, 48, fx=60.0, tau=3.0),
+            look_camera((2.5, 2.8, 1.4), -2.0, 96, 64, fx=80.0, tau=9.0),
+            look_camera((3.2, 1.0, 0.9), 3.0, 48, 48, fx=40.0, tau=4.5)]
+
+
+def test_shared_cut_of_one_camera_is_its_cut(box10k):
+    for tau in [0.0, 5.0, 20.0]:
+        cam = look_camera((-1.0, 1.0, 1.5), 0.4, 64, 48, fx=60.0, tau=tau)
+        ids, _ = O.select_cut(box10k, cam)
+        a, off, _ = O.select_cut_shared(box10k, [cam], [0, 1], frustum=False)
+        assert np.array_equal(a, ids) and off.tolist() == [0, len(ids)]
+        culled, _ = O.frustum_state(box10k, cam)
+        b, _, _ = O.select_cut_shared(box10k, [cam], [0, 1], frustum=True)
+        assert np.array_equal(b, ids[~culled[ids]])
+
+
+@pytest.mark.parametrize("frustum", [False, True])
+def test_shared_cut_is_the_deepest_member_choice_per_path(box10k, frustum):
+    """Brute force over root-to-leaf paths: with c's own cut at depth n_c on a
+    path and its first culled node at depth i_c (none: past the leaf), the
+    group's cut holds the path's node at depth max_c min(i_c, n_c) when some
+    member keeps that node, and nothing else on the path."""
+    s = box10k
+    cams = _group_cams()
+    paths = _leaf_paths(s)
+    depth = (paths >= 0).sum(1)
+    gb = [0, 1, len(cams)]       # a single camera, then three together
+    ids, off, near = O.select_cut_shared(s, cams, gb, frustum=frustum)
+    for g in range(len(gb) - 1):
+        members = cams[gb[g]:gb[g + 1]]
+        sel = np.zeros(s.n_nodes, bool)
+        sel[ids[off[g]:off[g + 1]]] = True
+        D = np.zeros(len(paths), np.int64)
+        kept_any = np.zeros(s.n_nodes, bool)
+        for cam in members:
+            own = np.zeros(s.n_nodes, bool)
+            own[O.select_cut(s, cam)[0]] = True
+            culled = O.frustum_state(s, cam)[0] if frustum else np.zeros(s.n_nodes, bool)
+            kept_any |= ~culled
+            on = np.where(paths >= 0, own[np.maximum(paths, 0)], False)
+            assert np.all(on.sum(1) == 1)
+            n_c = on.argmax(1)
+            cu = np.where(paths >= 0, culled[np.maximum(paths, 0)], False)
+            i_c = np.where(cu.any(1), cu.argmax(1), depth)
+            D = np.maximum(D, np.minimum(i_c, n_c))
+        rows = np.arange(len(paths))
+        at = paths[rows, D]
+        want = np.zeros_like(paths, dtype=bool)
+        want[rows, D] = kept_any[at]
+        got = np.where(paths >= 0, sel[np.maximum(paths, 0)], False)
+        clean = ~np.where(paths >= 0, near[g][np.maximum(paths, 0)], False).any(1)
+        assert clean.mean() > 0.97
+        assert np.array_equal(got[clean], want[clean])
+        if frustum:
+            assert np.all(kept_any[ids[off[g]:off[g + 1]]])
+
+
+def test_shared_cut_covers_what_members_see(box10k):
+    """Antichain, and every leaf some member keeps has exactly one selected
+    ancestor-or-self; a finer member's tau makes the shared cut at least as
+    fine as its own."""
+    s = box10k
+    cams = _group_cams()
+    ids, off, _ = O.select_cut_shared(s, cams, [0, len(cams)], frustum=True)
+    sel = np.zeros(s.n_nodes, bool)
+    sel[ids] = True
+    kept = np.zeros(s.n_nodes, bool)
+    for cam in cams:
+        kept |= ~O.frustum_state(s, cam)[0]
+    leaves = np.flatnonzero((s.child_count == 0) & kept)
+    count = sel[leaves].astype(np.int64)
+    anc = s.parent[leaves].astype(np.int64)
+    while np.any(anc >= 0):
+        a = anc >= 0
+        count[a] += sel[anc[a]]
+        anc[a] = s.parent[anc[a]]
+    assert len(leaves) > 0 and np.all(count == 1)
+    anc = s.parent[ids].astype(np.int64)
+    while np.any(anc >= 0):
+        a = anc >= 0
+        assert not np.any(sel[anc[a]])
+        anc[a] = s.parent[anc[a]]
+    # unculled, all four cameras' cuts are coarser than or equal to the shared one
+    full, _, _ = O.select_cut_shared(s, cams, [0, len(cams)], frustum=False)
+    fsel = np.zeros(s.n_nodes, bool)
+    fsel[full] = True
+    for cam in cams:
+        own, _ = O.select_cut(s, cam)
+        for n in own[:: max(1, len(own) // 500)]:
+            # n or one of its ancestors is selected, or n has selected descendants
+            a, hit = int(n), False
+            while a >= 0 and not hit:
+                hit = fsel[a]
+                a = int(s.parent[a])
+            assert not hit or fsel[n], "the shared cut must not be coarser than a member's"
+
+
+# ---------------------------------------------------------------------------
 # projection
 # ---------------------------------------------------------------------------
 
