@@ -49,6 +49,8 @@ def parse():
                     help="skip the level-of-detail blending leg")
     ap.add_argument("--no-slice", action="store_true",
                     help="skip the GS-slice occupancy leg")
+    ap.add_argument("--no-cut-variants", action="store_true",
+                    help="skip the frustum-culled / shared cut leg")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="seconds of simulated agent load for the serving leg (0: skip)")
     ap.add_argument("--serving-scene", default="floor8m")
@@ -481,6 +483,8 @@ def run_ours(args, world, rank, local, pg):
             blend["max_abs_err_vs_oracle"] = max(errs)
         out["lod_blend"] = blend
         R.set_lod_blend(False)
+    if not args.no_cut_variants:
+        out["cut_variants"] = run_cut_variants(args, R, scene, cams, rank, stream)
     if not args.no_slice:
         out["gs_slice"] = run_slice(args, R, scene, stored, deq, rank, stream)
     R.close()
@@ -488,6 +492,75 @@ def run_ours(args, world, rank, local, pg):
         out["serving"] = run_serving(args, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# level-of-detail cut variants on the batch's cameras
+# ---------------------------------------------------------------------------
+
+def run_cut_variants(args, R, scene, cams, rank, stream):
+    """The batch's cameras are walker-major (consecutive cameras are nearby
+    poses of one walk). Times one cut per camera, the same with the frustum
+    cull, and one frustum-culled cut per group of 8 consecutive cameras;
+    reports the cut sizes and, for the first group, agreement with the
+    oracle away from float32-reachable decisions."""
+    import torch
+    import oracle as O
+    n = len(cams)
+    M = int(scene.n_nodes)
+    # a cut is an antichain of the tree: at most one leaf count per camera
+    cap = min(n * int(scene.n_leaves), (1 << 31) - 1)
+    hbm, kind = measured_peaks()
+    groups8 = list(range(0, n, 8)) + [n]
+    variants = [
+        ("per_camera", n, lambda: R.select_cut(cams, cap=cap, stream=stream)),
+        ("per_camera_frustum", n, lambda: R.select_cut_shared(
+            cams, list(range(n + 1)), frustum=True, cap=cap, stream=stream)),
+        ("shared_8_frustum", len(groups8) - 1, lambda: R.select_cut_shared(
+            cams, groups8, frustum=True, cap=cap, stream=stream)),
+    ]
+    out = {"cameras": n, "nodes": M}
+    res = {}
+    for name, units, fn in variants:
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ids, off = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = min(ms)
+        total = int(off[-1].item())
+        # algorithmic bytes: each unit reads every node's two box words once
+        # (the parent's are cache hits) and writes its selected ids
+        nbytes = units * M * 32 + 4 * total
+        if name == "shared_8_frustum":
+            res[name] = (ids, off)
+        del ids
+        out[name] = {"ms": round(t, 3), "units": units, "cut_nodes_total": total,
+                     "node_camera_tests_per_s": round(M * n / (t * 1e-3) / 1e9, 2),
+                     "unit_tests": "G/s", "algorithmic_GBps": round(nbytes / (t * 1e-3) / 1e9, 1),
+                     "frac_of_hbm": round(nbytes / (t * 1e-3) / 1e9 / hbm, 3),
+                     "hbm_peak": f"{hbm:.0f} GB/s ({kind})"}
+    out["frustum_cut_fraction"] = round(
+        out["per_camera_frustum"]["cut_nodes_total"] / max(out["per_camera"]["cut_nodes_total"], 1), 4)
+    if rank == 0 and not args.no_cpu:
+        gb = groups8[:2]
+        sa = O.SceneArrays(scene)
+        t0 = time.time()
+        want, woff, near = O.select_cut_shared(sa, cams[:gb[1]], gb, frustum=True)
+        ids, off = res["shared_8_frustum"]
+        got = ids[: int(off[1].item())].cpu().numpy()
+        a, b_ = np.zeros(M, bool), np.zeros(M, bool)
+        a[got] = True
+        b_[want[woff[0]:woff[1]]] = True
+        out["oracle_group0_s"] = round(time.time() - t0, 2)
+        out["group0_mismatch_away_from_threshold"] = int(((a != b_) & (near[0] == 0)).sum())
+        out["group0_near_frac"] = float(near[0].mean())
+    return out
 
 
 # ---------------------------------------------------------------------------

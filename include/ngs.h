@@ -184,6 +184,34 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *ctx, const ngs_gaussians *g, const ng
 NGS_API ngs_status ngs_select_cut(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                                   int32_t *d_ids, int64_t *d_offsets, int64_t cap, void *stream);
 
+/* Frustum-culled and shared cuts (Sec. III-B: the levels are selected per
+ * view, dynamically).
+ *  - Frustum cull (flags & NGS_CUT_FRUSTUM): the view volume of a camera with
+ *    a guard band of g = guard_px pixels, {x : t_z >= 0.2, -g <= u <= W + g,
+ *    -g <= v <= H + g} (t = R_wc (x - pos), u = fx t_x / t_z + cx,
+ *    v = fy t_y / t_z + cy), is the intersection of five half-spaces (near,
+ *    left, right, top, bottom); a node whose box lies wholly outside one of
+ *    them is culled, and with it its subtree.
+ *  - Shared cuts: the cameras form n_groups consecutive groups, group g being
+ *    cams[group_begin[g] .. group_begin[g + 1]) (host int32 [n_groups + 1],
+ *    group_begin[0] = 0, strictly ascending, group_begin[n_groups] = n_cams).
+ *    Node n is fine enough for a group when every member culls it (cull on)
+ *    or has s(n) <= tau; n is selected iff (leaf or fine(n)) and (root or not
+ *    fine(parent)) and, with the cull on, some member keeps it. On every
+ *    root-to-leaf path this is the deepest of the members' own choices, so
+ *    each member gets at least the detail it asks for wherever it sees.
+ * A group of one camera without the cull gives ngs_select_cut's cut. Output
+ * as ngs_select_cut, per group: ascending ids in d_ids[d_offsets[g] ..
+ * d_offsets[g + 1]) (device int32 [cap], device int64 [n_groups + 1]).
+ * NGS_ERR_INVALID_ARG for a bad group table, unknown flags, a negative or
+ * non-finite guard, or a bad camera; NGS_ERR_CAPACITY if the cuts exceed cap
+ * (the offsets still hold their sizes). Synchronises the stream. */
+#define NGS_CUT_FRUSTUM 1
+NGS_API ngs_status ngs_select_cut_shared(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
+                                         const int32_t *group_begin, int32_t n_groups,
+                                         uint32_t flags, float guard_px, int32_t *d_ids,
+                                         int64_t *d_offsets, int64_t cap, void *stream);
+
 /* Renders n_cams views (host camera array) into d_images[c] (host array of
  * device pointers), each float32 planar [3][height][width], background 0.
  * Per pixel p and the Gaussians g of its tile in (depth, node id) order:

@@ -33,7 +33,8 @@ EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_l
            "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune", "ngs_server_start",
            "ngs_server_submit", "ngs_server_poll", "ngs_server_wait_all", "ngs_server_stats",
            "ngs_server_stop", "ngs_selftest_wait_timeout", "ngs_slice_occupancy",
-           "ngs_nav_fields", "ngs_nav_paths"]
+           "ngs_nav_fields", "ngs_nav_paths", "ngs_select_cut_shared"]
+CUT_FRUSTUM = 1
 
 
 class NgsError(RuntimeError):
@@ -128,6 +129,9 @@ def load(build_if_missing: bool = True):
     L.ngs_load_scene.argtypes = [vp, C.POINTER(Gaussians), C.POINTER(Hierarchy)]
     L.ngs_select_cut.restype = i32
     L.ngs_select_cut.argtypes = [vp, C.POINTER(Camera), i32, vp, vp, i64, vp]
+    L.ngs_select_cut_shared.restype = i32
+    L.ngs_select_cut_shared.argtypes = [vp, C.POINTER(Camera), i32, vp, i32, C.c_uint32,
+                                        C.c_float, vp, vp, i64, vp]
     L.ngs_render.restype = i32
     L.ngs_render.argtypes = [vp, C.POINTER(Camera), i32, C.POINTER(vp), vp]
     L.ngs_render_host.restype = i32

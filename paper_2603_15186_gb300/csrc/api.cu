@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ngs_internal.cuh"
+#include "cut.h"
 #include "nav.h"
 
 using namespace ngs;
@@ -81,6 +82,8 @@ struct ngs_ctx {
     uint32_t *stats_dev = nullptr;     // per sub-batch: cut, visible, pairs, pad
     int stats_cap = 0;
     uint32_t *cut_off32 = nullptr;     // scratch for ngs_select_cut offsets
+    CutCam *cut_cams = nullptr;        // ngs_select_cut_shared: cameras and groups
+    int32_t *cut_groups = nullptr;
 
     // occupancy-derived persistent grids
     int grid_cut = 0, grid_pre = 0, grid_sort32 = 0, grid_sort64 = 0, grid_scan = 0,
@@ -174,9 +177,13 @@ void free_work(ngs_ctx *c) {
     }
     dfree(c->stats_dev);
     dfree(c->cut_off32);
+    dfree(c->cut_cams);
+    dfree(c->cut_groups);
     c->w = Work();
     c->stats_dev = nullptr;
     c->cut_off32 = nullptr;
+    c->cut_cams = nullptr;
+    c->cut_groups = nullptr;
     c->work_ready = false;
 }
 
@@ -278,6 +285,8 @@ ngs_status ensure_work(ngs_ctx *c) {
     c->stats_cap = 4096;
     A(dalloc(&c->stats_dev, (size_t)c->stats_cap * 4));
     A(dalloc(&c->cut_off32, kMaxCamsPerBatch + 1));
+    A(dalloc(&c->cut_cams, kMaxCamsPerBatch));
+    A(dalloc(&c->cut_groups, kMaxCamsPerBatch + 1));
     A(dalloc(&w.work64, 2));
     if (st != NGS_OK) {
         free_work(c);
@@ -346,6 +355,27 @@ void fill_cam(DevCamera &d, const ngs_camera &k, int tw, int th, float *image) {
     d.tiles_x = (k.width + tw - 1) / tw;
     d.tiles_y = (k.height + th - 1) / th;
     d.image = image;
+}
+
+// The five planes of the camera's view volume widened by `guard` pixels, in
+// world terms: a_k = R^T m_k for the camera-frame normals m_k of the near,
+// left, right, top and bottom half-spaces m_k . t + b_k >= 0.
+void fill_cut_cam(CutCam &d, const ngs_camera &k, float guard) {
+    std::memset(&d, 0, sizeof(d));
+    const double g = guard, W = k.width, H = k.height;
+    const double m[5][3] = {{0.0, 0.0, 1.0},
+                            {k.fx, 0.0, k.cx + g},
+                            {-k.fx, 0.0, W + g - k.cx},
+                            {0.0, k.fy, k.cy + g},
+                            {0.0, -k.fy, H + g - k.cy}};
+    for (int j = 0; j < 5; ++j)
+        for (int i = 0; i < 3; ++i)
+            d.a[j][i] = (float)(m[j][0] * k.R_wc[i] + m[j][1] * k.R_wc[3 + i] +
+                                m[j][2] * k.R_wc[6 + i]);
+    d.b0 = -kNearZ;
+    for (int i = 0; i < 3; ++i) d.pos[i] = k.pos[i];
+    d.fx = k.fx;
+    d.tau = k.tau;
 }
 
 int bits_for(uint32_t n) {
@@ -1041,6 +1071,46 @@ NGS_API ngs_status ngs_select_cut(ngs_ctx *c, const ngs_camera *cams, int32_t n_
                c->cut_off32, w.counters, w.counters + TK_CUT, w.status, w.epoch, 0, w.err,
                c->grid_cut, st);
     k_offsets_to_i64<<<(n_cams + 256) / 256, 256, 0, st>>>(c->cut_off32, d_offsets, n_cams);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return check_err(c);
+}
+
+NGS_API ngs_status ngs_select_cut_shared(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
+                                         const int32_t *group_begin, int32_t n_groups,
+                                         uint32_t flags, float guard_px, int32_t *d_ids,
+                                         int64_t *d_offsets, int64_t cap, void *stream) {
+    if (!c) return NGS_ERR_INVALID_ARG;
+    if (!c->loaded) return NGS_ERR_NOT_LOADED;
+    if (!cams || !group_begin || !d_ids || !d_offsets || n_cams <= 0 ||
+        n_cams > kMaxCamsPerBatch || n_groups <= 0 || n_groups > n_cams || cap < 0)
+        return NGS_ERR_INVALID_ARG;
+    if ((flags & ~(uint32_t)NGS_CUT_FRUSTUM) != 0 || !std::isfinite(guard_px) || guard_px < 0.0f)
+        return NGS_ERR_INVALID_ARG;
+    if (group_begin[0] != 0 || group_begin[n_groups] != n_cams) return NGS_ERR_INVALID_ARG;
+    for (int32_t g = 0; g < n_groups; ++g)
+        if (group_begin[g + 1] <= group_begin[g]) return NGS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_cams; ++i)
+        if (!camera_ok(cams[i])) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    ngs_status s = ensure_work(c);
+    if (s != NGS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<CutCam> hc(n_cams);
+    for (int i = 0; i < n_cams; ++i) fill_cut_cam(hc[i], cams[i], guard_px);
+    Work &w = c->w;
+    if ((s = epoch_guard(c, st, kEpochStride)) != NGS_OK) return s;
+    CK(cudaMemcpyAsync(c->cut_cams, hc.data(), sizeof(CutCam) * n_cams, cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaMemcpyAsync(c->cut_groups, group_begin, sizeof(int32_t) * (n_groups + 1),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
+    k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
+    launch_cut_shared((flags & NGS_CUT_FRUSTUM) != 0, c->scene.box_lo, c->scene.box_hi,
+                      c->scene.n, c->cut_cams, c->cut_groups, n_groups, (uint32_t *)d_ids,
+                      std::min<int64_t>(cap, (1ll << 32) - 1), c->cut_off32, w.counters,
+                      w.counters + TK_CUT, w.status, w.epoch, 0, w.err, c->grid_cut, st);
+    k_offsets_to_i64<<<(n_groups + 256) / 256, 256, 0, st>>>(c->cut_off32, d_offsets, n_groups);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return check_err(c);

@@ -9,14 +9,24 @@
 // so s never decreases towards the root and every root-to-leaf path holds
 // exactly one selected node.
 //
-// One pass, order preserving: partitions are (camera, block of 2048 nodes) in
-// camera-major order, taken from an atomic ticket so every predecessor of a
-// partition is already running; each partition counts its selected nodes,
-// finds its output offset by decoupled look-back and writes the ids in
-// ascending order. HBM traffic per node and camera: the node's two box words
+// Variants (Sec. III-B's per-view, dynamic selection of levels): a frustum
+// cull drops the nodes whose box lies wholly outside one of the five planes of
+// a camera's view volume (near plane 0.2, image rectangle widened by a guard
+// band), and a group of cameras can share one cut, in which a node is fine
+// enough when it is for every member that does not cull it. Boxes nest and the
+// float32 tests below are monotone in the box bounds (each step rounds
+// monotonically), so both the cull and "fine enough" spread from a node to its
+// whole subtree and the result stays an antichain of the tree.
+//
+// One pass, order preserving: partitions are (camera or group, block of 2048
+// nodes) in camera-major order, taken from an atomic ticket so every
+// predecessor of a partition is already running; each partition counts its
+// selected nodes, finds its output offset by decoupled look-back and writes
+// the ids in ascending order. HBM traffic per node and camera: the node's two box words
 // (32 B) plus its parent's (mostly L1/L2 hits: siblings share a parent), and
 // 4 B per selected node.
 #include "ngs_internal.cuh"
+#include "cut.h"
 
 namespace ngs {
 
@@ -26,18 +36,100 @@ constexpr int kCutPart = kCutThreads * kCutItems;
 
 int cut_partition_nodes() { return kCutPart; }
 
-__global__ void __launch_bounds__(kCutThreads)
-k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int64_t n_nodes,
-      const DevCamera *__restrict__ cams, int n_cams, uint32_t *__restrict__ ids, int64_t cap,
-      uint32_t *__restrict__ offsets, uint32_t *__restrict__ counters, uint32_t *ticket,
-      uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+// Selection of the plain cut: one camera per unit.
+struct PlainSelect {
+    const float4 *box_lo, *box_hi;
+    const DevCamera *cams;
+    float px, py, pz, fx, tau;
+    __device__ __forceinline__ void begin(int c) {
+        px = cams[c].pos[0]; py = cams[c].pos[1]; pz = cams[c].pos[2];
+        fx = cams[c].fx; tau = cams[c].tau;
+    }
+    __device__ __forceinline__ bool operator()(int64_t node) const {
+        return cut_selects(box_lo, box_hi, node, px, py, pz, fx, tau);
+    }
+};
+
+// True when the box lies wholly outside one of the camera's five half-spaces:
+// the largest value of a_k . (x - pos) + b_k over the box (per axis the larger
+// of the two faces' terms) is negative.
+__device__ __forceinline__ bool frustum_culled(const CutCam &k, const float4 lo, const float4 hi) {
+    const float dl0 = __fsub_rn(lo.x, k.pos[0]), dh0 = __fsub_rn(hi.x, k.pos[0]);
+    const float dl1 = __fsub_rn(lo.y, k.pos[1]), dh1 = __fsub_rn(hi.y, k.pos[1]);
+    const float dl2 = __fsub_rn(lo.z, k.pos[2]), dh2 = __fsub_rn(hi.z, k.pos[2]);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const float t0 = fmaxf(__fmul_rn(k.a[j][0], dl0), __fmul_rn(k.a[j][0], dh0));
+        const float t1 = fmaxf(__fmul_rn(k.a[j][1], dl1), __fmul_rn(k.a[j][1], dh1));
+        const float t2 = fmaxf(__fmul_rn(k.a[j][2], dl2), __fmul_rn(k.a[j][2], dh2));
+        const float m = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), t2), j == 0 ? k.b0 : 0.0f);
+        if (m < 0.0f) return true;
+    }
+    return false;
+}
+
+// Selection of a shared cut: one group of cameras per unit. n is fine enough
+// for the group when every member culls it (kFrustum) or has s(n) <= tau; n is
+// selected iff (leaf or fine(n)) and (root or not fine(parent)) and, with
+// kFrustum, some member keeps it.
+template <bool kFrustum>
+struct SharedSelect {
+    const float4 *box_lo, *box_hi;
+    const CutCam *cams;
+    const int32_t *group_begin;
+    int c0, c1;
+    __device__ __forceinline__ void begin(int g) {
+        c0 = group_begin[g];
+        c1 = group_begin[g + 1];
+    }
+    __device__ __forceinline__ bool operator()(int64_t node) const {
+        const float4 lo = box_lo[node], hi = box_hi[node];
+        const int parent = __float_as_int(lo.w);
+        const bool leaf = __float_as_int(hi.w) == 0;
+        float4 plo = lo, phi = hi;
+        if (parent >= 0) {
+            plo = box_lo[parent];
+            phi = box_hi[parent];
+        }
+        bool fine_p = true, seen = !kFrustum;
+        for (int c = c0; c < c1; ++c) {
+            const CutCam &k = cams[c];
+            bool vis_n = true, vis_p = true;
+            if (kFrustum) {
+                vis_n = !frustum_culled(k, lo, hi);
+                // a culled parent culls the node, so a kept node's parent is kept
+                vis_p = vis_n || (parent >= 0 && !frustum_culled(k, plo, phi));
+                seen = seen || vis_n;
+            }
+            // neither a leaf nor fine enough for this member: not selected
+            if (!leaf && vis_n &&
+                !(granularity(lo, hi, k.pos[0], k.pos[1], k.pos[2], k.fx) <= k.tau))
+                return false;
+            if (parent >= 0 && fine_p && vis_p &&
+                !(granularity(plo, phi, k.pos[0], k.pos[1], k.pos[2], k.fx) <= k.tau))
+                fine_p = false;
+        }
+        return (parent < 0 || !fine_p) && seen;
+    }
+};
+
+// Persistent loop over (unit, node block) partitions: count the selected
+// nodes of the block, find the output offset by decoupled look-back, write
+// the ids in ascending order.
+template <class Select>
+__device__ __forceinline__ void cut_partitions(Select sel, int64_t n_nodes, int n_units,
+                                               uint32_t *__restrict__ ids, int64_t cap,
+                                               uint32_t *__restrict__ offsets,
+                                               uint32_t *__restrict__ counters, uint32_t *ticket,
+                                               uint64_t *status, const uint32_t *epoch_ptr,
+                                               uint32_t epoch_off, int *err) {
     __shared__ uint32_t s_part;
     __shared__ uint32_t s_cnt[kCutItems * 8];   // per (item row, warp), then exclusive
     __shared__ uint32_t s_excl;
     if (*err) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nblk = (n_nodes + kCutPart - 1) / kCutPart;
-    const int64_t nparts = nblk * n_cams;
+    const int64_t nparts = nblk * n_units;
     const uint32_t epoch = *epoch_ptr + epoch_off;
     for (;;) {
         if (tid == 0) s_part = atomicAdd(ticket, 1u);
@@ -46,15 +138,13 @@ k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int6
         if (part >= nparts) break;
         const int c = (int)(part / nblk);
         const int64_t b = part - (int64_t)c * nblk;
-        const float px = cams[c].pos[0], py = cams[c].pos[1], pz = cams[c].pos[2];
-        const float fx = cams[c].fx, tau = cams[c].tau;
+        sel.begin(c);
         uint32_t bal[kCutItems];
 #pragma unroll
         for (int k = 0; k < kCutItems; ++k) {
             const int64_t node = b * kCutPart + k * kCutThreads + tid;
-            const bool sel =
-                node < n_nodes && cut_selects(box_lo, box_hi, node, px, py, pz, fx, tau);
-            bal[k] = __ballot_sync(0xffffffffu, sel);
+            const bool on = node < n_nodes && sel(node);
+            bal[k] = __ballot_sync(0xffffffffu, on);
             if (lane == 0) s_cnt[k * 8 + warp] = __popc(bal[k]);
         }
         __syncthreads();
@@ -84,7 +174,7 @@ k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int6
                 s_excl = prev;
                 if (b == 0) offsets[c] = prev;
                 if (part == nparts - 1) {
-                    offsets[n_cams] = prev + total;
+                    offsets[n_units] = prev + total;
                     counters[CNT_CUT] = prev + total;
                     if ((int64_t)prev + total > cap) latch_error(err, kErrCapacity);
                 }
@@ -103,11 +193,51 @@ k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int6
     }
 }
 
+__global__ void __launch_bounds__(kCutThreads)
+k_cut(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi, int64_t n_nodes,
+      const DevCamera *__restrict__ cams, int n_cams, uint32_t *__restrict__ ids, int64_t cap,
+      uint32_t *__restrict__ offsets, uint32_t *__restrict__ counters, uint32_t *ticket,
+      uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off, int *err) {
+    PlainSelect sel{box_lo, box_hi, cams, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    cut_partitions(sel, n_nodes, n_cams, ids, cap, offsets, counters, ticket, status, epoch_ptr,
+                   epoch_off, err);
+}
+
+template <bool kFrustum>
+__global__ void __launch_bounds__(kCutThreads)
+k_cut_shared(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi,
+             int64_t n_nodes, const CutCam *__restrict__ cams,
+             const int32_t *__restrict__ group_begin, int n_groups, uint32_t *__restrict__ ids,
+             int64_t cap, uint32_t *__restrict__ offsets, uint32_t *__restrict__ counters,
+             uint32_t *ticket, uint64_t *status, const uint32_t *epoch_ptr, uint32_t epoch_off,
+             int *err) {
+    SharedSelect<kFrustum> sel{box_lo, box_hi, cams, group_begin, 0, 0};
+    cut_partitions(sel, n_nodes, n_groups, ids, cap, offsets, counters, ticket, status,
+                   epoch_ptr, epoch_off, err);
+}
+
 void launch_cut(const SceneDev &sc, const DevCamera *cams, int n_cams, uint32_t *ids, int64_t cap,
                 uint32_t *offsets, uint32_t *counters, uint32_t *ticket, uint64_t *status,
                 const uint32_t *epoch, uint32_t epoch_off, int *err, int grid, cudaStream_t st) {
     k_cut<<<grid, kCutThreads, 0, st>>>(sc.box_lo, sc.box_hi, sc.n, cams, n_cams, ids, cap,
                                         offsets, counters, ticket, status, epoch, epoch_off, err);
+}
+
+void launch_cut_shared(bool frustum, const float4 *box_lo, const float4 *box_hi, int64_t n_nodes,
+                       const CutCam *cams, const int32_t *group_begin, int n_groups,
+                       uint32_t *ids, int64_t cap, uint32_t *offsets, uint32_t *counters,
+                       uint32_t *ticket, uint64_t *status, const uint32_t *epoch,
+                       uint32_t epoch_off, int *err, int grid, cudaStream_t st) {
+    if (frustum)
+        k_cut_shared<true><<<grid, kCutThreads, 0, st>>>(box_lo, box_hi, n_nodes, cams,
+                                                         group_begin, n_groups, ids, cap, offsets,
+                                                         counters, ticket, status, epoch,
+                                                         epoch_off, err);
+    else
+        k_cut_shared<false><<<grid, kCutThreads, 0, st>>>(box_lo, box_hi, n_nodes, cams,
+                                                          group_begin, n_groups, ids, cap,
+                                                          offsets, counters, ticket, status,
+                                                          epoch, epoch_off, err);
 }
 
 }  // namespace ngs

@@ -262,6 +262,25 @@ class Renderer:
               "ngs_select_cut")
         return ids, off
 
+    def select_cut_shared(self, cams, group_begin, frustum: bool = True, guard: float = 0.0,
+                          cap: Optional[int] = None, stream=None):
+        """One LOD cut per group of cameras (group g = cams[group_begin[g]:
+        group_begin[g+1]]), optionally frustum-culled with a guard band of
+        ``guard`` pixels: (ids int32 CUDA tensor, offsets int64 CUDA tensor
+        [n_groups + 1])."""
+        torch = _torch()
+        gb = np.ascontiguousarray(group_begin, dtype=np.int32)
+        ng = len(gb) - 1
+        cap = int(cap if cap is not None else max(ng, 1) * self.n_nodes)
+        ids = torch.empty(max(cap, 1), dtype=torch.int32, device=f"cuda:{self.device}")
+        off = torch.empty(max(ng, 0) + 1, dtype=torch.int64, device=f"cuda:{self.device}")
+        arr = camera_array(cams)
+        check(self.L.ngs_select_cut_shared(self.h, arr, len(cams), gb.ctypes.data_as(C.c_void_p),
+                                           ng, _lib.CUT_FRUSTUM if frustum else 0, float(guard),
+                                           C.c_void_p(ids.data_ptr()), C.c_void_p(off.data_ptr()),
+                                           cap, _stream_ptr(stream)), "ngs_select_cut_shared")
+        return ids, off
+
     def tile_lists(self, cam_index: int, n_tiles: int, cap: int):
         """(ranges [tiles, 2] int64, node ids int32) of one camera of the last render."""
         ranges = np.zeros((n_tiles, 2), dtype=np.int64)

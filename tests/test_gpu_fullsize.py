@@ -1,8 +1,9 @@
 """GPU parity at the full workload sizes: the 1M-leaf floor (640x480 views,
 plain FP32), the 4M-leaf floor (1280x720 views with FP16 / BF16 attributes, and
 the 256-camera mixed-resolution batch in the configuration the benchmark times:
-batched, graph-captured, autotuned tile and staging depth), and the 8M-leaf
-two-wing floor served to many agents. The oracle renders sampled views whole;
+batched, graph-captured, autotuned tile and staging depth, and its first cameras'
+frustum-culled shared cuts), and the 8M-leaf two-wing floor served to many
+agents. The oracle renders sampled views whole;
 the rest of a batch is checked by properties that hold at any size (every
 image equals its camera rendered alone, and a graph replay gives the same
 bits). The oracle renders the cut the GPU selected once that cut is checked
@@ -127,6 +128,41 @@ def test_floor4m_batch256_benchmark_configuration(floor4m):
     for i in rng.choice(len(cams), 16, replace=False):
         alone = R.render([cams[int(i)]])[0].cpu().numpy()
         assert np.array_equal(alone, first[int(i)])
+    R.close()
+
+
+def test_floor4m_shared_frustum_cuts(floor4m):
+    """The benchmark's first 16 cameras (consecutive poses of one walk) in two
+    groups of 8 with the frustum cull, in the launch the benchmark times: each
+    group's cut equals the oracle's away from float32-reachable decisions. A
+    camera's frustum-culled cut is its plain cut minus the culled nodes, so it
+    is a subset of the plain cut, bit for bit."""
+    _need_gpu()
+    from paper_2603_15186_gb300 import Renderer
+    cams = mixed_batch_cameras(floor4m, 256, 1002)[:16]
+    R = Renderer(device=0)
+    R.load_scene(floor4m, attr_dtype="f16", stored=quantize_attributes(floor4m, "f16")[0])
+    gb = [0, 8, 16]
+    ids, off = R.select_cut_shared(cams, gb, frustum=True)
+    ids, off = ids.cpu().numpy(), off.cpu().numpy()
+    sa = O.SceneArrays(floor4m)
+    want, woff, near = O.select_cut_shared(sa, cams, gb, frustum=True)
+    M = floor4m.n_nodes
+    for g in range(2):
+        a, b = np.zeros(M, bool), np.zeros(M, bool)
+        got = ids[off[g]:off[g + 1]]
+        assert np.all(np.diff(got) > 0)
+        a[got] = True
+        b[want[woff[g]:woff[g + 1]]] = True
+        assert not np.any((a != b) & (near[g] == 0))
+        assert near[g].mean() < 1e-3
+    plain, poff = R.select_cut(cams[:2])
+    culled, pcoff = R.select_cut_shared(cams[:2], [0, 1, 2], frustum=True)
+    plain, poff, culled, pcoff = (t.cpu().numpy() for t in (plain, poff, culled, pcoff))
+    for c in range(2):
+        f = culled[pcoff[c]:pcoff[c + 1]]
+        p = plain[poff[c]:poff[c + 1]]
+        assert 0 < len(f) < len(p) and np.all(np.isin(f, p))
     R.close()
 
 

@@ -99,6 +99,75 @@ def test_cut_matches_oracle(R, box10k, tau):
 
 
 # ---------------------------------------------------------------------------
+# frustum-culled and shared cuts
+# ---------------------------------------------------------------------------
+
+def _compare_groups(ids, off, scene, cams, gb, frustum, guard):
+    ids, off = ids.cpu().numpy(), off.cpu().numpy()
+    want, woff, near = O.select_cut_shared(scene, cams, gb, frustum=frustum, guard=guard)
+    M = scene.n_nodes
+    for g in range(len(gb) - 1):
+        got = ids[off[g]:off[g + 1]]
+        assert np.all(np.diff(got) > 0)
+        a, b = np.zeros(M, bool), np.zeros(M, bool)
+        a[got] = True
+        b[want[woff[g]:woff[g + 1]]] = True
+        bad = (a != b) & (near[g] == 0)
+        assert not bad.any(), f"group {g}: {int(bad.sum())} decisions differ"
+        assert near[g].mean() < 0.01
+
+
+def _group_walk_cams(scene):
+    taus = [5.0, 6.0, 12.0, 4.0, 20.0, 10.0, 30.0, 8.0, 16.0, 40.0]
+    cams = walk_cameras(scene, 10, 21, 160, 120, fx=150.0, taus=taus)
+    cams[3] = look_camera((-3.0, 3.0, 1.5), math.pi, 33, 17, fx=30.0, tau=2.0)  # outside, away
+    cams[7].width, cams[7].height, cams[7].cx, cams[7].cy = 97, 61, 40.0, 35.5   # off-centre
+    return cams
+
+
+@pytest.mark.parametrize("frustum,guard", [(False, 0.0), (True, 0.0), (True, 32.0)])
+def test_shared_cut_matches_oracle(R, small_floor, frustum, guard):
+    """Groups of 1, 1, 3 and 5 cameras: every group's cut equals the oracle's
+    on every node whose decisions (tau threshold, frustum planes, for any
+    member, at the node or its parent) are not within float32 reach."""
+    R.load_scene(small_floor)
+    cams = _group_walk_cams(small_floor)
+    gb = [0, 1, 3, 4, 10]
+    ids, off = R.select_cut_shared(cams, gb, frustum=frustum, guard=guard)
+    _compare_groups(ids, off, small_floor, cams, gb, frustum, guard)
+    if frustum:
+        assert int(off[3].item()) == int(off[2].item())   # the camera facing away sees nothing
+
+
+def test_shared_cut_of_single_cameras_is_the_plain_cut(R, small_floor):
+    R.load_scene(small_floor)
+    cams = _group_walk_cams(small_floor)
+    ids, off = R.select_cut(cams)
+    ids2, off2 = R.select_cut_shared(cams, list(range(len(cams) + 1)), frustum=False)
+    n = int(off[-1].item())
+    assert torch.equal(off, off2) and torch.equal(ids[:n], ids2[:n])
+
+
+def test_shared_cut_rejects_bad_groups_and_reports_capacity(R, small_floor):
+    from paper_2603_15186_gb300 import NgsError
+    R.load_scene(small_floor)
+    cams = _group_walk_cams(small_floor)
+    for gb in ([0, 5], [1, 10], [0, 4, 4, 10], [0, 6, 3, 10]):
+        with pytest.raises(NgsError) as e:
+            R.select_cut_shared(cams, gb)
+        assert e.value.status == 1
+    with pytest.raises(NgsError) as e:
+        R.select_cut_shared(cams, [0, 10], guard=-1.0)
+    assert e.value.status == 1
+    with pytest.raises(NgsError) as e:
+        R.select_cut_shared(cams, [0, 4, 10], cap=100)
+    assert e.value.status == 4
+    # the context survives: the next call succeeds and agrees with the oracle
+    ids, off = R.select_cut_shared(cams, [0, 4, 10])
+    _compare_groups(ids, off, small_floor, cams, [0, 4, 10], True, 0.0)
+
+
+# ---------------------------------------------------------------------------
 # full render
 # ---------------------------------------------------------------------------
 
