@@ -21,6 +21,8 @@ namespace {
 
 constexpr uint32_t kEpochStride = 32;   // epoch values reserved per sub-batch
 constexpr int kMaxCamsPerBatch = 1024;
+// ngs_select_cut takes the camera-blocked two-pass cut from this many cameras on
+constexpr int kCutBlockedMinCams = 4;
 constexpr int kMaxCamsPerCall = 1 << 16;
 constexpr int kTuneShapes = NGS_TUNE_SHAPES;
 
@@ -84,6 +86,8 @@ struct ngs_ctx {
     uint32_t *cut_off32 = nullptr;     // scratch for ngs_select_cut offsets
     CutCam *cut_cams = nullptr;        // ngs_select_cut_shared: cameras and groups
     int32_t *cut_groups = nullptr;
+    uint32_t *cut_counts = nullptr;    // many-camera ngs_select_cut: (camera, block) counts
+    uint32_t *cut_poff = nullptr;      // and their scanned offsets
 
     // occupancy-derived persistent grids
     int grid_cut = 0, grid_pre = 0, grid_sort32 = 0, grid_sort64 = 0, grid_scan = 0,
@@ -179,11 +183,15 @@ void free_work(ngs_ctx *c) {
     dfree(c->cut_off32);
     dfree(c->cut_cams);
     dfree(c->cut_groups);
+    dfree(c->cut_counts);
+    dfree(c->cut_poff);
     c->w = Work();
     c->stats_dev = nullptr;
     c->cut_off32 = nullptr;
     c->cut_cams = nullptr;
     c->cut_groups = nullptr;
+    c->cut_counts = nullptr;
+    c->cut_poff = nullptr;
     c->work_ready = false;
 }
 
@@ -287,6 +295,8 @@ ngs_status ensure_work(ngs_ctx *c) {
     A(dalloc(&c->cut_off32, kMaxCamsPerBatch + 1));
     A(dalloc(&c->cut_cams, kMaxCamsPerBatch));
     A(dalloc(&c->cut_groups, kMaxCamsPerBatch + 1));
+    A(dalloc(&c->cut_counts, (size_t)(nblk * kMaxCamsPerBatch)));
+    A(dalloc(&c->cut_poff, (size_t)(nblk * kMaxCamsPerBatch)));
     A(dalloc(&w.work64, 2));
     if (st != NGS_OK) {
         free_work(c);
@@ -1067,10 +1077,27 @@ NGS_API ngs_status ngs_select_cut(ngs_ctx *c, const ngs_camera *cams, int32_t n_
     CK(cudaMemcpyAsync(w.cams, hc.data(), sizeof(DevCamera) * n_cams, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
-    launch_cut(c->scene, w.cams, n_cams, (uint32_t *)d_ids, std::min<int64_t>(cap, (1ll << 32) - 1),
-               c->cut_off32, w.counters, w.counters + TK_CUT, w.status, w.epoch, 0, w.err,
-               c->grid_cut, st);
-    k_offsets_to_i64<<<(n_cams + 256) / 256, 256, 0, st>>>(c->cut_off32, d_offsets, n_cams);
+    const int64_t cap32 = std::min<int64_t>(cap, (1ll << 32) - 1);
+    if (n_cams >= kCutBlockedMinCams) {
+        // count per (camera, block), scan in camera-major order, write
+        const SceneDev &sc = c->scene;
+        const int64_t nblk = (sc.n + cut_partition_nodes() - 1) / cut_partition_nodes();
+        const int64_t np = nblk * n_cams;
+        launch_cut_blocked(false, sc.box_lo, sc.box_hi, sc.n, w.cams, n_cams, c->cut_counts,
+                           nullptr, cap32, w.counters + TK_CUT, w.err, c->grid_cut, st);
+        const int64_t sparts = (np + scan_partition() - 1) / scan_partition();
+        launch_scan_u32(c->cut_counts, c->cut_poff, nullptr, np, c->cut_off32,
+                        w.counters + TK_SCAN, w.status, w.epoch, 0, w.err,
+                        (int)std::min<int64_t>(sparts, c->grid_scan), st);
+        launch_cut_cam_offsets(c->cut_poff, c->cut_off32, nblk, n_cams, cap32, d_offsets,
+                               w.counters, w.err, st);
+        launch_cut_blocked(true, sc.box_lo, sc.box_hi, sc.n, w.cams, n_cams, c->cut_poff,
+                           (uint32_t *)d_ids, cap32, w.counters + TK_PRE, w.err, c->grid_cut, st);
+    } else {
+        launch_cut(c->scene, w.cams, n_cams, (uint32_t *)d_ids, cap32, c->cut_off32, w.counters,
+                   w.counters + TK_CUT, w.status, w.epoch, 0, w.err, c->grid_cut, st);
+        k_offsets_to_i64<<<(n_cams + 256) / 256, 256, 0, st>>>(c->cut_off32, d_offsets, n_cams);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return check_err(c);

@@ -216,6 +216,148 @@ k_cut_shared(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_h
                    epoch_ptr, epoch_off, err);
 }
 
+// Many-camera plain cut. A partition is (node block b, chunk of kCutCams
+// cameras), taken in block-major order so that a block's boxes come from HBM
+// once and from L2 for its other chunks; every camera of the chunk is tested
+// on the node and parent boxes loaded once. Pass 1 stores each camera's count
+// for the block; pass 2 (after a scan of the counts in camera-major order)
+// recomputes the selection and writes the ids at the scanned offset plus the
+// prefix within the block. No partition waits on another.
+constexpr int kCutCams = 8;
+static_assert(kCutThreads / 32 == kCutCams, "one warp scans one camera's row counts");
+
+template <bool kWrite>
+__global__ void __launch_bounds__(kCutThreads)
+k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi,
+              int64_t n_nodes, const DevCamera *__restrict__ cams, int n_cams,
+              uint32_t *__restrict__ part_vals, uint32_t *__restrict__ ids, int64_t cap,
+              uint32_t *ticket, const int *err) {
+    __shared__ float s_cam[kCutCams][5];                   // pos xyz, fx, tau
+    __shared__ uint32_t s_bal[kCutCams][kCutItems * 8];    // ballot per (camera, row, warp)
+    __shared__ uint32_t s_off[kCutCams][kCutItems * 8];    // its exclusive offset in the block
+    __shared__ uint32_t s_part;
+    if (*err) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t nblk = (n_nodes + kCutPart - 1) / kCutPart;
+    const int nchunk = (n_cams + kCutCams - 1) / kCutCams;
+    const int64_t nparts = nblk * nchunk;
+    for (;;) {
+        if (tid == 0) s_part = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int64_t part = s_part;
+        if (part >= nparts) break;
+        const int64_t b = part / nchunk;
+        const int c0 = (int)(part - b * nchunk) * kCutCams;
+        const int nc = min(kCutCams, n_cams - c0);
+        if (tid < kCutCams * 5) {
+            const int j = tid / 5, f = tid - 5 * j;
+            float v = 0.0f;
+            if (j < nc) {
+                const DevCamera &k = cams[c0 + j];
+                v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : k.tau);
+            }
+            s_cam[j][f] = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int k = 0; k < kCutItems; ++k) {
+            const int64_t node = b * kCutPart + k * kCutThreads + tid;
+            const bool valid = node < n_nodes;
+            float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo, plo = lo, phi = lo;
+            int parent = -1;
+            bool leaf = true;
+            if (valid) {
+                lo = box_lo[node];
+                hi = box_hi[node];
+                parent = __float_as_int(lo.w);
+                leaf = __float_as_int(hi.w) == 0;
+                if (parent >= 0) {
+                    plo = box_lo[parent];
+                    phi = box_hi[parent];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kCutCams; ++j) {
+                bool sel = false;
+                if (valid && j < nc) {
+                    const float px = s_cam[j][0], py = s_cam[j][1], pz = s_cam[j][2];
+                    const float fx = s_cam[j][3], tau = s_cam[j][4];
+                    // the rule of cut_selects, parent first (most nodes lie below the cut)
+                    sel = (parent < 0 || granularity(plo, phi, px, py, pz, fx) > tau) &&
+                          (leaf || granularity(lo, hi, px, py, pz, fx) <= tau);
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, sel);
+                if (lane == 0) s_bal[j][k * 8 + warp] = bal;
+            }
+        }
+        __syncthreads();
+        if (warp < nc) {
+            // warp j: exclusive scan of camera j's 64 (row, warp) counts in node order
+            const int j = warp;
+            const uint32_t v0 = __popc(s_bal[j][2 * lane]), v1 = __popc(s_bal[j][2 * lane + 1]);
+            uint32_t incl = v0 + v1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t excl = incl - (v0 + v1);
+            s_off[j][2 * lane] = excl;
+            s_off[j][2 * lane + 1] = excl + v0;
+            if (!kWrite && lane == 31) part_vals[(int64_t)(c0 + j) * nblk + b] = incl;
+        }
+        if (kWrite) {
+            __syncthreads();
+            for (int j = 0; j < nc; ++j) {
+                const uint64_t base = part_vals[(int64_t)(c0 + j) * nblk + b];
+#pragma unroll
+                for (int k = 0; k < kCutItems; ++k) {
+                    const uint32_t bal = s_bal[j][k * 8 + warp];
+                    if ((bal >> lane) & 1u) {
+                        const uint64_t pos =
+                            base + s_off[j][k * 8 + warp] + __popc(bal & lanemask_lt());
+                        if (pos < (uint64_t)cap)
+                            ids[pos] = (uint32_t)(b * kCutPart + k * kCutThreads + tid);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_cut_cam_offsets(const uint32_t *__restrict__ part_off,
+                                  const uint32_t *__restrict__ total, int64_t nblk, int n_cams,
+                                  int64_t cap, int64_t *__restrict__ offsets,
+                                  uint32_t *__restrict__ counters, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n_cams) return;
+    const uint32_t t = *total;
+    offsets[i] = i < n_cams ? (int64_t)part_off[(int64_t)i * nblk] : (int64_t)t;
+    if (i == n_cams) {
+        counters[CNT_CUT] = t;
+        if ((int64_t)t > cap) latch_error(err, kErrCapacity);
+    }
+}
+
+void launch_cut_blocked(bool write, const float4 *box_lo, const float4 *box_hi, int64_t n_nodes,
+                        const DevCamera *cams, int n_cams, uint32_t *part_vals, uint32_t *ids,
+                        int64_t cap, uint32_t *ticket, const int *err, int grid, cudaStream_t st) {
+    if (write)
+        k_cut_blocked<true><<<grid, kCutThreads, 0, st>>>(box_lo, box_hi, n_nodes, cams, n_cams,
+                                                          part_vals, ids, cap, ticket, err);
+    else
+        k_cut_blocked<false><<<grid, kCutThreads, 0, st>>>(box_lo, box_hi, n_nodes, cams, n_cams,
+                                                           part_vals, ids, cap, ticket, err);
+}
+
+void launch_cut_cam_offsets(const uint32_t *part_off, const uint32_t *total, int64_t nblk,
+                            int n_cams, int64_t cap, int64_t *offsets, uint32_t *counters,
+                            int *err, cudaStream_t st) {
+    k_cut_cam_offsets<<<(n_cams + 256) / 256, 256, 0, st>>>(part_off, total, nblk, n_cams, cap,
+                                                            offsets, counters, err);
+}
+
 void launch_cut(const SceneDev &sc, const DevCamera *cams, int n_cams, uint32_t *ids, int64_t cap,
                 uint32_t *offsets, uint32_t *counters, uint32_t *ticket, uint64_t *status,
                 const uint32_t *epoch, uint32_t epoch_off, int *err, int grid, cudaStream_t st) {

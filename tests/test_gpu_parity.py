@@ -98,6 +98,40 @@ def test_cut_matches_oracle(R, box10k, tau):
         compare_cut(ids[off[c]:off[c + 1]], box10k, cam)
 
 
+def _many_cams(tau):
+    cams = [camera_c0(tau)]
+    for i in range(10):
+        cams.append(look_camera((-3.0 + 0.9 * i, 2.0 - 0.5 * i, 1.2 + 0.1 * i), 0.6 * i,
+                                64 + 8 * i, 48, fx=40.0 + 9.0 * i, tau=tau * (0.5 + 0.15 * i)))
+    return cams
+
+
+@pytest.mark.parametrize("tau", [0.0, 4.0, 16.0, 60.0])
+def test_cut_many_cameras_matches_oracle(R, box10k, tau):
+    """Eleven cameras take the camera-blocked two-pass cut (chunks of 8 and 3):
+    each camera's cut equals the oracle's away from tau, and equals the
+    single-camera kernel's cut bit for bit."""
+    R.load_scene(box10k)
+    cams = _many_cams(tau)
+    ids, off = R.select_cut(cams)
+    ids, off = ids.cpu().numpy(), off.cpu().numpy()
+    for c, cam in enumerate(cams):
+        compare_cut(ids[off[c]:off[c + 1]], box10k, cam)
+        one, o1 = R.select_cut([cam])
+        assert np.array_equal(one[: int(o1[1].item())].cpu().numpy(), ids[off[c]:off[c + 1]])
+
+
+def test_cut_many_cameras_capacity(R, box10k):
+    from paper_2603_15186_gb300 import NgsError
+    R.load_scene(box10k)
+    cams = _many_cams(0.0)
+    with pytest.raises(NgsError) as e:
+        R.select_cut(cams, cap=1000)
+    assert e.value.status == 4
+    ids, off = R.select_cut(cams)
+    assert int(off[-1].item()) == 11 * 10_000     # tau = 0: every camera's cut is all leaves
+
+
 # ---------------------------------------------------------------------------
 # frustum-culled and shared cuts
 # ---------------------------------------------------------------------------
