@@ -179,8 +179,10 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *ctx, const ngs_gaussians *g, const ng
  * with s(n) = fx * (longest side of box(n)) / (distance from pos to box(n)),
  * s = +inf when the camera is inside the box. Writes the selected ids of
  * camera c, ascending, to d_ids[d_offsets[c] .. d_offsets[c+1]) (device
- * int32, capacity cap entries; d_offsets: device int64 [n_cams + 1]).
- * Returns NGS_ERR_CAPACITY (after synchronising) if the cut exceeds cap. */
+ * int32, capacity cap entries; d_offsets: device int64 [n_cams + 1]);
+ * 1 <= n_cams <= 1024, and the cuts together hold fewer than 2^32 ids.
+ * Synchronises the stream. Returns NGS_ERR_CAPACITY if the cuts exceed cap
+ * (the offsets still hold their sizes). */
 NGS_API ngs_status ngs_select_cut(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                                   int32_t *d_ids, int64_t *d_offsets, int64_t cap, void *stream);
 
@@ -200,8 +202,8 @@ NGS_API ngs_status ngs_select_cut(ngs_ctx *ctx, const ngs_camera *cams, int32_t 
  *    fine(parent)) and, with the cull on, some member keeps it. On every
  *    root-to-leaf path this is the deepest of the members' own choices, so
  *    each member gets at least the detail it asks for wherever it sees.
- * A group of one camera without the cull gives ngs_select_cut's cut. Output
- * as ngs_select_cut, per group: ascending ids in d_ids[d_offsets[g] ..
+ * A group of one camera without the cull gives ngs_select_cut's cut.
+ * 1 <= n_groups <= n_cams <= 1024. Output as ngs_select_cut, per group: ascending ids in d_ids[d_offsets[g] ..
  * d_offsets[g + 1]) (device int32 [cap], device int64 [n_groups + 1]).
  * NGS_ERR_INVALID_ARG for a bad group table, unknown flags, a negative or
  * non-finite guard, or a bad camera; NGS_ERR_CAPACITY if the cuts exceed cap
