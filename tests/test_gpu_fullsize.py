@@ -1,9 +1,10 @@
 """GPU parity at the full workload sizes: the 1M-leaf floor (640x480 views,
 plain FP32), the 4M-leaf floor (1280x720 views with FP16 / BF16 attributes, and
 the 256-camera mixed-resolution batch in the configuration the benchmark times:
-batched, graph-captured, autotuned tile and staging depth, and its first cameras'
-frustum-culled shared cuts), and the 8M-leaf two-wing floor served to many
-agents. The oracle renders sampled views whole;
+batched, graph-captured, autotuned tile and staging depth; the same batch with
+level-of-detail blending; its first cameras' frustum-culled shared cuts; the
+GS-slice grid and the navigation on it), and the 8M-leaf two-wing floor served
+to many agents. The oracle renders sampled views whole;
 the rest of a batch is checked by properties that hold at any size (every
 image equals its camera rendered alone, and a graph replay gives the same
 bits). The oracle renders the cut the GPU selected once that cut is checked
@@ -128,6 +129,79 @@ def test_floor4m_batch256_benchmark_configuration(floor4m):
     for i in rng.choice(len(cams), 16, replace=False):
         alone = R.render([cams[int(i)]])[0].cpu().numpy()
         assert np.array_equal(alone, first[int(i)])
+    R.close()
+
+
+def test_floor4m_lod_blend_benchmark_batch(floor4m):
+    """Level-of-detail blending on the benchmark's 256 cameras in its launch
+    configuration (32x32 tiles composited in 16x16 blocks, staging batch 128,
+    graph-captured sub-batches): one view per resolution against the oracle's
+    blended render of the cut the GPU selected."""
+    _need_gpu()
+    from paper_2603_15186_gb300 import Renderer
+    stored, deq = quantize_attributes(floor4m, "f16")
+    R = Renderer(device=0, tile=(32, 32), batch=128)
+    R.load_scene(floor4m, attr_dtype="f16", stored=stored)
+    R.set_cta(16, 16)
+    R.set_lod_blend(True)
+    cams = mixed_batch_cameras(floor4m, 256, 1002)
+    imgs = R.render(cams)
+    sample = [next(k for k, c in enumerate(cams) if c.width == res) for res in (320, 640, 1280)]
+    sa = O.SceneArrays(floor4m, overrides=deq)
+    for i in sample:
+        ids, off = R.select_cut([cams[i]])
+        gpu = ids[: int(off[1].item())].cpu().numpy()
+        compare_cut(gpu, floor4m, cams[i])
+        ref = O.render(sa, cams[i], tile=(32, 32), ids=gpu.astype(np.int32), blend=True)
+        _check(imgs[i].cpu().numpy(), ref)
+    R.close()
+
+
+def test_floor4m_slice_and_navigation_full_grid(floor4m):
+    """The benchmark's GS-slice grid (the 4M leaves, FP16 attributes, 5 cm cells
+    over the scene's box, 13 planes from 0.05 m) against the oracle: slice
+    values within 1e-3 away from the 1/255 cut-off, occupancy equal away from
+    the threshold; then the blocked map, 9 distance fields and 64 agents'
+    paths on that occupancy bit for bit."""
+    _need_gpu()
+    from types import SimpleNamespace
+    from paper_2603_15186_gb300 import Renderer
+    stored, deq = quantize_attributes(floor4m, "f16")
+    R = Renderer(device=0)
+    R.load_scene(floor4m, attr_dtype="f16", stored=stored)
+    lo, hi = floor4m.aabb_min[0], floor4m.aabb_max[0]
+    grid = SimpleNamespace(x0=float(lo[0]), y0=float(lo[1]), cell=0.05,
+                           nx=int(np.ceil((hi[0] - lo[0]) / 0.05)),
+                           ny=int(np.ceil((hi[1] - lo[1]) / 0.05)), z0=0.05, dz=0.1, nz=13,
+                           threshold=0.5)
+    val, occ = R.slice_occupancy(grid)
+    torch.cuda.synchronize()
+    got, gocc = val.cpu().numpy().astype(np.float64), occ.cpu().numpy()
+    want, wocc = O.slice_occupancy(O.SceneArrays(floor4m, overrides=deq), grid)
+    exempt = (np.minimum(got, want) <= 1.0 / 255.0 + 1e-3) & (np.abs(got - want) > 1e-3)
+    assert exempt.mean() < 0.01
+    assert np.abs(got - want)[~exempt].max() <= 1e-3
+    near = np.abs(want - grid.threshold) <= 1e-3
+    assert np.array_equal(gocc[~near], wocc[~near])
+    rng = np.random.default_rng(77)
+    b_ref = O.nav_blocked(gocc, 1, 9, 2)
+    free = np.argwhere(b_ref == 0)
+    goals = [tuple(int(v) for v in free[k][::-1]) for k in rng.choice(len(free), 9, replace=False)]
+    blocked, dist = R.nav_fields(occ, goals, 1, 9, 2)
+    torch.cuda.synchronize()
+    assert np.array_equal(blocked.cpu().numpy(), b_ref)
+    dist_h = dist.cpu().numpy().view(np.uint32)
+    refs = [O.nav_field(b_ref, g) for g in goals]
+    for g in range(len(goals)):
+        assert np.array_equal(dist_h[g], refs[g]), g
+    starts = [(int(free[k][1]), int(free[k][0]), int(rng.integers(len(goals))))
+              for k in rng.choice(len(free), 64, replace=False)]
+    paths, lens = R.nav_paths(dist, starts, 4096)
+    paths, lens = paths.cpu().numpy(), lens.cpu().numpy()
+    for a, (i, j, g) in enumerate(starts):
+        ref = O.nav_path(refs[g], (i, j), 4096)
+        assert lens[a] == len(ref) and np.array_equal(paths[a, :lens[a]], ref), a
+    assert (lens > 1).mean() > 0.5
     R.close()
 
 
