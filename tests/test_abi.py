@@ -72,14 +72,15 @@ int main(void) {
   printf("%d %d %d %d %d %d %d %d %d %d %d\n", NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H,
          NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL, NGS_OPT_CTA_W,
          NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL, NGS_OPT_LOD_BLEND);
+  printf("%d\n", NGS_CUT_FRUSTUM);
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
-    a, b, t, o = subprocess.run([str(exe)], capture_output=True, text=True,
-                                check=True).stdout.split("\n")[:4]
+    a, b, t, o, f = subprocess.run([str(exe)], capture_output=True, text=True,
+                                   check=True).stdout.split("\n")[:5]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [C.sizeof(_lib.Camera), C.sizeof(_lib.Gaussians), C.sizeof(_lib.Hierarchy),
@@ -95,6 +96,7 @@ int main(void) {
         _lib.NGS_OPT_GRAPH, _lib.NGS_OPT_STAGE_TIMING, _lib.NGS_OPT_BLOCK_CULL,
         _lib.NGS_OPT_CTA_W, _lib.NGS_OPT_CTA_H, _lib.NGS_OPT_PAIRS_PER_PIXEL,
         _lib.NGS_OPT_LOD_BLEND]
+    assert int(f) == _lib.CUT_FRUSTUM
 
 
 def test_renderer_fails_loudly_without_gpu():
