@@ -118,7 +118,7 @@ enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
        NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7,
        NGS_OPT_CTA_W = 8, NGS_OPT_CTA_H = 9, NGS_OPT_PAIRS_PER_PIXEL = 10,
-       NGS_OPT_LOD_BLEND = 11 };
+       NGS_OPT_LOD_BLEND = 11, NGS_OPT_COMPOSITE_ORDER = 12 };
 /* NGS_OPT_TILE_W / NGS_OPT_TILE_H: tile width 8, 16 or 32, height 8, 16 or 32;
  * a render accepts the shapes 8x8, 16x8, 16x16, 16x32, 32x16 and 32x32
  * (INVALID_ARG else).
@@ -142,11 +142,16 @@ enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH =
  * within those bounds).
  * NGS_OPT_PAIRS_PER_PIXEL (1..4096, default 48): the planner's estimate of
  * (tile, Gaussian) pairs per pixel, used to fit sub-batches into
- * pair_capacity; it is raised automatically to 1.25x the largest density a
- * render observed. A render whose pairs still exceed the capacity latches
- * NGS_ERR_CAPACITY.
+ * pair_capacity; it is raised automatically to 1.25x the densest sub-batch a
+ * render observed (read by ngs_last_stats, and by ngs_synchronize when it
+ * returns NGS_ERR_CAPACITY, so that rendering the same cameras again fits). A
+ * render whose pairs still exceed the capacity latches NGS_ERR_CAPACITY.
  * NGS_OPT_BLOCK_CULL (default 1): skip, per camera, node blocks that provably
- * hold no visible Gaussian; 0 tests every node (same images, slower). */
+ * hold no visible Gaussian; 0 tests every node (same images, slower).
+ * NGS_OPT_COMPOSITE_ORDER (default 1): the batched path's persistent
+ * compositing CTAs take the tiles of a sub-batch in order of decreasing list
+ * length (classes of half an octave), so that long lists do not start last;
+ * 0 takes them in tile order. Same images. */
 
 typedef struct {
     int64_t cut_total;       /* selected nodes over all cameras of the last render */
@@ -160,6 +165,14 @@ typedef struct {
     int32_t kernels;         /* kernel launches of the last render */
     int32_t cta_w, cta_h;    /* compositing block of the last render */
     int32_t reserved;
+    /* batched path: milliseconds, summed over the sub-batches, from the moment
+     * the first compositing CTA of a launch found its work queue empty to the
+     * end of the launch's last CTA (the launch's tail); 0 in the plain path */
+    double composite_tail_ms;
+    /* batched path: (node, camera) candidates the fused cut + preprocess
+     * passed to its full preprocess (the visible ones and the holes left by
+     * those that turned out invisible); -1 in the plain path */
+    int64_t candidate_total;
 } ngs_stats;
 
 NGS_API const char *ngs_strerror(ngs_status s);
@@ -180,7 +193,9 @@ NGS_API ngs_status ngs_load_scene(ngs_ctx *ctx, const ngs_gaussians *g, const ng
  * s = +inf when the camera is inside the box. Writes the selected ids of
  * camera c, ascending, to d_ids[d_offsets[c] .. d_offsets[c+1]) (device
  * int32, capacity cap entries; d_offsets: device int64 [n_cams + 1]);
- * 1 <= n_cams <= 1024, and the cuts together hold fewer than 2^32 ids.
+ * 1 <= n_cams <= 1024. A cut holds at most one id per leaf, and the offsets
+ * are counted in 32 bits: a call with n_cams x (leaves of the scene) >= 2^32
+ * returns NGS_ERR_CAPACITY before any work (split the cameras over calls).
  * Synchronises the stream. Returns NGS_ERR_CAPACITY if the cuts exceed cap
  * (the offsets still hold their sizes). */
 NGS_API ngs_status ngs_select_cut(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
@@ -207,7 +222,8 @@ NGS_API ngs_status ngs_select_cut(ngs_ctx *ctx, const ngs_camera *cams, int32_t 
  * d_offsets[g + 1]) (device int32 [cap], device int64 [n_groups + 1]).
  * NGS_ERR_INVALID_ARG for a bad group table, unknown flags, a negative or
  * non-finite guard, or a bad camera; NGS_ERR_CAPACITY if the cuts exceed cap
- * (the offsets still hold their sizes). Synchronises the stream. */
+ * (the offsets still hold their sizes), or before any work when n_groups x
+ * (leaves of the scene) >= 2^32. Synchronises the stream. */
 #define NGS_CUT_FRUSTUM 1
 NGS_API ngs_status ngs_select_cut_shared(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                                          const int32_t *group_begin, int32_t n_groups,
@@ -224,7 +240,11 @@ NGS_API ngs_status ngs_render(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_ca
                               float *const *d_images, void *stream);
 
 /* As ngs_render, then copies each image to h_images[c] (host memory, pinned
- * or pageable) and synchronises the stream. */
+ * or pageable) and synchronises the stream. A batched render whose pairs
+ * overflowed pair_capacity is planned again from the pair counts the device
+ * reported (smaller sub-batches) and redone, up to 4 renders in all; it
+ * returns NGS_ERR_CAPACITY only if that does not suffice (for example one
+ * camera alone exceeds the capacity). */
 NGS_API ngs_status ngs_render_host(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                                    float *const *h_images, void *stream);
 
@@ -363,6 +383,10 @@ NGS_API ngs_status ngs_scan_u32(ngs_ctx *ctx, const uint32_t *d_in, uint32_t *d_
  * request per launch) and renders them as one batch; requests arriving
  * meanwhile join the next launch, and launches of different lanes overlap on
  * the device. Each request's image is the same bits as when rendered alone.
+ * A launch whose (tile, Gaussian) pairs overflow its lane's buffer does not
+ * fail its requests: the lane re-plans from the pairs the device counted,
+ * admission raises its estimate to the lane's, and the requests return to the
+ * front of the queue (a request is failed after 3 such launches).
  * The scene must not be reloaded while a server runs.
  * ------------------------------------------------------------------------ */
 typedef struct ngs_server ngs_server;
@@ -381,6 +405,7 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> completion latency */
     double mpix;                              /* megapixels of completed requests */
     double span_s;                            /* first submit -> last completion */
+    int64_t requeued;                         /* requests put back after a launch overflowed */
 } ngs_serving_stats;
 
 /* Starts the worker thread on the calling thread's current device. */
@@ -414,11 +439,20 @@ NGS_API ngs_status ngs_server_stop(ngs_server *s);
  *    that device current); make that first call before any stream capture.
  *  - Every call shares the array: calls whose work overlaps on the GPU
  *    (different streams, unordered threads) race and give undefined results.
- *  - Asynchronous on `stream`; a device-side wait that gives up is not
- *    reported by this call (its kernels still finish). */
+ *  - Asynchronous on `stream`. A device-side wait that gives up (its kernels
+ *    still finish, the result is then undefined) is latched in the array and
+ *    reported by ngs_sort_pairs_static_status(); it does not stop later calls. */
 NGS_API ngs_status ngs_sort_pairs_static(void *d_keys, uint32_t *d_vals, int64_t n,
                                          int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
                                          void *stream);
+
+/* Status of the allocation-free sort on the calling thread's current device:
+ * synchronises `stream`, then returns (and clears) the first device-side
+ * error latched by an ngs_sort_pairs_static call on this device since the
+ * previous query (NGS_OK if none, or if no call has run on the device).
+ * Allocates nothing. Query on the stream the sorts ran on, or after they
+ * completed. */
+NGS_API ngs_status ngs_sort_pairs_static_status(void *stream);
 
 #ifdef __cplusplus
 }

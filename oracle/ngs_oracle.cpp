@@ -70,10 +70,15 @@ typedef struct {
     double tau;
 } orc_camera;
 
-// per cut slot, columns of the float64 preprocess table
+// per cut slot, columns of the float64 preprocess table; PC_E* are bounds on
+// how far a float32 renderer's values may lie from these (see "float32 error
+// model" below): centre (px), the entries a, b, c of Sigma2D (px^2), the
+// relative error common to the three conic coefficients (from inverting),
+// log2 of the opacity, and the support half-widths (px)
 enum {
     PC_VISIBLE = 0, PC_U, PC_V, PC_CONIC_A, PC_CONIC_B, PC_CONIC_C, PC_COV_A, PC_COV_B,
-    PC_COV_C, PC_DEPTH, PC_OPACITY, PC_R, PC_G, PC_B, PC_HX, PC_HY, PC_NCOLS
+    PC_COV_C, PC_DEPTH, PC_OPACITY, PC_R, PC_G, PC_B, PC_HX, PC_HY,
+    PC_EU, PC_EV, PC_ESA, PC_ESB, PC_ESC, PC_ERHO, PC_EQL, PC_EHX, PC_EHY, PC_NCOLS
 };
 
 static const double kNear = 0.2;           // near plane (view z)
@@ -182,6 +187,58 @@ int64_t orc_select_cut(const orc_scene *sc, const orc_camera *cam, int32_t *ids_
     }
     return cnt;
 }
+
+// ---------------------------------------------------------------------------
+// float32 error model of a renderer (test infrastructure: which decisions a
+// float32 evaluation of steps 2 and 4 may take differently from float64)
+// ---------------------------------------------------------------------------
+//
+// A renderer that evaluates the same definitions in float32 (unit roundoff
+// u = 2^-24) differs from the float64 values of this oracle by rounding. The
+// bounds below are first-order forward error bounds: every elementary float32
+// operation (add, multiply, fused multiply-add, division, square root) is
+// charged u times the magnitude of its result, a k-term dot product k u times
+// the sum of the magnitudes of its terms, and the library functions (exp, log,
+// reciprocal square root) 4 u relative; the sums of magnitudes are evaluated
+// at the float64 values, and the terms of the T Sigma T^T products at their
+// own magnitudes. Against an independent float32 evaluation these first-order
+// bounds run 10 (centre) to 1000 (conic) times above the observed errors, so
+// no further safety factor is applied (kErrSafety = 1). No particular
+// operation order is assumed.
+//   view vector  t_r = R_r . (mu - c): 6 u sum_k |R_rk d_k| (d_k = mu_k - c_k
+//                rounded, three products, two sums)
+//   centre       u = fx t_x / t_z + cx: fx/t_z (e_tx + |t_x| (3u + e_tz/t_z)) + u |u|
+//   3D cov.      every entry of R S^2 R^T: 25 u trace(Sigma) (quaternion
+//                normalisation and rotation 8 u per entry, exp 4 u, products)
+//   J W rows     entries fx/t_z W_0 - fx t_x/t_z^2 W_2 (and the y row): each
+//                entry off by at most tau_r (from the errors of t and 1/t_z)
+//   Sigma2D      a = T_0 Sigma T_0^T + 0.3 etc.: 6 tau_r t_r s + t_r^2 (e_S + 7 u s)
+//                + u |a| with t_r = sum_j |T_rj|, s = max |Sigma_jk|
+//   conic        the conic Q = Sigma2D^-1 as (c, -b, a) / det: an error dS of
+//                Sigma2D moves d^T Q d by -w^T dS w with w = Q d; the rounding
+//                of det = a c - b^2 (2 u (a c + b^2) / det relative) and of the
+//                reciprocal scales all three coefficients alike (relative rho);
+//                each coefficient then carries 3 u of its own rounding
+//   exponent     q = A dx^2 + B dx dy + C dy^2 + log2 o (A, B, C the conic
+//                scaled by -log2(e)/2, log2(e), -log2(e)/2): log2(e)/2 w^T |dS| w
+//                + rho |q - log2 o| + 3 u (|A| dx^2 + |B dx dy| + |C| dy^2) +
+//                the centre error times |grad q| + the log2 o error, plus 10 u
+//                (|A| (|dx| + 16)^2 + |B| (|dx| + 16) |dy| + |C| dy^2 + |log2 o|)
+//                for evaluating it relative to a reference column up to 16 px
+//                from the pixel, plus 2e-6 for the hardware exp2 (relative
+//                error below 2^-20)
+//   support      h = sqrt(K a) + 1/64, K = 2 ln(255 o): (h - 1/64) (e_K/K + e_a/a)/2
+//                + 3 u h
+// A decision of step 4 is "near threshold" when the float64 value lies within
+// this bound of the threshold: alpha >= 1/255 (|log2(o G) - log2(1/255)| <=
+// E_q) and T (1 - alpha) >= 1e-4 (relative error of T accumulated from the
+// (1 - alpha) factors). Such a decision may go either way in float32. Where
+// the bound itself exceeds kEqMax (a Gaussian so elongated or so close to the
+// near plane that its float32 alpha is uncertain by more than a few percent),
+// the pixel is not enumerated but marked unchecked.
+static const double kU32 = 5.9604644775390625e-08;   // 2^-24
+static const double kErrSafety = 1.0;
+static const double kLog2e = 1.4426950408889634;
 
 // ---------------------------------------------------------------------------
 // 2. preprocess
@@ -316,6 +373,68 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
         const double K = 2.0 * std::log(255.0 * opac);
         const double hx = std::sqrt(K * a) + kRectMargin;
         const double hy = std::sqrt(K * cc) + kRectMargin;
+        // float32 error model (see above)
+        {
+            const double uu = kU32;
+            double m[3] = {0.0, 0.0, 0.0};
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k) m[r] += std::fabs(cam->R[3 * r + k] * d[k]);
+            const double etx = 6.0 * uu * m[0], ety = 6.0 * uu * m[1], etz = 6.0 * uu * m[2];
+            const double rz = etz / tz;
+            const double eu = cam->fx / tz * (etx + std::fabs(tx) * (3.0 * uu + rz)) + uu * std::fabs(u);
+            const double ev = cam->fy / tz * (ety + std::fabs(ty) * (3.0 * uu + rz)) + uu * std::fabs(v);
+            // 3D covariance entries (blended: own and parent's)
+            double tr = S[0] + S[4] + S[8];
+            const int32_t par = sc->parent[g];
+            if (blend && par >= 0) {
+                double Sp[9];
+                orc_cov3d(sc->quat + 4 * par, sc->log_scale + 3 * par, Sp);
+                tr += Sp[0] + Sp[4] + Sp[8];
+            }
+            const double eS = 25.0 * uu * tr;
+            double smax = 0.0;
+            for (int k = 0; k < 9; ++k) smax = std::max(smax, std::fabs(S[k]));
+            // rows of T = J W: bounds of the entry errors and the row sums
+            const double ax = cam->fx / tz, bx = cam->fx * std::fabs(tx) / (tz * tz);
+            const double ay = cam->fy / tz, by = cam->fy * std::fabs(ty) / (tz * tz);
+            const double tau0 = ax * (2.0 * uu + rz) +
+                                cam->fx / (tz * tz) * (5.0 * uu * std::fabs(tx) + etx + 2.0 * std::fabs(tx) * rz) +
+                                2.0 * uu * (ax + bx);
+            const double tau1 = ay * (2.0 * uu + rz) +
+                                cam->fy / (tz * tz) * (5.0 * uu * std::fabs(ty) + ety + 2.0 * std::fabs(ty) * rz) +
+                                2.0 * uu * (ay + by);
+            // magnitudes of the terms of T Sigma T^T: M[r][c] = sum_jk |T_rj| |S_jk| |T_ck|,
+            // and with one T row replaced by ones (for the T errors)
+            double t0 = 0.0, t1 = 0.0, M00 = 0.0, M01 = 0.0, M11 = 0.0, N0 = 0.0, N1 = 0.0;
+            for (int k = 0; k < 3; ++k) { t0 += std::fabs(T[k]); t1 += std::fabs(T[3 + k]); }
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const double sjk = std::fabs(S[3 * j + k]);
+                    M00 += std::fabs(T[j]) * sjk * std::fabs(T[k]);
+                    M01 += std::fabs(T[j]) * sjk * std::fabs(T[3 + k]);
+                    M11 += std::fabs(T[3 + j]) * sjk * std::fabs(T[3 + k]);
+                    N0 += sjk * std::fabs(T[k]);
+                    N1 += sjk * std::fabs(T[3 + k]);
+                }
+            (void)smax;
+            const double ea = 2.0 * tau0 * N0 + t0 * t0 * eS + 7.0 * uu * M00 + uu * a;
+            const double ec = 2.0 * tau1 * N1 + t1 * t1 * eS + 7.0 * uu * M11 + uu * cc;
+            const double eb = tau0 * N1 + tau1 * N0 + t0 * t1 * eS + 7.0 * uu * M01 +
+                              uu * std::fabs(b);
+            // relative error common to the conic coefficients: det's rounding, the
+            // reciprocal and the scaling by log2(e)
+            const double rho = 2.0 * uu * (a * cc + b * b) / det + 3.0 * uu;
+            const double eql = 8.0 * uu * std::max(1.0, std::fabs(std::log2(opac)));
+            // support half-widths
+            const double eK = 2.0 * 6.0 * uu * std::max(1.0, std::fabs(std::log(255.0 * opac)));
+            const double ehx = 0.5 * (hx - kRectMargin) * (eK / K + ea / a) + 3.0 * uu * hx;
+            const double ehy = 0.5 * (hy - kRectMargin) * (eK / K + ec / cc) + 3.0 * uu * hy;
+            o[PC_EU] = kErrSafety * eu; o[PC_EV] = kErrSafety * ev;
+            o[PC_ESA] = kErrSafety * ea; o[PC_ESB] = kErrSafety * eb;
+            o[PC_ESC] = kErrSafety * ec; o[PC_ERHO] = kErrSafety * rho;
+            o[PC_EQL] = kErrSafety * eql;
+            o[PC_EHX] = kErrSafety * ehx; o[PC_EHY] = kErrSafety * ehy;
+        }
         int32_t x0 = (int32_t)std::floor((u - hx) / tile_w);
         int32_t x1 = (int32_t)std::floor((u + hx) / tile_w);
         int32_t y0 = (int32_t)std::floor((v - hy) / tile_h);
@@ -394,35 +513,122 @@ void orc_bin_pairs(const int32_t *rect, const uint32_t *depth_key, int64_t n, in
 // 4./5. compositing
 // ---------------------------------------------------------------------------
 
-// Blends the Gaussians list[0..len) (slots into the preprocess table, front to
-// back) at pixel centre (px, py). Returns the flag: 1 when the result may
-// differ from a float32 evaluation by more than rounding, i.e. some Gaussian
-// met while T >= 0.02 had alpha within 2e-4 relative of the 1/255 cut-off.
-static int blend_pixel(const double *pre, const uint32_t *list, int64_t len, double px, double py,
-                       double *rgb_out, int64_t *n_used) {
-    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
-    int flag = 0;
-    int64_t used = 0;
-    for (int64_t k = 0; k < len; ++k) {
+// Bound E_q on how far a float32 renderer's exponent q = log2(o G) of
+// Gaussian g at the pixel offset (dx, dy) may lie from the float64 value (the
+// error model above; g's error columns are filled by the preprocess).
+static double exponent_error(const double *g, double dx, double dy) {
+    const double A = -0.5 * kLog2e * g[PC_CONIC_A], B = -kLog2e * g[PC_CONIC_B];
+    const double C = -0.5 * kLog2e * g[PC_CONIC_C];
+    const double L = std::log2(g[PC_OPACITY]);
+    // w = Q d: how d^T Q d moves with the entries of Sigma2D
+    const double w0 = g[PC_CONIC_A] * dx + g[PC_CONIC_B] * dy;
+    const double w1 = g[PC_CONIC_B] * dx + g[PC_CONIC_C] * dy;
+    const double e_cov = 0.5 * kLog2e *
+                         (w0 * w0 * g[PC_ESA] + 2.0 * std::fabs(w0 * w1) * g[PC_ESB] +
+                          w1 * w1 * g[PC_ESC]);
+    const double quad = std::fabs(A) * dx * dx + std::fabs(B * dx * dy) + std::fabs(C) * dy * dy;
+    const double qmL = std::fabs(A * dx * dx + B * dx * dy + C * dy * dy);
+    const double ax = std::fabs(dx) + 16.0, ay = std::fabs(dy);
+    const double W = std::fabs(A) * ax * ax + std::fabs(B) * ax * ay + std::fabs(C) * ay * ay +
+                     std::fabs(L);
+    return e_cov + g[PC_ERHO] * qmL + kErrSafety * 3.0 * kU32 * quad + g[PC_EQL] +
+           std::fabs(2.0 * A * dx + B * dy) * g[PC_EU] +
+           std::fabs(B * dx + 2.0 * C * dy) * g[PC_EV] + kErrSafety * 10.0 * kU32 * W + 2e-6;
+}
+
+static const double kLog2AlphaMin = -7.9943534368588578;   // log2(1/255)
+static const double kEqMax = 2.0;                           // log2 units: a factor 4 in alpha
+
+// exponent_error for one preprocess row (exported for the tests that pin it)
+double orc_exponent_error(const double *g, double dx, double dy) {
+    return exponent_error(g, dx, dy);
+}
+
+// One front-to-back walk of a pixel's list (step 4), in float64, from list
+// position k with transmittance T (relative float32 error bound relT) and
+// colour C. At position k the threshold and stop decisions may be forced
+// (force_pass / force_stop: -1 = take the float64 decision, 0/1 = the given
+// outcome). When `alts` is given, every near-threshold decision met on the way
+// also spawns the walk that takes it the other way, and every walk appends its
+// final colour to *alts (at most max_alts; *overflow is set beyond that).
+// Returns the number of near-threshold decisions met on this walk.
+static int walk_pixel(const double *pre, const uint32_t *list, int64_t len, int64_t k, double px,
+                      double py, double T, double relT, const double *C0, int force_pass,
+                      int force_stop, std::vector<double> *alts, int max_alts, bool *overflow,
+                      double *rgb_out, bool *unchecked) {
+    double C[3] = {C0[0], C0[1], C0[2]};
+    int near = 0;
+    for (; k < len; ++k) {
         const double *g = pre + (int64_t)list[k] * PC_NCOLS;
         const double dx = px - g[PC_U], dy = py - g[PC_V];
         const double power = -0.5 * (g[PC_CONIC_A] * dx * dx + g[PC_CONIC_C] * dy * dy) -
                              g[PC_CONIC_B] * dx * dy;
         const double a = g[PC_OPACITY] * std::exp(power);
-        if (T >= 0.02 && std::fabs(std::log(255.0 * a)) <= 2e-4) flag = 1;
-        const double alpha = std::min(kAlphaMax, a);
-        if (alpha < kAlphaMin) continue;
+        const double q = a > 0.0 ? std::log2(a) : -INFINITY;
+        const double eq = exponent_error(g, dx, dy);
+        bool pass = a >= kAlphaMin;
+        if (force_pass >= 0) {
+            pass = force_pass != 0;
+        } else if (std::fabs(q - kLog2AlphaMin) <= eq) {
+            if (eq > kEqMax) {
+                if (unchecked) *unchecked = true;
+            } else {
+                ++near;
+                if (alts) walk_pixel(pre, list, len, k, px, py, T, relT, C, pass ? 0 : 1, -1,
+                                     alts, max_alts, overflow, nullptr, unchecked);
+            }
+        }
+        force_pass = -1;
+        if (!pass) {
+            force_stop = -1;
+            continue;
+        }
+        // a Gaussian taken against its float64 decision has alpha at the threshold
+        const double alpha = std::max(std::min(kAlphaMax, a), a < kAlphaMin ? kAlphaMin : 0.0);
         const double test_T = T * (1.0 - alpha);
-        if (test_T < kTMin) break;
+        // relative float32 error of T (1 - alpha): T's, alpha's through 1 - alpha, rounding
+        const double rel = relT + alpha * M_LN2 * eq / (1.0 - alpha) + 2.0 * kU32;
+        bool stop = test_T < kTMin;
+        if (force_stop >= 0) {
+            stop = force_stop != 0;
+        } else if (std::fabs(test_T - kTMin) <= kTMin * rel) {
+            ++near;
+            if (alts) walk_pixel(pre, list, len, k, px, py, T, relT, C, 1, stop ? 0 : 1, alts,
+                                 max_alts, overflow, nullptr, unchecked);
+        }
+        force_stop = -1;
+        if (stop) break;
         C[0] += alpha * T * g[PC_R];
         C[1] += alpha * T * g[PC_G];
         C[2] += alpha * T * g[PC_B];
         T = test_T;
-        ++used;
+        relT = rel;
     }
-    rgb_out[0] = C[0]; rgb_out[1] = C[1]; rgb_out[2] = C[2];
-    if (n_used) *n_used = used;
-    return flag;
+    if (alts) {
+        if ((int)(alts->size() / 3) < max_alts) {
+            alts->push_back(C[0]); alts->push_back(C[1]); alts->push_back(C[2]);
+        } else {
+            *overflow = true;
+        }
+    }
+    if (rgb_out) { rgb_out[0] = C[0]; rgb_out[1] = C[1]; rgb_out[2] = C[2]; }
+    return near;
+}
+
+// Blends the Gaussians list[0..len) (slots into the preprocess table, front to
+// back) at pixel centre (px, py), every decision in float64. Returns the flag:
+// 1 when some threshold or stop decision on the way was near threshold (a
+// float32 renderer may take it the other way; orc_alternatives lists the
+// outcomes), 2 when a near-threshold decision's bound exceeded kEqMax (the
+// outcomes are not enumerated), else 0.
+static int blend_pixel(const double *pre, const uint32_t *list, int64_t len, double px, double py,
+                       double *rgb_out, int64_t *n_used) {
+    const double zero[3] = {0.0, 0.0, 0.0};
+    bool unchecked = false;
+    const int near = walk_pixel(pre, list, len, 0, px, py, 1.0, 0.0, zero, -1, -1, nullptr, 0,
+                                nullptr, rgb_out, &unchecked);
+    if (n_used) *n_used = 0;
+    return unchecked ? 2 : near > 0 ? 1 : 0;
 }
 
 // Tiled compositing. image: [3][H][W] float64, flags: [H][W].
@@ -467,6 +673,43 @@ void orc_render_bruteforce(const double *pre, const uint32_t *depth_key, int64_t
         out[3 * p] = rgb[0]; out[3 * p + 1] = rgb[1]; out[3 * p + 2] = rgb[2];
         if (flags) flags[p] = (uint8_t)f;
     }
+}
+
+// Every outcome of the near-threshold decisions of the tiled compositing at
+// the pixels pix[0..npix) ((x, y) integer pairs): for pixel p, n_out[p]
+// outcomes (the float64 walk and each combination of near-threshold decisions
+// taken the other way, as its walks meet them) in out[p][0..n_out[p])[3]; at
+// most max_out, n_out[p] = max_out + 1 when there were more (out holds the
+// first max_out). n_out[p] is negated when some decision's bound exceeded
+// kEqMax (that decision was taken the float64 way only: unchecked).
+void orc_alternatives(const double *pre, const uint32_t *vals, const int64_t *ranges,
+                      int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                      const int32_t *pix, int64_t npix, int32_t max_out, double *out,
+                      int32_t *n_out) {
+    const int32_t tiles_x = (width + tile_w - 1) / tile_w;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npix; ++p) {
+        const int32_t x = pix[2 * p], y = pix[2 * p + 1];
+        const int64_t t = (int64_t)(y / tile_h) * tiles_x + x / tile_w;
+        const int64_t r0 = ranges[2 * t], r1 = ranges[2 * t + 1];
+        std::vector<double> alts;
+        bool overflow = false, unchecked = false;
+        const double zero[3] = {0.0, 0.0, 0.0};
+        walk_pixel(pre, vals + r0, r1 - r0, 0, x + 0.5, y + 0.5, 1.0, 0.0, zero, -1, -1, &alts,
+                   max_out, &overflow, nullptr, &unchecked);
+        const int n = (int)(alts.size() / 3);
+        for (int k = 0; k < 3 * n; ++k) out[(int64_t)p * max_out * 3 + k] = alts[k];
+        n_out[p] = overflow ? max_out + 1 : n;
+        if (unchecked) n_out[p] = -n_out[p];
+    }
+}
+
+// The float64 view depth of a mean: R_2 . (mu - c) (the depth that orders
+// Gaussians front to back; no rounding beyond float64).
+double orc_view_depth64(const float *mu, const orc_camera *cam) {
+    double z = 0.0;
+    for (int k = 0; k < 3; ++k) z += cam->R[6 + k] * ((double)mu[k] - cam->pos[k]);
+    return z;
 }
 
 // ---------------------------------------------------------------------------
@@ -769,6 +1012,16 @@ int32_t orc_num_threads(void) {
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+// Threads of the parallel loops from now on (n >= 1; used to time the oracle
+// single-threaded and on every core).
+void orc_set_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }
 

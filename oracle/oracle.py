@@ -25,7 +25,9 @@ import numpy as np
 from . import build as _build
 
 PC = SimpleNamespace(VISIBLE=0, U=1, V=2, CONIC_A=3, CONIC_B=4, CONIC_C=5, COV_A=6, COV_B=7,
-                     COV_C=8, DEPTH=9, OPACITY=10, R=11, G=12, B=13, HX=14, HY=15, NCOLS=16)
+                     COV_C=8, DEPTH=9, OPACITY=10, R=11, G=12, B=13, HX=14, HY=15,
+                     EU=16, EV=17, ESA=18, ESB=19, ESC=20, ERHO=21, EQL=22, EHX=23, EHY=24,
+                     NCOLS=25)
 
 
 class _Scene(C.Structure):
@@ -78,7 +80,15 @@ def lib():
             L.orc_cov3d.argtypes = [vp, vp, vp]
             L.orc_depth_f32.restype = C.c_float
             L.orc_depth_f32.argtypes = [vp, C.POINTER(_Camera)]
+            L.orc_exponent_error.restype = C.c_double
+            L.orc_exponent_error.argtypes = [vp, C.c_double, C.c_double]
+            L.orc_view_depth64.restype = C.c_double
+            L.orc_view_depth64.argtypes = [vp, C.POINTER(_Camera)]
+            L.orc_alternatives.restype = None
+            L.orc_alternatives.argtypes = [vp, vp, vp, i32, i32, i32, i32, vp, i64, i32, vp, vp]
             L.orc_num_threads.restype = i32
+            L.orc_set_threads.restype = None
+            L.orc_set_threads.argtypes = [i32]
             L.orc_slice_params.restype = None
             L.orc_slice_params.argtypes = [vp, vp, vp]
             L.orc_slice_value.restype = C.c_double
@@ -227,7 +237,10 @@ def bin_pairs(rect, key, cam, tile=(16, 16)):
 
 
 def composite_tiled(pre, vals, ranges, cam, tile=(16, 16)):
-    """Image [3, H, W] float64 and per-pixel near-discontinuity flags [H, W]."""
+    """Image [3, H, W] float64 (every decision in float64) and per-pixel flags
+    [H, W]: 1 where some threshold or stop decision was near threshold (a
+    float32 renderer may take it the other way; ``alternatives`` lists the
+    outcomes)."""
     H, W = int(cam.height), int(cam.width)
     img = np.empty((3, H, W), dtype=np.float64)
     flags = np.empty((H, W), dtype=np.uint8)
@@ -237,6 +250,25 @@ def composite_tiled(pre, vals, ranges, cam, tile=(16, 16)):
     lib().orc_composite_tiled(_p(pre), _p(vals), _p(ranges), W, H, int(tile[0]), int(tile[1]),
                               _p(img), _p(flags))
     return img, flags
+
+
+def alternatives(pre, vals, ranges, cam, pixels, tile=(16, 16), max_out=64):
+    """Every outcome of the near-threshold decisions of the tiled compositing
+    at ``pixels`` ((n, 2) integer (x, y)): (rgb [n, max_out, 3] float64,
+    count [n] int32; count = max_out + 1 when there were more outcomes, and
+    negative when a decision's error bound was too large to enumerate)."""
+    pixels = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+    n = len(pixels)
+    out = np.zeros((n, max_out, 3), dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.int32)
+    if n:
+        pre = np.ascontiguousarray(pre, dtype=np.float64)
+        vals = np.ascontiguousarray(vals, dtype=np.uint32)
+        ranges = np.ascontiguousarray(ranges, dtype=np.int64)
+        lib().orc_alternatives(_p(pre), _p(vals), _p(ranges), int(cam.width), int(cam.height),
+                               int(tile[0]), int(tile[1]), _p(pixels), n, int(max_out), _p(out),
+                               _p(cnt))
+    return out, cnt
 
 
 def render_bruteforce(pre, key, pixels=None, cam=None):
@@ -268,7 +300,7 @@ def render(scene, cam, tile=(16, 16), ids=None, blend=False):
     keys, vals, ranges = bin_pairs(rect, key, cam, tile)
     img, flags = composite_tiled(pre, vals, ranges, cam, tile)
     return SimpleNamespace(ids=ids, near=near, pre=pre, key=key, rect=rect, keys=keys, vals=vals,
-                           ranges=ranges, image=img, flags=flags, tile=tuple(tile))
+                           ranges=ranges, image=img, flags=flags, tile=tuple(tile), cam=cam)
 
 
 def sh_basis(dirs):
@@ -288,6 +320,20 @@ def cov3d(quat, log_scale):
     for i in range(len(quat)):
         L.orc_cov3d(_p(quat[i]), _p(log_scale[i]), out[i].ctypes.data_as(C.c_void_p))
     return out
+
+
+def exponent_error(row, dx, dy):
+    """Bound on a float32 renderer's error in log2(o G) of the Gaussian of
+    preprocess row ``row`` at pixel offset (dx, dy) (the oracle's float32 error
+    model)."""
+    row = np.ascontiguousarray(row, dtype=np.float64)
+    return float(lib().orc_exponent_error(_p(row), float(dx), float(dy)))
+
+
+def view_depth64(mu, cam):
+    """The float64 view depth R_2 . (mu - c) of one mean (no float32 step)."""
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    return float(lib().orc_view_depth64(_p(mu), C.byref(camera_struct(cam))))
 
 
 def depth_f32(mu, cam):
@@ -385,8 +431,14 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on."""
+    lib().orc_set_threads(int(n))
+
+
 __all__ = ["PC", "SceneArrays", "camera_struct", "select_cut", "preprocess", "bin_pairs",
            "composite_tiled", "render_bruteforce", "render", "sh_basis", "cov3d", "depth_f32",
-           "tiles_xy", "num_threads", "lib", "granularity_f32", "blend_parent_weight",
+           "view_depth64", "alternatives", "exponent_error",
+           "tiles_xy", "num_threads", "set_threads", "lib", "granularity_f32", "blend_parent_weight",
            "blend_gaussian", "slice_params", "slice_value", "slice_occupancy", "nav_blocked",
            "nav_field", "nav_path", "frustum_state", "select_cut_shared"]

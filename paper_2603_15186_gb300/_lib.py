@@ -16,6 +16,7 @@ NGS_OPT_BLOCK_CULL = 7
 NGS_OPT_CTA_W, NGS_OPT_CTA_H = 8, 9
 NGS_OPT_PAIRS_PER_PIXEL = 10
 NGS_OPT_LOD_BLEND = 11
+NGS_OPT_COMPOSITE_ORDER = 12
 # (binning tile, compositing block) candidates of ngs_autotune, in its order
 TUNE_SHAPES = [((8, 8), (8, 8)), ((16, 8), (16, 8)), ((16, 16), (16, 16)), ((16, 32), (16, 32)),
                ((32, 16), (32, 16)), ((32, 32), (32, 32)), ((16, 16), (16, 8)),
@@ -30,7 +31,8 @@ STAGES = ["cut_preprocess", "gather_keys", "depth_hist", "depth_pass0", "depth_p
 EXPORTS = ["ngs_strerror", "ngs_create", "ngs_destroy", "ngs_set_option", "ngs_load_scene",
            "ngs_select_cut", "ngs_render", "ngs_render_host", "ngs_synchronize",
            "ngs_last_stats", "ngs_stage_times", "ngs_debug_tile_lists", "ngs_sort_pairs",
-           "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_autotune", "ngs_server_start",
+           "ngs_scan_u32", "ngs_sort_pairs_static", "ngs_sort_pairs_static_status",
+           "ngs_autotune", "ngs_server_start",
            "ngs_server_submit", "ngs_server_poll", "ngs_server_wait_all", "ngs_server_stats",
            "ngs_server_stop", "ngs_selftest_wait_timeout", "ngs_slice_occupancy",
            "ngs_nav_fields", "ngs_nav_paths", "ngs_select_cut_shared"]
@@ -89,7 +91,7 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("launches", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("max_ms", C.c_double), ("mpix", C.c_double),
-                ("span_s", C.c_double)]
+                ("span_s", C.c_double), ("requeued", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -98,7 +100,8 @@ class Stats(C.Structure):
                 ("evaluations", C.c_int64), ("sub_batches", C.c_int32),
                 ("graph_replayed", C.c_int32), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
                 ("batch", C.c_int32), ("mode", C.c_int32), ("kernels", C.c_int32),
-                ("cta_w", C.c_int32), ("cta_h", C.c_int32), ("reserved", C.c_int32)]
+                ("cta_w", C.c_int32), ("cta_h", C.c_int32), ("reserved", C.c_int32),
+                ("composite_tail_ms", C.c_double), ("candidate_total", C.c_int64)]
 
 
 _lib = None
@@ -148,6 +151,8 @@ def load(build_if_missing: bool = True):
     L.ngs_sort_pairs.argtypes = [vp, vp, vp, i64, i32, i32, i32, vp]
     L.ngs_sort_pairs_static.restype = i32
     L.ngs_sort_pairs_static.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    L.ngs_sort_pairs_static_status.restype = i32
+    L.ngs_sort_pairs_static_status.argtypes = [vp]
     L.ngs_nav_fields.restype = i32
     L.ngs_nav_fields.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, vp, i32, vp, vp, vp]
     L.ngs_nav_paths.restype = i32

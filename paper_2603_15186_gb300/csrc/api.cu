@@ -25,6 +25,8 @@ constexpr int kMaxCamsPerBatch = 1024;
 constexpr int kCutBlockedMinCams = 4;
 constexpr int kMaxCamsPerCall = 1 << 16;
 constexpr int kTuneShapes = NGS_TUNE_SHAPES;
+// renders of one ngs_render_host call after a pair-buffer overflow
+constexpr int kCapacityRetries = 4;
 
 struct SubBatch {
     int c0, c1;          // cameras [c0, c1)
@@ -74,6 +76,7 @@ struct ngs_ctx {
     bool use_graph = true;
     bool block_cull = true;
     bool lod_blend = false;            // level-of-detail blending toward parents
+    bool composite_order = true;       // batched compositing takes tiles longest list first
     SceneDev scene;
     bool loaded = false;
     bool owns_scene = true;           // false for serving lanes sharing a scene
@@ -167,15 +170,18 @@ __global__ void k_wait_probe(const uint64_t *status, const uint32_t *epoch_ptr, 
     look_back(status, 1, 1, *epoch_ptr + kEpochStride - 1, &prev, err);
 }
 
+// per sub-batch: cut, visible and pair totals, and the cut + preprocess
+// candidates (slots allocated, the low word of the 64-bit counter)
 __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
     if (threadIdx.x < 3) stats[threadIdx.x] = counters[threadIdx.x];
+    if (threadIdx.x == 3) stats[3] = counters[CNT_ALLOC];
 }
 
 void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
     dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.group_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.rect_sorted); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
-    dfree(w.hist); dfree(w.cams); dfree(w.work64);
+    dfree(w.hist); dfree(w.cams); dfree(w.work64); dfree(w.order);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
     }
@@ -297,7 +303,8 @@ ngs_status ensure_work(ngs_ctx *c) {
     A(dalloc(&c->cut_groups, kMaxCamsPerBatch + 1));
     A(dalloc(&c->cut_counts, (size_t)(nblk * kMaxCamsPerBatch)));
     A(dalloc(&c->cut_poff, (size_t)(nblk * kMaxCamsPerBatch)));
-    A(dalloc(&w.work64, 2));
+    A(dalloc(&w.work64, kWork64Words));
+    A(dalloc(&w.order, (size_t)w.ranges_cap));
     if (st != NGS_OK) {
         free_work(c);
         return st;
@@ -503,21 +510,25 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     const int cgrid = (int)std::min<int64_t>(
         items, (int64_t)c->num_sms *
                    std::max(1, composite_blocks_per_sm(c->scene.attr_dtype, cw, ch, c->batch)));
+    if (c->composite_order) launch_tile_order(w.ranges, sb.n_tiles, w.order, w.err, st);
     launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, cw, ch, c->batch, true, cams, nc,
                      sb.n_tiles, w.ranges, w.pval[psel], w.rec, w.counters + TK_COMPOSITE,
-                     std::max(cgrid, 1), w.err, w.work64, st);
+                     std::max(cgrid, 1), w.err, w.work64,
+                     c->composite_order ? w.order : nullptr,
+                     sb_index < kTailSlots ? w.work64 + 2 + 2 * sb_index : nullptr, st);
     mark(c, sb_index, MK_COMPOSITE, st);
     if (sb_index < c->stats_cap / 4)
         k_copy_stats<<<1, 32, 0, st>>>(w.counters, c->stats_dev + 4 * sb_index);
 }
 
-int kernels_of(const SubBatch &sb, bool batched) {
+int kernels_of(const SubBatch &sb, bool batched, bool order) {
     // epoch bump, live partitions, fused cut + preprocess, partition scan and
     // key gather (which also counts the depth histograms); depth sort (digit
     // scan, 4 passes); pair offsets, duplication; tile sort (digit scan and
     // passes, the last one writing the tile ranges) or, with a single tile,
     // the ranges kernel; compositing; and in the batched path the stats copy
-    return 5 + 5 + 2 + (sb.tile_passes > 0 ? 1 + sb.tile_passes : 1) + 1 + (batched ? 1 : 0);
+    return 5 + 5 + 2 + (sb.tile_passes > 0 ? 1 + sb.tile_passes : 1) + 1 + (batched ? 1 : 0) +
+           (batched && order ? 1 : 0);
 }
 
 ngs_status read_u32(const uint32_t *d, uint32_t *h, cudaStream_t st) {
@@ -536,6 +547,28 @@ ngs_status check_err(ngs_ctx *c) {
     return NGS_OK;
 }
 
+// Raises the planner's pairs-per-pixel estimate to 1.25x the densest
+// sub-batch of the last batched render (pairs counted by the device, also when
+// they overflowed the buffer), so that the next plan of the same cameras fits.
+// Synchronous (reads the per-sub-batch counts).
+ngs_status learn_pair_density(ngs_ctx *c) {
+    if (c->mode != NGS_MODE_BATCHED || c->last_plan.empty() || !c->work_ready) return NGS_OK;
+    const int n = std::min<int>((int)c->last_plan.size(), c->stats_cap / 4);
+    std::vector<uint32_t> h((size_t)4 * std::max(n, 1));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(h.data(), c->stats_dev, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost));
+    double dens = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const SubBatch &sb = c->last_plan[i];
+        int64_t pix = 0;
+        for (int k = sb.c0; k < sb.c1 && k < (int)c->host_cams.size(); ++k)
+            pix += (int64_t)c->host_cams[k].width * c->host_cams[k].height;
+        if (pix > 0) dens = std::max(dens, (double)h[4 * i + 2] / (double)pix);
+    }
+    c->pairs_per_pixel = std::min(4096.0, std::max(c->pairs_per_pixel, 1.25 * dens));
+    return NGS_OK;
+}
+
 // Plain per-view path: one camera at a time, every stage sized from counts
 // read back to the host, one CTA per partition, no graph.
 ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
@@ -544,7 +577,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
     int64_t cut_tot = 0, vis_tot = 0, pair_tot = 0;
     ngs_status es0 = ensure_events(c, n_cams);
     if (es0 != NGS_OK) return es0;
-    CK(cudaMemsetAsync(w.work64, 0, 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(w.work64, 0, kWork64Words * sizeof(unsigned long long), st));
     c->kernels_per_render = 0;
     for (int ci = 0; ci < n_cams; ++ci) {
         SubBatch sb{ci, ci + 1, 0, 0};
@@ -643,10 +676,10 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         launch_composite(c->scene.attr_dtype, c->tile_w, c->tile_h, cw, ch, c->batch, false,
                          cams, 1, sb.n_tiles, w.ranges, w.pval[psel], w.rec,
                          w.counters + TK_COMPOSITE, (int)std::max<uint32_t>(items, 1), w.err,
-                         w.work64, st);
+                         w.work64, nullptr, nullptr, st);
         mark(c, ci, MK_COMPOSITE, st);
         CK(cudaGetLastError());
-        c->kernels_per_render += kernels_of(sb, false);
+        c->kernels_per_render += kernels_of(sb, false, false);
         cut_tot += n_cut; vis_tot += n_vis; pair_tot += n_pairs;
         c->last_plan.push_back(sb);
         c->last_plan.back().c0 = ci;
@@ -657,6 +690,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
     c->stats.pair_total = pair_tot;
     c->stats.sub_batches = n_cams;
     c->stats.graph_replayed = 0;
+    c->stats.candidate_total = -1;
     return NGS_OK;
 }
 
@@ -670,6 +704,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     key.push_back(c->batch); key.push_back((int64_t)c->scene_version);
     key.push_back(cta_w_of(c)); key.push_back(cta_h_of(c));
     key.push_back(c->lod_blend ? 1 : 0);
+    key.push_back(c->composite_order ? 1 : 0);
     for (int i = 0; i < n_cams; ++i) {
         key.push_back(c->host_cams[i].width);
         key.push_back(c->host_cams[i].height);
@@ -680,7 +715,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     if ((es = ensure_events(c, (int)sbs.size())) != NGS_OK) return es;
     key.push_back(c->timing ? 1 : 0);
     c->kernels_per_render = 0;
-    for (const SubBatch &sb : sbs) c->kernels_per_render += kernels_of(sb, true);
+    for (const SubBatch &sb : sbs) c->kernels_per_render += kernels_of(sb, true, c->composite_order);
     CK(cudaMemcpyAsync(w.cams, c->host_cams.data(), sizeof(DevCamera) * n_cams,
                        cudaMemcpyHostToDevice, st));
     if (c->use_graph) {
@@ -688,7 +723,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
             drop_graph(c);
             if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaMemsetAsync(w.work64, 0, 2 * sizeof(unsigned long long), c->cap_stream);
+            cudaMemsetAsync(w.work64, 0, kWork64Words * sizeof(unsigned long long), c->cap_stream);
             for (size_t i = 0; i < sbs.size(); ++i) enqueue_batched(c, sbs[i], (int)i, c->cap_stream);
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -709,7 +744,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
         }
         CK(cudaGraphLaunch(c->gexec, st));
     } else {
-        CK(cudaMemsetAsync(w.work64, 0, 2 * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(w.work64, 0, kWork64Words * sizeof(unsigned long long), st));
         for (size_t i = 0; i < sbs.size(); ++i) enqueue_batched(c, sbs[i], (int)i, st);
         c->stats.graph_replayed = 0;
     }
@@ -717,6 +752,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     c->last_plan = sbs;
     c->stats.sub_batches = (int32_t)sbs.size();
     c->stats.cut_total = c->stats.visible_total = c->stats.pair_total = -1;  // filled on demand
+    c->stats.candidate_total = -1;
     c->stats_pending = true;
     return NGS_OK;
 }
@@ -808,8 +844,12 @@ ngs_status ngs::lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pa
     l->use_graph = false;   // every launch has a different camera mix
     l->block_cull = parent->block_cull;
     l->lod_blend = parent->lod_blend;
+    l->composite_order = parent->composite_order;
+    l->pairs_per_pixel = parent->pairs_per_pixel;
     return NGS_OK;
 }
+
+double ngs::ctx_pairs_per_pixel(const ngs_ctx *c) { return c->pairs_per_pixel; }
 
 extern "C" {
 
@@ -937,6 +977,10 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         return NGS_OK;
     case NGS_OPT_LOD_BLEND:
         c->lod_blend = v != 0;
+        drop_graph(c);
+        return NGS_OK;
+    case NGS_OPT_COMPOSITE_ORDER:
+        c->composite_order = v != 0;
         drop_graph(c);
         return NGS_OK;
     }
@@ -1067,6 +1111,11 @@ NGS_API ngs_status ngs_select_cut(ngs_ctx *c, const ngs_camera *cams, int32_t n_
         return NGS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (!camera_ok(cams[i])) return NGS_ERR_INVALID_ARG;
+    // a cut is an antichain of the tree (at most one id per leaf): below this
+    // bound the 32-bit offsets cannot wrap
+    if ((int64_t)n_cams * std::max<int64_t>(c->scene.n_leaves, 1) >= ((int64_t)1 << 32))
+        return NGS_ERR_CAPACITY;
+    cudaSetDevice(c->device);
     ngs_status s = ensure_work(c);
     if (s != NGS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1119,6 +1168,8 @@ NGS_API ngs_status ngs_select_cut_shared(ngs_ctx *c, const ngs_camera *cams, int
         if (group_begin[g + 1] <= group_begin[g]) return NGS_ERR_INVALID_ARG;
     for (int i = 0; i < n_cams; ++i)
         if (!camera_ok(cams[i])) return NGS_ERR_INVALID_ARG;
+    if ((int64_t)n_groups * std::max<int64_t>(c->scene.n_leaves, 1) >= ((int64_t)1 << 32))
+        return NGS_ERR_CAPACITY;
     cudaSetDevice(c->device);
     ngs_status s = ensure_work(c);
     if (s != NGS_OK) return s;
@@ -1166,6 +1217,7 @@ NGS_API ngs_status ngs_selftest_wait_timeout(ngs_ctx *c, void *stream) {
 
 NGS_API ngs_status ngs_synchronize(ngs_ctx *c, void *stream) {
     if (!c) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     if (c->latched != NGS_OK) {
         ngs_status s = c->latched;
@@ -1173,7 +1225,11 @@ NGS_API ngs_status ngs_synchronize(ngs_ctx *c, void *stream) {
         return s;
     }
     if (!c->work_ready) return NGS_OK;
-    return check_err(c);
+    const ngs_status s = check_err(c);
+    // a batched render that overflowed the pair buffer: the next plan of the
+    // same cameras uses the densities the device counted
+    if (s == NGS_ERR_CAPACITY) learn_pair_density(c);
+    return s;
 }
 
 NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
@@ -1203,7 +1259,16 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n
         off += (size_t)3 * cams[i].width * cams[i].height;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    ngs_status s = render_common(c, cams, n_cams, dimg.data(), st);
+    // a batched render whose pairs overflow the buffer is planned again from
+    // the densities the device counted (smaller sub-batches) and redone
+    ngs_status s = NGS_OK;
+    for (int attempt = 0; attempt < kCapacityRetries; ++attempt) {
+        s = render_common(c, cams, n_cams, dimg.data(), st);
+        if (s != NGS_OK) return s;
+        if (c->mode != NGS_MODE_BATCHED) break;
+        s = ngs_synchronize(c, stream);
+        if (s != NGS_ERR_CAPACITY) break;
+    }
     if (s != NGS_OK) return s;
     for (int i = 0; i < n_cams; ++i)
         CK(cudaMemcpyAsync(h_images[i], dimg[i], sizeof(float) * 3 * cams[i].width * cams[i].height,
@@ -1213,12 +1278,21 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n
 
 NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
     if (!c || !out) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
     if (c->work_ready) {
-        unsigned long long w64[2] = {0, 0};
+        unsigned long long w64[kWork64Words] = {};
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(w64, c->w.work64, sizeof(w64), cudaMemcpyDeviceToHost));
         c->stats.records_staged = (int64_t)w64[0];
         c->stats.evaluations = (int64_t)w64[1];
+        // per sub-batch: ~(first CTA to find the queue empty), last CTA's end
+        double tail = 0.0;
+        if (c->mode == NGS_MODE_BATCHED)
+            for (int k = 0; k < kTailSlots && k < (int)c->last_plan.size(); ++k) {
+                const unsigned long long t0 = ~w64[2 + 2 * k], t1 = w64[3 + 2 * k];
+                if (w64[2 + 2 * k] && t1 >= t0) tail += (double)(t1 - t0) * 1e-6;
+            }
+        c->stats.composite_tail_ms = tail;
     }
     c->stats.kernels = c->kernels_per_render;
     if (c->stats_pending && c->work_ready) {
@@ -1227,13 +1301,15 @@ NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {
         const int n = std::min<int>((int)c->last_plan.size(), c->stats_cap / 4);
         std::vector<uint32_t> h((size_t)4 * std::max(n, 1));
         CK(cudaMemcpy(h.data(), c->stats_dev, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost));
-        int64_t a = 0, b = 0, p = 0;
-        for (int i = 0; i < n; ++i) { a += h[4 * i]; b += h[4 * i + 1]; p += h[4 * i + 2]; }
+        int64_t a = 0, b = 0, p = 0, q = 0;
+        for (int i = 0; i < n; ++i) {
+            a += h[4 * i]; b += h[4 * i + 1]; p += h[4 * i + 2]; q += h[4 * i + 3];
+        }
         c->stats.cut_total = a; c->stats.visible_total = b; c->stats.pair_total = p;
+        c->stats.candidate_total = q;
         // keep the planner's pair estimate above what was observed
-        int64_t pix = 0;
-        for (const DevCamera &d : c->host_cams) pix += (int64_t)d.width * d.height;
-        if (pix > 0) c->pairs_per_pixel = std::max(c->pairs_per_pixel, 1.25 * (double)p / pix);
+        ngs_status ls = learn_pair_density(c);
+        if (ls != NGS_OK) return ls;
     }
     *out = c->stats;
     return NGS_OK;
@@ -1306,6 +1382,7 @@ NGS_API ngs_status ngs_autotune(ngs_ctx *c, const ngs_camera *cams, int32_t n_ca
 NGS_API ngs_status ngs_stage_times(ngs_ctx *c, double *ms, int32_t n) {
     if (!c || !ms || n <= 0) return NGS_ERR_INVALID_ARG;
     if (!c->timing || c->ev_groups == 0) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
     const int groups = c->mode == NGS_MODE_PLAIN ? (int)c->host_cams.size()
                                                  : (int)c->last_plan.size();
     for (int k = 0; k < n; ++k) ms[k] = 0.0;
@@ -1329,6 +1406,7 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     // the work buffers hold the last sub-batch only
     const SubBatch &sb = c->last_plan.back();
     if (cam < sb.c0 || cam >= sb.c1) return NGS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
     CK(cudaDeviceSynchronize());
     Work &w = c->w;
     const DevCamera &d = c->host_cams[cam];
@@ -1352,12 +1430,17 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     if (hi > lo && h_nodes) {
         std::vector<uint32_t> vals(hi - lo);
         CK(cudaMemcpy(vals.data(), w.pval[psel] + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost));
-        // records live in per-camera regions of n slots; fetch each one's rect
+        // the node id is in the rect of each record: copy the span of records
+        // the pairs refer to once, then look them up
+        uint32_t r0 = UINT32_MAX, r1 = 0;
         for (int64_t k = 0; k < hi - lo; ++k) {
-            uint4 r;
-            CK(cudaMemcpy(&r, w.rect + vals[k], sizeof(uint4), cudaMemcpyDeviceToHost));
-            h_nodes[k] = (int32_t)r.w;
+            r0 = std::min(r0, vals[k]);
+            r1 = std::max(r1, vals[k]);
         }
+        std::vector<uint4> rects((size_t)r1 - r0 + 1);
+        CK(cudaMemcpy(rects.data(), w.rect + r0, rects.size() * sizeof(uint4),
+                      cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < hi - lo; ++k) h_nodes[k] = (int32_t)rects[vals[k] - r0].w;
     }
     (void)npairs;
     return NGS_OK;

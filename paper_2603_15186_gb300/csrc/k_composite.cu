@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(CompLayout<R, TW, TH, BATCH>::NT)
 k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
             const R *__restrict__ rec, uint32_t *ticket, int persistent, const int *err,
-            unsigned long long *work64, int sub_x, int sub_y) {
+            unsigned long long *work64, int sub_x, int sub_y, const uint32_t *__restrict__ order,
+            unsigned long long *tail) {
     using Lay = CompLayout<R, TW, TH, BATCH>;
     constexpr int NT = Lay::NT, BH = Lay::BH, WBW = Lay::WBW, NWX = Lay::NWX;
     constexpr int NRPW = Lay::NRPW;
@@ -182,9 +183,14 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
             __syncthreads();
             item = s_tile;
         }
-        if (item >= n_items) break;
-        const uint32_t tile = nsub == 1 ? item : item / nsub;
+        if (item >= n_items) {
+            // the first CTA to find the queue empty marks the start of the tail
+            if (tail && tid == 0) atomicMax(&tail[0], ~globaltimer_ns());
+            break;
+        }
+        uint32_t tile = nsub == 1 ? item : item / nsub;
         const int sub = (int)(item - tile * nsub);
+        if (order) tile = order[tile];   // tiles taken longest list first
         int lo = 0, hi = n_cams - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -329,53 +335,82 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                 __syncwarp();
             }
             if (T2.x > 0.0f || T2.y > 0.0f) {
-                uint32_t live_groups = 0;   // groups of four, counted per live pixel
                 // both pixels in packed (f32x2) arithmetic, every step the same
                 // rounded operation per pixel as a scalar evaluation:
                 //   q = (A lx + a1) lx + a0; alpha = min(0.99, 2^q), 0 if
                 //   q < log2(1/255); T' = T (1 - alpha); a pixel ends (unblended)
                 //   at the record with T' < 1e-4; else C += (alpha T) c, T = T'.
-                // The two decisions are 0/1 factors (mq, m): a record below the
-                // threshold gets alpha = 0 and T' = T; the ending record gets
-                // weight alpha (T m) = 0 and leaves T = T' m = 0, which keeps the
-                // pixel ended (every later T' is 0). All of these are exact, so
-                // there are no per-record branches; a lane leaves after the
-                // group of four in which both its pixels ended.
+                // The threshold decision is an exact 0/1 factor mq (a record
+                // below it gets alpha = 0 and T' = T: no per-record branch). A
+                // group of four records is first blended as if no pixel ended in
+                // it; only if a live pixel's T' fell below 1e-4 somewhere in the
+                // group (T only decreases, so its last T' tells) is the group
+                // redone from its start with the stop decision per record (factor
+                // m: the ending record gets weight alpha (T m) = 0 and leaves
+                // T = T' m = 0). With m = 1 both forms round identically, so the
+                // bits do not depend on where the groups fall. An ended pixel
+                // keeps T = 0 exactly (a live T stays >= 1e-4 * (1 - 0.99)), and a
+                // lane leaves after the group in which both its pixels ended.
+                const bool alive_x = T2.x > 0.0f, alive_y = T2.y > 0.0f;
+                int end_x = -1, end_y = -1, groups = 0;
                 const int len4 = (len + 3) & ~3;
+                // alpha of list entry e (its record index j) at both pixels
+                auto alpha2 = [&](int e, uint32_t j) {
+                    const float4 cf = my_coef[e * NRPW + rp];
+                    const float4 bA = s_pair[j].bA;
+                    const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
+                    const float2 q = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
+                    const float2 mq = make_float2(q.x >= kLog2AlphaMin ? 1.0f : 0.0f,
+                                                  q.y >= kLog2AlphaMin ? 1.0f : 0.0f);
+                    return __fmul2_rn(make_float2(fminf(kAlphaMax, ex2_approx(q.x)),
+                                                  fminf(kAlphaMax, ex2_approx(q.y))),
+                                      mq);
+                };
+#pragma unroll 1
                 for (int i = 0; i < len4; i += 4) {
                     const uint4 jv = *reinterpret_cast<const uint4 *>(my_list + i);
                     const uint32_t jj[4] = {jv.x, jv.y, jv.z, jv.w};
-                    float2 q[4];
+                    float2 Tn = T2, rn = cr2, gn = cg2, bn = cb2;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float4 cf = my_coef[(i + u) * NRPW + rp];
-                        const float4 bA = s_pair[jj[u]].bA;
-                        const float2 t = __ffma2_rn(make_float2(bA.z, bA.w), lx2, make_float2(cf.x, cf.y));
-                        q[u] = __ffma2_rn(t, lx2, make_float2(cf.z, cf.w));
-                    }
-                    live_groups += (T2.x > 0.0f ? 1u : 0u) + (T2.y > 0.0f ? 1u : 0u);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float2 mq = make_float2(q[u].x >= kLog2AlphaMin ? 1.0f : 0.0f,
-                                                      q[u].y >= kLog2AlphaMin ? 1.0f : 0.0f);
-                        const float2 al = __fmul2_rn(make_float2(fminf(kAlphaMax, ex2_approx(q[u].x)),
-                                                                 fminf(kAlphaMax, ex2_approx(q[u].y))),
-                                                     mq);
-                        const float2 t2 = __fmul2_rn(T2, __ffma2_rn(al, kMinusOne2, kOne2));
-                        const float2 m = make_float2(t2.x >= kTMin ? 1.0f : 0.0f,
-                                                     t2.y >= kTMin ? 1.0f : 0.0f);
-                        const float2 w2 = __fmul2_rn(al, __fmul2_rn(T2, m));
+                        const float2 al = alpha2(i + u, jj[u]);
+                        const float2 w2 = __fmul2_rn(al, Tn);
                         const PairRec &pr = s_pair[jj[u]];
                         const float4 c_rg = pr.rg;
                         const float4 c_b = pr.bA;
-                        cr2 = __ffma2_rn(w2, make_float2(c_rg.x, c_rg.y), cr2);
-                        cg2 = __ffma2_rn(w2, make_float2(c_rg.z, c_rg.w), cg2);
-                        cb2 = __ffma2_rn(w2, make_float2(c_b.x, c_b.y), cb2);
-                        T2 = __fmul2_rn(t2, m);
+                        rn = __ffma2_rn(w2, make_float2(c_rg.x, c_rg.y), rn);
+                        gn = __ffma2_rn(w2, make_float2(c_rg.z, c_rg.w), gn);
+                        bn = __ffma2_rn(w2, make_float2(c_b.x, c_b.y), bn);
+                        Tn = __fmul2_rn(Tn, __ffma2_rn(al, kMinusOne2, kOne2));
                     }
-                    if (!(T2.x > 0.0f || T2.y > 0.0f)) break;
+                    ++groups;
+                    if ((Tn.x < kTMin && Tn.x != 0.0f) || (Tn.y < kTMin && Tn.y != 0.0f)) {
+                        // a live pixel ends in this group: redo it with the stop test
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float2 al = alpha2(i + u, jj[u]);
+                            const float2 t2 = __fmul2_rn(T2, __ffma2_rn(al, kMinusOne2, kOne2));
+                            const float2 m = make_float2(t2.x >= kTMin ? 1.0f : 0.0f,
+                                                         t2.y >= kTMin ? 1.0f : 0.0f);
+                            const float2 w2 = __fmul2_rn(al, __fmul2_rn(T2, m));
+                            const PairRec &pr = s_pair[jj[u]];
+                            const float4 c_rg = pr.rg;
+                            const float4 c_b = pr.bA;
+                            cr2 = __ffma2_rn(w2, make_float2(c_rg.x, c_rg.y), cr2);
+                            cg2 = __ffma2_rn(w2, make_float2(c_rg.z, c_rg.w), cg2);
+                            cb2 = __ffma2_rn(w2, make_float2(c_b.x, c_b.y), cb2);
+                            T2 = __fmul2_rn(t2, m);
+                        }
+                        if (end_x < 0 && T2.x == 0.0f) end_x = groups;
+                        if (end_y < 0 && T2.y == 0.0f) end_y = groups;
+                        if (!(T2.x > 0.0f || T2.y > 0.0f)) break;
+                    } else {
+                        T2 = Tn; cr2 = rn; cg2 = gn; cb2 = bn;
+                    }
                 }
-                evals += 4ull * live_groups;
+                // groups of four counted per pixel alive at their start
+                evals += 4ull * (uint32_t)((alive_x ? (end_x >= 0 ? end_x : groups) : 0) +
+                                           (alive_y ? (end_y >= 0 ? end_y : groups) : 0));
             }
         }
         const int64_t plane = (int64_t)cam.width * cam.height;
@@ -400,6 +435,49 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
         if (lane == 0 && evals) atomicAdd(&work64[1], evals);
         if (tid == 0 && staged) atomicAdd(&work64[0], staged);
     }
+    if (tail && tid == 0) atomicMax(&tail[1], globaltimer_ns());
+}
+
+// Work order of a persistent compositing launch: the tiles of a sub-batch
+// sorted by the length of their lists, longest first, in 63 classes (half
+// octaves of the length; empty lists last), so that the longest lists start
+// first and the launch does not end waiting on a late long one. One CTA; the
+// order within a class is whatever the shared-memory atomics give (the pixels
+// do not depend on the order in which tiles are composited).
+__device__ __forceinline__ uint32_t length_class(uint2 rg) {
+    const uint32_t first = ~rg.x;
+    if (!(first < rg.y)) return 63u;
+    const uint32_t len = rg.y - first;
+    const int lg = 31 - __clz(len);
+    const uint32_t half = lg > 0 ? (len >> (lg - 1)) & 1u : 0u;
+    return 62u - min(62u, 2u * (uint32_t)lg + half);
+}
+
+__global__ void __launch_bounds__(1024)
+k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *__restrict__ order,
+             const int *err) {
+    __shared__ uint32_t s_hist[64], s_cur[64];
+    if (*err) return;
+    if (threadIdx.x < 64) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        atomicAdd(&s_hist[length_class(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < 64; ++k) {
+            s_cur[k] = acc;
+            acc += s_hist[k];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        order[atomicAdd(&s_cur[length_class(ranges[t])], 1u)] = t;
+}
+
+void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, const int *err,
+                       cudaStream_t st) {
+    k_tile_order<<<1, 1024, 0, st>>>(ranges, n_tiles, order, err);
 }
 
 template <typename R, int TW, int TH, int BATCH>
@@ -440,6 +518,8 @@ struct CompLaunch {
     const int *err;
     unsigned long long *work64;
     int sub_x, sub_y;
+    const uint32_t *order;
+    unsigned long long *tail;
     cudaStream_t st;
 };
 
@@ -448,7 +528,7 @@ static void launch_one(const CompLaunch &a) {
     k_composite<R, TW, TH, BATCH>
         <<<a.grid, CompLayout<R, TW, TH, BATCH>::NT, comp_smem<R, TW, TH, BATCH>(), a.st>>>(
             a.cams, a.n_cams, a.n_tiles, a.ranges, a.pval, (const R *)a.rec, a.ticket,
-            a.persistent, a.err, a.work64, a.sub_x, a.sub_y);
+            a.persistent, a.err, a.work64, a.sub_x, a.sub_y, a.order, a.tail);
 }
 
 template <typename R, int TW, int TH>
@@ -472,9 +552,9 @@ void launch_composite(int attr_dtype, int tile_w, int tile_h, int cta_w, int cta
                       bool persistent, const DevCamera *cams, int n_cams, uint32_t n_tiles,
                       const uint2 *ranges, const uint32_t *pval, const void *rec,
                       uint32_t *ticket, int grid, const int *err, unsigned long long *work64,
-                      cudaStream_t st) {
+                      const uint32_t *order, unsigned long long *tail, cudaStream_t st) {
     const CompLaunch a{cams, n_cams, n_tiles, ranges, pval, rec, ticket, persistent ? 1 : 0,
-                       grid, err, work64, tile_w / cta_w, tile_h / cta_h, st};
+                       grid, err, work64, tile_w / cta_w, tile_h / cta_h, order, tail, st};
     if (attr_dtype == NGS_F32) launch_r<Rec32>(cta_w, cta_h, batch, a);
     else launch_r<Rec16>(cta_w, cta_h, batch, a);
 }

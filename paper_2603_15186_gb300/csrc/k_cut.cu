@@ -103,10 +103,10 @@ struct SharedSelect {
             }
             // neither a leaf nor fine enough for this member: not selected
             if (!leaf && vis_n &&
-                !(granularity(lo, hi, k.pos[0], k.pos[1], k.pos[2], k.fx) <= k.tau))
+                !fine_enough(lo, hi, k.pos[0], k.pos[1], k.pos[2], k.fx, k.tau))
                 return false;
             if (parent >= 0 && fine_p && vis_p &&
-                !(granularity(plo, phi, k.pos[0], k.pos[1], k.pos[2], k.fx) <= k.tau))
+                !fine_enough(plo, phi, k.pos[0], k.pos[1], k.pos[2], k.fx, k.tau))
                 fine_p = false;
         }
         return (parent < 0 || !fine_p) && seen;
@@ -283,8 +283,8 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
                     const float px = s_cam[j][0], py = s_cam[j][1], pz = s_cam[j][2];
                     const float fx = s_cam[j][3], tau = s_cam[j][4];
                     // the rule of cut_selects, parent first (most nodes lie below the cut)
-                    sel = (parent < 0 || granularity(plo, phi, px, py, pz, fx) > tau) &&
-                          (leaf || granularity(lo, hi, px, py, pz, fx) <= tau);
+                    sel = (parent < 0 || !fine_enough(plo, phi, px, py, pz, fx, tau)) &&
+                          (leaf || fine_enough(lo, hi, px, py, pz, fx, tau));
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, sel);
                 if (lane == 0) s_bal[j][k * 8 + warp] = bal;

@@ -282,7 +282,9 @@ __device__ __forceinline__ bool precull(const CamLite &cam, const NodeCull &nd, 
     const float tx = __fmaf_rn(cam.R[0], dx, __fmaf_rn(cam.R[1], dy, __fmul_rn(cam.R[2], dz)));
     const float ty = __fmaf_rn(cam.R[3], dx, __fmaf_rn(cam.R[4], dy, __fmul_rn(cam.R[5], dz)));
     const float K = nd.K, smax = nd.smax;
-    const float iz = 1.0f / tz32;
+    // approximate reciprocal and square roots (relative error ~1e-7, far
+    // inside the slack of the test below)
+    const float iz = __fdividef(1.0f, tz32);
     const float ax = cam.fx * iz, bx = -cam.fx * tx * iz * iz;
     const float ay = cam.fy * iz, by = -cam.fy * ty * iz * iz;
     const float t00 = ax * cam.R[0] + bx * cam.R[6], t01 = ax * cam.R[1] + bx * cam.R[7],
@@ -290,10 +292,10 @@ __device__ __forceinline__ bool precull(const CamLite &cam, const NodeCull &nd, 
     const float t10 = ay * cam.R[3] + by * cam.R[6], t11 = ay * cam.R[4] + by * cam.R[7],
                 t12 = ay * cam.R[5] + by * cam.R[8];
     const float s2 = smax * smax;
-    const float hxb =
-        sqrtf(K * ((t00 * t00 + t01 * t01 + t02 * t02) * s2 + kBlur)) * 1.0002f + kRectMargin;
-    const float hyb =
-        sqrtf(K * ((t10 * t10 + t11 * t11 + t12 * t12) * s2 + kBlur)) * 1.0002f + kRectMargin;
+    const float qx = K * ((t00 * t00 + t01 * t01 + t02 * t02) * s2 + kBlur);
+    const float qy = K * ((t10 * t10 + t11 * t11 + t12 * t12) * s2 + kBlur);
+    const float hxb = (qx > 0.0f ? qx * rsqrtf(qx) : 0.0f) * 1.0002f + kRectMargin;
+    const float hyb = (qy > 0.0f ? qy * rsqrtf(qy) : 0.0f) * 1.0002f + kRectMargin;
     const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
     const float sx = 1e-4f * (fabsf(u) + hxb) + 0.02f, sy = 1e-4f * (fabsf(v) + hyb) + 0.02f;
     if (u + hxb + sx < 0.0f || u - hxb - sx >= (float)(cam.tiles_x * tile_w)) return false;
@@ -686,10 +688,10 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
                 const CamLite &cam = S.cam[i];
                 const bool sel =
                     valid &&
-                    (leaf || granularity(lo, hi, cam.pos[0], cam.pos[1], cam.pos[2], cam.fx) <=
-                                 cam.tau) &&
-                    (par < 0 || granularity(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
-                                            cam.fx) > cam.tau);
+                    (leaf || fine_enough(lo, hi, cam.pos[0], cam.pos[1], cam.pos[2], cam.fx,
+                                         cam.tau)) &&
+                    (par < 0 || !fine_enough(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
+                                             cam.fx, cam.tau));
                 const bool cand =
                     sel && (kBlend ? !seg_dead && !block_culled(seg_lo, seg_hi, cam, tile_w, tile_h)
                                    : precull(cam, nd, tile_w, tile_h));

@@ -7,9 +7,10 @@
 //
 // Stability: keys are loaded warp-striped (item i of lane l is key
 // base + 32 ITEMS w + 32 i + l), each warp ranks its items in that order (peers
-// = lanes holding the same digit, from eight ballots per item), warps are
-// offset in order, and partitions in ticket order; equal digits therefore keep
-// their input order, which is what the two-stage binning needs.
+// = lanes holding the same digit, from one shared-memory OR of lane bits per
+// item), warps are offset in order, and partitions in ticket order; equal
+// digits therefore keep their input order, which is what the two-stage binning
+// needs.
 //
 // Forward progress: partition ids come from an atomic ticket, so every
 // partition a look-back waits on is held by a CTA that is already running.
@@ -97,6 +98,7 @@ template <typename K>
 struct SortSmem {
     static constexpr int kPart = kOsThreads * SortShape<K>::kItems;
     uint32_t whist[kOsWarps][kRadix];     // per-warp digit counts, then warp offsets
+    uint32_t match[kOsWarps][kRadix];     // per-warp lane masks of one item's digits (kept 0)
     uint32_t dstart[kRadix];              // block-local start of each digit
     uint32_t gstart[kRadix];              // global start of each digit for this partition
     uint32_t wtot[kRadix / 32];
@@ -129,6 +131,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
     const int64_t nparts = (n + PART - 1) / PART;
     const uint32_t epoch = *epoch_ptr + epoch_off;
     const uint32_t lt = lanemask_lt();
+    for (int i = tid; i < kOsWarps * kRadix; i += kOsThreads) (&S.match[0][0])[i] = 0;
     for (;;) {
         if (tid == 0) S.part = atomicAdd(ticket, 1u);
         for (int i = tid; i < kOsWarps * kRadix; i += kOsThreads) (&S.whist[0][0])[i] = 0;
@@ -144,21 +147,31 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             const int64_t idx = base + i * 32 + lane;
             key[i] = idx < n ? kin[idx] : (K)0;
         }
+        // rank of each item among the warp's earlier items with its digit:
+        // the lanes sharing a digit (peers) are found by one shared-memory OR
+        // of the lane bits into the warp's mask of that digit (the lowest
+        // peer clears it again), or directly when every valid lane of the
+        // warp has the same digit (common in the high digits of depth keys)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const bool valid = base + i * 32 + lane < n;
             const uint32_t d = digit_of(key[i], shift, mask);
-            uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const uint32_t bit = (d >> b) & 1u;
-                const uint32_t bb = __ballot_sync(0xffffffffu, bit);
-                peers &= bit ? bb : ~bb;
+            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, __ffs(vmask | 1u) - 1);
+            const bool uniform = __all_sync(0xffffffffu, !valid || d == d0);
+            uint32_t peers = valid ? vmask : 0u;
+            if (!uniform) {
+                if (valid) atomicOr(&S.match[warp][d], 1u << lane);
+                __syncwarp();
+                peers = valid ? S.match[warp][d] : 0u;
             }
             uint32_t before = 0;
             if (valid) before = S.whist[warp][d];
             __syncwarp();
-            if (valid && (peers & lt) == 0) S.whist[warp][d] = before + __popc(peers);
+            if (valid && (peers & lt) == 0) {
+                S.whist[warp][d] = before + __popc(peers);
+                if (!uniform) S.match[warp][d] = 0u;
+            }
             __syncwarp();
             rank[i] = before + __popc(peers & lt);
         }

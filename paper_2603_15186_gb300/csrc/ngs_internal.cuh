@@ -106,6 +106,12 @@ __device__ __forceinline__ void latch_error(int *status, int code) {
     atomicCAS(status, 0, code);
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -135,7 +141,9 @@ __device__ __forceinline__ uint64_t peek(const uint64_t *slot) {
 
 // Granularity of a node box seen from camera centre (px, py, pz):
 // s = fx * (longest box side) / (distance from the centre to the box), +inf
-// when the centre is inside the box (level-of-detail cut, Sec. III-B).
+// when the centre is inside the box (level-of-detail cut, Sec. III-B). Its
+// value feeds the level-of-detail blend weight; cut decisions use
+// fine_enough below.
 __device__ __forceinline__ float granularity(const float4 lo, const float4 hi, const float px,
                                              const float py, const float pz, const float fx) {
     const float gx = fmaxf(fmaxf(__fsub_rn(lo.x, px), 0.0f), __fsub_rn(px, hi.x));
@@ -148,6 +156,27 @@ __device__ __forceinline__ float granularity(const float4 lo, const float4 hi, c
     return __fdiv_rn(__fmul_rn(fx, ext), __fsqrt_rn(d2));
 }
 
+// s(n) <= tau for the node box lo..hi, decided without the square root and
+// the division of the granularity: fx ext <= tau sqrt(d2) <=> (fx ext)^2 <=
+// tau^2 d2 (both sides >= 0), false when the camera is inside the box (s =
+// +inf). Every kernel that takes a cut decision uses this one sequence of
+// rounded operations, so all cut forms agree bit for bit; it differs from a
+// comparison of the rounded granularity only within a few units in the last
+// place of the threshold, far inside the 1e-5 tolerance around tau.
+__device__ __forceinline__ bool fine_enough(const float4 lo, const float4 hi, const float px,
+                                            const float py, const float pz, const float fx,
+                                            const float tau) {
+    const float gx = fmaxf(fmaxf(__fsub_rn(lo.x, px), 0.0f), __fsub_rn(px, hi.x));
+    const float gy = fmaxf(fmaxf(__fsub_rn(lo.y, py), 0.0f), __fsub_rn(py, hi.y));
+    const float gz = fmaxf(fmaxf(__fsub_rn(lo.z, pz), 0.0f), __fsub_rn(pz, hi.z));
+    const float d2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
+    const float ext = fmaxf(fmaxf(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y)),
+                            __fsub_rn(hi.z, lo.z));
+    if (d2 == 0.0f) return false;
+    const float a = __fmul_rn(fx, ext);
+    return __fmul_rn(a, a) <= __fmul_rn(__fmul_rn(tau, tau), d2);
+}
+
 // The cut rule for node `node`: (leaf or s(n) <= tau) and (root or s(parent) > tau).
 __device__ __forceinline__ bool cut_selects(const float4 *__restrict__ box_lo,
                                             const float4 *__restrict__ box_hi, int64_t node,
@@ -155,10 +184,10 @@ __device__ __forceinline__ bool cut_selects(const float4 *__restrict__ box_lo,
     const float4 lo = box_lo[node], hi = box_hi[node];
     const int parent = __float_as_int(lo.w);
     const int nchild = __float_as_int(hi.w);
-    const bool own = (nchild == 0) || granularity(lo, hi, px, py, pz, fx) <= tau;
+    const bool own = (nchild == 0) || fine_enough(lo, hi, px, py, pz, fx, tau);
     if (!own) return false;
     if (parent < 0) return true;
-    return granularity(box_lo[parent], box_hi[parent], px, py, pz, fx) > tau;
+    return !fine_enough(box_lo[parent], box_hi[parent], px, py, pz, fx, tau);
 }
 
 // Decoupled look-back for one running sum: returns the exclusive prefix of
@@ -243,9 +272,15 @@ struct Work {
     uint2 *ranges = nullptr;          int64_t ranges_cap = 0;
     uint32_t *hist = nullptr;         // [passes][256] radix histograms
     DevCamera *cams = nullptr;        int64_t cams_cap = 0;
-    // compositing work counters: [0] records staged, [1] pixel-Gaussian evaluations
+    // compositing work counters: [0] records staged, [1] pixel-Gaussian
+    // evaluations, then per sub-batch (up to kTailSlots) the tail words of its
+    // compositing launch
     unsigned long long *work64 = nullptr;
+    uint32_t *order = nullptr;        // compositing work order of a sub-batch's tiles
 };
+
+constexpr int kTailSlots = 64;
+constexpr int kWork64Words = 2 + 2 * kTailSlots;
 
 // ticket slots in Work::counters
 enum : int {
@@ -365,18 +400,27 @@ void launch_slice(const SceneDev &sc, const SliceGrid &g, float *value, uint8_t 
                   unsigned long long *work, int num_sms, cudaStream_t st);
 
 // tile_w x tile_h: binning tile; cta_w x cta_h: the block one CTA composites
-// (equal to the tile, or a compiled shape dividing it)
+// (equal to the tile, or a compiled shape dividing it). order (optional, a
+// permutation of the tiles): the order in which persistent CTAs take them.
+// tail (optional, 2 words zeroed by the caller): ~(time the first CTA found
+// the work queue empty) and the time the last CTA finished, as atomicMax.
 void launch_composite(int attr_dtype, int tile_w, int tile_h, int cta_w, int cta_h, int batch,
                       bool persistent, const DevCamera *cams, int n_cams, uint32_t n_tiles,
                       const uint2 *ranges, const uint32_t *pval, const void *rec,
                       uint32_t *ticket, int grid, const int *err, unsigned long long *work64,
-                      cudaStream_t st);
+                      const uint32_t *order, unsigned long long *tail, cudaStream_t st);
+// the tiles [0, n_tiles) of a sub-batch, longest list first (classes of half
+// an octave), into order[n_tiles]
+void launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, const int *err,
+                       cudaStream_t st);
 int composite_blocks_per_sm(int attr_dtype, int tile_w, int tile_h, int batch);
 void composite_init_attributes();
 
 // serving lanes: contexts sharing a parent's resident scene
 ngs_status lane_create(ngs_ctx *parent, int64_t record_capacity, int64_t pair_capacity,
                        ngs_ctx **out);
+// the planner's current pairs-per-pixel estimate of a context
+double ctx_pairs_per_pixel(const ngs_ctx *c);
 
 inline size_t rec_bytes(int attr_dtype) {
     return attr_dtype == NGS_F32 ? sizeof(Rec32) : sizeof(Rec16);

@@ -30,7 +30,12 @@ struct Request {
     ngs_camera cam;
     float *image;
     Clock::time_point t_submit;
+    int tries = 0;       // launches that overflowed a work buffer with this request
 };
+
+// launches a request may take part in that overflow a work buffer before it
+// is failed (each overflow re-plans the lane from the counted pairs)
+constexpr int kMaxCapacityRetries = 3;
 
 struct Lane {
     ngs_ctx *ctx = nullptr;
@@ -56,7 +61,7 @@ struct ngs_server {
     // completion records, indexed by ticket - 1: 0 pending, 1 done, 2 failed
     std::vector<uint8_t> state;
     std::vector<float> latency_ms;
-    int64_t submitted = 0, completed = 0, failed = 0, launches = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, launches = 0, requeued = 0;
     double mpix = 0.0;
     Clock::time_point t_first, t_last;
     bool any = false;
@@ -71,6 +76,26 @@ void finish_lane(ngs_server *s, Lane &l) {
     const ngs_status st = ngs_synchronize(l.ctx, l.stream);
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lock(s->mu);
+    if (st == NGS_ERR_CAPACITY) {
+        // the launch overflowed a work buffer: the lane's planner has taken the
+        // pair densities the device counted, admission follows it, and the
+        // requests go back to the front of the queue in their order
+        s->cfg.pairs_per_pixel = std::max(s->cfg.pairs_per_pixel, ngs::ctx_pairs_per_pixel(l.ctx));
+        for (auto it = l.reqs.rbegin(); it != l.reqs.rend(); ++it) {
+            Request r = *it;
+            if (++r.tries > kMaxCapacityRetries) {
+                s->state[(size_t)(r.ticket - 1)] = 2;
+                ++s->failed;
+            } else {
+                s->pending.push_front(r);
+                ++s->requeued;
+            }
+        }
+        l.reqs.clear();
+        l.busy = false;
+        s->cv.notify_all();
+        return;
+    }
     for (const Request &r : l.reqs) {
         const size_t i = (size_t)(r.ticket - 1);
         if (st == NGS_OK) {
@@ -203,7 +228,7 @@ NGS_API ngs_status ngs_server_submit(ngs_server *s, const ngs_camera *cam, float
         return NGS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) return NGS_ERR_INVALID_ARG;
-    Request r{s->next_ticket++, *cam, d_image, Clock::now()};
+    Request r{s->next_ticket++, *cam, d_image, Clock::now(), 0};
     if (!s->any) {
         s->t_first = r.t_submit;
         s->any = true;
@@ -259,6 +284,7 @@ NGS_API ngs_status ngs_server_stats(ngs_server *s, ngs_serving_stats *out) {
     out->completed = s->completed;
     out->failed = s->failed;
     out->launches = s->launches;
+    out->requeued = s->requeued;
     out->p50_ms = pct(0.50);
     out->p99_ms = pct(0.99);
     out->mean_ms = lat.empty() ? 0.0 : sum / lat.size();

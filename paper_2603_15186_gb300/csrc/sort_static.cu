@@ -12,11 +12,14 @@
 // allocating routine.
 //
 // The array is shared by every call on a device and keeps the last call's
-// contents: tickets, histograms and the error word are cleared at the start of
-// each call, and the look-back status words are told apart from earlier calls'
-// by an epoch that each call advances. Calls whose work overlaps on the GPU
-// (different streams, or different host threads without ordering) race on the
-// array and give undefined results.
+// contents: tickets and histograms are cleared at the start of each call, and
+// the look-back status words are told apart from earlier calls' by an epoch
+// that each call advances. A device-side error of a call (a bounded look-back
+// wait that gave up) is moved, by the next call's first kernel, from the
+// working error word into a latched word, so that it stops no later call;
+// ngs_sort_pairs_static_status() returns and clears it. Calls whose work
+// overlaps on the GPU (different streams, or different host threads without
+// ordering) race on the array and give undefined results.
 //
 // Host code must not hand the array's name to a kernel: in host code it is a
 // stand-in symbol, not a device address. Its device address is looked up once
@@ -44,8 +47,9 @@ constexpr size_t kOffStatus = align256(kOffVals + 4 * kStaticMaxPairs); // look-
 constexpr size_t kOffHist = align256(kOffStatus + 8 * 256 * kStaticParts);
 constexpr size_t kOffTickets = align256(kOffHist + 4 * 8 * 256);
 constexpr size_t kOffEpoch = align256(kOffTickets + 4 * 8);
-constexpr size_t kOffErr = align256(kOffEpoch + 4);
-constexpr size_t kScratchBytes = align256(kOffErr + 4);
+constexpr size_t kOffErr = align256(kOffEpoch + 4);       // error of the running call
+constexpr size_t kOffLatched = kOffErr + 4;                 // first error since the last query
+constexpr size_t kScratchBytes = align256(kOffLatched + 4);
 
 }  // namespace
 
@@ -58,7 +62,13 @@ unsigned char *g_addr[kStaticMaxDevices] = {};
 uint64_t g_calls[kStaticMaxDevices] = {};
 int g_sms[kStaticMaxDevices] = {};
 
-__global__ void k_static_bump(uint32_t *epoch, uint32_t inc) { *epoch += inc; }
+// Start of a call: keeps the previous call's error (if any) in the latched
+// word, clears the working error word and advances the epoch.
+__global__ void k_static_begin(uint32_t *epoch, uint32_t inc, int *err, int *latched) {
+    if (*err != 0 && *latched == 0) *latched = *err;
+    *err = 0;
+    *epoch += inc;
+}
 
 }  // namespace
 
@@ -123,10 +133,8 @@ extern "C" NGS_API ngs_status ngs_sort_pairs_static(void *d_keys, uint32_t *d_va
                 return NGS_ERR_CUDA;
         }
     }
-    if (cudaMemsetAsync(tickets, 0, 4 * 8, st) != cudaSuccess ||
-        cudaMemsetAsync(err, 0, 4, st) != cudaSuccess)
-        return NGS_ERR_CUDA;
-    k_static_bump<<<1, 1, 0, st>>>(epoch, 32u);
+    if (cudaMemsetAsync(tickets, 0, 4 * 8, st) != cudaSuccess) return NGS_ERR_CUDA;
+    k_static_begin<<<1, 1, 0, st>>>(epoch, 32u, err, (int *)(base + kOffLatched));
     SortArgs a{};
     a.keys[0] = d_keys; a.keys[1] = base + kOffKeys;
     a.vals[0] = d_vals; a.vals[1] = (uint32_t *)(base + kOffVals);
@@ -148,4 +156,25 @@ extern "C" NGS_API ngs_status ngs_sort_pairs_static(void *d_keys, uint32_t *d_va
             return NGS_ERR_CUDA;
     }
     return cudaGetLastError() == cudaSuccess ? NGS_OK : NGS_ERR_CUDA;
+}
+
+extern "C" NGS_API ngs_status ngs_sort_pairs_static_status(void *stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NGS_ERR_CUDA;
+    if (dev < 0 || dev >= kStaticMaxDevices) return NGS_ERR_INVALID_ARG;
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        base = g_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return NGS_ERR_CUDA;
+    if (!base) return NGS_OK;   // no call has run on this device yet
+    int words[2] = {0, 0};      // working and latched error words
+    if (cudaMemcpyAsync(words, base + kOffErr, sizeof(words), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(base + kOffErr, 0, sizeof(words), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return NGS_ERR_CUDA;
+    return (ngs_status)(words[1] != 0 ? words[1] : words[0]);
 }

@@ -108,6 +108,12 @@ class Renderer:
         """Level-of-detail blending of every cut node toward its parent."""
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_LOD_BLEND, 1 if on else 0), "lod blend")
 
+    def set_composite_order(self, longest_first: bool):
+        """Batched compositing takes tiles longest list first (default) or in
+        tile order; the images are the same."""
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_COMPOSITE_ORDER, 1 if longest_first else 0),
+              "composite order")
+
     def set_stage_timing(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_STAGE_TIMING, 1 if on else 0),
               "stage timing")

@@ -69,9 +69,10 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %d %zu %zu\n", sizeof(ngs_tune_result), offsetof(ngs_tune_result, ms),
          offsetof(ngs_tune_result, batch), offsetof(ngs_stats, cta_w), sizeof(ngs_server_config),
          NGS_TUNE_SHAPES, sizeof(ngs_slice_grid), offsetof(ngs_slice_grid, threshold));
-  printf("%d %d %d %d %d %d %d %d %d %d %d\n", NGS_OPT_MODE, NGS_OPT_TILE_W, NGS_OPT_TILE_H,
-         NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL, NGS_OPT_CTA_W,
-         NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL, NGS_OPT_LOD_BLEND);
+  printf("%d %d %d %d %d %d %d %d %d %d %d %d %zu\n", NGS_OPT_MODE, NGS_OPT_TILE_W,
+         NGS_OPT_TILE_H, NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL,
+         NGS_OPT_CTA_W, NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL, NGS_OPT_LOD_BLEND,
+         NGS_OPT_COMPOSITE_ORDER, offsetof(ngs_stats, composite_tail_ms));
   printf("%d\n", NGS_CUT_FRUSTUM);
   return 0;
 }
@@ -95,7 +96,7 @@ int main(void) {
         _lib.NGS_OPT_MODE, _lib.NGS_OPT_TILE_W, _lib.NGS_OPT_TILE_H, _lib.NGS_OPT_BATCH,
         _lib.NGS_OPT_GRAPH, _lib.NGS_OPT_STAGE_TIMING, _lib.NGS_OPT_BLOCK_CULL,
         _lib.NGS_OPT_CTA_W, _lib.NGS_OPT_CTA_H, _lib.NGS_OPT_PAIRS_PER_PIXEL,
-        _lib.NGS_OPT_LOD_BLEND]
+        _lib.NGS_OPT_LOD_BLEND, _lib.NGS_OPT_COMPOSITE_ORDER, _lib.Stats.composite_tail_ms.offset]
     assert int(f) == _lib.CUT_FRUSTUM
 
 

@@ -8,7 +8,8 @@ import pytest
 
 import oracle as O
 from scenegen import camera_c0, look_camera, make_floor_scene, quantize_attributes, walk_cameras
-from tests.gpu_helpers import clear_tau, compare_cut, compare_image, compare_tile_lists
+from tests.gpu_helpers import (clear_tau, compare_cut, compare_image, compare_tile_lists,
+                               compare_tile_order_f64)
 
 pytestmark = pytest.mark.gpu
 
@@ -223,6 +224,8 @@ def test_render_small_box_view(R, box10k, tau):
     n_tiles = len(ref.ranges)
     rng, nodes = R.tile_lists(0, n_tiles, len(ref.keys) + 4096)
     compare_tile_lists(rng, nodes, ref, (16, 16))
+    pairs, _, _ = compare_tile_order_f64(rng, nodes, box10k.pos, cam)
+    assert pairs > 1000
 
 
 def _floor_cams(scene):
@@ -258,7 +261,31 @@ def test_render_batch_matches_oracle_and_plain(R, small_floor):
     ref = O.render(small_floor, cams[2])
     rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
     compare_tile_lists(rng, nodes, ref, (16, 16))
+    pairs, _, _ = compare_tile_order_f64(rng, nodes, small_floor.pos, cams[2])
+    assert pairs > 1000
     R.set_mode("batched")
+
+
+def test_composite_order_changes_no_pixel(R, small_floor):
+    """Batched compositing in longest-list-first order and in tile order
+    (several sub-batches of small tiles): the same bits, and the launch tail
+    is measured in the longest-first form."""
+    R.load_scene(small_floor)
+    cams = _floor_cams(small_floor) * 3
+    R.set_tile(8, 8)
+    R.set_mode("batched")
+    try:
+        R.set_composite_order(True)
+        a = [t.cpu().numpy() for t in R.render(cams)]
+        st = R.stats()
+        assert st["composite_tail_ms"] >= 0.0
+        R.set_composite_order(False)
+        b = [t.cpu().numpy() for t in R.render(cams)]
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    finally:
+        R.set_composite_order(True)
+        R.set_tile(16, 16)
 
 
 def test_lod_blend_matches_oracle(R, small_floor):

@@ -46,3 +46,48 @@ def test_serving_alone_equals_mixed(small_floor):
         assert torch.equal(ref, im)
     compare_image(alone.cpu().numpy(), O.render(small_floor, probe))
     R.close()
+
+
+def test_pair_overflow_is_replanned_not_lost(small_floor):
+    """A pair buffer too small for the planner's first estimate, forced on
+    the host side (pairs-per-pixel estimate 1, a 2^18-pair buffer): the
+    host-buffer render re-plans from the pair counts the device reported and
+    redoes the batch, and the serving loop puts the overflowing launch's
+    requests back in the queue instead of failing them. Every image equals
+    its camera rendered alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_15186_gb300 import Renderer, Server
+    cams = mixed_batch_cameras(small_floor, 24, seed=35, resolutions=((96, 72), (160, 120)),
+                               n_walkers=4)
+    ref = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22, pair_capacity=1 << 24)
+    ref.load_scene(small_floor)
+    alone = [ref.render([c])[0].cpu().numpy() for c in cams]
+    small = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22,
+                     pair_capacity=1 << 18)
+    small.load_scene(small_floor)
+    small.set_mode("batched")
+    small.set_pairs_per_pixel(1)
+    got = small.render_host(cams)
+    st = small.stats()
+    assert st["sub_batches"] > 1
+    for a, b in zip(alone, got):
+        assert np.array_equal(a, b)
+    # serving: lanes start from the same low estimate and a small buffer
+    srv = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22, pair_capacity=1 << 24)
+    srv.load_scene(small_floor)
+    srv.set_pairs_per_pixel(1)
+    S = Server(srv, lanes=2, max_cams=16, pair_budget=1 << 22, pairs_per_pixel=1.0,
+               lane_pair_capacity=1 << 18)
+    imgs = [torch.zeros((3, c.height, c.width), device="cuda") for c in cams]
+    for c, im in zip(cams, imgs):
+        S.submit(c, im)
+    S.wait_all()
+    sst = S.stats()
+    S.stop()
+    assert sst["completed"] == len(cams) and sst["failed"] == 0
+    assert sst["requeued"] > 0
+    for a, im in zip(alone, imgs):
+        assert np.array_equal(a, im.cpu().numpy())
+    for r in (ref, small, srv):
+        r.close()
