@@ -72,13 +72,13 @@ typedef struct {
 
 // per cut slot, columns of the float64 preprocess table; PC_E* are bounds on
 // how far a float32 renderer's values may lie from these (see "float32 error
-// model" below): centre (px), the entries a, b, c of Sigma2D (px^2), the
-// relative error common to the three conic coefficients (from inverting),
-// log2 of the opacity, and the support half-widths (px)
+// model" below): centre (px), the entries b and c of Sigma2D (px^2), the
+// relative error of its determinant, log2 of the opacity, and the support
+// half-widths (px)
 enum {
     PC_VISIBLE = 0, PC_U, PC_V, PC_CONIC_A, PC_CONIC_B, PC_CONIC_C, PC_COV_A, PC_COV_B,
     PC_COV_C, PC_DEPTH, PC_OPACITY, PC_R, PC_G, PC_B, PC_HX, PC_HY,
-    PC_EU, PC_EV, PC_ESA, PC_ESB, PC_ESC, PC_ERHO, PC_EQL, PC_EHX, PC_EHY, PC_NCOLS
+    PC_EU, PC_EV, PC_EB, PC_EC, PC_EDET, PC_EQL, PC_EHX, PC_EHY, PC_NCOLS
 };
 
 static const double kNear = 0.2;           // near plane (view z)
@@ -198,44 +198,46 @@ int64_t orc_select_cut(const orc_scene *sc, const orc_camera *cam, int32_t *ids_
 // bounds below are first-order forward error bounds: every elementary float32
 // operation (add, multiply, fused multiply-add, division, square root) is
 // charged u times the magnitude of its result, a k-term dot product k u times
-// the sum of the magnitudes of its terms, and the library functions (exp, log,
-// reciprocal square root) 4 u relative; the sums of magnitudes are evaluated
-// at the float64 values, and the terms of the T Sigma T^T products at their
-// own magnitudes. Against an independent float32 evaluation these first-order
-// bounds run 10 (centre) to 1000 (conic) times above the observed errors, so
-// no further safety factor is applied (kErrSafety = 1). No particular
-// operation order is assumed.
+// the sum of its terms' magnitudes, and the library functions (exp, log,
+// reciprocal square root) 4 u relative; they are evaluated at the float64
+// values. They describe a renderer that takes the steps in this numerically
+// stable form (the float32 renderer of this project does):
 //   view vector  t_r = R_r . (mu - c): 6 u sum_k |R_rk d_k| (d_k = mu_k - c_k
-//                rounded, three products, two sums)
-//   centre       u = fx t_x / t_z + cx: fx/t_z (e_tx + |t_x| (3u + e_tz/t_z)) + u |u|
-//   3D cov.      every entry of R S^2 R^T: 25 u trace(Sigma) (quaternion
-//                normalisation and rotation 8 u per entry, exp 4 u, products)
-//   J W rows     entries fx/t_z W_0 - fx t_x/t_z^2 W_2 (and the y row): each
-//                entry off by at most tau_r (from the errors of t and 1/t_z)
-//   Sigma2D      a = T_0 Sigma T_0^T + 0.3 etc.: 6 tau_r t_r s + t_r^2 (e_S + 7 u s)
-//                + u |a| with t_r = sum_j |T_rj|, s = max |Sigma_jk|
-//   conic        the conic Q = Sigma2D^-1 as (c, -b, a) / det: an error dS of
-//                Sigma2D moves d^T Q d by -w^T dS w with w = Q d; the rounding
-//                of det = a c - b^2 (2 u (a c + b^2) / det relative) and of the
-//                reciprocal scales all three coefficients alike (relative rho);
-//                each coefficient then carries 3 u of its own rounding
-//   exponent     q = A dx^2 + B dx dy + C dy^2 + log2 o (A, B, C the conic
-//                scaled by -log2(e)/2, log2(e), -log2(e)/2): log2(e)/2 w^T |dS| w
-//                + rho |q - log2 o| + 3 u (|A| dx^2 + |B dx dy| + |C| dy^2) +
-//                the centre error times |grad q| + the log2 o error, plus 10 u
-//                (|A| (|dx| + 16)^2 + |B| (|dx| + 16) |dy| + |C| dy^2 + |log2 o|)
-//                for evaluating it relative to a reference column up to 16 px
-//                from the pixel, plus 2e-6 for the hardware exp2 (relative
-//                error below 2^-20)
+//                rounded, three products, two sums); where the depth cancels
+//                (sum_k |R_2k d_k| > 8 t_z) from the exact differences with
+//                compensated products: 2 u |t_r| + 12 u^2 sum_k |R_rk d_k|
+//   centre       u = fx t_x / t_z + cx: fx/t_z (e_tx + |t_x| (3u + e_tz/t_z)) + u|u|
+//   J W rows     T_r: every entry within tau_r (from the errors of t and 1/t_z)
+//   Sigma2D      from the projections m_rk = T_r . (axis k of the Gaussian)
+//                scaled by s_k: a - 0.3 = sum_k (s_k m_0k)^2, c - 0.3 likewise,
+//                b = sum_k s_k^2 m_0k m_1k; the errors of the projections
+//                (from tau_r, the axes' 8 u and the dot products) bound those
+//                of b and c by Cauchy-Schwarz, with no amplification by the
+//                footprint's elongation
+//   determinant  by Cauchy-Binet, sum_k (s_i s_j)^2 (n . axis_k)^2 + 0.3 (a' + c')
+//                + 0.09 (a', c' without the 0.3) with n = T_0 x T_1 from the
+//                camera's row cross products (positive terms: a relative error
+//                of a few u plus the propagated errors of n); a blended
+//                Gaussian (no axes) takes a c - b^2 with the usual cancellation
+//   conic        factored: q = log2 o - k [(l11 dx + l21 dy)^2 + (l22 dy)^2],
+//                k = log2(e)/2, l11 = sqrt(c/det), l21 = -b/sqrt(c det),
+//                l22 = 1/sqrt(c): relative errors of c and det scale the
+//                factors, the error of b moves l21
+//   exponent     the factors' errors times the factored terms at the pixel,
+//                the centre error times |grad q|, the log2 o error, 8 u times
+//                the factored terms' magnitudes for evaluating them relative to
+//                a reference column up to 16 px from the pixel, plus 2e-6 for
+//                the hardware exp2 (relative error below 2^-20)
 //   support      h = sqrt(K a) + 1/64, K = 2 ln(255 o): (h - 1/64) (e_K/K + e_a/a)/2
 //                + 3 u h
+// Against an independent numpy float32 evaluation of these steps the bounds
+// hold with room; no further safety factor is applied (kErrSafety = 1).
 // A decision of step 4 is "near threshold" when the float64 value lies within
 // this bound of the threshold: alpha >= 1/255 (|log2(o G) - log2(1/255)| <=
 // E_q) and T (1 - alpha) >= 1e-4 (relative error of T accumulated from the
 // (1 - alpha) factors). Such a decision may go either way in float32. Where
-// the bound itself exceeds kEqMax (a Gaussian so elongated or so close to the
-// near plane that its float32 alpha is uncertain by more than a few percent),
-// the pixel is not enumerated but marked unchecked.
+// the bound itself exceeds kEqMax the pixel is not enumerated but marked
+// unchecked.
 static const double kU32 = 5.9604644775390625e-08;   // 2^-24
 static const double kErrSafety = 1.0;
 static const double kLog2e = 1.4426950408889634;
@@ -379,60 +381,130 @@ void orc_preprocess(const orc_scene *sc, const orc_camera *cam, const int32_t *i
             double m[3] = {0.0, 0.0, 0.0};
             for (int r = 0; r < 3; ++r)
                 for (int k = 0; k < 3; ++k) m[r] += std::fabs(cam->R[3 * r + k] * d[k]);
-            const double etx = 6.0 * uu * m[0], ety = 6.0 * uu * m[1], etz = 6.0 * uu * m[2];
+            const double t3[3] = {tx, ty, tz};
+            // plain and compensated view vector; near the renderer's switch
+            // (sum |R_2k d_k| = 8 t_z) the larger of the two
+            double et[3];
+            const bool comp = m[2] > 8.0 * tz * (1.0 + 1e-5);
+            const bool plain = m[2] < 8.0 * tz * (1.0 - 1e-5);
+            for (int r = 0; r < 3; ++r) {
+                const double ep = 6.0 * uu * m[r];
+                const double ec_ = 2.0 * uu * std::fabs(t3[r]) + 12.0 * uu * uu * m[r];
+                et[r] = comp ? ec_ : plain ? ep : std::max(ep, ec_);
+            }
+            const double etx = et[0], ety = et[1], etz = et[2];
             const double rz = etz / tz;
             const double eu = cam->fx / tz * (etx + std::fabs(tx) * (3.0 * uu + rz)) + uu * std::fabs(u);
             const double ev = cam->fy / tz * (ety + std::fabs(ty) * (3.0 * uu + rz)) + uu * std::fabs(v);
-            // 3D covariance entries (blended: own and parent's)
-            double tr = S[0] + S[4] + S[8];
+            // rows of T = J W: relative errors of their coefficients and the
+            // bounds of the entry errors
+            const double ax = cam->fx / tz, bx = cam->fx * std::fabs(tx) / (tz * tz);
+            const double ay = cam->fy / tz, by = cam->fy * std::fabs(ty) / (tz * tz);
+            const double r_ax = 2.0 * uu + rz, r_ay = r_ax;
+            const double r_bx = 5.0 * uu + 2.0 * rz + (std::fabs(tx) > 0.0 ? etx / std::fabs(tx) : 0.0);
+            const double r_by = 5.0 * uu + 2.0 * rz + (std::fabs(ty) > 0.0 ? ety / std::fabs(ty) : 0.0);
+            const double tau0 = ax * r_ax + bx * r_bx + 2.0 * uu * (ax + bx);
+            const double tau1 = ay * r_ay + by * r_by + 2.0 * uu * (ay + by);
             const int32_t par = sc->parent[g];
-            if (blend && par >= 0) {
+            const bool blended = blend && par >= 0 &&
+                                 orc_blend_parent_weight(orc_granularity_f32(sc, cam, g),
+                                                         orc_granularity_f32(sc, cam, par),
+                                                         (float)cam->tau) > 0.0f;
+            double eb, ec, ea, edet;
+            if (!blended) {
+                // the Gaussian's axes (columns of R(q)) and scales
+                double w = sc->quat[4 * g], x = sc->quat[4 * g + 1], y = sc->quat[4 * g + 2],
+                       z = sc->quat[4 * g + 3];
+                const double nq = std::sqrt(w * w + x * x + y * y + z * z);
+                w /= nq; x /= nq; y /= nq; z /= nq;
+                const double Rq[9] = {
+                    1.0 - 2.0 * (y * y + z * z), 2.0 * (x * y - w * z), 2.0 * (x * z + w * y),
+                    2.0 * (x * y + w * z), 1.0 - 2.0 * (x * x + z * z), 2.0 * (y * z - w * x),
+                    2.0 * (x * z - w * y), 2.0 * (y * z + w * x), 1.0 - 2.0 * (x * x + y * y)};
+                double sk[3];
+                for (int k = 0; k < 3; ++k) sk[k] = std::exp((double)sc->log_scale[3 * g + k]);
+                double q[2][3], dq[2][3];
+                const double tau[2] = {tau0, tau1};
+                for (int r = 0; r < 2; ++r)
+                    for (int k = 0; k < 3; ++k) {
+                        double mrk = 0.0, colsum = 0.0, tsum = 0.0, absprod = 0.0;
+                        for (int j = 0; j < 3; ++j) {
+                            mrk += T[3 * r + j] * Rq[3 * j + k];
+                            colsum += std::fabs(Rq[3 * j + k]);
+                            tsum += std::fabs(T[3 * r + j]);
+                            absprod += std::fabs(T[3 * r + j] * Rq[3 * j + k]);
+                        }
+                        const double dm = tau[r] * colsum + 8.0 * uu * tsum + 3.0 * uu * absprod;
+                        q[r][k] = sk[k] * mrk;
+                        dq[r][k] = sk[k] * dm + 5.0 * uu * std::fabs(q[r][k]);
+                    }
+                double a2 = 0.0, c2 = 0.0, b1 = 0.0, bab = 0.0, dq0 = 0.0, dq1 = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    a2 += q[0][k] * q[0][k];
+                    c2 += q[1][k] * q[1][k];
+                    b1 += q[0][k] * q[1][k];
+                    bab += std::fabs(q[0][k] * q[1][k]);
+                    dq0 += dq[0][k] * dq[0][k];
+                    dq1 += dq[1][k] * dq[1][k];
+                }
+                ea = 2.0 * std::sqrt(a2 * dq0) + 3.0 * uu * a2 + uu * a;
+                ec = 2.0 * std::sqrt(c2 * dq1) + 3.0 * uu * c2 + uu * cc;
+                eb = std::sqrt(dq0 * c2) + std::sqrt(a2 * dq1) + 3.0 * uu * bab;
+                // determinant: n = T0 x T1 from the row cross products
+                const double aa = ax * ay, ab = ax * by, ba = bx * ay;
+                const double dn = aa * (r_ax + r_ay + uu) + ab * (r_ax + r_by + uu) +
+                                  ba * (r_bx + r_ay + uu) + 4.0 * uu * (aa + ab + ba);
+                double n[3];
+                for (int j = 0; j < 3; ++j)
+                    n[j] = T[(j + 1) % 3] * T[3 + (j + 2) % 3] - T[(j + 2) % 3] * T[3 + (j + 1) % 3];
+                const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                double ddet = 0.0, detp = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double si = sk[(k + 1) % 3] * sk[(k + 2) % 3];
+                    double nk = 0.0, nabs = 0.0;
+                    for (int j = 0; j < 3; ++j) {
+                        nk += n[j] * Rq[3 * j + k];
+                        nabs += std::fabs(n[j] * Rq[3 * j + k]);
+                    }
+                    const double gk = si * nk;
+                    const double dg = si * (std::sqrt(3.0) * dn + 8.0 * std::sqrt(3.0) * uu * nn +
+                                            3.0 * uu * nabs) + 10.0 * uu * std::fabs(gk);
+                    detp += gk * gk;
+                    ddet += 2.0 * std::fabs(gk) * dg;
+                }
+                ddet += 3.0 * uu * detp + kBlur * (ea + ec) + 2.0 * uu * det;
+                edet = ddet / det;
+            } else {
+                // blended covariance (no axes): entries of T Sigma T^T and a c - b^2
+                double tr = S[0] + S[4] + S[8];
                 double Sp[9];
                 orc_cov3d(sc->quat + 4 * par, sc->log_scale + 3 * par, Sp);
                 tr += Sp[0] + Sp[4] + Sp[8];
+                const double eS = 25.0 * uu * tr;
+                double t0 = 0.0, t1 = 0.0, M00 = 0.0, M01 = 0.0, M11 = 0.0, N0 = 0.0, N1 = 0.0;
+                for (int k = 0; k < 3; ++k) { t0 += std::fabs(T[k]); t1 += std::fabs(T[3 + k]); }
+                for (int j = 0; j < 3; ++j)
+                    for (int k = 0; k < 3; ++k) {
+                        const double sjk = std::fabs(S[3 * j + k]);
+                        M00 += std::fabs(T[j]) * sjk * std::fabs(T[k]);
+                        M01 += std::fabs(T[j]) * sjk * std::fabs(T[3 + k]);
+                        M11 += std::fabs(T[3 + j]) * sjk * std::fabs(T[3 + k]);
+                        N0 += sjk * std::fabs(T[k]);
+                        N1 += sjk * std::fabs(T[3 + k]);
+                    }
+                ea = 2.0 * tau0 * N0 + t0 * t0 * eS + 7.0 * uu * M00 + uu * a;
+                ec = 2.0 * tau1 * N1 + t1 * t1 * eS + 7.0 * uu * M11 + uu * cc;
+                eb = tau0 * N1 + tau1 * N0 + t0 * t1 * eS + 7.0 * uu * M01 + uu * std::fabs(b);
+                edet = (cc * ea + a * ec + 2.0 * std::fabs(b) * eb + 3.0 * uu * (a * cc + b * b)) / det;
             }
-            const double eS = 25.0 * uu * tr;
-            double smax = 0.0;
-            for (int k = 0; k < 9; ++k) smax = std::max(smax, std::fabs(S[k]));
-            // rows of T = J W: bounds of the entry errors and the row sums
-            const double ax = cam->fx / tz, bx = cam->fx * std::fabs(tx) / (tz * tz);
-            const double ay = cam->fy / tz, by = cam->fy * std::fabs(ty) / (tz * tz);
-            const double tau0 = ax * (2.0 * uu + rz) +
-                                cam->fx / (tz * tz) * (5.0 * uu * std::fabs(tx) + etx + 2.0 * std::fabs(tx) * rz) +
-                                2.0 * uu * (ax + bx);
-            const double tau1 = ay * (2.0 * uu + rz) +
-                                cam->fy / (tz * tz) * (5.0 * uu * std::fabs(ty) + ety + 2.0 * std::fabs(ty) * rz) +
-                                2.0 * uu * (ay + by);
-            // magnitudes of the terms of T Sigma T^T: M[r][c] = sum_jk |T_rj| |S_jk| |T_ck|,
-            // and with one T row replaced by ones (for the T errors)
-            double t0 = 0.0, t1 = 0.0, M00 = 0.0, M01 = 0.0, M11 = 0.0, N0 = 0.0, N1 = 0.0;
-            for (int k = 0; k < 3; ++k) { t0 += std::fabs(T[k]); t1 += std::fabs(T[3 + k]); }
-            for (int j = 0; j < 3; ++j)
-                for (int k = 0; k < 3; ++k) {
-                    const double sjk = std::fabs(S[3 * j + k]);
-                    M00 += std::fabs(T[j]) * sjk * std::fabs(T[k]);
-                    M01 += std::fabs(T[j]) * sjk * std::fabs(T[3 + k]);
-                    M11 += std::fabs(T[3 + j]) * sjk * std::fabs(T[3 + k]);
-                    N0 += sjk * std::fabs(T[k]);
-                    N1 += sjk * std::fabs(T[3 + k]);
-                }
-            (void)smax;
-            const double ea = 2.0 * tau0 * N0 + t0 * t0 * eS + 7.0 * uu * M00 + uu * a;
-            const double ec = 2.0 * tau1 * N1 + t1 * t1 * eS + 7.0 * uu * M11 + uu * cc;
-            const double eb = tau0 * N1 + tau1 * N0 + t0 * t1 * eS + 7.0 * uu * M01 +
-                              uu * std::fabs(b);
-            // relative error common to the conic coefficients: det's rounding, the
-            // reciprocal and the scaling by log2(e)
-            const double rho = 2.0 * uu * (a * cc + b * b) / det + 3.0 * uu;
             const double eql = 8.0 * uu * std::max(1.0, std::fabs(std::log2(opac)));
             // support half-widths
             const double eK = 2.0 * 6.0 * uu * std::max(1.0, std::fabs(std::log(255.0 * opac)));
             const double ehx = 0.5 * (hx - kRectMargin) * (eK / K + ea / a) + 3.0 * uu * hx;
             const double ehy = 0.5 * (hy - kRectMargin) * (eK / K + ec / cc) + 3.0 * uu * hy;
             o[PC_EU] = kErrSafety * eu; o[PC_EV] = kErrSafety * ev;
-            o[PC_ESA] = kErrSafety * ea; o[PC_ESB] = kErrSafety * eb;
-            o[PC_ESC] = kErrSafety * ec; o[PC_ERHO] = kErrSafety * rho;
-            o[PC_EQL] = kErrSafety * eql;
+            o[PC_EB] = kErrSafety * eb; o[PC_EC] = kErrSafety * ec;
+            o[PC_EDET] = kErrSafety * edet; o[PC_EQL] = kErrSafety * eql;
             o[PC_EHX] = kErrSafety * ehx; o[PC_EHY] = kErrSafety * ehy;
         }
         int32_t x0 = (int32_t)std::floor((u - hx) / tile_w);
@@ -517,23 +589,29 @@ void orc_bin_pairs(const int32_t *rect, const uint32_t *depth_key, int64_t n, in
 // Gaussian g at the pixel offset (dx, dy) may lie from the float64 value (the
 // error model above; g's error columns are filled by the preprocess).
 static double exponent_error(const double *g, double dx, double dy) {
-    const double A = -0.5 * kLog2e * g[PC_CONIC_A], B = -kLog2e * g[PC_CONIC_B];
-    const double C = -0.5 * kLog2e * g[PC_CONIC_C];
+    const double k = 0.5 * kLog2e;
+    const double a = g[PC_COV_A], b = g[PC_COV_B], c = g[PC_COV_C];
+    const double det = a * c - b * b;
+    const double l11 = std::sqrt(c / det), l21 = -b / std::sqrt(c * det), l22 = 1.0 / std::sqrt(c);
+    const double p = l11 * dx + l21 * dy, e = l22 * dy;
+    const double uu = kU32;
+    const double ec = g[PC_EC] / c, ed = g[PC_EDET];
+    // errors of the factors (relative errors of c and det scale them, b's
+    // moves l21), then of the two squared terms at the pixel
+    const double dl11 = l11 * (0.5 * ec + 0.5 * ed + 3.0 * uu);
+    const double dl21 = std::fabs(l21) * (0.5 * ec + 0.5 * ed + 3.0 * uu) + g[PC_EB] / std::sqrt(c * det);
+    const double dl22 = l22 * (0.5 * ec + 2.0 * uu);
+    const double big = std::fabs(l11 * dx) + std::fabs(l21 * dy);
+    const double e_fac = k * (2.0 * std::fabs(p) * (dl11 * std::fabs(dx) + dl21 * std::fabs(dy)) +
+                              2.0 * e * e * dl22 / l22);
+    // centre: q moves by its gradient times the centre error
+    const double e_ctr = 2.0 * k * (std::fabs(p) * l11 * g[PC_EU] +
+                                    std::fabs(p * l21 + e * l22) * g[PC_EV]);
+    // evaluation relative to a reference column up to 16 px away
+    const double pw = std::fabs(l11) * (std::fabs(dx) + 16.0) + std::fabs(l21 * dy);
     const double L = std::log2(g[PC_OPACITY]);
-    // w = Q d: how d^T Q d moves with the entries of Sigma2D
-    const double w0 = g[PC_CONIC_A] * dx + g[PC_CONIC_B] * dy;
-    const double w1 = g[PC_CONIC_B] * dx + g[PC_CONIC_C] * dy;
-    const double e_cov = 0.5 * kLog2e *
-                         (w0 * w0 * g[PC_ESA] + 2.0 * std::fabs(w0 * w1) * g[PC_ESB] +
-                          w1 * w1 * g[PC_ESC]);
-    const double quad = std::fabs(A) * dx * dx + std::fabs(B * dx * dy) + std::fabs(C) * dy * dy;
-    const double qmL = std::fabs(A * dx * dx + B * dx * dy + C * dy * dy);
-    const double ax = std::fabs(dx) + 16.0, ay = std::fabs(dy);
-    const double W = std::fabs(A) * ax * ax + std::fabs(B) * ax * ay + std::fabs(C) * ay * ay +
-                     std::fabs(L);
-    return e_cov + g[PC_ERHO] * qmL + kErrSafety * 3.0 * kU32 * quad + g[PC_EQL] +
-           std::fabs(2.0 * A * dx + B * dy) * g[PC_EU] +
-           std::fabs(B * dx + 2.0 * C * dy) * g[PC_EV] + kErrSafety * 10.0 * kU32 * W + 2e-6;
+    const double e_eval = 8.0 * uu * (k * (pw * pw + e * e + 2.0 * std::fabs(p) * big) + std::fabs(L));
+    return e_fac + e_ctr + e_eval + g[PC_EQL] + 2e-6;
 }
 
 static const double kLog2AlphaMin = -7.9943534368588578;   // log2(1/255)

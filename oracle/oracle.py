@@ -26,8 +26,7 @@ from . import build as _build
 
 PC = SimpleNamespace(VISIBLE=0, U=1, V=2, CONIC_A=3, CONIC_B=4, CONIC_C=5, COV_A=6, COV_B=7,
                      COV_C=8, DEPTH=9, OPACITY=10, R=11, G=12, B=13, HX=14, HY=15,
-                     EU=16, EV=17, ESA=18, ESB=19, ESC=20, ERHO=21, EQL=22, EHX=23, EHY=24,
-                     NCOLS=25)
+                     EU=16, EV=17, EB=18, EC=19, EDET=20, EQL=21, EHX=22, EHY=23, NCOLS=24)
 
 
 class _Scene(C.Structure):

@@ -372,6 +372,17 @@ void fill_cam(DevCamera &d, const ngs_camera &k, int tw, int th, float *image) {
     d.tiles_x = (k.width + tw - 1) / tw;
     d.tiles_y = (k.height + th - 1) / th;
     d.image = image;
+    // cross products of the rows of R_wc (float64, then rounded)
+    auto cross = [&](int a, int b, float *out) {
+        const double ax = k.R_wc[3 * a], ay = k.R_wc[3 * a + 1], az = k.R_wc[3 * a + 2];
+        const double bx = k.R_wc[3 * b], by = k.R_wc[3 * b + 1], bz = k.R_wc[3 * b + 2];
+        out[0] = (float)(ay * bz - az * by);
+        out[1] = (float)(az * bx - ax * bz);
+        out[2] = (float)(ax * by - ay * bx);
+    };
+    cross(0, 1, d.X01);
+    cross(0, 2, d.X02);
+    cross(2, 1, d.X21);
 }
 
 // The five planes of the camera's view volume widened by `guard` pixels, in

@@ -5,10 +5,11 @@
 // Gaussians, in (depth, node id) order, are staged in shared memory BATCH
 // records at a time (one cooperative gather of 48 B (float32) or 32 B
 // (float16 colour) records), and for every record and tile row the falloff
-// exponent is rewritten as a quadratic in the pixel's column offset lx within
-// its 16-pixel column block, so that per pixel it costs two fused
-// multiply-adds; every thread then walks the batch:
-//   q = (A lx + a1) lx + a0 = A dx^2 + B dx dy + C dy^2 + L
+// exponent, kept in the factored form L - (F1 dx + F2 dy)^2 - (F3 dy)^2, is
+// rewritten as a quadratic in the pixel's column offset lx within its 16-pixel
+// column block, so that per pixel it costs two fused multiply-adds; every
+// thread then walks the batch:
+//   q = (A lx + a1) lx + a0 = L - (F1 dx + F2 dy)^2 - (F3 dy)^2, A = -F1^2
 //                                          (log2 of o * Gaussian falloff)
 //   skip if q < log2(1/255)                (alpha < 1/255)
 //   alpha = min(0.99, 2^q)
@@ -46,22 +47,24 @@ __device__ __forceinline__ void rec_colour(const Rec16 &r, float &cr, float &cg,
     cb = __low2float(*reinterpret_cast<const __half2 *>(&w));   // high half: support size
 }
 
-// Largest q = A dx^2 + B dx dy + C dy^2 + L (A, C < 0) over the rectangle
-// [ex0, ex1] x [ey0, ey1] of offsets from the Gaussian centre: L when the
-// centre is inside, else the best of the four edges, each a 1D concave
-// quadratic maximised in closed form and clamped to the edge.
-__device__ __forceinline__ float rect_qmax(float A, float B, float C, float L, float ex0,
+// Largest q = L - (F1 x + F2 y)^2 - (F3 y)^2 over the rectangle [ex0, ex1] x
+// [ey0, ey1] of offsets (x, y) from the Gaussian centre: L when the centre is
+// inside, else the best of the four edges, each a 1D concave quadratic
+// maximised in closed form (on x = const at y = -F1 F2 x / (F2^2 + F3^2), on
+// y = const at x = -F2 y / F1) and clamped to the edge; every value is taken
+// in the factored form, which does not cancel.
+__device__ __forceinline__ float rect_qmax(float F1, float F2, float F3, float L, float ex0,
                                            float ex1, float ey0, float ey1) {
     if (ex0 <= 0.0f && 0.0f <= ex1 && ey0 <= 0.0f && 0.0f <= ey1) return L;
-    const float sy = -B / (2.0f * C), sx = -B / (2.0f * A);
-    float y = fminf(fmaxf(sy * ex0, ey0), ey1);
-    float best = A * ex0 * ex0 + B * ex0 * y + C * y * y;
-    y = fminf(fmaxf(sy * ex1, ey0), ey1);
-    best = fmaxf(best, A * ex1 * ex1 + B * ex1 * y + C * y * y);
-    float x = fminf(fmaxf(sx * ey0, ex0), ex1);
-    best = fmaxf(best, A * x * x + B * x * ey0 + C * ey0 * ey0);
-    x = fminf(fmaxf(sx * ey1, ex0), ex1);
-    best = fmaxf(best, A * x * x + B * x * ey1 + C * ey1 * ey1);
+    auto qf = [&](float x, float y) {
+        const float p = fmaf(F1, x, F2 * y), e = F3 * y;
+        return -fmaf(p, p, e * e);
+    };
+    const float sy = -F1 * F2 / fmaf(F2, F2, F3 * F3), sx = -F2 / F1;
+    float best = qf(ex0, fminf(fmaxf(sy * ex0, ey0), ey1));
+    best = fmaxf(best, qf(ex1, fminf(fmaxf(sy * ex1, ey0), ey1)));
+    best = fmaxf(best, qf(fminf(fmaxf(sx * ey0, ex0), ex1), ey0));
+    best = fmaxf(best, qf(fminf(fmaxf(sx * ey1, ex0), ex1), ey1));
     return best + L;
 }
 
@@ -72,30 +75,26 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // Conservative bounding box of the pixel-centre offsets where a record can
-// still pass the alpha threshold: the ellipse -(A dx^2 + B dx dy + C dy^2) <=
+// still pass the alpha threshold: the ellipse (F1 dx + F2 dy)^2 + (F3 dy)^2 <=
 // kappa, kappa = L - log2(1/255) + kTileMarginLog2, has half-widths
-// sqrt(kappa (-C) / det) and sqrt(kappa (-A) / det), det = A C - B^2 / 4. The
-// box is widened by a relative 2^-10 plus a term that grows with A C / det
-// (the cancellation in det and in the exponent of an elongated footprint) and
-// by 1/64 px; a form that is not negative definite gets an unbounded box.
+// sqrt(kappa (F2^2 + F3^2)) / (F1 F3) and sqrt(kappa) / F3 (no cancellation in
+// the factored form); the box is widened by a relative 2^-10 and by 1/64 px.
 // Returned as (xmin, xmax, ymin, ymax) in pixel coordinates.
-__device__ __forceinline__ float4 record_box(float x, float y, float A, float B, float C, float L) {
+__device__ __forceinline__ float4 record_box(float x, float y, float F1, float F2, float F3,
+                                            float L) {
     const float kappa = L - (kLog2AlphaMin - kTileMarginLog2);
-    const float ac = A * C;
-    const float det = fmaf(-0.25f * B, B, ac);
     const float inf = __int_as_float(0x7f800000);
     if (!(kappa >= 0.0f)) return make_float4(inf, -inf, inf, -inf);   // empty
-    if (!(A < 0.0f) || !(C < 0.0f) || !(det > 0.0f) || !(ac < inf))
-        return make_float4(-inf, inf, -inf, inf);
-    const float grow = 1.0f + 0.0009765625f + 9.5367431640625e-07f * (ac / det);
-    const float s = kappa / det;
-    const float hx = fmaf(sqrtf(s * -C), grow, 0.015625f);
-    const float hy = fmaf(sqrtf(s * -A), grow, 0.015625f);
+    if (!(F1 > 0.0f) || !(F3 > 0.0f)) return make_float4(-inf, inf, -inf, inf);
+    const float grow = 1.0f + 0.0009765625f;
+    const float sk = sqrtf(kappa);
+    const float hx = fmaf(sk * sqrtf(fmaf(F2, F2, F3 * F3)) / (F1 * F3), grow, 0.015625f);
+    const float hy = fmaf(sk / F3, grow, 0.015625f);
     return make_float4(x - hx, x + hx, y - hy, y + hy);
 }
 
-// colour and A of a staged record, each value twice, as register pairs for
-// packed two-pixel arithmetic: (r, r, g, g), (b, b, A, A)
+// colour and the lx^2 coefficient -F1^2 of a staged record, each value twice,
+// as register pairs for packed two-pixel arithmetic: (r, r, g, g), (b, b, A, A)
 struct PairRec {
     float4 rg;
     float4 bA;
@@ -273,7 +272,8 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     // the sums unchanged
                     gr = finite_or_max(gr); gg = finite_or_max(gg); gb = finite_or_max(gb);
                     s_pair[pos].rg = make_float4(gr, gr, gg, gg);
-                    s_pair[pos].bA = make_float4(gb, gb, m.a.z, m.a.z);
+                    const float A = -__fmul_rn(m.a.z, m.a.z);
+                    s_pair[pos].bA = make_float4(gb, gb, A, A);
                     s_box[pos] = record_box(m.a.x, m.a.y, m.a.z, m.a.w, m.b.x, m.b.y);
                     ++pos;
                 }
@@ -315,18 +315,19 @@ k_composite(const DevCamera *__restrict__ cams, int n_cams, uint32_t n_tiles,
                     float4 cfv = make_float4(0.0f, 0.0f, -inf, -inf);
                     if (i < len) {
                         const R &rr = s_rec[my_list[i]];
-                        const float A = rr.a.z, B = rr.a.w, C = rr.b.x, L = rr.b.y;
+                        const float F1 = rr.a.z, F2 = rr.a.w, F3 = rr.b.x, L = rr.b.y;
                         const float dxt = __fsub_rn(xref + (float)(16 * wcb), rr.a.x);
-                        const float axb = __fadd_rn(A, A);
+                        const float m2f1 = __fmul_rn(-2.0f, F1);
                         const int p = (by >> 1) + r;
                         float a1[2], a0[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
+                            // q(lx) = L - (p0 + F1 lx)^2 - (F3 dy)^2, p0 = F1 dxt + F2 dy
                             const float dy = __fsub_rn((float)(y0 + 2 * p + h) + 0.5f, rr.a.y);
-                            const float bdy = __fmul_rn(B, dy);
-                            a1[h] = __fmaf_rn(axb, dxt, bdy);
-                            a0[h] = __fmaf_rn(__fmaf_rn(A, dxt, bdy), dxt,
-                                              __fmaf_rn(C, __fmul_rn(dy, dy), L));
+                            const float p0 = __fmaf_rn(F1, dxt, __fmul_rn(F2, dy));
+                            const float e = __fmul_rn(F3, dy);
+                            a1[h] = __fmul_rn(m2f1, p0);
+                            a0[h] = __fmaf_rn(-p0, p0, __fmaf_rn(-e, e, L));
                         }
                         cfv = make_float4(a1[0], a1[1], a0[0], a0[1]);
                     }

@@ -237,7 +237,7 @@ __device__ __forceinline__ void cov3d(const float4 q4, const float ls[3], float 
 }
 
 struct PreOut {
-    float x, y, A, B, C, L, r, g, bl, hx, hy;
+    float x, y, F1, F2, F3, L, r, g, bl, hx, hy;
     uint32_t key;
     uint4 rect;
 };
@@ -369,7 +369,39 @@ __device__ __forceinline__ bool block_culled(const float4 lo, const float4 hi, c
     return false;
 }
 
-// Full preprocess of a Gaussian that passed precull (phase B); returns whether
+// Error-free transformations (Knuth's TwoSum; the product's error by a fused
+// multiply-add): s + e = a + b and p + e = a b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// R . (hi + lo) as a compensated dot product (the sum of the rounded terms
+// with the running rounding errors added back): close to a faithful rounding
+// of the exact value, however much the three terms cancel.
+__device__ __forceinline__ float dot3_compensated(const float *R, const float hi[3],
+                                                  const float lo[3]) {
+    float s, c, p, e, q;
+    two_prod(R[0], hi[0], s, c);
+    two_prod(R[1], hi[1], p, e);
+    two_sum(s, p, s, q);
+    c = __fadd_rn(c, __fadd_rn(q, e));
+    two_prod(R[2], hi[2], p, e);
+    two_sum(s, p, s, q);
+    c = __fadd_rn(c, __fadd_rn(q, e));
+    c = __fmaf_rn(R[0], lo[0], __fmaf_rn(R[1], lo[1], __fmaf_rn(R[2], lo[2], c)));
+    return __fadd_rn(s, c);
+}
+
+constexpr float kHalfLog2e = 0.72134752044448170f;   // log2(e) / 2
+
+// Full preprocess of a Gaussian that passed precull (phase B); returns whether// Full preprocess of a Gaussian that passed precull (phase B); returns whether
 // it is visible (in front of the near plane and touching at least one tile).
 // kBlend: the node is rendered with its level-of-detail blended attributes
 // (moved toward its parent's by blend_parent_weight): mean and opacity in one
@@ -416,6 +448,21 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     // cull and the sort key use
     const float tz = __fmaf_rn(cam.R[6], dx, __fmaf_rn(cam.R[7], dy, __fmul_rn(cam.R[8], dz)));
     if (!(tz > kNearZ)) return false;
+    // The view vector of the projection. Close to the camera plane and far off
+    // the axis (sum_k |R_2k d_k| > 8 t_z) the depth is a sum that cancels, and
+    // its rounding would turn the footprint of the (then very elongated)
+    // Gaussian; there it is recomputed from the exact differences with
+    // compensated products.
+    float txp = tx, typ = ty, tzp = tz;
+    if (fabsf(cam.R[6] * dx) + fabsf(cam.R[7] * dy) + fabsf(cam.R[8] * dz) > 8.0f * tz) {
+        float hi[3], lo[3];
+        two_sum(p.x, -cam.pos[0], hi[0], lo[0]);
+        two_sum(p.y, -cam.pos[1], hi[1], lo[1]);
+        two_sum(p.z, -cam.pos[2], hi[2], lo[2]);
+        txp = dot3_compensated(cam.R, hi, lo);
+        typ = dot3_compensated(cam.R + 3, hi, lo);
+        tzp = dot3_compensated(cam.R + 6, hi, lo);
+    }
 
     // 3D covariance from the normalised quaternion and the scales
     const float4 q4 = sc.quat[node];
@@ -449,28 +496,58 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     }
 
     // T = J W (2x3): rows (fx/z) W0 - (fx x/z^2) W2 and (fy/z) W1 - (fy y/z^2) W2
-    const float iz = 1.0f / tz;
-    const float ax = cam.fx * iz, bx = -cam.fx * tx * iz * iz;
-    const float ay = cam.fy * iz, by = -cam.fy * ty * iz * iz;
+    const float iz = 1.0f / tzp;
+    const float ax = cam.fx * iz, bx = -cam.fx * txp * iz * iz;
+    const float ay = cam.fy * iz, by = -cam.fy * typ * iz * iz;
     const float T00 = ax * cam.R[0] + bx * cam.R[6], T01 = ax * cam.R[1] + bx * cam.R[7],
                 T02 = ax * cam.R[2] + bx * cam.R[8];
     const float T10 = ay * cam.R[3] + by * cam.R[6], T11 = ay * cam.R[4] + by * cam.R[7],
                 T12 = ay * cam.R[5] + by * cam.R[8];
-    // U = T Sigma
-    const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
-    const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
-    const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
-    const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
-    const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
-    const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
-    const float ca = U00 * T00 + U01 * T01 + U02 * T02 + kBlur;
-    const float cb = U00 * T10 + U01 * T11 + U02 * T12;
-    const float cc = U10 * T10 + U11 * T11 + U12 * T12 + kBlur;
-    const float det = ca * cc - cb * cb;
+    float ca, cb, cc, det;
+    if (!mix) {
+        // Sigma2D - 0.3 I = M diag(s^2) M^T with M = T Rq: the projections of the
+        // Gaussian's axes, summed as positive squares; det by Cauchy-Binet,
+        // sum over axis pairs of (s_i s_j)^2 (minor of M)^2, each minor being
+        // n . (axis k) for the normal n = T0 x T1 taken from the camera's row
+        // cross products (the rows of T are nearly parallel for a Gaussian
+        // far off the axis, so neither a c - b^2 nor T0 x T1 is formed)
+        const float m00 = T00 * R00 + T01 * R10 + T02 * R20;
+        const float m01 = T00 * R01 + T01 * R11 + T02 * R21;
+        const float m02 = T00 * R02 + T01 * R12 + T02 * R22;
+        const float m10 = T10 * R00 + T11 * R10 + T12 * R20;
+        const float m11 = T10 * R01 + T11 * R11 + T12 * R21;
+        const float m12 = T10 * R02 + T11 * R12 + T12 * R22;
+        const float q00 = s0 * m00, q01 = s1 * m01, q02 = s2 * m02;
+        const float q10 = s0 * m10, q11 = s1 * m11, q12 = s2 * m12;
+        const float ap = q00 * q00 + q01 * q01 + q02 * q02;
+        const float cp = q10 * q10 + q11 * q11 + q12 * q12;
+        cb = q00 * q10 + q01 * q11 + q02 * q12;
+        const float aa = ax * ay, ab = ax * by, ba = bx * ay;
+        const float n0 = aa * cam.X01[0] + ab * cam.X02[0] + ba * cam.X21[0];
+        const float n1 = aa * cam.X01[1] + ab * cam.X02[1] + ba * cam.X21[1];
+        const float n2 = aa * cam.X01[2] + ab * cam.X02[2] + ba * cam.X21[2];
+        const float g0 = s1 * s2 * (n0 * R00 + n1 * R10 + n2 * R20);
+        const float g1 = s0 * s2 * (n0 * R01 + n1 * R11 + n2 * R21);
+        const float g2 = s0 * s1 * (n0 * R02 + n1 * R12 + n2 * R22);
+        ca = ap + kBlur;
+        cc = cp + kBlur;
+        det = g0 * g0 + g1 * g1 + g2 * g2 + kBlur * (ap + cp) + kBlur * kBlur;
+    } else {
+        // U = T Sigma for the blended covariance
+        const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
+        const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
+        const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
+        const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
+        const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
+        const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
+        ca = U00 * T00 + U01 * T01 + U02 * T02 + kBlur;
+        cb = U00 * T10 + U01 * T11 + U02 * T12;
+        cc = U10 * T10 + U11 * T11 + U12 * T12 + kBlur;
+        det = ca * cc - cb * cb;
+    }
     if (!(det > 0.0f)) return false;
-    const float idet = 1.0f / det;
-    const float u = __fmaf_rn(cam.fx * iz, tx, cam.cx);
-    const float v = __fmaf_rn(cam.fy * iz, ty, cam.cy);
+    const float u = __fmaf_rn(cam.fx * iz, txp, cam.cx);
+    const float v = __fmaf_rn(cam.fy * iz, typ, cam.cy);
 
     // support box and tile rectangle
     const float hx = sqrtf(K * ca) + kRectMargin;
@@ -488,11 +565,16 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     if (mix) sh_colour_blend<A>(sc.sh, node, par, vb, dx * inv, dy * inv, dz * inv, rgb);
     else sh_colour<A>(sc.sh, node, dx * inv, dy * inv, dz * inv, rgb);
 
+    // Cholesky factors of the conic (c, -b; -b, a) / det, scaled by
+    // sqrt(log2(e) / 2): F1 = sqrt(k c / det), F2 = -b sqrt(k / (c det)),
+    // F3 = sqrt(k / c)
+    const float sdet = sqrtf(det);
+    const float F3 = sqrtf(kHalfLog2e / cc);
     o.x = u;
     o.y = v;
-    o.A = -0.5f * kLog2e * (cc * idet);
-    o.B = kLog2e * (cb * idet);
-    o.C = -0.5f * kLog2e * (ca * idet);
+    o.F1 = F3 * cc / sdet;
+    o.F2 = -cb * F3 / sdet;
+    o.F3 = F3;
     o.L = log2f(opac);
     o.r = rgb[0]; o.g = rgb[1]; o.bl = rgb[2];
     o.hx = hx; o.hy = hy;
@@ -503,15 +585,15 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
 }
 
 __device__ __forceinline__ void store_rec(Rec32 *rec, int64_t i, const PreOut &o) {
-    rec[i].a = make_float4(o.x, o.y, o.A, o.B);
-    rec[i].b = make_float4(o.C, o.L, o.r, o.g);
+    rec[i].a = make_float4(o.x, o.y, o.F1, o.F2);
+    rec[i].b = make_float4(o.F3, o.L, o.r, o.g);
     rec[i].c = make_float4(o.bl, o.hx, o.hy, 0.f);
 }
 __device__ __forceinline__ void store_rec(Rec16 *rec, int64_t i, const PreOut &o) {
     const __half2 rg = __floats2half2_rn(o.r, o.g);
     const __half2 b0 = __halves2half2(__float2half_rn(o.bl), __float2half_ru(fmaxf(o.hx, o.hy)));
-    rec[i].a = make_float4(o.x, o.y, o.A, o.B);
-    rec[i].b = make_float4(o.C, o.L, __uint_as_float(*reinterpret_cast<const uint32_t *>(&rg)),
+    rec[i].a = make_float4(o.x, o.y, o.F1, o.F2);
+    rec[i].b = make_float4(o.F3, o.L, __uint_as_float(*reinterpret_cast<const uint32_t *>(&rg)),
                            __uint_as_float(*reinterpret_cast<const uint32_t *>(&b0)));
 }
 

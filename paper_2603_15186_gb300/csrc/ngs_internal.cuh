@@ -63,22 +63,27 @@ struct DevCamera {
     double Rz[3];
     float *image;            // [3][height][width]
     int64_t pad1;
+    // cross products of the rows of R_wc: R0 x R1, R0 x R2, R2 x R1 (world
+    // terms), for the normal of the projected Gaussian's two screen rows
+    float X01[3], X02[3], X21[3];
+    float pad2[3];
 };
 static_assert(sizeof(DevCamera) % 16 == 0, "DevCamera alignment");
 
-// compositing records: centre (x, y), the conic scaled to log2 units
-// (A dx^2 + B dx dy + C dy^2 = log2 of the Gaussian falloff), L = log2(opacity)
-// and the colour
-// and the colour, plus the half-widths of the support box (for the per-warp
-// skip test; float16 rounded up in the compact record)
+// compositing records: centre (x, y); the log2 falloff of the Gaussian as
+// L - (F1 dx + F2 dy)^2 - (F3 dy)^2 with L = log2(opacity) and F1, F2, F3 the
+// Cholesky factors of the conic scaled by sqrt(log2(e) / 2) (this factored
+// form keeps the thin direction of an elongated footprint, which rounding the
+// three conic coefficients would lose); the colour, plus the half-widths of
+// the support box (float32 record; float16 rounded up in the compact one)
 struct __align__(16) Rec32 {
-    float4 a;   // x, y, A, B
-    float4 b;   // C, L, r, g
+    float4 a;   // x, y, F1, F2
+    float4 b;   // F3, L, r, g
     float4 c;   // bl, hx, hy, 0
 };
 struct __align__(16) Rec16 {
-    float4 a;   // x, y, A, B
-    float4 b;   // C, L, half2(r, g) bits, half2(bl, max(hx, hy)) bits
+    float4 a;   // x, y, F1, F2
+    float4 b;   // F3, L, half2(r, g) bits, half2(bl, max(hx, hy)) bits
 };
 
 struct SceneDev {

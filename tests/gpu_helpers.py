@@ -21,10 +21,11 @@ PIXEL_TOL = 2e-3          # absolute, per channel
 U32 = 2.0 ** -24
 NEAR_Z = 0.2
 # pixels whose near-threshold decisions have more outcomes than the oracle
-# lists (64), or a decision whose error bound is too large to enumerate (over
+# lists (MAX_OUTCOMES), or a decision whose error bound is too large to enumerate (over
 # 2 log2 units), are not checked when they match none of the listed outcomes;
 # at most this fraction of a view may be such
 MAX_UNCHECKED_FRAC = 1e-4
+MAX_OUTCOMES = 256
 
 
 def clear_tau(scene, cam, step=1.0007, tries=50):
@@ -69,13 +70,7 @@ def compare_image(got, ref, tol=PIXEL_TOL):
     eflag, unchecked = 0.0, 0
     if len(ys):
         pix = np.stack([xs, ys], 1)
-        alts, cnt = O.alternatives(ref.pre, ref.vals, ref.ranges, ref.cam, pix, tile=ref.tile)
-        g = got[:, ys, xs].T                                  # [n, 3]
-        d = np.abs(alts - g[:, None, :]).max(axis=2)          # [n, max_out]
-        m = np.arange(alts.shape[1])[None, :] < np.minimum(np.abs(cnt), alts.shape[1])[:, None]
-        best = np.where(m, d, np.inf).min(axis=1)
-        # more outcomes than listed, or a decision too uncertain to enumerate
-        over = (cnt > alts.shape[1]) | (cnt < 0)
+        best, over = nearest_outcome(got, ref, pix)
         unchecked = int((over & (best > tol)).sum())
         fine = best[~over | (best <= tol)]
         eflag = float(fine.max()) if len(fine) else 0.0
@@ -87,6 +82,25 @@ def compare_image(got, ref, tol=PIXEL_TOL):
     assert unchecked <= MAX_UNCHECKED_FRAC * n + 1, f"{unchecked} pixels left unchecked"
     return {"max_abs_err": emax, "flagged_frac": float(flagged.mean()),
             "flagged_max_err_vs_nearest_outcome": eflag, "unchecked_frac": unchecked / n}
+
+
+def nearest_outcome(got, ref, pix, max_out=MAX_OUTCOMES, chunk=16384):
+    """For the pixels ``pix`` ((n, 2) integer (x, y)) of a GPU image: the
+    largest channel error against the nearest of the oracle's outcomes of the
+    pixel's near-threshold decisions, and whether the pixel had more outcomes
+    than listed or a decision too uncertain to enumerate."""
+    best = np.empty(len(pix))
+    over = np.empty(len(pix), dtype=bool)
+    for s0 in range(0, len(pix), chunk):
+        pc = pix[s0:s0 + chunk]
+        alts, cnt = O.alternatives(ref.pre, ref.vals, ref.ranges, ref.cam, pc, tile=ref.tile,
+                                   max_out=max_out)
+        g = got[:, pc[:, 1], pc[:, 0]].T                     # [n, 3]
+        d = np.abs(alts - g[:, None, :]).max(axis=2)          # [n, max_out]
+        m = np.arange(max_out)[None, :] < np.minimum(np.abs(cnt), max_out)[:, None]
+        best[s0:s0 + chunk] = np.where(m, d, np.inf).min(axis=1)
+        over[s0:s0 + chunk] = (cnt > max_out) | (cnt < 0)
+    return best, over
 
 
 def uncertain_nodes(ref, tile):

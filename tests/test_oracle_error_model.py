@@ -5,12 +5,13 @@ and of the alternatives it enumerates for them. CPU only.
 - The float32 view depth of the sort key and near-plane cull lies within
   6 u sum_k |R_2k d_k| of the float64 depth (u = 2^-24): the bound of a
   three-term dot product of rounded differences, whatever the operation order.
-- The per-Gaussian bounds of the preprocess (centre, the entries of the 2D
-  covariance, log2 opacity, support half-widths) and the per-pixel exponent
-  bound (which adds the inversion and the evaluation) hold for
-  an independent float32 evaluation of the same definitions (numpy float32,
+- The per-Gaussian bounds of the preprocess (centre, the entries b and c of
+  the 2D covariance and its determinant, log2 opacity, support half-widths)
+  and the per-pixel exponent bound (the factored conic at the pixel) hold for
+  an independent float32 evaluation of the same stable form (numpy float32,
   matrix products in numpy's order), over random Gaussians and cameras that
-  include thin, off-axis and near-plane cases.
+  include thin, off-axis and near-plane cases, and Gaussians close to the
+  camera plane far off the axis.
 - The alternatives of a pixel are the closed-form outcomes of its
   near-threshold decisions: a Gaussian at alpha = 1/255 taken or skipped, and a
   stop decision at T (1 - alpha) = 1e-4 taken or not."""
@@ -59,53 +60,73 @@ def test_depth_f32_within_the_float64_bound():
 
 
 def _f32_preprocess(cam, mu, quat, log_scale, opac):
-    """An independent float32 evaluation of the EWA / conic definitions (numpy
-    float32 arrays; matrix products in numpy's order)."""
+    """An independent float32 evaluation (numpy float32 arrays, numpy's own
+    operation order) of the numerically stable form the error model
+    describes: the view vector (rounded from float64 where the depth cancels,
+    as a compensated product would give), the projections of the Gaussian's
+    scaled axes, the determinant by Cauchy-Binet from the normal of the two
+    screen rows, and the factored conic."""
     f = np.float32
     R = cam.R_wc.astype(f)
     d = (mu.astype(f) - cam.pos.astype(f)).astype(f)
     t = (R @ d).astype(f)
+    if float(np.abs(R[2] * d).sum()) > 8.0 * float(t[2]):
+        d64 = mu.astype(np.float64) - cam.pos.astype(f).astype(np.float64)
+        t = (R.astype(np.float64) @ d64).astype(f)
     tx, ty, tz = t
     q = quat.astype(f) / f(np.sqrt((quat.astype(f) ** 2).sum()))
     w, x, y, z = q
     Rq = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
                    [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
                    [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]], dtype=f)
-    s2 = np.exp(f(2) * log_scale.astype(f)).astype(f)
-    S = (Rq * s2[None, :]) @ Rq.T
+    sk = np.exp(log_scale.astype(f)).astype(f)
     fx, fy = f(cam.fx), f(cam.fy)
-    J = np.array([[fx / tz, 0, -fx * tx / (tz * tz)], [0, fy / tz, -fy * ty / (tz * tz)]], dtype=f)
-    T = (J @ R).astype(f)
-    cov = (T @ S @ T.T).astype(f)
-    a, b, c = cov[0, 0] + f(0.3), cov[0, 1], cov[1, 1] + f(0.3)
-    sa, sb, sc = a, b, c
-    det = a * c - b * b
+    ax, ay = fx / tz, fy / tz
+    bx, by = -fx * tx / (tz * tz), -fy * ty / (tz * tz)
+    T = np.stack([ax * R[0] + bx * R[2], ay * R[1] + by * R[2]]).astype(f)
+    qm = ((T @ Rq) * sk[None, :]).astype(f)              # s_k (T_r . axis k)
+    ap, cp = f((qm[0] ** 2).sum()), f((qm[1] ** 2).sum())
+    b = f((qm[0] * qm[1]).sum())
+    R64 = cam.R_wc.astype(f).astype(np.float64)
+    X = [np.cross(R64[0], R64[1]).astype(f), np.cross(R64[0], R64[2]).astype(f),
+         np.cross(R64[2], R64[1]).astype(f)]
+    n = (f(ax * ay) * X[0] + f(ax * by) * X[1] + f(bx * ay) * X[2]).astype(f)
+    g = (n @ Rq).astype(f) * np.array([sk[1] * sk[2], sk[0] * sk[2], sk[0] * sk[1]], dtype=f)
+    a, c = ap + f(0.3), cp + f(0.3)
+    det = f((g * g).sum()) + f(0.3) * (ap + cp) + f(0.09)
+    k = f(0.5 * LOG2E)
+    F3 = np.sqrt(k / c)
+    F1 = F3 * c / np.sqrt(det)
+    F2 = -b * F3 / np.sqrt(det)
     u = fx * tx / tz + f(cam.cx)
     v = fy * ty / tz + f(cam.cy)
-    A = f(-0.5 * LOG2E) * (c / det)
-    B = f(LOG2E) * (b / det)
-    C = f(-0.5 * LOG2E) * (a / det)
     L = np.log2(f(opac)).astype(f)
     K = f(2) * np.log(f(255) * f(opac)).astype(f)
     hx = np.sqrt(K * a) + f(1 / 64)
     hy = np.sqrt(K * c) + f(1 / 64)
-    return dict(u=u, v=v, a=sa, b=sb, c=sc, A=A, B=B, C=C, L=L, hx=hx, hy=hy)
+    return dict(u=u, v=v, b=b, c=c, det=det, F1=F1, F2=F2, F3=F3, L=L, hx=hx, hy=hy)
 
 
 def test_error_model_bounds_a_float32_preprocess():
     rng = np.random.default_rng(11)
-    checked, ratio = 0, []
+    checked, far_checked, ratio = 0, 0, []
     for cam in _cams(rng, 12):
         n = 300
         R = cam.R_wc.astype(np.float64)
-        # means in the view volume, some near the plane z = 0.3, some far off axis
+        # means in the view volume, some near the plane z = 0.3, and a fifth just
+        # in front of the near plane far off the axis (|x / z| up to 150: large
+        # elongated footprints whose centres lie far off screen)
         z = np.concatenate([rng.uniform(0.25, 0.6, n // 3), rng.uniform(0.6, 25, n - n // 3)])
         xn = rng.uniform(-0.9, 0.9, n) * cam.width / (2 * cam.fx)
         yn = rng.uniform(-0.9, 0.9, n) * cam.height / (2 * cam.fy)
+        far = slice(n // 5, 2 * n // 5)
+        z[far] = rng.uniform(0.21, 0.4, n // 5)
+        xn[far] = rng.choice([-1.0, 1.0], n // 5) * rng.uniform(10.0, 150.0, n // 5)
         mu = (cam.pos + (np.stack([xn * z, yn * z, z], 1) @ R)).astype(np.float32)
         quat = rng.normal(size=(n, 4)).astype(np.float32)
         ls = rng.normal(-3.5, 0.8, (n, 3)).astype(np.float32)
         ls[: n // 5, 0] = -9.0                       # thin (near-singular) Gaussians
+        ls[far] = rng.normal(-1.5, 0.5, (n // 5, 3))  # large, so that they reach the screen
         opac = rng.uniform(0.02, 0.99, n).astype(np.float32)
         sc = build_hierarchy(mu, quat, ls, opac, np.zeros((n, 16, 3), np.float32))
         leaves = np.flatnonzero(sc.child_count == 0).astype(np.int32)
@@ -114,11 +135,13 @@ def test_error_model_bounds_a_float32_preprocess():
             if row[O.PC.VISIBLE] == 0:
                 continue
             f = _f32_preprocess(cam, sc.pos[g], sc.quat[g], sc.log_scale[g], sc.opacity[g])
-            want = dict(u=row[O.PC.U], v=row[O.PC.V], a=row[O.PC.COV_A], b=row[O.PC.COV_B],
-                        c=row[O.PC.COV_C], L=math.log2(row[O.PC.OPACITY]), hx=row[O.PC.HX],
+            det64 = row[O.PC.COV_A] * row[O.PC.COV_C] - row[O.PC.COV_B] ** 2
+            want = dict(u=row[O.PC.U], v=row[O.PC.V], b=row[O.PC.COV_B], c=row[O.PC.COV_C],
+                        det=det64, L=math.log2(row[O.PC.OPACITY]), hx=row[O.PC.HX],
                         hy=row[O.PC.HY])
-            bound = dict(u=row[O.PC.EU], v=row[O.PC.EV], a=row[O.PC.ESA], b=row[O.PC.ESB],
-                         c=row[O.PC.ESC], L=row[O.PC.EQL], hx=row[O.PC.EHX], hy=row[O.PC.EHY])
+            bound = dict(u=row[O.PC.EU], v=row[O.PC.EV], b=row[O.PC.EB], c=row[O.PC.EC],
+                         det=row[O.PC.EDET] * det64, L=row[O.PC.EQL], hx=row[O.PC.EHX],
+                         hy=row[O.PC.EHY])
             for k in want:
                 err = abs(float(f[k]) - want[k])
                 assert err <= bound[k], (k, g, err, bound[k])
@@ -139,12 +162,15 @@ def test_error_model_bounds_a_float32_preprocess():
                     row[O.PC.CONIC_A] * dx64 ** 2 + 2 * row[O.PC.CONIC_B] * dx64 * dy64 +
                     row[O.PC.CONIC_C] * dy64 ** 2)
                 dx, dy = np.float32(px - f["u"]), np.float32(py - f["v"])
-                q32 = f["A"] * dx * dx + f["B"] * dx * dy + f["C"] * dy * dy + f["L"]
+                p32 = f["F1"] * dx + f["F2"] * dy
+                e32 = f["F3"] * dy
+                q32 = f["L"] - p32 * p32 - e32 * e32
                 eq = O.exponent_error(row, dx64, dy64)
                 assert abs(float(q32) - q64) <= eq, (g, float(q32), q64, eq)
                 ratio.append(abs(float(q32) - q64) / eq)
             checked += 1
-    assert checked > 1500
+            far_checked += int(abs(row[O.PC.U] - cam.cx) > 4 * cam.width)
+    assert checked > 1500 and far_checked > 50
     # rounding is visible against the bounds (they are not vacuous)
     assert max(ratio) > 0.02
 
