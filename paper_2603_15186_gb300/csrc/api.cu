@@ -1143,16 +1143,18 @@ NGS_API ngs_status ngs_select_cut(ngs_ctx *c, const ngs_camera *cams, int32_t n_
         const SceneDev &sc = c->scene;
         const int64_t nblk = (sc.n + cut_partition_nodes() - 1) / cut_partition_nodes();
         const int64_t np = nblk * n_cams;
-        launch_cut_blocked(false, sc.box_lo, sc.box_hi, sc.n, w.cams, n_cams, c->cut_counts,
-                           nullptr, cap32, w.counters + TK_CUT, w.err, c->grid_cut, st);
+        launch_cut_blocked(false, sc.box_lo, sc.box_hi, sc.n, w.cams, nullptr, n_cams,
+                           c->cut_counts, nullptr, cap32, w.counters + TK_CUT, w.err, c->grid_cut,
+                           st);
         const int64_t sparts = (np + scan_partition() - 1) / scan_partition();
         launch_scan_u32(c->cut_counts, c->cut_poff, nullptr, np, c->cut_off32,
                         w.counters + TK_SCAN, w.status, w.epoch, 0, w.err,
                         (int)std::min<int64_t>(sparts, c->grid_scan), st);
         launch_cut_cam_offsets(c->cut_poff, c->cut_off32, nblk, n_cams, cap32, d_offsets,
                                w.counters, w.err, st);
-        launch_cut_blocked(true, sc.box_lo, sc.box_hi, sc.n, w.cams, n_cams, c->cut_poff,
-                           (uint32_t *)d_ids, cap32, w.counters + TK_PRE, w.err, c->grid_cut, st);
+        launch_cut_blocked(true, sc.box_lo, sc.box_hi, sc.n, w.cams, nullptr, n_cams,
+                           c->cut_poff, (uint32_t *)d_ids, cap32, w.counters + TK_PRE, w.err,
+                           c->grid_cut, st);
     } else {
         launch_cut(c->scene, w.cams, n_cams, (uint32_t *)d_ids, cap32, c->cut_off32, w.counters,
                    w.counters + TK_CUT, w.status, w.epoch, 0, w.err, c->grid_cut, st);
@@ -1195,9 +1197,31 @@ NGS_API ngs_status ngs_select_cut_shared(ngs_ctx *c, const ngs_camera *cams, int
                        cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(w.counters, 0, N_COUNTERS * sizeof(uint32_t), st));
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
+    const int64_t cap32 = std::min<int64_t>(cap, (1ll << 32) - 1);
+    if (n_groups == n_cams && n_cams >= kCutBlockedMinCams && (flags & NGS_CUT_FRUSTUM)) {
+        // one frustum-culled cut per camera: the camera-blocked two-pass form
+        const SceneDev &sc = c->scene;
+        const int64_t nblk = (sc.n + cut_partition_nodes() - 1) / cut_partition_nodes();
+        const int64_t np = nblk * n_cams;
+        launch_cut_blocked(false, sc.box_lo, sc.box_hi, sc.n, nullptr, c->cut_cams, n_cams,
+                           c->cut_counts, nullptr, cap32, w.counters + TK_CUT, w.err, c->grid_cut,
+                           st);
+        const int64_t sparts = (np + scan_partition() - 1) / scan_partition();
+        launch_scan_u32(c->cut_counts, c->cut_poff, nullptr, np, c->cut_off32,
+                        w.counters + TK_SCAN, w.status, w.epoch, 0, w.err,
+                        (int)std::min<int64_t>(sparts, c->grid_scan), st);
+        launch_cut_cam_offsets(c->cut_poff, c->cut_off32, nblk, n_cams, cap32, d_offsets,
+                               w.counters, w.err, st);
+        launch_cut_blocked(true, sc.box_lo, sc.box_hi, sc.n, nullptr, c->cut_cams, n_cams,
+                           c->cut_poff, (uint32_t *)d_ids, cap32, w.counters + TK_PRE, w.err,
+                           c->grid_cut, st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        return check_err(c);
+    }
     launch_cut_shared((flags & NGS_CUT_FRUSTUM) != 0, c->scene.box_lo, c->scene.box_hi,
                       c->scene.n, c->cut_cams, c->cut_groups, n_groups, (uint32_t *)d_ids,
-                      std::min<int64_t>(cap, (1ll << 32) - 1), c->cut_off32, w.counters,
+                      cap32, c->cut_off32, w.counters,
                       w.counters + TK_CUT, w.status, w.epoch, 0, w.err, c->grid_cut, st);
     k_offsets_to_i64<<<(n_groups + 256) / 256, 256, 0, st>>>(c->cut_off32, d_offsets, n_groups);
     CK(cudaGetLastError());

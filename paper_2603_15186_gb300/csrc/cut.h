@@ -38,10 +38,13 @@ void launch_cut_shared(bool frustum, const float4 *box_lo, const float4 *box_hi,
 // selected nodes of camera c in block b; a chained scan of those counts in
 // camera-major order gives each (camera, block) its output offset; the
 // writing pass reads those offsets from part_vals and writes the ids. Both
-// passes return at once if *err is set.
+// passes return at once if *err is set. With ccams (instead of cams, which is
+// then unused) each camera's cut is frustum-culled against its planes: the
+// shared cut of a group of one camera.
 void launch_cut_blocked(bool write, const float4 *box_lo, const float4 *box_hi, int64_t n_nodes,
-                        const DevCamera *cams, int n_cams, uint32_t *part_vals, uint32_t *ids,
-                        int64_t cap, uint32_t *ticket, const int *err, int grid, cudaStream_t st);
+                        const DevCamera *cams, const CutCam *ccams, int n_cams,
+                        uint32_t *part_vals, uint32_t *ids, int64_t cap, uint32_t *ticket,
+                        const int *err, int grid, cudaStream_t st);
 
 // offsets[c] = part_off[c * nblk] for c < n_cams, offsets[n_cams] = *total
 // (int64); latches the capacity error when *total exceeds cap.

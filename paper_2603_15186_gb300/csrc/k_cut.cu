@@ -223,16 +223,22 @@ k_cut_shared(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_h
 // for the block; pass 2 (after a scan of the counts in camera-major order)
 // recomputes the selection and writes the ids at the scanned offset plus the
 // prefix within the block. No partition waits on another.
+// With kFrustum (a frustum-culled cut per camera, i.e. shared cuts in groups of
+// one) a node is also dropped when its box lies outside one of the camera's
+// five planes: for a single camera that is its plain cut minus the culled
+// nodes (a culled parent culls the node).
 constexpr int kCutCams = 8;
 static_assert(kCutThreads / 32 == kCutCams, "one warp scans one camera's row counts");
 
-template <bool kWrite>
+template <bool kWrite, bool kFrustum>
 __global__ void __launch_bounds__(kCutThreads)
 k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_hi,
-              int64_t n_nodes, const DevCamera *__restrict__ cams, int n_cams,
+              int64_t n_nodes, const DevCamera *__restrict__ cams,
+              const CutCam *__restrict__ ccams, int n_cams,
               uint32_t *__restrict__ part_vals, uint32_t *__restrict__ ids, int64_t cap,
               uint32_t *ticket, const int *err) {
     __shared__ float s_cam[kCutCams][5];                   // pos xyz, fx, tau
+    __shared__ CutCam s_ccam[kFrustum ? kCutCams : 1];     // the cameras' planes
     __shared__ uint32_t s_bal[kCutCams][kCutItems * 8];    // ballot per (camera, row, warp)
     __shared__ uint32_t s_off[kCutCams][kCutItems * 8];    // its exclusive offset in the block
     __shared__ uint32_t s_part;
@@ -253,10 +259,21 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
             const int j = tid / 5, f = tid - 5 * j;
             float v = 0.0f;
             if (j < nc) {
-                const DevCamera &k = cams[c0 + j];
-                v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : k.tau);
+                if (kFrustum) {
+                    const CutCam &k = ccams[c0 + j];
+                    v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : k.tau);
+                } else {
+                    const DevCamera &k = cams[c0 + j];
+                    v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : k.tau);
+                }
             }
             s_cam[j][f] = v;
+        }
+        if (kFrustum && tid < kCutCams * (int)(sizeof(CutCam) / 4)) {
+            const int j = tid / (int)(sizeof(CutCam) / 4), f = tid - j * (int)(sizeof(CutCam) / 4);
+            if (j < nc)
+                reinterpret_cast<float *>(&s_ccam[j])[f] =
+                    reinterpret_cast<const float *>(&ccams[c0 + j])[f];
         }
         __syncthreads();
 #pragma unroll 1
@@ -276,17 +293,32 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
                     phi = box_hi[parent];
                 }
             }
+            uint32_t m = 0;   // bit j: camera j selects the node
 #pragma unroll
             for (int j = 0; j < kCutCams; ++j) {
-                bool sel = false;
                 if (valid && j < nc) {
                     const float px = s_cam[j][0], py = s_cam[j][1], pz = s_cam[j][2];
                     const float fx = s_cam[j][3], tau = s_cam[j][4];
                     // the rule of cut_selects, parent first (most nodes lie below the cut)
-                    sel = (parent < 0 || !fine_enough(plo, phi, px, py, pz, fx, tau)) &&
-                          (leaf || fine_enough(lo, hi, px, py, pz, fx, tau));
+                    if ((parent < 0 || !fine_enough(plo, phi, px, py, pz, fx, tau)) &&
+                        (leaf || fine_enough(lo, hi, px, py, pz, fx, tau)))
+                        m |= 1u << j;
                 }
-                const uint32_t bal = __ballot_sync(0xffffffffu, sel);
+            }
+            if (kFrustum) {
+                // not unrolled: the planes stay in shared memory instead of
+                // occupying registers for all cameras of the chunk at once
+                uint32_t rest = m;
+#pragma unroll 1
+                while (rest) {
+                    const int j = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    if (frustum_culled(s_ccam[j], lo, hi)) m &= ~(1u << j);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kCutCams; ++j) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (m >> j) & 1u);
                 if (lane == 0) s_bal[j][k * 8 + warp] = bal;
             }
         }
@@ -341,14 +373,23 @@ __global__ void k_cut_cam_offsets(const uint32_t *__restrict__ part_off,
 }
 
 void launch_cut_blocked(bool write, const float4 *box_lo, const float4 *box_hi, int64_t n_nodes,
-                        const DevCamera *cams, int n_cams, uint32_t *part_vals, uint32_t *ids,
-                        int64_t cap, uint32_t *ticket, const int *err, int grid, cudaStream_t st) {
-    if (write)
-        k_cut_blocked<true><<<grid, kCutThreads, 0, st>>>(box_lo, box_hi, n_nodes, cams, n_cams,
-                                                          part_vals, ids, cap, ticket, err);
-    else
-        k_cut_blocked<false><<<grid, kCutThreads, 0, st>>>(box_lo, box_hi, n_nodes, cams, n_cams,
-                                                           part_vals, ids, cap, ticket, err);
+                        const DevCamera *cams, const CutCam *ccams, int n_cams,
+                        uint32_t *part_vals, uint32_t *ids, int64_t cap, uint32_t *ticket,
+                        const int *err, int grid, cudaStream_t st) {
+    if (ccams) {
+        if (write)
+            k_cut_blocked<true, true><<<grid, kCutThreads, 0, st>>>(
+                box_lo, box_hi, n_nodes, cams, ccams, n_cams, part_vals, ids, cap, ticket, err);
+        else
+            k_cut_blocked<false, true><<<grid, kCutThreads, 0, st>>>(
+                box_lo, box_hi, n_nodes, cams, ccams, n_cams, part_vals, ids, cap, ticket, err);
+    } else if (write) {
+        k_cut_blocked<true, false><<<grid, kCutThreads, 0, st>>>(
+            box_lo, box_hi, n_nodes, cams, ccams, n_cams, part_vals, ids, cap, ticket, err);
+    } else {
+        k_cut_blocked<false, false><<<grid, kCutThreads, 0, st>>>(
+            box_lo, box_hi, n_nodes, cams, ccams, n_cams, part_vals, ids, cap, ticket, err);
+    }
 }
 
 void launch_cut_cam_offsets(const uint32_t *part_off, const uint32_t *total, int64_t nblk,

@@ -183,6 +183,24 @@ def test_shared_cut_of_single_cameras_is_the_plain_cut(R, small_floor):
     assert torch.equal(off, off2) and torch.equal(ids[:n], ids2[:n])
 
 
+@pytest.mark.parametrize("guard", [0.0, 32.0])
+def test_frustum_cut_per_camera_blocked_equals_single_pass(R, small_floor, guard):
+    """Frustum-culled cuts of groups of one camera: the camera-blocked
+    two-pass kernel (four or more cameras) gives each camera the same ids as
+    the single-pass kernel on that camera alone, and agrees with the oracle
+    away from flagged decisions."""
+    R.load_scene(small_floor)
+    cams = _group_walk_cams(small_floor)
+    n = len(cams)
+    ids, off = R.select_cut_shared(cams, list(range(n + 1)), frustum=True, guard=guard)
+    ids, off = ids.cpu().numpy(), off.cpu().numpy()
+    for c in range(n):
+        one, o1 = R.select_cut_shared([cams[c]], [0, 1], frustum=True, guard=guard)
+        assert np.array_equal(ids[off[c]:off[c + 1]], one[: int(o1[1].item())].cpu().numpy())
+    _compare_groups(torch.from_numpy(ids), torch.from_numpy(off), small_floor, cams,
+                    list(range(n + 1)), True, guard)
+
+
 def test_shared_cut_rejects_bad_groups_and_reports_capacity(R, small_floor):
     from paper_2603_15186_gb300 import NgsError
     R.load_scene(small_floor)
