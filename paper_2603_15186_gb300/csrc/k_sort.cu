@@ -99,8 +99,7 @@ struct SortSmem {
     static constexpr int kPart = kOsThreads * SortShape<K>::kItems;
     uint32_t whist[kOsWarps][kRadix];     // per-warp digit counts, then warp offsets
     uint32_t match[kOsWarps][kRadix];     // per-warp lane masks of one item's digits (kept 0)
-    uint32_t dstart[kRadix];              // block-local start of each digit
-    uint32_t gstart[kRadix];              // global start of each digit for this partition
+    uint32_t gstart[kRadix];              // global output position of staged slot 0 of each digit's run
     uint32_t wtot[kRadix / 32];
     K keys[kPart];
     uint32_t vals[kPart];
@@ -176,9 +175,11 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             rank[i] = before + __popc(peers & lt);
         }
         __syncthreads();
-        // threads 0..255 own one digit each: warp offsets, partition total,
-        // look-back, and the block-local scan of the totals
-        uint32_t run = 0, incl = 0;
+        // threads 0..255 own one digit each: warp offsets and the partition's
+        // total (published at once for the successors' look-back), then the
+        // block-local scan of the totals
+        uint32_t run = 0, incl = 0, ds = 0;
+        uint64_t *slot = status + part * kRadix + tid;
         if (tid < kRadix) {
             const int d = tid;
 #pragma unroll
@@ -187,16 +188,7 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
                 S.whist[w][d] = run;
                 run += t;
             }
-            uint64_t *slot = status + part * kRadix + d;
-            uint32_t prev = 0;
-            if (part == 0) {
-                publish(slot, pack_status(kFlagPrefix, epoch, run));
-            } else {
-                publish(slot, pack_status(kFlagAgg, epoch, run));
-                look_back(status + d, part, kRadix, epoch, &prev, err);
-                publish(slot, pack_status(kFlagPrefix, epoch, prev + run));
-            }
-            S.gstart[d] = digit_base[d] + prev;
+            publish(slot, pack_status(part == 0 ? kFlagPrefix : kFlagAgg, epoch, run));
             incl = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -207,32 +199,51 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         }
         __syncthreads();
         if (tid < kRadix) {
+            // block-local start of digit d, folded into every warp's offset of
+            // d (one lookup per item when staging)
             uint32_t wbase = 0;
             for (int w = 0; w < warp; ++w) wbase += S.wtot[w];
-            S.dstart[tid] = wbase + incl - run;
+            ds = wbase + incl - run;
+#pragma unroll
+            for (int w = 0; w < kOsWarps; ++w) S.whist[w][tid] += ds;
         }
         __syncthreads();
-        // stage keys, then values, in digit order
+        // stage the keys in digit order, then request the values (they arrive
+        // while the digit owners look back)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             if (base + i * 32 + lane < n) {
                 const uint32_t d = digit_of(key[i], shift, mask);
-                rank[i] += S.dstart[d] + S.whist[warp][d];
+                rank[i] += S.whist[warp][d];
                 S.keys[rank[i]] = key[i];
             }
         }
+        uint32_t val[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const int64_t idx = base + i * 32 + lane;
-            if (idx < n) S.vals[rank[i]] = kIdentity ? (uint32_t)idx : vin[idx];
+            val[i] = kIdentity ? (uint32_t)idx : (idx < n ? vin[idx] : 0u);
         }
+        if (tid < kRadix) {
+            // the partition's exclusive prefix of digit d by decoupled look-back;
+            // output position = gstart[d] + staged position (modulo 2^32)
+            uint32_t prev = 0;
+            if (part > 0) {
+                look_back(status + tid, part, kRadix, epoch, &prev, err);
+                publish(slot, pack_status(kFlagPrefix, epoch, prev + run));
+            }
+            S.gstart[tid] = digit_base[tid] + prev - ds;
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if (base + i * 32 + lane < n) S.vals[rank[i]] = val[i];
         __syncthreads();
         const int64_t rem = n - part * PART;
         const int cnt = rem < PART ? (int)rem : PART;
         for (int j = tid; j < cnt; j += kOsThreads) {
             const K k = S.keys[j];
             const uint32_t d = digit_of(k, shift, mask);
-            const int64_t g = (int64_t)S.gstart[d] + (j - S.dstart[d]);
+            const int64_t g = (int64_t)(S.gstart[d] + (uint32_t)j);
             if (kOut == 0) kout[g] = k;
             vout[g] = S.vals[j];
             if (kOut == 2) {
