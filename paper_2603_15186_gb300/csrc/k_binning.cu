@@ -72,6 +72,12 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v[kScanItems], uint32_t 
 // [out[i], out[i] + in_i) holds element c * kDupChunk (c < chunk_cap), and
 // rect_out[i] = rect[idx[i]] with idx[i] in w: the one gather of the rects in
 // depth order, so that the pair emission reads them sequentially.
+// Global memory is read and written warp-striped (consecutive lanes,
+// consecutive elements: whole sectors per instruction); the scan itself runs
+// on kScanItems consecutive elements per thread, exchanged through a shared
+// array padded by one word per 32 (conflict-free both ways).
+__device__ __forceinline__ int scan_slot(int k) { return k + (k >> 5); }
+
 template <bool kGather>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
@@ -80,6 +86,7 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
        const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, uint32_t *chunk_first,
        int64_t chunk_cap, uint4 *__restrict__ rect_out) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_val[kScanPart + kScanPart / 32];
     __shared__ uint32_t s_part, s_prev;
     if (*err) return;
     const int tid = threadIdx.x;
@@ -92,24 +99,32 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
         __syncthreads();
         const int64_t part = s_part;
         if (part >= nparts) break;
-        const int64_t base = part * kScanPart + (int64_t)tid * kScanItems;
-        uint32_t v[kScanItems], a[kScanItems];
+        const int64_t pbase = part * kScanPart;
+        // striped: element pbase + i * threads + tid
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) {
-            const int64_t j = base + i;
+            const int k = i * kScanThreads + tid;
+            const int64_t j = pbase + k;
+            uint32_t v = 0;
             if (j < n) {
                 if (kGather) {
                     const uint32_t r = idx[j];
                     uint4 rr = rect[r];
-                    v[i] = rect_area(rr);
+                    v = rect_area(rr);
                     rr.w = r;
                     rect_out[j] = rr;
                 } else {
-                    v[i] = in[j];
+                    v = in[j];
                 }
-            } else {
-                v[i] = 0;
             }
+            s_val[scan_slot(k)] = v;
+        }
+        __syncthreads();
+        // blocked: elements pbase + tid * kScanItems + i
+        uint32_t v[kScanItems], a[kScanItems];
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            v[i] = s_val[scan_slot(tid * kScanItems + i)];
             a[i] = v[i];
         }
         const uint32_t total = block_scan(v, s_warp);
@@ -134,19 +149,24 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
         }
         __syncthreads();
         const uint32_t prev = s_prev;
+        const int64_t base = pbase + (int64_t)tid * kScanItems;
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) {
+            const uint32_t lo = prev + v[i];
+            s_val[scan_slot(tid * kScanItems + i)] = lo;
             const int64_t j = base + i;
-            if (j < n) {
-                const uint32_t lo = prev + v[i];
-                out[j] = lo;
-                if (kGather && a[i]) {
-                    const uint64_t hi = (uint64_t)lo + a[i];
-                    for (uint64_t c = ((uint64_t)lo + kDupChunk - 1) / kDupChunk;
-                         c * kDupChunk < hi && (int64_t)c < chunk_cap; ++c)
-                        chunk_first[c] = (uint32_t)j;
-                }
+            if (kGather && a[i] && j < n) {
+                const uint64_t hi = (uint64_t)lo + a[i];
+                for (uint64_t c = ((uint64_t)lo + kDupChunk - 1) / kDupChunk;
+                     c * kDupChunk < hi && (int64_t)c < chunk_cap; ++c)
+                    chunk_first[c] = (uint32_t)j;
             }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int k = i * kScanThreads + tid;
+            if (pbase + k < n) out[pbase + k] = s_val[scan_slot(k)];
         }
         __syncthreads();
     }
@@ -173,28 +193,33 @@ void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const ui
 // K4: the pair array is cut into chunks of kDupChunk pairs, so every CTA
 // iteration writes the same number of pairs however many tiles a Gaussian
 // covers. A chunk starts at the record chunk_first[c] (from K3); its records
-// are staged kDupWindow at a time (offsets, rectangles, record ids, camera
-// tile bases), and each thread's pair finds its record by binary search over
-// the staged offsets. Tile-digit histograms of the radix passes that follow
-// are accumulated on the way.
+// are staged kDupWindow at a time (first pair, first tile key, tile-row
+// stride and rectangle width with its reciprocal, record id). Each pair finds
+// its record through a map of the window's pairs: every record marks its first
+// pair with its window index and a block-wide running maximum fills the rest
+// (record starts increase with the index). Tile-digit histograms of the radix
+// passes that follow are accumulated on the way.
 __global__ void __launch_bounds__(kDupThreads)
 k_duplicate(const uint4 *__restrict__ rect_sorted,
             const uint32_t *__restrict__ poff, const uint32_t *__restrict__ chunk_first,
             const uint32_t *n_vis_p, const uint32_t *n_pairs_p, int64_t pair_cap,
             const DevCamera *__restrict__ cams, uint32_t *__restrict__ pkey,
             uint32_t *__restrict__ pval, uint32_t *hist, int passes, int *err) {
+    constexpr int kPer = kDupChunk / kDupThreads;   // map entries per thread
     __shared__ uint32_t s_h[3][256];       // digit counts of the tile keys, per radix pass
     __shared__ uint32_t s_off[kDupWindow + 1];
-    __shared__ uint4 s_rect[kDupWindow];
+    __shared__ uint4 s_rec[kDupWindow];    // (first tile key, tiles_x, width, 1 / width)
     __shared__ uint32_t s_idx[kDupWindow];
-    __shared__ uint2 s_cam[kDupWindow];    // (tile base, tiles_x) of each record's camera
+    __shared__ uint16_t s_map[kDupChunk];  // window index of each pair's record
+    __shared__ uint32_t s_warp[kDupThreads / 32];
+    static_assert(kDupWindow <= 65536 && kDupChunk % kDupThreads == 0, "map layout");
     if (*err) return;
     const uint32_t n_vis = *n_vis_p, n_pairs = *n_pairs_p;
     if ((int64_t)n_pairs > pair_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(err, kErrCapacity);
         return;
     }
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (hist)
         for (int i = tid; i < 3 * 256; i += kDupThreads) (&s_h[0][0])[i] = 0;
     const int64_t n_chunks = ((int64_t)n_pairs + kDupChunk - 1) / kDupChunk;
@@ -207,36 +232,69 @@ k_duplicate(const uint4 *__restrict__ rect_sorted,
             const int64_t rem = (int64_t)n_vis - r0;
             const int cnt = rem < kDupWindow ? (int)rem : kDupWindow;
             __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) s_map[tid * kPer + i] = 0;
             for (int j = tid; j < cnt; j += kDupThreads) {
-                const uint4 rr = rect_sorted[r0 + j];   // record index in w
+                const uint4 rr = rect_sorted[r0 + j];   // rect, camera, record index in w
+                const uint32_t x0 = rr.x & 0xffffu, y0 = rr.x >> 16, x1 = rr.y & 0xffffu;
+                const uint32_t w = x1 - x0 + 1u;
+                const uint32_t tb = cams[rr.z].tile_base, tsx = (uint32_t)cams[rr.z].tiles_x;
+                s_rec[j] = make_uint4(tb + y0 * tsx + x0, tsx, w, __float_as_uint(1.0f / (float)w));
                 s_idx[j] = rr.w;
-                s_rect[j] = rr;
-                s_cam[j] = make_uint2(cams[rr.z].tile_base, (uint32_t)cams[rr.z].tiles_x);
                 s_off[j] = poff[r0 + j];
             }
             if (tid == 0) s_off[cnt] = (r0 + cnt < (int64_t)n_vis) ? poff[r0 + cnt] : n_pairs;
             __syncthreads();
             const uint32_t q1 = min(p1, s_off[cnt]);
+            // mark each record's first pair in [q, q1) (record 0 may start before q)
+            for (int j = tid + 1; j < cnt; j += kDupThreads) {
+                const uint32_t st = s_off[j];
+                if (st < q1) s_map[st - q] = (uint16_t)j;
+            }
+            __syncthreads();
+            {
+                // running maximum over the map, kPer consecutive entries per thread
+                uint32_t m[kPer], run = 0;
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    run = max(run, (uint32_t)s_map[tid * kPer + i]);
+                    m[i] = run;
+                }
+                uint32_t incl = run;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl = max(incl, t);
+                }
+                if (lane == 31) s_warp[warp] = incl;
+                uint32_t before = __shfl_up_sync(0xffffffffu, incl, 1);
+                if (lane == 0) before = 0;
+                __syncthreads();
+#pragma unroll
+                for (int w = 0; w < kDupThreads / 32; ++w)
+                    if (w < warp) before = max(before, s_warp[w]);
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) s_map[tid * kPer + i] = (uint16_t)max(before, m[i]);
+            }
+            __syncthreads();
             // uniform trip count: every lane of a warp reaches the warp collectives
             for (uint32_t base = q; base < q1; base += kDupThreads) {
                 const uint32_t p = base + tid;
                 const bool valid = p < q1;
                 uint32_t key = 0;
                 if (valid) {
-                    int lo = 0, hi = cnt - 1;   // last j with s_off[j] <= p
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_off[mid] <= p) lo = mid; else hi = mid - 1;
-                    }
-                    const uint4 r = s_rect[lo];
-                    const uint32_t k = p - s_off[lo];
-                    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
-                    const uint32_t w = x1 - x0 + 1u;
-                    const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-                    const uint2 cm = s_cam[lo];
-                    key = cm.x + ty * cm.y + tx;
+                    const int j = s_map[p - q];
+                    const uint4 r = s_rec[j];
+                    // tile (tx, ty) = k mod / div width: a float quotient, then one
+                    // integer correction (its error is below 1 for k < 2^24)
+                    const uint32_t k = p - s_off[j];
+                    int ty = (int)((float)k * __uint_as_float(r.w));
+                    int tx = (int)k - ty * (int)r.z;
+                    if (tx < 0) { --ty; tx += (int)r.z; }
+                    else if (tx >= (int)r.z) { ++ty; tx -= (int)r.z; }
+                    key = r.x + (uint32_t)ty * r.y + (uint32_t)tx;
                     pkey[p] = key;
-                    pval[p] = s_idx[lo];
+                    pval[p] = s_idx[j];
                 }
                 if (hist) {
                     // neighbouring pairs mostly share their high digits: a warp whose
