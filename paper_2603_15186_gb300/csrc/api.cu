@@ -914,7 +914,7 @@ NGS_API ngs_status ngs_create(const ngs_config *cfg, ngs_ctx **out) {
     x->grid_pre = 4 * x->num_sms;
     x->grid_sort32 = 2 * x->num_sms;
     x->grid_sort64 = 2 * x->num_sms;
-    x->grid_scan = 4 * x->num_sms;
+    x->grid_scan = 5 * x->num_sms;
     x->grid_dup = 8 * x->num_sms;
     x->grid_ranges = 16 * x->num_sms;
     *out = x;
