@@ -293,10 +293,36 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
                     phi = box_hi[parent];
                 }
             }
+            // kFrustum: the cameras whose view volume the union of the warp's
+            // node boxes can meet (a box outside a half-space has every box it
+            // contains outside too, also in float32: the tests are monotone in
+            // the bounds); the others cull all 32 nodes without a test per node
+            uint32_t live = (1u << nc) - 1u;
+            if (kFrustum) {
+                const float inf = __int_as_float(0x7f800000);
+                float4 ulo = valid ? lo : make_float4(inf, inf, inf, 0.f);
+                float4 uhi = valid ? hi : make_float4(-inf, -inf, -inf, 0.f);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ulo.x = fminf(ulo.x, __shfl_xor_sync(0xffffffffu, ulo.x, o));
+                    ulo.y = fminf(ulo.y, __shfl_xor_sync(0xffffffffu, ulo.y, o));
+                    ulo.z = fminf(ulo.z, __shfl_xor_sync(0xffffffffu, ulo.z, o));
+                    uhi.x = fmaxf(uhi.x, __shfl_xor_sync(0xffffffffu, uhi.x, o));
+                    uhi.y = fmaxf(uhi.y, __shfl_xor_sync(0xffffffffu, uhi.y, o));
+                    uhi.z = fmaxf(uhi.z, __shfl_xor_sync(0xffffffffu, uhi.z, o));
+                }
+                uint32_t keep = 0;
+                if (ulo.x <= uhi.x) {   // some valid node
+#pragma unroll 1
+                    for (int j = 0; j < nc; ++j)
+                        if (!frustum_culled(s_ccam[j], ulo, uhi)) keep |= 1u << j;
+                }
+                live = keep;
+            }
             uint32_t m = 0;   // bit j: camera j selects the node
 #pragma unroll
             for (int j = 0; j < kCutCams; ++j) {
-                if (valid && j < nc) {
+                if (valid && j < nc && ((live >> j) & 1u)) {
                     const float px = s_cam[j][0], py = s_cam[j][1], pz = s_cam[j][2];
                     const float fx = s_cam[j][3], tau = s_cam[j][4];
                     // the rule of cut_selects, parent first (most nodes lie below the cut)
