@@ -183,17 +183,17 @@ def measured_peaks():
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the launches of one timed step of this workload at 32x32 tiles in 16x16
-# compositing blocks, batch 128) from the ncu capture summarised in
-# profiles/traffic_batch256_floor4m_f16.md. Each figure is tied to the sources
-# of the kernel it was taken on (sha256 of the files, concatenated, first 16 hex
-# digits) and reads null once they change.
+# over the launches of one render of this workload at 32x32 tiles in 16x16
+# compositing blocks, batch 128; for "onesweep" over all 18 radix passes) from
+# the one-pass ncu capture summarised in profiles/traffic_batch256_floor4m_f16.md.
+# Each figure is tied to the sources of the kernel it was taken on (sha256 of
+# the files, concatenated, first 16 hex digits) and reads null once they change.
 MEASURED_TRAFFIC = {
-    "onesweep": (1_272_611_968, ("k_sort.cu", "ngs_internal.cuh"), "ddf49ffbd0dc47d8"),
-    "composite": (607_214_762, ("k_composite.cu", "ngs_internal.cuh"), "3352ec3e04f8b776"),
-    "cut_preprocess": (4_074_056_789, ("k_preprocess.cu", "ngs_internal.cuh"), "f75000aca5ba55bf"),
-    "duplicate": (2_314_059_178, ("k_binning.cu", "ngs_internal.cuh"), "6841a493ada61746"),
-    "pair_offsets": (2_114_417_237, ("k_binning.cu", "ngs_internal.cuh"), "6841a493ada61746"),
+    "onesweep": (1_258_000_000, ("k_sort.cu", "ngs_internal.cuh"), "ef81afe60039874b"),
+    "composite": (712_700_000, ("k_composite.cu", "ngs_internal.cuh"), "77013030d44543c8"),
+    "cut_preprocess": (4_074_800_000, ("k_preprocess.cu", "ngs_internal.cuh"), "7685d1d51c3c160b"),
+    "duplicate": (2_315_800_000, ("k_binning.cu", "ngs_internal.cuh"), "e1e33bc0755acb8e"),
+    "pair_offsets": (2_062_000_000, ("k_binning.cu", "ngs_internal.cuh"), "e1e33bc0755acb8e"),
 }
 
 
