@@ -60,7 +60,10 @@ __device__ __forceinline__ float rect_qmax(float F1, float F2, float F3, float L
         const float p = fmaf(F1, x, F2 * y), e = F3 * y;
         return -fmaf(p, p, e * e);
     };
-    const float sy = -F1 * F2 / fmaf(F2, F2, F3 * F3), sx = -F2 / F1;
+    // the slopes only place the point evaluated on each edge: an approximate
+    // quotient moves it by a relative 1e-6, which lowers the value found by far
+    // less than the threshold margin (the maximum is flat there)
+    const float sy = __fdividef(-F1 * F2, fmaf(F2, F2, F3 * F3)), sx = __fdividef(-F2, F1);
     float best = qf(ex0, fminf(fmaxf(sy * ex0, ey0), ey1));
     best = fmaxf(best, qf(ex1, fminf(fmaxf(sy * ex1, ey0), ey1)));
     best = fmaxf(best, qf(fminf(fmaxf(sx * ey0, ex0), ex1), ey0));
@@ -78,8 +81,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // still pass the alpha threshold: the ellipse (F1 dx + F2 dy)^2 + (F3 dy)^2 <=
 // kappa, kappa = L - log2(1/255) + kTileMarginLog2, has half-widths
 // sqrt(kappa (F2^2 + F3^2)) / (F1 F3) and sqrt(kappa) / F3 (no cancellation in
-// the factored form); the box is widened by a relative 2^-10 and by 1/64 px.
-// Returned as (xmin, xmax, ymin, ymax) in pixel coordinates.
+// the factored form); the box is widened by a relative 2^-10 and by 1/64 px,
+// far more than the relative 1e-6 of the approximate square roots and
+// quotients taken here. Returned as (xmin, xmax, ymin, ymax) in pixel
+// coordinates.
 __device__ __forceinline__ float4 record_box(float x, float y, float F1, float F2, float F3,
                                             float L) {
     const float kappa = L - (kLog2AlphaMin - kTileMarginLog2);
@@ -87,9 +92,10 @@ __device__ __forceinline__ float4 record_box(float x, float y, float F1, float F
     if (!(kappa >= 0.0f)) return make_float4(inf, -inf, inf, -inf);   // empty
     if (!(F1 > 0.0f) || !(F3 > 0.0f)) return make_float4(-inf, inf, -inf, inf);
     const float grow = 1.0f + 0.0009765625f;
-    const float sk = sqrtf(kappa);
-    const float hx = fmaf(sk * sqrtf(fmaf(F2, F2, F3 * F3)) / (F1 * F3), grow, 0.015625f);
-    const float hy = fmaf(sk / F3, grow, 0.015625f);
+    const float sk = kappa > 0.0f ? kappa * rsqrtf(kappa) : 0.0f;
+    const float m = fmaf(F2, F2, F3 * F3);   // >= F3^2 > 0
+    const float hx = fmaf(__fdividef(sk * (m * rsqrtf(m)), F1 * F3), grow, 0.015625f);
+    const float hy = fmaf(__fdividef(sk, F3), grow, 0.015625f);
     return make_float4(x - hx, x + hx, y - hy, y + hy);
 }
 
