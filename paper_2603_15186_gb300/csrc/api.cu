@@ -117,6 +117,14 @@ struct ngs_ctx {
     int ev_groups = 0;
     int kernels_per_render = 0;
 
+    // batched renders record ev_sb[k] once sub-batch k's images are complete
+    // (into the graph as external event nodes), so that ngs_render_host can
+    // copy a sub-batch's images to the host while the next ones render, on
+    // copy_stream; ev_copied joins the copies back into the caller's stream
+    std::vector<cudaEvent_t> ev_sb;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied = nullptr;
+
     // navigation scratch (occupied-any map, goals, frontier queues), grown on demand
     unsigned char *nav_tmp = nullptr;
     size_t nav_tmp_bytes = 0;
@@ -235,11 +243,31 @@ ngs_status ensure_events(ngs_ctx *c, int groups) {
     return NGS_OK;
 }
 
+// Records e on st; under stream capture as an external event node (which the
+// host and other streams can wait on after each graph launch). The external
+// flag is only accepted while the stream is capturing.
+void record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
+ngs_status ensure_sb_events(ngs_ctx *c, int n) {
+    while ((int)c->ev_sb.size() < n) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->ev_sb.push_back(e);
+    }
+    return NGS_OK;
+}
+
 void mark(ngs_ctx *c, int group, int k, cudaStream_t st) {
-    // external: under stream capture this becomes an event-record node that
-    // the host can wait on and time after each graph launch
-    if (c->timing)
-        cudaEventRecordWithFlags(c->ev[(size_t)group * kMarks + k], st, cudaEventRecordExternal);
+    // under stream capture an event-record node that the host can wait on and
+    // time after each graph launch
+    if (c->timing) record_event(c->ev[(size_t)group * kMarks + k], st);
 }
 
 struct SortHook {
@@ -528,6 +556,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
                      c->composite_order ? w.order : nullptr,
                      sb_index < kTailSlots ? w.work64 + 2 + 2 * sb_index : nullptr, st);
     mark(c, sb_index, MK_COMPOSITE, st);
+    record_event(c->ev_sb[sb_index], st);
     if (sb_index < c->stats_cap / 4)
         k_copy_stats<<<1, 32, 0, st>>>(w.counters, c->stats_dev + 4 * sb_index);
 }
@@ -724,6 +753,7 @@ ngs_status render_batched(ngs_ctx *c, int n_cams, cudaStream_t st) {
     ngs_status es = epoch_guard(c, st, kEpochStride * sbs.size());
     if (es != NGS_OK) return es;
     if ((es = ensure_events(c, (int)sbs.size())) != NGS_OK) return es;
+    if ((es = ensure_sb_events(c, (int)sbs.size())) != NGS_OK) return es;
     key.push_back(c->timing ? 1 : 0);
     c->kernels_per_render = 0;
     for (const SubBatch &sb : sbs) c->kernels_per_render += kernels_of(sb, true, c->composite_order);
@@ -928,7 +958,10 @@ NGS_API ngs_status ngs_destroy(ngs_ctx *c) {
     if (c->nav_tmp) dfree(c->nav_tmp);
     drop_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->ev_copied) cudaEventDestroy(c->ev_copied);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_sb) cudaEventDestroy(e);
     free_work(c);
     free_scene(c);
     dfree(c->sort_tmp_keys);
@@ -1294,21 +1327,46 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n
         off += (size_t)3 * cams[i].width * cams[i].height;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // cameras [i0, i1) to the host, consecutive images whose host buffers
+    // also follow each other in one copy
+    auto copy_out = [&](int i0, int i1, cudaStream_t cs) -> ngs_status {
+        for (int i = i0; i < i1;) {
+            size_t bytes = sizeof(float) * 3 * cams[i].width * cams[i].height;
+            int j = i + 1;
+            while (j < i1 && h_images[j] == h_images[j - 1] + 3 * (size_t)cams[j - 1].width *
+                                                                 cams[j - 1].height) {
+                bytes += sizeof(float) * 3 * cams[j].width * cams[j].height;
+                ++j;
+            }
+            CK(cudaMemcpyAsync(h_images[i], dimg[i], bytes, cudaMemcpyDeviceToHost, cs));
+            i = j;
+        }
+        return NGS_OK;
+    };
     // a batched render whose pairs overflow the buffer is planned again from
-    // the densities the device counted (smaller sub-batches) and redone
+    // the densities the device counted (smaller sub-batches) and redone;
+    // each sub-batch's images are copied out as soon as they are complete
     ngs_status s = NGS_OK;
     for (int attempt = 0; attempt < kCapacityRetries; ++attempt) {
         s = render_common(c, cams, n_cams, dimg.data(), st);
         if (s != NGS_OK) return s;
-        if (c->mode != NGS_MODE_BATCHED) break;
+        if (c->mode != NGS_MODE_BATCHED) {
+            if ((s = copy_out(0, n_cams, st)) != NGS_OK) return s;
+            return ngs_synchronize(c, stream);
+        }
+        if (!c->copy_stream) CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        if (!c->ev_copied) CK(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+        for (size_t k = 0; k < c->last_plan.size(); ++k) {
+            CK(cudaStreamWaitEvent(c->copy_stream, c->ev_sb[k], 0));
+            if ((s = copy_out(c->last_plan[k].c0, c->last_plan[k].c1, c->copy_stream)) != NGS_OK)
+                return s;
+        }
+        CK(cudaEventRecord(c->ev_copied, c->copy_stream));
+        CK(cudaStreamWaitEvent(st, c->ev_copied, 0));
         s = ngs_synchronize(c, stream);
         if (s != NGS_ERR_CAPACITY) break;
     }
-    if (s != NGS_OK) return s;
-    for (int i = 0; i < n_cams; ++i)
-        CK(cudaMemcpyAsync(h_images[i], dimg[i], sizeof(float) * 3 * cams[i].width * cams[i].height,
-                           cudaMemcpyDeviceToHost, st));
-    return ngs_synchronize(c, stream);
+    return s;
 }
 
 NGS_API ngs_status ngs_last_stats(ngs_ctx *c, ngs_stats *out) {

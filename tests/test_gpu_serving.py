@@ -91,3 +91,42 @@ def test_pair_overflow_is_replanned_not_lost(small_floor):
         assert np.array_equal(a, im.cpu().numpy())
     for r in (ref, small, srv):
         r.close()
+
+
+def test_render_host_contiguous_pinned_buffer(small_floor):
+    """The host-buffer render copies each sub-batch's images out while the next
+    sub-batches render, one copy per run of consecutive images whose host
+    buffers follow each other: into one pinned buffer (one copy per sub-batch)
+    and into separate arrays (one copy per image) the images equal the device
+    render of the same cameras bit for bit, over several sub-batches."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes as C
+    from paper_2603_15186_gb300 import Renderer
+    from paper_2603_15186_gb300.renderer import camera_array
+    cams = mixed_batch_cameras(small_floor, 24, seed=36, resolutions=((96, 72), (160, 120)),
+                               n_walkers=4)
+    R = Renderer(device=0, cut_capacity=1 << 22, record_capacity=1 << 22, pair_capacity=1 << 20)
+    R.load_scene(small_floor)
+    R.set_mode("batched")
+    R.set_pairs_per_pixel(400)          # a high estimate: several sub-batches
+    ref = [im.cpu().numpy() for im in R.render(cams)]
+    assert R.stats()["sub_batches"] > 1
+    sizes = [3 * c.width * c.height for c in cams]
+    host = torch.full((sum(sizes),), -1.0, dtype=torch.float32).pin_memory()
+    ptrs, off = [], 0
+    for n in sizes:
+        ptrs.append(C.c_void_p(host.data_ptr() + 4 * off))
+        off += n
+    for _ in range(2):                  # the second call replays the graph
+        R.render_host_ptrs(camera_array(cams), len(cams), (C.c_void_p * len(cams))(*ptrs))
+        off = 0
+        for c, n, r in zip(cams, sizes, ref):
+            got = host[off:off + n].numpy().reshape(3, c.height, c.width)
+            assert np.array_equal(got, r)
+            off += n
+        host.fill_(-1.0)
+    got = R.render_host(cams)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    R.close()
