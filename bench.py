@@ -509,7 +509,7 @@ def run_ours(args, world, rank, local, pg):
         out["e2e"] = {"value": round(world * pixels / (e2e_s * 1e6), 2), "unit": "Mpix/s",
                       "h2d_bytes_per_step": len(cams) * C.sizeof(_lib.Camera),
                       "d2h_bytes_per_step": 12 * pixels, "ms_per_step": round(e2e_s * 1e3, 3),
-                      "path": "ngs_render_host: camera table H2D, render, images D2H to pinned host"}
+                      "path": "ngs_render_host: camera table H2D, render; the compositing kernels write the images into pinned host memory (device-mapped), synchronised"}
 
     # CPU oracle baseline on a bounded sample, and parity of the batched images
     if rank == 0 and not args.no_cpu:

@@ -239,8 +239,13 @@ NGS_API ngs_status ngs_select_cut_shared(ngs_ctx *ctx, const ngs_camera *cams, i
 NGS_API ngs_status ngs_render(ngs_ctx *ctx, const ngs_camera *cams, int32_t n_cams,
                               float *const *d_images, void *stream);
 
-/* As ngs_render, then copies each image to h_images[c] (host memory, pinned
- * or pageable) and synchronises the stream. A batched render whose pairs
+/* As ngs_render into host memory, then synchronises the stream. h_images[c]
+ * holds 3 x H x W floats. Page-locked memory the device can address
+ * (cudaHostAlloc'd or registered and mapped) is written directly by the
+ * render kernels; other host memory (pageable) receives a copy of each
+ * sub-batch's images as soon as they are complete, while the next sub-batches
+ * render. A buffer smaller than its image is undefined behaviour either way
+ * (written past its end). A batched render whose pairs
  * overflowed pair_capacity is planned again from the pair counts the device
  * reported (smaller sub-batches) and redone, up to 4 renders in all; it
  * returns NGS_ERR_CAPACITY only if that does not suffice (for example one

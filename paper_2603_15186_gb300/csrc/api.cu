@@ -1305,12 +1305,39 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n
     if (!c) return NGS_ERR_INVALID_ARG;
     if (!cams || !h_images || n_cams <= 0) return NGS_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
-    // device images are carved from one buffer owned by the call
     size_t total = 0;
     for (int i = 0; i < n_cams; ++i) {
         if (!camera_ok(cams[i]) || !h_images[i]) return NGS_ERR_INVALID_ARG;
         total += (size_t)3 * cams[i].width * cams[i].height;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    // Page-locked host memory that the device can address (cudaHostAlloc'd or
+    // registered, mapped): the compositing kernels write the pixels straight
+    // into it, so the images cross to the host while the render runs
+    {
+        std::vector<float *> hdev(n_cams);
+        bool mapped = true;
+        for (int i = 0; i < n_cams && mapped; ++i) {
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, h_images[i]) != cudaSuccess ||
+                a.type != cudaMemoryTypeHost || !a.devicePointer) {
+                cudaGetLastError();   // an unregistered pointer is not an error here
+                mapped = false;
+            } else {
+                hdev[i] = static_cast<float *>(a.devicePointer);
+            }
+        }
+        if (mapped) {
+            ngs_status s = NGS_OK;
+            for (int attempt = 0; attempt < kCapacityRetries; ++attempt) {
+                if ((s = render_common(c, cams, n_cams, hdev.data(), st)) != NGS_OK) return s;
+                s = ngs_synchronize(c, stream);
+                if (s != NGS_ERR_CAPACITY || c->mode != NGS_MODE_BATCHED) break;
+            }
+            return s;
+        }
+    }
+    // otherwise device images carved from one buffer owned by the call
     static thread_local float *dbuf = nullptr;
     static thread_local size_t dcap = 0;
     if (total > dcap) {
@@ -1326,7 +1353,6 @@ NGS_API ngs_status ngs_render_host(ngs_ctx *c, const ngs_camera *cams, int32_t n
         dimg[i] = dbuf + off;
         off += (size_t)3 * cams[i].width * cams[i].height;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     // cameras [i0, i1) to the host, consecutive images whose host buffers
     // also follow each other in one copy
     auto copy_out = [&](int i0, int i1, cudaStream_t cs) -> ngs_status {

@@ -94,11 +94,11 @@ def test_pair_overflow_is_replanned_not_lost(small_floor):
 
 
 def test_render_host_contiguous_pinned_buffer(small_floor):
-    """The host-buffer render copies each sub-batch's images out while the next
-    sub-batches render, one copy per run of consecutive images whose host
-    buffers follow each other: into one pinned buffer (one copy per sub-batch)
-    and into separate arrays (one copy per image) the images equal the device
-    render of the same cameras bit for bit, over several sub-batches."""
+    """The host-buffer render writes into page-locked host memory directly
+    (one pinned buffer holding every image) and copies into pageable arrays
+    each sub-batch's images while the next sub-batches render; both equal the
+    device render of the same cameras bit for bit, over several sub-batches
+    and a graph replay."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import ctypes as C
