@@ -953,32 +953,44 @@ k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
         const uint32_t ncand = info.y >> 16;
         int64_t pos = part_pos[idx];
         // the partition's slots hold its candidates in node order; the visible
-        // ones are packed to their dense positions, holes are skipped. Uniform
-        // trip count: every lane reaches the warp collectives
-        for (uint32_t k0 = 0; k0 < ncand; k0 += 32) {
-            const uint32_t k = k0 + lane;
-            uint32_t key = kKeyHole;
-            if (k < ncand && (int64_t)info.x + k < cap) key = dkey_sparse[info.x + k];
-            const bool vis = key != kKeyHole;
-            const uint32_t vb = __ballot_sync(0xffffffffu, vis);
-            const int64_t dst = pos + __popc(vb & lanemask_lt());
-            const bool valid = vis && dst < cap;
-            if (valid) {
-                dkey[dst] = key;
-                didx[dst] = info.x + k;
-            }
-            pos += __popc(vb);
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            if (vmask) {
-                const int leader = __ffs(vmask) - 1;
+        // ones are packed to their dense positions, holes are skipped. Four
+        // rows of 32 slots are requested at once (one memory round trip), then
+        // packed row by row. Uniform trip count: every lane reaches the warp
+        // collectives
+        constexpr int kRows = 4;
+        for (uint32_t k0 = 0; k0 < ncand; k0 += 32 * kRows) {
+            uint32_t keys[kRows];
 #pragma unroll
-                for (int qd = 0; qd < 4; ++qd) {
-                    const uint32_t d = (key >> (8 * qd)) & 255u;
-                    const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
-                    if (__all_sync(0xffffffffu, !valid || d == dl)) {
-                        if (lane == leader) atomicAdd(&s_h[qd][d], (uint32_t)__popc(vmask));
-                    } else if (valid) {
-                        atomicAdd(&s_h[qd][d], 1u);
+            for (int u = 0; u < kRows; ++u) {
+                const uint32_t k = k0 + 32 * u + lane;
+                keys[u] = kKeyHole;
+                if (k < ncand && (int64_t)info.x + k < cap) keys[u] = dkey_sparse[info.x + k];
+            }
+#pragma unroll
+            for (int u = 0; u < kRows; ++u) {
+                const uint32_t k = k0 + 32 * u + lane;
+                const uint32_t key = keys[u];
+                const bool vis = key != kKeyHole;
+                const uint32_t vb = __ballot_sync(0xffffffffu, vis);
+                const int64_t dst = pos + __popc(vb & lanemask_lt());
+                const bool valid = vis && dst < cap;
+                if (valid) {
+                    dkey[dst] = key;
+                    didx[dst] = info.x + k;
+                }
+                pos += __popc(vb);
+                const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                if (vmask) {
+                    const int leader = __ffs(vmask) - 1;
+#pragma unroll
+                    for (int qd = 0; qd < 4; ++qd) {
+                        const uint32_t d = (key >> (8 * qd)) & 255u;
+                        const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+                        if (__all_sync(0xffffffffu, !valid || d == dl)) {
+                            if (lane == leader) atomicAdd(&s_h[qd][d], (uint32_t)__popc(vmask));
+                        } else if (valid) {
+                            atomicAdd(&s_h[qd][d], 1u);
+                        }
                     }
                 }
             }
