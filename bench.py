@@ -387,15 +387,16 @@ def run_ours(args, world, rank, local, pg):
 
         def alu_entry():
             # the compositing kernel is bound by FP32 issue: per pixel-Gaussian
-            # evaluation its inner loop issues 11 FP32-pipe lane operations in
+            # evaluation its inner loop issues 10.5 FP32-pipe lane operations in
             # the common path (exponent from per-row coefficients 2, threshold
             # compare 1, threshold factor 1, clamp 1, weight alpha T 1, colour 3,
-            # T (1 - alpha) 2) and one exp2; the stop test runs once per group
-            # of four records (a group in which a pixel stops is redone with it)
+            # T - alpha T 1, and the stop test's two compares once per group of
+            # four records: 0.5) and one exp2 (a group in which a pixel stops is
+            # redone with the stop factor: extra work on top of this bound)
             sms = torch.cuda.get_device_properties(local).multi_processor_count
             mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) \
                 if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
-            peak_e = sms * 128 * mhz * 1e6 / 11.0 / 1e12
+            peak_e = sms * 128 * mhz * 1e6 / 10.5 / 1e12
             n_launch = max(launches_of("composite"), 1)
             dur_ms = gt["composite"] / n_launch
             ach = stats["evaluations"] / n_launch / (dur_ms * 1e-3) / 1e12
@@ -403,7 +404,7 @@ def run_ours(args, world, rank, local, pg):
             return {"kernel": "composite", "bound": "alu", "achieved": round(ach, 3),
                     "peak": round(peak_e, 3), "unit": "Teval/s", "frac": round(ach / peak_e, 4),
                     "traffic": measured_traffic("composite"),
-                    "peak_kind": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz / 11 FP32 lane ops "
+                    "peak_kind": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz / 10.5 FP32 lane ops "
                                  "per evaluation (the inner loop's common path)",
                     "launches_per_step": n_launch, "avg_launch_ms": round(dur_ms, 4),
                     "hbm_achieved_gbs": round(hb, 1)}
