@@ -129,4 +129,11 @@ def test_render_host_contiguous_pinned_buffer(small_floor):
     got = R.render_host(cams)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+    # the plain per-view path writes into the pinned buffer the same way
+    R.set_mode("plain")
+    R.render_host_ptrs(camera_array(cams), len(cams), (C.c_void_p * len(cams))(*ptrs))
+    off = 0
+    for c, n, r in zip(cams, sizes, ref):
+        assert np.array_equal(host[off:off + n].numpy().reshape(3, c.height, c.width), r)
+        off += n
     R.close()
