@@ -246,6 +246,24 @@ def test_render_small_box_view(R, box10k, tau):
     assert pairs > 1000
 
 
+def test_large_footprints_span_many_tiles_and_windows(R, box10k):
+    """A close, long-focal camera on the box scene with 8x8 tiles: Gaussians
+    cover up to hundreds of tiles, so a record's pairs spread over several
+    pair chunks and a chunk can start inside a record; the tile lists and
+    the image still match the oracle's."""
+    R.load_scene(box10k)
+    cam = look_camera((1.0, 2.0, 1.2), 0.0, 512, 384, fx=600.0, tau=0.0)
+    ref = O.render(box10k, cam, tile=(8, 8))
+    area = (ref.rect[:, 2] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 1] + 1)
+    assert area.max() > 2048          # one record holds more than a whole pair chunk
+    img = _render_one(R, box10k, cam, tile=(8, 8))
+    compare_image(img, ref)
+    n_tiles = len(ref.ranges)
+    rng, nodes = R.tile_lists(0, n_tiles, len(ref.keys) + 4096)
+    compare_tile_lists(rng, nodes, ref, (8, 8))
+    R.set_tile(16, 16)
+
+
 def _floor_cams(scene):
     cams = walk_cameras(scene, 4, 77, 160, 120, fx=150.0, tau=0.0)
     cams[1].width, cams[1].height, cams[1].cx, cams[1].cy = 97, 61, 48.5, 30.5   # ragged tiles
