@@ -512,14 +512,15 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     launch_sort(da, c->grid_sort32, st);
     eo += 4;
     const int dsel = 4 & 1;  // four passes: the result is back in buffer 0
+    // the tile sort's digit histograms are counted by the offset scan
+    cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st);
     launch_pair_offsets(w.rect, w.didx[dsel], w.counters + CNT_VIS, w.poff, w.counters,
                         w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
-                        w.chunk_first, w.rect_sorted, c->grid_scan, st);
+                        w.chunk_first, w.rect_sorted, cams, w.hist, sb.tile_passes,
+                        c->grid_scan, st);
     mark(c, sb_index, MK_POFF, st);
-    cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st);
     launch_duplicate(w.rect_sorted, w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
-                     w.pair_cap, cams, w.pkey[0], w.pval[0], w.hist, sb.tile_passes, w.err,
-                     c->grid_dup, st);
+                     w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, c->grid_dup, st);
     mark(c, sb_index, MK_DUP, st);
     int psel = 0;
     SortHook th{c, sb_index, MK_THIST, st};
@@ -530,7 +531,7 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
         pa.n_dev = w.counters + CNT_PAIRS; pa.n_host = -1; pa.n_max = w.pair_cap;
         pa.key_bytes = 4; pa.begin_bit = 0; pa.end_bit = 8 * sb.tile_passes;
         pa.vals_identity = false;
-        pa.hist_ready = true;   // counted by the duplication kernel
+        pa.hist_ready = true;   // counted by the offset scan
         pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
         pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
         pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;
@@ -670,19 +671,19 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         eo += 4;
         const int gscan = std::max<int64_t>(1, ((int64_t)n_vis + scan_partition() - 1) /
                                                    scan_partition());
+        CK(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st));
         launch_pair_offsets(w.rect, w.didx[0], w.counters + CNT_VIS, w.poff, w.counters,
                             w.pair_cap, w.counters + TK_SCAN, w.status, w.epoch, eo++, w.err,
-                            w.chunk_first, w.rect_sorted, gscan, st);
+                            w.chunk_first, w.rect_sorted, cams, w.hist, sb.tile_passes, gscan,
+                            st);
         mark(c, ci, MK_POFF, st);
         if ((s = read_u32(w.counters + CNT_PAIRS, &n_pairs, st)) != NGS_OK) return s;
         if ((s = check_err(c)) != NGS_OK) return s;
         if ((int64_t)n_pairs > w.pair_cap) return NGS_ERR_CAPACITY;
         const int gdup = (int)std::max<int64_t>(
             1, std::min<int64_t>(((int64_t)n_pairs + 2047) / 2048, 8 * (int64_t)c->num_sms));
-        CK(cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * 256 * 3, st));
         launch_duplicate(w.rect_sorted, w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
-                         w.pair_cap, cams, w.pkey[0], w.pval[0], w.hist, sb.tile_passes, w.err,
-                         gdup, st);
+                         w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, gdup, st);
         mark(c, ci, MK_DUP, st);
         int psel = 0;
         SortHook th{c, ci, MK_THIST, st};
@@ -695,7 +696,7 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
             pa.n_dev = nullptr; pa.n_host = n_pairs; pa.n_max = w.pair_cap;
             pa.key_bytes = 4; pa.begin_bit = 0; pa.end_bit = 8 * sb.tile_passes;
             pa.vals_identity = false;
-            pa.hist_ready = true;   // counted by the duplication kernel
+            pa.hist_ready = true;   // counted by the offset scan
             pa.hist = w.hist; pa.tickets = w.counters + TK_SORT0 + 4; pa.status = w.status;
             pa.epoch = w.epoch; pa.epoch_off = eo; pa.err = w.err;
             pa.hook = c->timing ? sort_hook : nullptr; pa.hook_user = &th;

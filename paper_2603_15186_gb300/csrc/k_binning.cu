@@ -78,18 +78,60 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v[kScanItems], uint32_t 
 // array padded by one word per 32 (conflict-free both ways).
 __device__ __forceinline__ int scan_slot(int k) { return k + (k >> 5); }
 
+// Digit counts of the radix passes over the consecutive tile keys
+// [k0, k0 + w) (one row of a Gaussian's tile rectangle). Pass 0 (the low 8
+// bits): w >> 8 to every digit (full) and one to each digit of the cyclic run
+// of w & 255 digits from k0 & 255, added as +1/-1 at its ends (d0, a
+// difference array read back by a prefix sum); passes 1, 2: a count per
+// digit value the run crosses (hh).
+struct TileDigits {
+    uint32_t d0[257];
+    uint32_t full;
+    uint32_t hh[2][256];
+};
+__device__ __forceinline__ void tile_digits_add(TileDigits &H, uint32_t k0, uint32_t w,
+                                                int passes) {
+    const uint32_t full = w >> 8, r = w & 255u, d = k0 & 255u;
+    if (full) atomicAdd(&H.full, full);
+    if (r) {
+        atomicAdd(&H.d0[d], 1u);
+        if (d + r <= 256u) {
+            atomicAdd(&H.d0[d + r], 0xffffffffu);
+        } else {
+            atomicAdd(&H.d0[0], 1u);
+            atomicAdd(&H.d0[d + r - 256u], 0xffffffffu);
+        }
+    }
+    for (int q = 1; q < passes; ++q) {
+        const int sh = 8 * q;
+        const uint64_t a = k0, e = (uint64_t)k0 + w;
+        for (uint64_t v = a >> sh; (v << sh) < e; ++v) {
+            const uint64_t lo = v << sh > a ? v << sh : a;
+            const uint64_t hi = (v + 1) << sh < e ? (v + 1) << sh : e;
+            atomicAdd(&H.hh[q - 1][v & 255u], (uint32_t)(hi - lo));
+        }
+    }
+}
+
 template <bool kGather>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
        const uint32_t *__restrict__ idx, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
        uint32_t *total_out, int64_t total_cap, uint32_t *ticket, uint64_t *status,
        const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, uint32_t *chunk_first,
-       int64_t chunk_cap, uint4 *__restrict__ rect_out) {
+       int64_t chunk_cap, uint4 *__restrict__ rect_out, const DevCamera *__restrict__ cams,
+       uint32_t *hist, int passes) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_val[kScanPart + kScanPart / 32];
     __shared__ uint32_t s_part, s_prev;
+    __shared__ TileDigits s_td;
     if (*err) return;
     const int tid = threadIdx.x;
+    if (kGather && hist) {
+        for (int i = tid; i < (int)(sizeof(TileDigits) / 4); i += kScanThreads)
+            reinterpret_cast<uint32_t *>(&s_td)[i] = 0;
+        __syncthreads();
+    }
     const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     const int64_t nparts = (n + kScanPart - 1) / kScanPart;
     const uint32_t epoch = *epoch_ptr + epoch_off;
@@ -111,6 +153,15 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
                     const uint32_t r = idx[j];
                     uint4 rr = rect[r];
                     v = rect_area(rr);
+                    if (hist) {
+                        // the tile keys of the Gaussian's pairs, row by row
+                        const uint32_t x0 = rr.x & 0xffffu, y0 = rr.x >> 16;
+                        const uint32_t x1 = rr.y & 0xffffu, y1 = rr.y >> 16;
+                        const uint32_t tb = cams[rr.z].tile_base;
+                        const uint32_t tsx = (uint32_t)cams[rr.z].tiles_x;
+                        for (uint32_t ty = y0; ty <= y1; ++ty)
+                            tile_digits_add(s_td, tb + ty * tsx + x0, x1 - x0 + 1u, passes);
+                    }
                     rr.w = r;
                     rect_out[j] = rr;
                 } else {
@@ -170,6 +221,28 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
         }
         __syncthreads();
     }
+    if (kGather && hist) {
+        // the CTA's digit counts into hist: pass 0 from the prefix sum of its
+        // difference array (one digit per thread), passes 1, 2 directly
+        static_assert(kScanThreads == 256, "one thread per digit");
+        const int lane = tid & 31, warp = tid >> 5;
+        __syncthreads();
+        uint32_t x = s_td.d0[tid];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        for (int w = 0; w < warp; ++w) x += s_warp[w];
+        const uint32_t c0 = x + s_td.full;
+        if (c0) atomicAdd(&hist[tid], c0);
+        for (int q = 1; q < passes; ++q) {
+            const uint32_t v = s_td.hh[q - 1][tid];
+            if (v) atomicAdd(&hist[q * 256 + tid], v);
+        }
+    }
 }
 
 void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
@@ -177,17 +250,19 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, i
                      uint32_t epoch_off, int *err, int grid, cudaStream_t st) {
     k_scan<false><<<grid, kScanThreads, 0, st>>>(in, nullptr, nullptr, out, n_dev, n_host, total,
                                                  -1, ticket, status, epoch, epoch_off, err,
-                                                 nullptr, 0, nullptr);
+                                                 nullptr, 0, nullptr, nullptr, nullptr, 0);
 }
 
 void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         uint32_t *chunk_first, uint4 *rect_sorted, int grid, cudaStream_t st) {
+                         uint32_t *chunk_first, uint4 *rect_sorted, const DevCamera *cams,
+                         uint32_t *hist, int passes, int grid, cudaStream_t st) {
     k_scan<true><<<grid, kScanThreads, 0, st>>>(nullptr, rect, sorted_idx, poff, n_vis, -1,
                                                 counters + CNT_PAIRS, pair_cap, ticket, status,
                                                 epoch, epoch_off, err, chunk_first,
-                                                dup_chunks(pair_cap), rect_sorted);
+                                                dup_chunks(pair_cap), rect_sorted, cams,
+                                                passes > 0 ? hist : nullptr, passes);
 }
 
 // K4: the pair array is cut into chunks of kDupChunk pairs, so every CTA
@@ -197,16 +272,15 @@ void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const ui
 // stride and rectangle width with its reciprocal, record id). Each pair finds
 // its record through a map of the window's pairs: every record marks its first
 // pair with its window index and a block-wide running maximum fills the rest
-// (record starts increase with the index). Tile-digit histograms of the radix
-// passes that follow are accumulated on the way.
+// (record starts increase with the index). The tile-digit histograms of the
+// radix passes that follow are counted by K3, per rectangle row.
 __global__ void __launch_bounds__(kDupThreads)
 k_duplicate(const uint4 *__restrict__ rect_sorted,
             const uint32_t *__restrict__ poff, const uint32_t *__restrict__ chunk_first,
             const uint32_t *n_vis_p, const uint32_t *n_pairs_p, int64_t pair_cap,
             const DevCamera *__restrict__ cams, uint32_t *__restrict__ pkey,
-            uint32_t *__restrict__ pval, uint32_t *hist, int passes, int *err) {
+            uint32_t *__restrict__ pval, int *err) {
     constexpr int kPer = kDupChunk / kDupThreads;   // map entries per thread
-    __shared__ uint32_t s_h[3][256];       // digit counts of the tile keys, per radix pass
     __shared__ uint32_t s_off[kDupWindow + 1];
     __shared__ uint4 s_rec[kDupWindow];    // (first tile key, tiles_x, width, 1 / width)
     __shared__ uint32_t s_idx[kDupWindow];
@@ -220,8 +294,6 @@ k_duplicate(const uint4 *__restrict__ rect_sorted,
         return;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (hist)
-        for (int i = tid; i < 3 * 256; i += kDupThreads) (&s_h[0][0])[i] = 0;
     const int64_t n_chunks = ((int64_t)n_pairs + kDupChunk - 1) / kDupChunk;
     for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         const uint32_t p0 = (uint32_t)(ch * kDupChunk);
@@ -277,54 +349,22 @@ k_duplicate(const uint4 *__restrict__ rect_sorted,
                 for (int i = 0; i < kPer; ++i) s_map[tid * kPer + i] = (uint16_t)max(before, m[i]);
             }
             __syncthreads();
-            // uniform trip count: every lane of a warp reaches the warp collectives
-            for (uint32_t base = q; base < q1; base += kDupThreads) {
-                const uint32_t p = base + tid;
-                const bool valid = p < q1;
-                uint32_t key = 0;
-                if (valid) {
-                    const int j = s_map[p - q];
-                    const uint4 r = s_rec[j];
-                    // tile (tx, ty) = k mod / div width: a float quotient, then one
-                    // integer correction (its error is below 1 for k < 2^24)
-                    const uint32_t k = p - s_off[j];
-                    int ty = (int)((float)k * __uint_as_float(r.w));
-                    int tx = (int)k - ty * (int)r.z;
-                    if (tx < 0) { --ty; tx += (int)r.z; }
-                    else if (tx >= (int)r.z) { ++ty; tx -= (int)r.z; }
-                    key = r.x + (uint32_t)ty * r.y + (uint32_t)tx;
-                    pkey[p] = key;
-                    pval[p] = s_idx[j];
-                }
-                if (hist) {
-                    // neighbouring pairs mostly share their high digits: a warp whose
-                    // valid lanes agree adds its count once
-                    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-                    if (vmask) {
-                        const int leader = __ffs(vmask) - 1;
-                        for (int qd = 0; qd < passes; ++qd) {
-                            const uint32_t d = (key >> (8 * qd)) & 255u;
-                            const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
-                            const bool same = __all_sync(0xffffffffu, !valid || d == dl);
-                            if (same) {
-                                if (lane == leader) atomicAdd(&s_h[qd][d], (uint32_t)__popc(vmask));
-                            } else if (valid) {
-                                atomicAdd(&s_h[qd][d], 1u);
-                            }
-                        }
-                    }
-                }
+            for (uint32_t p = q + tid; p < q1; p += kDupThreads) {
+                const int j = s_map[p - q];
+                const uint4 r = s_rec[j];
+                // tile (tx, ty) = k mod / div width: a float quotient, then one
+                // integer correction (its error is below 1 for k < 2^24)
+                const uint32_t k = p - s_off[j];
+                int ty = (int)((float)k * __uint_as_float(r.w));
+                int tx = (int)k - ty * (int)r.z;
+                if (tx < 0) { --ty; tx += (int)r.z; }
+                else if (tx >= (int)r.z) { ++ty; tx -= (int)r.z; }
+                pkey[p] = r.x + (uint32_t)ty * r.y + (uint32_t)tx;
+                pval[p] = s_idx[j];
             }
             q = q1;
             r0 += cnt;
             if (cnt == 0) break;
-        }
-    }
-    if (hist) {
-        __syncthreads();
-        for (int i = tid; i < passes * 256; i += kDupThreads) {
-            const uint32_t v = (&s_h[0][0])[i];
-            if (v) atomicAdd(&hist[i], v);
         }
     }
 }
@@ -332,10 +372,9 @@ k_duplicate(const uint4 *__restrict__ rect_sorted,
 void launch_duplicate(const uint4 *rect_sorted, const uint32_t *poff,
                       const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
                       int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
-                      uint32_t *hist, int passes, int *err, int grid, cudaStream_t st) {
+                      int *err, int grid, cudaStream_t st) {
     k_duplicate<<<grid, kDupThreads, 0, st>>>(rect_sorted, poff, chunk_first, n_vis, n_pairs,
-                                              pair_cap, cams, pkey, pval,
-                                              passes > 0 ? hist : nullptr, passes, err);
+                                              pair_cap, cams, pkey, pval, err);
 }
 
 // K6: ranges[t] = [first, end) of tile t in the sorted pair keys, stored as

@@ -244,6 +244,9 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
             const K k = S.keys[j];
             const uint32_t d = digit_of(k, shift, mask);
             const int64_t g = (int64_t)(S.gstart[d] + (uint32_t)j);
+            // digit counts that disagree with the keys (a caller's histogram)
+            // would place a key outside [0, n): never written there
+            if (g >= n) continue;
             if (kOut == 0) kout[g] = k;
             vout[g] = S.vals[j];
             if (kOut == 2) {

@@ -375,19 +375,20 @@ int scan_partition();
 
 // binning: tiles-touched scan over depth order (also the first record of every
 // pair chunk, chunk_first[dup_chunks(pair_cap)], and the rects in depth order,
-// record index in w, in rect_sorted), then pair emission
+// record index in w, in rect_sorted); with hist, it also adds the digit counts
+// of the pairs' tile keys (camera tile base + row * tiles_x + column) for
+// `passes` 8-bit radix passes to hist[passes][256] (zeroed by the caller)
 void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         uint32_t *chunk_first, uint4 *rect_sorted, int grid, cudaStream_t st);
+                         uint32_t *chunk_first, uint4 *rect_sorted, const DevCamera *cams,
+                         uint32_t *hist, int passes, int grid, cudaStream_t st);
 int64_t dup_chunks(int64_t pair_cap);
-// emits the pairs from the depth-ordered rects and, if hist is given, adds the
-// digit counts of their tile keys for `passes` 8-bit radix passes to hist
-// (zeroed by the caller)
+// emits the pairs from the depth-ordered rects
 void launch_duplicate(const uint4 *rect_sorted, const uint32_t *poff,
                       const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
                       int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
-                      uint32_t *hist, int passes, int *err, int grid, cudaStream_t st);
+                      int *err, int grid, cudaStream_t st);
 void launch_ranges(const uint32_t *pkey, const uint32_t *n_pairs, uint2 *ranges, int grid,
                    cudaStream_t st, const int *err);
 
