@@ -102,19 +102,19 @@ __device__ __forceinline__ void tile_digits_add(TileDigits &H, uint32_t k0, uint
             atomicAdd(&H.d0[d + r - 256u], 0xffffffffu);
         }
     }
+    // tile keys stay below 2^24 (a sub-batch's tiles), so k0 + w fits 32 bits
     for (int q = 1; q < passes; ++q) {
         const int sh = 8 * q;
-        const uint64_t a = k0, e = (uint64_t)k0 + w;
-        for (uint64_t v = a >> sh; (v << sh) < e; ++v) {
-            const uint64_t lo = v << sh > a ? v << sh : a;
-            const uint64_t hi = (v + 1) << sh < e ? (v + 1) << sh : e;
-            atomicAdd(&H.hh[q - 1][v & 255u], (uint32_t)(hi - lo));
+        const uint32_t e = k0 + w;
+        for (uint32_t v = k0 >> sh; (v << sh) < e; ++v) {
+            const uint32_t lo = max(v << sh, k0), hi = min((v + 1) << sh, e);
+            atomicAdd(&H.hh[q - 1][v & 255u], hi - lo);
         }
     }
 }
 
 template <bool kGather>
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kScanThreads, 4)
 k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
        const uint32_t *__restrict__ idx, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
        uint32_t *total_out, int64_t total_cap, uint32_t *ticket, uint64_t *status,
@@ -153,15 +153,6 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
                     const uint32_t r = idx[j];
                     uint4 rr = rect[r];
                     v = rect_area(rr);
-                    if (hist) {
-                        // the tile keys of the Gaussian's pairs, row by row
-                        const uint32_t x0 = rr.x & 0xffffu, y0 = rr.x >> 16;
-                        const uint32_t x1 = rr.y & 0xffffu, y1 = rr.y >> 16;
-                        const uint32_t tb = cams[rr.z].tile_base;
-                        const uint32_t tsx = (uint32_t)cams[rr.z].tiles_x;
-                        for (uint32_t ty = y0; ty <= y1; ++ty)
-                            tile_digits_add(s_td, tb + ty * tsx + x0, x1 - x0 + 1u, passes);
-                    }
                     rr.w = r;
                     rect_out[j] = rr;
                 } else {
@@ -196,6 +187,21 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
                 const uint64_t all = (uint64_t)prev + total;
                 if (total_out) *total_out = (uint32_t)all;
                 if (total_cap >= 0 && (int64_t)all > total_cap) latch_error(err, kErrCapacity);
+            }
+        }
+        if (kGather && hist && tid >= 32) {
+            // while warp 0 looks back, the other warps count the tile digits
+            // of the partition's Gaussians (each its tile keys, rectangle row
+            // by row), reading back the depth-ordered rects just written
+#pragma unroll 1
+            for (int k = tid - 32; k < kScanPart && pbase + k < n; k += kScanThreads - 32) {
+                const uint4 rr = rect_out[pbase + k];
+                const uint32_t x0 = rr.x & 0xffffu, y0 = rr.x >> 16;
+                const uint32_t x1 = rr.y & 0xffffu, y1 = rr.y >> 16;
+                const uint32_t tb = cams[rr.z].tile_base;
+                const uint32_t tsx = (uint32_t)cams[rr.z].tiles_x;
+                for (uint32_t ty = y0; ty <= y1; ++ty)
+                    tile_digits_add(s_td, tb + ty * tsx + x0, x1 - x0 + 1u, passes);
             }
         }
         __syncthreads();
