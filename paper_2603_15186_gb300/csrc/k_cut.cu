@@ -237,7 +237,7 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
               const CutCam *__restrict__ ccams, int n_cams,
               uint32_t *__restrict__ part_vals, uint32_t *__restrict__ ids, int64_t cap,
               uint32_t *ticket, const int *err) {
-    __shared__ float s_cam[kCutCams][5];                   // pos xyz, fx, tau
+    __shared__ float s_cam[kCutCams][5];                   // pos xyz, fx, tau^2 (rounded)
     __shared__ CutCam s_ccam[kFrustum ? kCutCams : 1];     // the cameras' planes
     __shared__ uint32_t s_bal[kCutCams][kCutItems * 8];    // ballot per (camera, row, warp)
     __shared__ uint32_t s_off[kCutCams][kCutItems * 8];    // its exclusive offset in the block
@@ -261,10 +261,10 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
             if (j < nc) {
                 if (kFrustum) {
                     const CutCam &k = ccams[c0 + j];
-                    v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : k.tau);
+                    v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : __fmul_rn(k.tau, k.tau));
                 } else {
                     const DevCamera &k = cams[c0 + j];
-                    v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : k.tau);
+                    v = f < 3 ? k.pos[f] : (f == 3 ? k.fx : __fmul_rn(k.tau, k.tau));
                 }
             }
             s_cam[j][f] = v;
@@ -319,15 +319,17 @@ k_cut_blocked(const float4 *__restrict__ box_lo, const float4 *__restrict__ box_
                 }
                 live = keep;
             }
+            const float ext_n = box_extent(lo, hi), ext_p = box_extent(plo, phi);
             uint32_t m = 0;   // bit j: camera j selects the node
 #pragma unroll
             for (int j = 0; j < kCutCams; ++j) {
                 if (valid && j < nc && ((live >> j) & 1u)) {
                     const float px = s_cam[j][0], py = s_cam[j][1], pz = s_cam[j][2];
-                    const float fx = s_cam[j][3], tau = s_cam[j][4];
+                    const float fx = s_cam[j][3], tau2 = s_cam[j][4];
                     // the rule of cut_selects, parent first (most nodes lie below the cut)
-                    if ((parent < 0 || !fine_enough(plo, phi, px, py, pz, fx, tau)) &&
-                        (leaf || fine_enough(lo, hi, px, py, pz, fx, tau)))
+                    if ((parent < 0 ||
+                         !fine_enough_pre(plo, phi, ext_p, px, py, pz, fx, tau2)) &&
+                        (leaf || fine_enough_pre(lo, hi, ext_n, px, py, pz, fx, tau2)))
                         m |= 1u << j;
                 }
             }

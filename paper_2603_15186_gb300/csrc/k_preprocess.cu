@@ -248,7 +248,7 @@ struct CamLite {
     float pos[3];
     float fx, fy, cx, cy, tau;
     int32_t tiles_x, tiles_y;
-    float pad;
+    float tau2;   // __fmul_rn(tau, tau), as the cut test takes it
 };
 
 // Camera-independent inputs of the conservative cull of one node: its
@@ -285,6 +285,12 @@ __device__ __forceinline__ bool precull(const CamLite &cam, const NodeCull &nd, 
     // approximate reciprocal and square roots (relative error ~1e-7, far
     // inside the slack of the test below)
     const float iz = __fdividef(1.0f, tz32);
+    const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
+    // a centre inside the tile grid: its support box meets a tile whatever
+    // its size (the test below would keep it too)
+    if (u >= 0.0f && u < (float)(cam.tiles_x * tile_w) && v >= 0.0f &&
+        v < (float)(cam.tiles_y * tile_h))
+        return true;
     const float ax = cam.fx * iz, bx = -cam.fx * tx * iz * iz;
     const float ay = cam.fy * iz, by = -cam.fy * ty * iz * iz;
     const float t00 = ax * cam.R[0] + bx * cam.R[6], t01 = ax * cam.R[1] + bx * cam.R[7],
@@ -296,7 +302,6 @@ __device__ __forceinline__ bool precull(const CamLite &cam, const NodeCull &nd, 
     const float qy = K * ((t10 * t10 + t11 * t11 + t12 * t12) * s2 + kBlur);
     const float hxb = (qx > 0.0f ? qx * rsqrtf(qx) : 0.0f) * 1.0002f + kRectMargin;
     const float hyb = (qy > 0.0f ? qy * rsqrtf(qy) : 0.0f) * 1.0002f + kRectMargin;
-    const float u = cam.fx * tx * iz + cam.cx, v = cam.fy * ty * iz + cam.cy;
     const float sx = 1e-4f * (fabsf(u) + hxb) + 0.02f, sy = 1e-4f * (fabsf(v) + hyb) + 0.02f;
     if (u + hxb + sx < 0.0f || u - hxb - sx >= (float)(cam.tiles_x * tile_w)) return false;
     if (v + hyb + sy < 0.0f || v - hyb - sy >= (float)(cam.tiles_y * tile_h)) return false;
@@ -710,6 +715,7 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             for (int k = 0; k < 9; ++k) l.R[k] = d.R[k];
             l.pos[0] = d.pos[0]; l.pos[1] = d.pos[1]; l.pos[2] = d.pos[2];
             l.fx = d.fx; l.fy = d.fy; l.cx = d.cx; l.cy = d.cy; l.tau = d.tau;
+            l.tau2 = __fmul_rn(d.tau, d.tau);
             l.tiles_x = d.tiles_x; l.tiles_y = d.tiles_y;
             S.gcam[tid] = (uint32_t)c;
             S.sel[tid] = 0;
@@ -765,15 +771,17 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
                 seg_lo.w = smax * (1.0f + 1e-5f);
                 seg_hi.w = K * (1.0f + 1e-5f) + 1e-6f;
             }
+            // the boxes' extents do not depend on the camera
+            const float ext_n = box_extent(lo, hi), ext_p = box_extent(plo, phi);
             uint32_t m = 0;
             for (int i = 0; i < gcnt; ++i) {
                 const CamLite &cam = S.cam[i];
                 const bool sel =
                     valid &&
-                    (leaf || fine_enough(lo, hi, cam.pos[0], cam.pos[1], cam.pos[2], cam.fx,
-                                         cam.tau)) &&
-                    (par < 0 || !fine_enough(plo, phi, cam.pos[0], cam.pos[1], cam.pos[2],
-                                             cam.fx, cam.tau));
+                    (leaf || fine_enough_pre(lo, hi, ext_n, cam.pos[0], cam.pos[1], cam.pos[2],
+                                             cam.fx, cam.tau2)) &&
+                    (par < 0 || !fine_enough_pre(plo, phi, ext_p, cam.pos[0], cam.pos[1],
+                                                 cam.pos[2], cam.fx, cam.tau2));
                 const bool cand =
                     sel && (kBlend ? !seg_dead && !block_culled(seg_lo, seg_hi, cam, tile_w, tile_h)
                                    : precull(cam, nd, tile_w, tile_h));

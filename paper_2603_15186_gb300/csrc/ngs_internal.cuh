@@ -168,18 +168,26 @@ __device__ __forceinline__ float granularity(const float4 lo, const float4 hi, c
 // rounded operations, so all cut forms agree bit for bit; it differs from a
 // comparison of the rounded granularity only within a few units in the last
 // place of the threshold, far inside the 1e-5 tolerance around tau.
-__device__ __forceinline__ bool fine_enough(const float4 lo, const float4 hi, const float px,
-                                            const float py, const float pz, const float fx,
-                                            const float tau) {
+__device__ __forceinline__ float box_extent(const float4 lo, const float4 hi) {
+    return fmaxf(fmaxf(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y)), __fsub_rn(hi.z, lo.z));
+}
+// The same with the camera-independent box extent and the camera's tau^2
+// (__fmul_rn(tau, tau)) taken beforehand: the same rounded operations.
+__device__ __forceinline__ bool fine_enough_pre(const float4 lo, const float4 hi, const float ext,
+                                                const float px, const float py, const float pz,
+                                                const float fx, const float tau2) {
     const float gx = fmaxf(fmaxf(__fsub_rn(lo.x, px), 0.0f), __fsub_rn(px, hi.x));
     const float gy = fmaxf(fmaxf(__fsub_rn(lo.y, py), 0.0f), __fsub_rn(py, hi.y));
     const float gz = fmaxf(fmaxf(__fsub_rn(lo.z, pz), 0.0f), __fsub_rn(pz, hi.z));
     const float d2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
-    const float ext = fmaxf(fmaxf(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y)),
-                            __fsub_rn(hi.z, lo.z));
     if (d2 == 0.0f) return false;
     const float a = __fmul_rn(fx, ext);
-    return __fmul_rn(a, a) <= __fmul_rn(__fmul_rn(tau, tau), d2);
+    return __fmul_rn(a, a) <= __fmul_rn(tau2, d2);
+}
+__device__ __forceinline__ bool fine_enough(const float4 lo, const float4 hi, const float px,
+                                            const float py, const float pz, const float fx,
+                                            const float tau) {
+    return fine_enough_pre(lo, hi, box_extent(lo, hi), px, py, pz, fx, __fmul_rn(tau, tau));
 }
 
 // The cut rule for node `node`: (leaf or s(n) <= tau) and (root or s(parent) > tau).
