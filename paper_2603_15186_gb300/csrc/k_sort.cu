@@ -149,27 +149,21 @@ k_onesweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__res
         // rank of each item among the warp's earlier items with its digit:
         // the lanes sharing a digit (peers) are found by one shared-memory OR
         // of the lane bits into the warp's mask of that digit (the lowest
-        // peer clears it again), or directly when every valid lane of the
-        // warp has the same digit (common in the high digits of depth keys)
+        // peer clears it again). (A shortcut for warps whose lanes all share
+        // one digit cost more in its test than it saved, even on depth keys.)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const bool valid = base + i * 32 + lane < n;
             const uint32_t d = digit_of(key[i], shift, mask);
-            const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-            const uint32_t d0 = __shfl_sync(0xffffffffu, d, __ffs(vmask | 1u) - 1);
-            const bool uniform = __all_sync(0xffffffffu, !valid || d == d0);
-            uint32_t peers = valid ? vmask : 0u;
-            if (!uniform) {
-                if (valid) atomicOr(&S.match[warp][d], 1u << lane);
-                __syncwarp();
-                peers = valid ? S.match[warp][d] : 0u;
-            }
+            if (valid) atomicOr(&S.match[warp][d], 1u << lane);
+            __syncwarp();
+            const uint32_t peers = valid ? S.match[warp][d] : 0u;
             uint32_t before = 0;
             if (valid) before = S.whist[warp][d];
             __syncwarp();
             if (valid && (peers & lt) == 0) {
                 S.whist[warp][d] = before + __popc(peers);
-                if (!uniform) S.match[warp][d] = 0u;
+                S.match[warp][d] = 0u;
             }
             __syncwarp();
             rank[i] = before + __popc(peers & lt);
