@@ -258,17 +258,17 @@ def stage_bytes(st, n_nodes, n_cams, pixels, tiles, attr="f16"):
     rec = 48 if attr == "f32" else 32
     V, P = st["visible_total"], st["pair_total"]
     return {
-        "cut_preprocess": st["sub_batches"] * n_nodes * 32 + V * (rec + 4 + 16),
+        "cut_preprocess": st["sub_batches"] * n_nodes * 32 + V * (rec + 4 + 8),
         "gather_keys": 12 * V,
         "depth_hist": 4 * V,
         # the last depth pass writes values only; the last tile pass writes
         # values and each tile's range (8 B per tile) instead of keys
         "depth_pass0": 16 * V, "depth_pass1": 16 * V, "depth_pass2": 16 * V, "depth_pass3": 12 * V,
-        # pair offsets: index, gathered rect and offset per Gaussian, plus the
-        # rect written in depth order for the pair emission, which reads it
-        # and the offset back sequentially
-        "pair_offsets": 40 * V,
-        "duplicate": 20 * V + 8 * P,
+        # pair offsets: index, gathered 8-byte rect and offset per Gaussian,
+        # plus the rect written in depth order for the pair emission, which
+        # reads it, the offset and the index back sequentially
+        "pair_offsets": 24 * V,
+        "duplicate": 16 * V + 8 * P,
         "tile_hist": 4 * P,
         "tile_pass0": 16 * P, "tile_pass1": 12 * P + 8 * tiles, "tile_pass2": 0,
         "ranges": 8 * tiles,

@@ -118,7 +118,7 @@ enum { NGS_MODE_BATCHED = 0, NGS_MODE_PLAIN = 1 };
 enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH = 4,
        NGS_OPT_GRAPH = 5, NGS_OPT_STAGE_TIMING = 6, NGS_OPT_BLOCK_CULL = 7,
        NGS_OPT_CTA_W = 8, NGS_OPT_CTA_H = 9, NGS_OPT_PAIRS_PER_PIXEL = 10,
-       NGS_OPT_LOD_BLEND = 11, NGS_OPT_COMPOSITE_ORDER = 12 };
+       NGS_OPT_LOD_BLEND = 11, NGS_OPT_COMPOSITE_ORDER = 12, NGS_OPT_NODE_IDS = 13 };
 /* NGS_OPT_TILE_W / NGS_OPT_TILE_H: tile width 8, 16 or 32, height 8, 16 or 32;
  * a render accepts the shapes 8x8, 16x8, 16x16, 16x32, 32x16 and 32x32
  * (INVALID_ARG else).
@@ -151,7 +151,10 @@ enum { NGS_OPT_MODE = 1, NGS_OPT_TILE_W = 2, NGS_OPT_TILE_H = 3, NGS_OPT_BATCH =
  * NGS_OPT_COMPOSITE_ORDER (default 1): the batched path's persistent
  * compositing CTAs take the tiles of a sub-batch in order of decreasing list
  * length (classes of half an octave), so that long lists do not start last;
- * 0 takes them in tile order. Same images. */
+ * 0 takes them in tile order. Same images.
+ * NGS_OPT_NODE_IDS (default 0): renders also keep each visible Gaussian's node
+ * id (4 bytes per record_capacity entry, allocated at the first such render),
+ * which ngs_debug_tile_lists reports. Same images. */
 
 typedef struct {
     int64_t cut_total;       /* selected nodes over all cameras of the last render */
@@ -305,7 +308,9 @@ NGS_API ngs_status ngs_stage_times(ngs_ctx *ctx, double *ms, int32_t n);
  * render, copied to host memory after synchronising: h_ranges [tiles][2]
  * (int64 start, end into h_nodes) and h_nodes [cap] (int32 node ids in
  * per-tile depth order). *n_pairs receives the number of pairs; returns
- * NGS_ERR_CAPACITY if it exceeds cap. tiles = ceil(W/tile_w)*ceil(H/tile_h). */
+ * NGS_ERR_CAPACITY if it exceeds cap. tiles = ceil(W/tile_w)*ceil(H/tile_h).
+ * h_nodes may be NULL (ranges only); non-NULL needs a last render made with
+ * NGS_OPT_NODE_IDS on (NGS_ERR_INVALID_ARG else). */
 NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *ctx, int32_t cam, int64_t *h_ranges,
                                         int32_t *h_nodes, int64_t cap, int64_t *n_pairs);
 

@@ -17,6 +17,7 @@ NGS_OPT_CTA_W, NGS_OPT_CTA_H = 8, 9
 NGS_OPT_PAIRS_PER_PIXEL = 10
 NGS_OPT_LOD_BLEND = 11
 NGS_OPT_COMPOSITE_ORDER = 12
+NGS_OPT_NODE_IDS = 13
 # (binning tile, compositing block) candidates of ngs_autotune, in its order
 TUNE_SHAPES = [((8, 8), (8, 8)), ((16, 8), (16, 8)), ((16, 16), (16, 16)), ((16, 32), (16, 32)),
                ((32, 16), (32, 16)), ((32, 32), (32, 32)), ((16, 16), (16, 8)),

@@ -77,6 +77,8 @@ struct ngs_ctx {
     bool block_cull = true;
     bool lod_blend = false;            // level-of-detail blending toward parents
     bool composite_order = true;       // batched compositing takes tiles longest list first
+    bool node_ids = false;             // keep each record's node id (ngs_debug_tile_lists)
+    bool last_node_ids = false;        // the last render kept them
     SceneDev scene;
     bool loaded = false;
     bool owns_scene = true;           // false for serving lanes sharing a scene
@@ -188,7 +190,7 @@ __global__ void k_copy_stats(const uint32_t *counters, uint32_t *stats) {
 void free_work(ngs_ctx *c) {
     Work &w = c->w;
     dfree(w.counters); dfree(w.epoch); dfree(w.status); dfree(w.err); dfree(w.cut_ids);
-    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.group_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.rect_sorted); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
+    dfree(w.cut_off); dfree(w.vis_count); dfree(w.part_list); dfree(w.group_list); dfree(w.part_info); dfree(w.part_pos); dfree(w.rec); dfree(w.rect); dfree(w.rect_sorted); dfree(w.node_id); dfree(w.poff); dfree(w.chunk_first); dfree(w.ranges);
     dfree(w.hist); dfree(w.cams); dfree(w.work64); dfree(w.order);
     for (int i = 0; i < 2; ++i) {
         dfree(w.dkey[i]); dfree(w.didx[i]); dfree(w.pkey[i]); dfree(w.pval[i]);
@@ -377,8 +379,15 @@ bool split_supported(const ngs_ctx *c) {
     return tile_supported(w, h) && c->tile_w % w == 0 && c->tile_h % h == 0;
 }
 
+constexpr int kMaxImageSide = 32768;
+// the binning stages pack tile coordinates (tiles of at least 8 pixels) and a
+// launch's camera index into 8 bytes (pack_rect)
+static_assert(kMaxImageSide / 8 <= (int)kRectCoordMax && kMaxCamsPerBatch <= 65536,
+              "packed tile rectangle");
+
 bool camera_ok(const ngs_camera &k) {
-    if (k.width <= 0 || k.height <= 0 || k.width > 32768 || k.height > 32768) return false;
+    if (k.width <= 0 || k.height <= 0 || k.width > kMaxImageSide || k.height > kMaxImageSide)
+        return false;
     const float v[] = {k.pos[0], k.pos[1], k.pos[2], k.fx, k.fy, k.cx, k.cy, k.tau};
     for (float f : v)
         if (!std::isfinite(f)) return false;
@@ -490,7 +499,8 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
     cudaMemsetAsync(w.ranges, 0, (size_t)sb.n_tiles * sizeof(uint2), st);
     k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
     uint32_t eo = 0;
-    launch_cutpre(c->scene, cams, nc, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
+    launch_cutpre(c->scene, cams, nc, w.rec, w.rec_cap, w.dkey[1], w.rect,
+                  c->node_ids ? w.node_id : nullptr, w.vis_count,
                   w.counters, w.part_list, w.group_list, w.part_info, w.err, c->tile_w, c->tile_h,
                   c->block_cull ? 1 : 0, c->lod_blend ? 1 : 0, c->grid_pre, st);
     mark(c, sb_index, MK_CUT, st);
@@ -519,8 +529,9 @@ void enqueue_batched(ngs_ctx *c, const SubBatch &sb, int sb_index, cudaStream_t 
                         w.chunk_first, w.rect_sorted, cams, w.hist, sb.tile_passes,
                         c->grid_scan, st);
     mark(c, sb_index, MK_POFF, st);
-    launch_duplicate(w.rect_sorted, w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
-                     w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, c->grid_dup, st);
+    launch_duplicate(w.rect_sorted, w.didx[dsel], w.poff, w.chunk_first, w.counters + CNT_VIS,
+                     w.counters + CNT_PAIRS, w.pair_cap, cams, w.pkey[0], w.pval[0], w.err,
+                     c->grid_dup, st);
     mark(c, sb_index, MK_DUP, st);
     int psel = 0;
     SortHook th{c, sb_index, MK_THIST, st};
@@ -636,7 +647,8 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         k_bump_epoch<<<1, 1, 0, st>>>(w.epoch, kEpochStride);
         uint32_t eo = 0;
         const int64_t nblk = (c->scene.n + cutpre_partition_nodes() - 1) / cutpre_partition_nodes();
-        launch_cutpre(c->scene, cams, 1, w.rec, w.rec_cap, w.dkey[1], w.rect, w.vis_count,
+        launch_cutpre(c->scene, cams, 1, w.rec, w.rec_cap, w.dkey[1], w.rect,
+                      c->node_ids ? w.node_id : nullptr, w.vis_count,
                       w.counters, w.part_list, w.group_list, w.part_info, w.err, c->tile_w, c->tile_h,
                       c->block_cull ? 1 : 0, c->lod_blend ? 1 : 0,
                       (int)std::min<int64_t>(nblk, c->grid_pre), st);
@@ -682,8 +694,9 @@ ngs_status render_plain(ngs_ctx *c, int n_cams, cudaStream_t st) {
         if ((int64_t)n_pairs > w.pair_cap) return NGS_ERR_CAPACITY;
         const int gdup = (int)std::max<int64_t>(
             1, std::min<int64_t>(((int64_t)n_pairs + 2047) / 2048, 8 * (int64_t)c->num_sms));
-        launch_duplicate(w.rect_sorted, w.poff, w.chunk_first, w.counters + CNT_VIS, w.counters + CNT_PAIRS,
-                         w.pair_cap, cams, w.pkey[0], w.pval[0], w.err, gdup, st);
+        launch_duplicate(w.rect_sorted, w.didx[0], w.poff, w.chunk_first, w.counters + CNT_VIS,
+                         w.counters + CNT_PAIRS, w.pair_cap, cams, w.pkey[0], w.pval[0], w.err,
+                         gdup, st);
         mark(c, ci, MK_DUP, st);
         int psel = 0;
         SortHook th{c, ci, MK_THIST, st};
@@ -809,6 +822,10 @@ ngs_status render_common(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
         if (!camera_ok(cams[i]) || !images[i]) return NGS_ERR_INVALID_ARG;
     ngs_status s = ensure_work(c);
     if (s != NGS_OK) return s;
+    if (c->node_ids && !c->w.node_id) {
+        s = dalloc(&c->w.node_id, (size_t)c->w.rec_cap);
+        if (s != NGS_OK) return s;
+    }
     if (c->latched != NGS_OK) {
         s = c->latched;
         c->latched = NGS_OK;
@@ -822,6 +839,7 @@ ngs_status render_common(ngs_ctx *c, const ngs_camera *cams, int32_t n_cams,
     }
     c->stats.tile_w = c->tile_w; c->stats.tile_h = c->tile_h;
     c->stats.batch = c->batch; c->stats.mode = c->mode;
+    c->last_node_ids = c->node_ids;
     c->stats.cta_w = cta_w_of(c); c->stats.cta_h = cta_h_of(c);
     return c->mode == NGS_MODE_PLAIN ? render_plain(c, n_cams, st) : render_batched(c, n_cams, st);
 }
@@ -1026,6 +1044,10 @@ NGS_API ngs_status ngs_set_option(ngs_ctx *c, int32_t opt, int64_t v) {
         return NGS_OK;
     case NGS_OPT_COMPOSITE_ORDER:
         c->composite_order = v != 0;
+        drop_graph(c);
+        return NGS_OK;
+    case NGS_OPT_NODE_IDS:
+        c->node_ids = v != 0;
         drop_graph(c);
         return NGS_OK;
     }
@@ -1523,6 +1545,8 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     if (!c || !h_ranges || !n_pairs) return NGS_ERR_INVALID_ARG;
     if (c->last_plan.empty() || cam < 0 || cam >= (int32_t)c->host_cams.size())
         return NGS_ERR_INVALID_ARG;
+    // node ids exist only for a render made with NGS_OPT_NODE_IDS on
+    if (h_nodes && (!c->last_node_ids || !c->w.node_id)) return NGS_ERR_INVALID_ARG;
     // the work buffers hold the last sub-batch only
     const SubBatch &sb = c->last_plan.back();
     if (cam < sb.c0 || cam >= sb.c1) return NGS_ERR_INVALID_ARG;
@@ -1550,17 +1574,17 @@ NGS_API ngs_status ngs_debug_tile_lists(ngs_ctx *c, int32_t cam, int64_t *h_rang
     if (hi > lo && h_nodes) {
         std::vector<uint32_t> vals(hi - lo);
         CK(cudaMemcpy(vals.data(), w.pval[psel] + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost));
-        // the node id is in the rect of each record: copy the span of records
-        // the pairs refer to once, then look them up
+        // copy the node ids of the span of records the pairs refer to once,
+        // then look them up
         uint32_t r0 = UINT32_MAX, r1 = 0;
         for (int64_t k = 0; k < hi - lo; ++k) {
             r0 = std::min(r0, vals[k]);
             r1 = std::max(r1, vals[k]);
         }
-        std::vector<uint4> rects((size_t)r1 - r0 + 1);
-        CK(cudaMemcpy(rects.data(), w.rect + r0, rects.size() * sizeof(uint4),
+        std::vector<uint32_t> ids((size_t)r1 - r0 + 1);
+        CK(cudaMemcpy(ids.data(), w.node_id + r0, ids.size() * sizeof(uint32_t),
                       cudaMemcpyDeviceToHost));
-        for (int64_t k = 0; k < hi - lo; ++k) h_nodes[k] = (int32_t)rects[vals[k] - r0].w;
+        for (int64_t k = 0; k < hi - lo; ++k) h_nodes[k] = (int32_t)ids[vals[k] - r0];
     }
     (void)npairs;
     return NGS_OK;

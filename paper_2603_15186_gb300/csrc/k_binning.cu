@@ -30,9 +30,9 @@ constexpr int kDupChunk = 2048;
 constexpr int kDupWindow = 512;       // records staged at a time
 int64_t dup_chunks(int64_t pair_cap) { return pair_cap / kDupChunk + 1; }
 
-__device__ __forceinline__ uint32_t rect_area(const uint4 r) {
-    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
-    return (x1 - x0 + 1u) * (y1 - y0 + 1u);
+__device__ __forceinline__ uint32_t rect_area(const uint2 r) {
+    const RectU u = unpack_rect(r);
+    return (u.x1 - u.x0 + 1u) * (u.y1 - u.y0 + 1u);
 }
 
 // Block-wide exclusive scan of kScanItems values per thread (blocked layout:
@@ -70,8 +70,8 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v[kScanItems], uint32_t 
 // in[i] (kGather = false) or area(rect[idx[i]]) (kGather = true).
 // With kGather, also chunk_first[c] = the input position whose output range
 // [out[i], out[i] + in_i) holds element c * kDupChunk (c < chunk_cap), and
-// rect_out[i] = rect[idx[i]] with idx[i] in w: the one gather of the rects in
-// depth order, so that the pair emission reads them sequentially.
+// rect_out[i] = rect[idx[i]]: the one gather of the rects in depth order, so
+// that the pair emission reads them sequentially.
 // Global memory is read and written warp-striped (consecutive lanes,
 // consecutive elements: whole sectors per instruction); the scan itself runs
 // on kScanItems consecutive elements per thread, exchanged through a shared
@@ -115,11 +115,11 @@ __device__ __forceinline__ void tile_digits_add(TileDigits &H, uint32_t k0, uint
 
 template <bool kGather>
 __global__ void __launch_bounds__(kScanThreads, 4)
-k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
+k_scan(const uint32_t *__restrict__ in, const uint2 *__restrict__ rect,
        const uint32_t *__restrict__ idx, uint32_t *out, const uint32_t *n_dev, int64_t n_host,
        uint32_t *total_out, int64_t total_cap, uint32_t *ticket, uint64_t *status,
        const uint32_t *epoch_ptr, uint32_t epoch_off, int *err, uint32_t *chunk_first,
-       int64_t chunk_cap, uint4 *__restrict__ rect_out, const DevCamera *__restrict__ cams,
+       int64_t chunk_cap, uint2 *__restrict__ rect_out, const DevCamera *__restrict__ cams,
        uint32_t *hist, int passes) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_val[kScanPart + kScanPart / 32];
@@ -150,10 +150,8 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
             uint32_t v = 0;
             if (j < n) {
                 if (kGather) {
-                    const uint32_t r = idx[j];
-                    uint4 rr = rect[r];
+                    const uint2 rr = rect[idx[j]];
                     v = rect_area(rr);
-                    rr.w = r;
                     rect_out[j] = rr;
                 } else {
                     v = in[j];
@@ -195,13 +193,11 @@ k_scan(const uint32_t *__restrict__ in, const uint4 *__restrict__ rect,
             // by row), reading back the depth-ordered rects just written
 #pragma unroll 1
             for (int k = tid - 32; k < kScanPart && pbase + k < n; k += kScanThreads - 32) {
-                const uint4 rr = rect_out[pbase + k];
-                const uint32_t x0 = rr.x & 0xffffu, y0 = rr.x >> 16;
-                const uint32_t x1 = rr.y & 0xffffu, y1 = rr.y >> 16;
-                const uint32_t tb = cams[rr.z].tile_base;
-                const uint32_t tsx = (uint32_t)cams[rr.z].tiles_x;
-                for (uint32_t ty = y0; ty <= y1; ++ty)
-                    tile_digits_add(s_td, tb + ty * tsx + x0, x1 - x0 + 1u, passes);
+                const RectU u = unpack_rect(rect_out[pbase + k]);
+                const uint32_t tb = cams[u.cam].tile_base;
+                const uint32_t tsx = (uint32_t)cams[u.cam].tiles_x;
+                for (uint32_t ty = u.y0; ty <= u.y1; ++ty)
+                    tile_digits_add(s_td, tb + ty * tsx + u.x0, u.x1 - u.x0 + 1u, passes);
             }
         }
         __syncthreads();
@@ -259,10 +255,10 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, i
                                                  nullptr, 0, nullptr, nullptr, nullptr, 0);
 }
 
-void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
+void launch_pair_offsets(const uint2 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         uint32_t *chunk_first, uint4 *rect_sorted, const DevCamera *cams,
+                         uint32_t *chunk_first, uint2 *rect_sorted, const DevCamera *cams,
                          uint32_t *hist, int passes, int grid, cudaStream_t st) {
     k_scan<true><<<grid, kScanThreads, 0, st>>>(nullptr, rect, sorted_idx, poff, n_vis, -1,
                                                 counters + CNT_PAIRS, pair_cap, ticket, status,
@@ -275,13 +271,14 @@ void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const ui
 // iteration writes the same number of pairs however many tiles a Gaussian
 // covers. A chunk starts at the record chunk_first[c] (from K3); its records
 // are staged kDupWindow at a time (first pair, first tile key, tile-row
-// stride and rectangle width with its reciprocal, record id). Each pair finds
+// stride and rectangle width with its reciprocal; record index from the
+// depth order K3 scanned). Each pair finds
 // its record through a map of the window's pairs: every record marks its first
 // pair with its window index and a block-wide running maximum fills the rest
 // (record starts increase with the index). The tile-digit histograms of the
 // radix passes that follow are counted by K3, per rectangle row.
 __global__ void __launch_bounds__(kDupThreads)
-k_duplicate(const uint4 *__restrict__ rect_sorted,
+k_duplicate(const uint2 *__restrict__ rect_sorted, const uint32_t *__restrict__ sorted_idx,
             const uint32_t *__restrict__ poff, const uint32_t *__restrict__ chunk_first,
             const uint32_t *n_vis_p, const uint32_t *n_pairs_p, int64_t pair_cap,
             const DevCamera *__restrict__ cams, uint32_t *__restrict__ pkey,
@@ -313,12 +310,12 @@ k_duplicate(const uint4 *__restrict__ rect_sorted,
 #pragma unroll
             for (int i = 0; i < kPer; ++i) s_map[tid * kPer + i] = 0;
             for (int j = tid; j < cnt; j += kDupThreads) {
-                const uint4 rr = rect_sorted[r0 + j];   // rect, camera, record index in w
-                const uint32_t x0 = rr.x & 0xffffu, y0 = rr.x >> 16, x1 = rr.y & 0xffffu;
-                const uint32_t w = x1 - x0 + 1u;
-                const uint32_t tb = cams[rr.z].tile_base, tsx = (uint32_t)cams[rr.z].tiles_x;
-                s_rec[j] = make_uint4(tb + y0 * tsx + x0, tsx, w, __float_as_uint(1.0f / (float)w));
-                s_idx[j] = rr.w;
+                const RectU u = unpack_rect(rect_sorted[r0 + j]);
+                const uint32_t w = u.x1 - u.x0 + 1u;
+                const uint32_t tb = cams[u.cam].tile_base, tsx = (uint32_t)cams[u.cam].tiles_x;
+                s_rec[j] = make_uint4(tb + u.y0 * tsx + u.x0, tsx, w,
+                                      __float_as_uint(1.0f / (float)w));
+                s_idx[j] = sorted_idx[r0 + j];
                 s_off[j] = poff[r0 + j];
             }
             if (tid == 0) s_off[cnt] = (r0 + cnt < (int64_t)n_vis) ? poff[r0 + cnt] : n_pairs;
@@ -375,12 +372,12 @@ k_duplicate(const uint4 *__restrict__ rect_sorted,
     }
 }
 
-void launch_duplicate(const uint4 *rect_sorted, const uint32_t *poff,
+void launch_duplicate(const uint2 *rect_sorted, const uint32_t *sorted_idx, const uint32_t *poff,
                       const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
                       int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
                       int *err, int grid, cudaStream_t st) {
-    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect_sorted, poff, chunk_first, n_vis, n_pairs,
-                                              pair_cap, cams, pkey, pval, err);
+    k_duplicate<<<grid, kDupThreads, 0, st>>>(rect_sorted, sorted_idx, poff, chunk_first, n_vis,
+                                              n_pairs, pair_cap, cams, pkey, pval, err);
 }
 
 // K6: ranges[t] = [first, end) of tile t in the sorted pair keys, stored as

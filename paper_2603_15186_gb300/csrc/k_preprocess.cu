@@ -25,8 +25,9 @@
 // HBM per cut Gaussian: 4 B id + 16 B position (always); quaternion
 // 16 B and scale/opacity 16 B (f32) or 8 B (f16/bf16) for those in front of
 // the near plane; SH 192 B (f32) or 96 B for those with a non-empty rectangle;
-// written per visible one: record 48 B (f32) or 32 B, key 4 B, rect 16 B
-// (tile rectangle, camera index, node id).
+// written per visible one: record 48 B (f32) or 32 B, key 4 B, rect 8 B
+// (tile rectangle, camera index; pack_rect), and the node id (4 B) when the
+// caller asks for it.
 #include <algorithm>
 
 #include "ngs_internal.cuh"
@@ -239,7 +240,7 @@ __device__ __forceinline__ void cov3d(const float4 q4, const float ls[3], float 
 struct PreOut {
     float x, y, F1, F2, F3, L, r, g, bl, hx, hy;
     uint32_t key;
-    uint4 rect;
+    uint32_t rx0, ry0, rx1, ry1;   // tile rectangle
 };
 
 // Camera fields the phase-A tests read, staged in shared memory per group.
@@ -584,8 +585,8 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev &sc, const DevCame
     o.r = rgb[0]; o.g = rgb[1]; o.bl = rgb[2];
     o.hx = hx; o.hy = hy;
     o.key = __float_as_uint(tz);
-    o.rect = make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16),
-                        0u, node);
+    o.rx0 = (uint32_t)x0; o.ry0 = (uint32_t)y0;
+    o.rx1 = (uint32_t)x1; o.ry1 = (uint32_t)y1;
     return true;
 }
 
@@ -685,7 +686,8 @@ static_assert(kGroupCams <= 16 && kPrePart <= 4096, "entries pack node and camer
 template <typename A, typename R, bool kBlend>
 __global__ void __launch_bounds__(kPreThreads, kBlend ? 3 : 0)
 k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restrict__ rec,
-         int64_t rec_cap, uint32_t *__restrict__ dkey, uint4 *__restrict__ rect,
+         int64_t rec_cap, uint32_t *__restrict__ dkey, uint2 *__restrict__ rect,
+         uint32_t *__restrict__ node_out,
          uint32_t *__restrict__ vis_count, uint32_t *counters,
          const uint32_t *__restrict__ part_list, const uint2 *__restrict__ group_list,
          uint2 *__restrict__ part_info, int *err, int tile_w, int tile_h) {
@@ -861,8 +863,8 @@ k_cutpre(SceneDev sc, const DevCamera *__restrict__ cams, int n_cams, R *__restr
             if (preprocess_one<A, kBlend>(sc, cams[c], node, tile_w, tile_h, o)) {
                 store_rec(rec, (int64_t)pos, o);
                 dkey[pos] = o.key;
-                o.rect.z = (uint32_t)c;
-                rect[pos] = o.rect;
+                rect[pos] = pack_rect(o.rx0, o.ry0, o.rx1, o.ry1, (uint32_t)c);
+                if (node_out) node_out[pos] = node;
                 atomicAdd(&S.nvis[i], 1u);
             } else {
                 dkey[pos] = kKeyHole;
@@ -1013,33 +1015,35 @@ k_part_gather(const uint32_t *__restrict__ part_list, int n_cams, int64_t nblk,
 
 template <bool kBlend>
 static void launch_cutpre_t(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
-                            int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect,
-                            uint32_t *vis_count, uint32_t *counters, uint32_t *part_list,
+                            int64_t rec_cap, uint32_t *dkey_sparse, uint2 *rect,
+                            uint32_t *node_id, uint32_t *vis_count, uint32_t *counters,
+                            uint32_t *part_list,
                             uint2 *group_list, uint2 *part_info, int *err, int tile_w, int tile_h,
                             int grid, cudaStream_t st) {
     switch (sc.attr_dtype) {
     case NGS_F16:
         k_cutpre<__half, Rec16, kBlend><<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
-            sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-            part_list, group_list, part_info, err, tile_w, tile_h);
+            sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, node_id, vis_count,
+            counters, part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     case NGS_BF16:
         k_cutpre<__nv_bfloat16, Rec16, kBlend>
             <<<grid, kPreThreads, sizeof(CutPreSmem<Rec16>), st>>>(
-                sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-                part_list, group_list, part_info, err, tile_w, tile_h);
+                sc, cams, n_cams, (Rec16 *)rec, rec_cap, dkey_sparse, rect, node_id, vis_count,
+                counters, part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     default:
         k_cutpre<float, Rec32, kBlend><<<grid, kPreThreads, sizeof(CutPreSmem<Rec32>), st>>>(
-            sc, cams, n_cams, (Rec32 *)rec, rec_cap, dkey_sparse, rect, vis_count, counters,
-            part_list, group_list, part_info, err, tile_w, tile_h);
+            sc, cams, n_cams, (Rec32 *)rec, rec_cap, dkey_sparse, rect, node_id, vis_count,
+            counters, part_list, group_list, part_info, err, tile_w, tile_h);
         break;
     }
 }
 
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
-                   int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
-                   uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
+                   int64_t rec_cap, uint32_t *dkey_sparse, uint2 *rect, uint32_t *node_id,
+                   uint32_t *vis_count, uint32_t *counters, uint32_t *part_list,
+                   uint2 *group_list, uint2 *part_info,
                    int *err, int tile_w, int tile_h, int use_block_cull, int blend, int grid,
                    cudaStream_t st) {
     const int64_t nblk = (sc.n + kPrePart - 1) / kPrePart;
@@ -1051,13 +1055,13 @@ void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *
                                                      group_list, part_info, counters, tile_w,
                                                      tile_h, use_block_cull, blend, err);
     if (blend)
-        launch_cutpre_t<true>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, vis_count,
-                              counters, part_list, group_list, part_info, err, tile_w, tile_h,
-                              grid, st);
+        launch_cutpre_t<true>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, node_id,
+                              vis_count, counters, part_list, group_list, part_info, err,
+                              tile_w, tile_h, grid, st);
     else
-        launch_cutpre_t<false>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, vis_count,
-                               counters, part_list, group_list, part_info, err, tile_w, tile_h,
-                               grid, st);
+        launch_cutpre_t<false>(sc, cams, n_cams, rec, rec_cap, dkey_sparse, rect, node_id,
+                               vis_count, counters, part_list, group_list, part_info, err,
+                               tile_w, tile_h, grid, st);
 }
 
 void launch_gather_keys(const uint32_t *vis_count, int n_cams, const SceneDev &sc,

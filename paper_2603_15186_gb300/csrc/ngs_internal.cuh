@@ -86,6 +86,27 @@ struct __align__(16) Rec16 {
     float4 b;   // F3, L, half2(r, g) bits, half2(bl, max(hx, hy)) bits
 };
 
+// A visible Gaussian's tile rectangle [x0, x1] x [y0, y1] (tile coordinates of
+// its camera, below 4096: images are at most 32768 pixels wide and high, tiles
+// at least 8) and its camera within the launch (below 65536) in 8 bytes:
+// x0 | y0 << 12 | camera bits 0-7 << 24, x1 | y1 << 12 | camera bits 8-15 << 24.
+constexpr uint32_t kRectCoordMax = 4096;
+struct RectU {
+    uint32_t x0, y0, x1, y1, cam;
+};
+__host__ __device__ __forceinline__ uint2 pack_rect(uint32_t x0, uint32_t y0, uint32_t x1,
+                                                    uint32_t y1, uint32_t cam) {
+    return make_uint2(x0 | (y0 << 12) | ((cam & 0xffu) << 24),
+                      x1 | (y1 << 12) | ((cam >> 8) << 24));
+}
+__host__ __device__ __forceinline__ RectU unpack_rect(const uint2 r) {
+    RectU u;
+    u.x0 = r.x & 0xfffu; u.y0 = (r.x >> 12) & 0xfffu;
+    u.x1 = r.y & 0xfffu; u.y1 = (r.y >> 12) & 0xfffu;
+    u.cam = (r.x >> 24) | ((r.y >> 24) << 8);
+    return u;
+}
+
 struct SceneDev {
     int64_t n = 0;
     // nodes without children: a cut is an antichain of the tree, so no camera
@@ -275,8 +296,9 @@ struct Work {
     void *rec = nullptr;              int64_t rec_cap = 0;
     uint32_t *dkey[2] = {nullptr, nullptr};
     uint32_t *didx[2] = {nullptr, nullptr};
-    uint4 *rect = nullptr;            // x0|y0<<16, x1|y1<<16, camera index, node id
-    uint4 *rect_sorted = nullptr;     // the visible rects in depth order, record index in w
+    uint2 *rect = nullptr;            // tile rectangle and camera (pack_rect)
+    uint2 *rect_sorted = nullptr;     // the visible rects in depth order
+    uint32_t *node_id = nullptr;      // node of each record, kept on request only
     uint32_t *poff = nullptr;         // pair offsets per sorted record
     uint32_t *chunk_first = nullptr;  // first sorted record of each pair chunk
     uint32_t *pkey[2] = {nullptr, nullptr};
@@ -324,8 +346,10 @@ int cut_partition_nodes();
 // camera in vis_count; counters[CNT_CUT], [CNT_LIVE], [CNT_GROUPS],
 // [CNT_ALLOC], [TK_PRE]. part_list and group_list hold part_cap entries.
 // blend: level-of-detail blending of every node toward its parent.
+// node_id (may be null): each visible record's node id.
 void launch_cutpre(const SceneDev &sc, const DevCamera *cams, int n_cams, void *rec,
-                   int64_t rec_cap, uint32_t *dkey_sparse, uint4 *rect, uint32_t *vis_count,
+                   int64_t rec_cap, uint32_t *dkey_sparse, uint2 *rect, uint32_t *node_id,
+                   uint32_t *vis_count,
                    uint32_t *counters, uint32_t *part_list, uint2 *group_list, uint2 *part_info,
                    int *err, int tile_w, int tile_h, int use_block_cull, int blend, int grid,
                    cudaStream_t st);
@@ -382,18 +406,19 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, const uint32_t *n_dev, i
 int scan_partition();
 
 // binning: tiles-touched scan over depth order (also the first record of every
-// pair chunk, chunk_first[dup_chunks(pair_cap)], and the rects in depth order,
-// record index in w, in rect_sorted); with hist, it also adds the digit counts
+// pair chunk, chunk_first[dup_chunks(pair_cap)], and the rects in depth order
+// in rect_sorted); with hist, it also adds the digit counts
 // of the pairs' tile keys (camera tile base + row * tiles_x + column) for
 // `passes` 8-bit radix passes to hist[passes][256] (zeroed by the caller)
-void launch_pair_offsets(const uint4 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
+void launch_pair_offsets(const uint2 *rect, const uint32_t *sorted_idx, const uint32_t *n_vis,
                          uint32_t *poff, uint32_t *counters, int64_t pair_cap, uint32_t *ticket,
                          uint64_t *status, const uint32_t *epoch, uint32_t epoch_off, int *err,
-                         uint32_t *chunk_first, uint4 *rect_sorted, const DevCamera *cams,
+                         uint32_t *chunk_first, uint2 *rect_sorted, const DevCamera *cams,
                          uint32_t *hist, int passes, int grid, cudaStream_t st);
 int64_t dup_chunks(int64_t pair_cap);
-// emits the pairs from the depth-ordered rects
-void launch_duplicate(const uint4 *rect_sorted, const uint32_t *poff,
+// emits the pairs from the depth-ordered rects and their record indices
+// (sorted_idx, as given to launch_pair_offsets)
+void launch_duplicate(const uint2 *rect_sorted, const uint32_t *sorted_idx, const uint32_t *poff,
                       const uint32_t *chunk_first, const uint32_t *n_vis, const uint32_t *n_pairs,
                       int64_t pair_cap, const DevCamera *cams, uint32_t *pkey, uint32_t *pval,
                       int *err, int grid, cudaStream_t st);

@@ -114,6 +114,11 @@ class Renderer:
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_COMPOSITE_ORDER, 1 if longest_first else 0),
               "composite order")
 
+    def set_node_ids(self, on: bool):
+        """Renders also keep each visible Gaussian's node id, which tile_lists
+        reports; the images are the same."""
+        check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_NODE_IDS, 1 if on else 0), "node ids")
+
     def set_stage_timing(self, on: bool):
         check(self.L.ngs_set_option(self.h, _lib.NGS_OPT_STAGE_TIMING, 1 if on else 0),
               "stage timing")
@@ -288,7 +293,8 @@ class Renderer:
         return ids, off
 
     def tile_lists(self, cam_index: int, n_tiles: int, cap: int):
-        """(ranges [tiles, 2] int64, node ids int32) of one camera of the last render."""
+        """(ranges [tiles, 2] int64, node ids int32) of one camera of the last
+        render, which must have been made with set_node_ids(True)."""
         ranges = np.zeros((n_tiles, 2), dtype=np.int64)
         nodes = np.zeros(max(cap, 1), dtype=np.int32)
         npairs = C.c_int64()
@@ -296,6 +302,15 @@ class Renderer:
                                           nodes.ctypes.data_as(C.c_void_p), cap,
                                           C.byref(npairs)), "ngs_debug_tile_lists")
         return ranges, nodes[:npairs.value]
+
+    def tile_ranges(self, cam_index: int, n_tiles: int, cap: int):
+        """(ranges [tiles, 2] int64, number of pairs) of one camera of the
+        last render; needs no node ids."""
+        ranges = np.zeros((n_tiles, 2), dtype=np.int64)
+        npairs = C.c_int64()
+        check(self.L.ngs_debug_tile_lists(self.h, cam_index, ranges.ctypes.data_as(C.c_void_p),
+                                          None, cap, C.byref(npairs)), "ngs_debug_tile_lists")
+        return ranges, npairs.value
 
     def sort_pairs(self, keys, vals, begin_bit: int = 0, end_bit: Optional[int] = None,
                    stream=None):

@@ -69,10 +69,10 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %d %zu %zu\n", sizeof(ngs_tune_result), offsetof(ngs_tune_result, ms),
          offsetof(ngs_tune_result, batch), offsetof(ngs_stats, cta_w), sizeof(ngs_server_config),
          NGS_TUNE_SHAPES, sizeof(ngs_slice_grid), offsetof(ngs_slice_grid, threshold));
-  printf("%d %d %d %d %d %d %d %d %d %d %d %d %zu\n", NGS_OPT_MODE, NGS_OPT_TILE_W,
+  printf("%d %d %d %d %d %d %d %d %d %d %d %d %d %zu\n", NGS_OPT_MODE, NGS_OPT_TILE_W,
          NGS_OPT_TILE_H, NGS_OPT_BATCH, NGS_OPT_GRAPH, NGS_OPT_STAGE_TIMING, NGS_OPT_BLOCK_CULL,
          NGS_OPT_CTA_W, NGS_OPT_CTA_H, NGS_OPT_PAIRS_PER_PIXEL, NGS_OPT_LOD_BLEND,
-         NGS_OPT_COMPOSITE_ORDER, offsetof(ngs_stats, composite_tail_ms));
+         NGS_OPT_COMPOSITE_ORDER, NGS_OPT_NODE_IDS, offsetof(ngs_stats, composite_tail_ms));
   printf("%d\n", NGS_CUT_FRUSTUM);
   return 0;
 }
@@ -96,7 +96,8 @@ int main(void) {
         _lib.NGS_OPT_MODE, _lib.NGS_OPT_TILE_W, _lib.NGS_OPT_TILE_H, _lib.NGS_OPT_BATCH,
         _lib.NGS_OPT_GRAPH, _lib.NGS_OPT_STAGE_TIMING, _lib.NGS_OPT_BLOCK_CULL,
         _lib.NGS_OPT_CTA_W, _lib.NGS_OPT_CTA_H, _lib.NGS_OPT_PAIRS_PER_PIXEL,
-        _lib.NGS_OPT_LOD_BLEND, _lib.NGS_OPT_COMPOSITE_ORDER, _lib.Stats.composite_tail_ms.offset]
+        _lib.NGS_OPT_LOD_BLEND, _lib.NGS_OPT_COMPOSITE_ORDER, _lib.NGS_OPT_NODE_IDS,
+        _lib.Stats.composite_tail_ms.offset]
     assert int(f) == _lib.CUT_FRUSTUM
 
 
@@ -107,3 +108,37 @@ def test_renderer_fails_loudly_without_gpu():
     from paper_2603_15186_gb300 import Renderer, NgsError
     with pytest.raises((NgsError, RuntimeError)):
         Renderer(device=0)
+
+
+def test_rect_packing_round_trips_at_its_limits(tmp_path):
+    """The 8-byte tile rectangle of the binning stages keeps every tile
+    coordinate an image of up to 32768 pixels can have with 8-pixel tiles
+    (0..4095) and every camera index of a launch (0..65535). Host code of the
+    library's own header, compiled by nvcc; no GPU."""
+    from paper_2603_15186_gb300 import build
+    prog = tmp_path / "rect.cu"
+    prog.write_text(r"""
+#include <cstdio>
+#include "ngs_internal.cuh"
+int main() {
+  const uint32_t co[] = {0u, 1u, 255u, 256u, 2047u, 4094u, 4095u};
+  const uint32_t cams[] = {0u, 1u, 255u, 256u, 1023u, 1024u, 65535u};
+  long bad = 0, n = 0;
+  for (uint32_t a : co) for (uint32_t b : co) for (uint32_t c : co) for (uint32_t d : co)
+    for (uint32_t k : cams) {
+      const ngs::RectU u = ngs::unpack_rect(ngs::pack_rect(a, b, c, d, k));
+      bad += u.x0 != a || u.y0 != b || u.x1 != c || u.y1 != d || u.cam != k;
+      ++n;
+    }
+  std::printf("%ld %ld %u\n", n, bad, ngs::kRectCoordMax);
+  return 0;
+}
+""")
+    exe = tmp_path / "rect"
+    subprocess.run([build.nvcc(), "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                    "-I", build.CSRC, str(prog), "-o", str(exe)], check=True)
+    n, bad, cmax = (int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.split())
+    assert n == 7 ** 5 and bad == 0
+    # 32768-pixel images in 8-pixel tiles: 4096 tiles per axis
+    assert cmax == 32768 // 8

@@ -73,6 +73,7 @@ def test_floor1m_plain_fp32_views():
     ids, off = ids.cpu().numpy(), off.cpu().numpy()
     for i, cam in enumerate(cams):
         compare_cut(ids[off[i]:off[i + 1]], scene, cam)
+    R.set_node_ids(True)
     R.render([cams[1]])
     ref = refs[1]
     rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
@@ -135,6 +136,7 @@ def test_floor4m_batch256_benchmark_configuration(floor4m):
     big = cams[sample[2]]
     tile = tuple(st_tile(R))
     ref = oracle_on_gpu_cut(R, floor4m, sa, big, tile=tile)
+    R.set_node_ids(True)
     alone = R.render([big])[0].cpu().numpy()
     assert np.array_equal(alone, first[sample[2]])
     rg, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)

@@ -237,6 +237,7 @@ def test_render_small_box_view(R, box10k, tau):
     cam = camera_c0(tau)
     ref = O.render(box10k, cam, tile=(16, 16))
     assert ref.near.sum() == 0
+    R.set_node_ids(True)
     img = _render_one(R, box10k, cam)
     compare_image(img, ref)
     n_tiles = len(ref.ranges)
@@ -244,6 +245,14 @@ def test_render_small_box_view(R, box10k, tau):
     compare_tile_lists(rng, nodes, ref, (16, 16))
     pairs, _, _ = compare_tile_order_f64(rng, nodes, box10k.pos, cam)
     assert pairs > 1000
+    # without node ids the same render gives the same pixels, and the tile
+    # lists report their ranges only
+    R.set_node_ids(False)
+    assert np.array_equal(_render_one(R, box10k, cam), img)
+    rng2, _ = R.tile_ranges(0, n_tiles, len(ref.keys) + 4096)
+    assert np.array_equal(rng2, rng)
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        R.tile_lists(0, n_tiles, len(ref.keys) + 4096)
 
 
 def test_large_footprints_span_many_tiles_and_windows(R, box10k):
@@ -256,11 +265,13 @@ def test_large_footprints_span_many_tiles_and_windows(R, box10k):
     ref = O.render(box10k, cam, tile=(8, 8))
     area = (ref.rect[:, 2] - ref.rect[:, 0] + 1) * (ref.rect[:, 3] - ref.rect[:, 1] + 1)
     assert area.max() > 2048          # one record holds more than a whole pair chunk
+    R.set_node_ids(True)
     img = _render_one(R, box10k, cam, tile=(8, 8))
     compare_image(img, ref)
     n_tiles = len(ref.ranges)
     rng, nodes = R.tile_lists(0, n_tiles, len(ref.keys) + 4096)
     compare_tile_lists(rng, nodes, ref, (8, 8))
+    R.set_node_ids(False)
     R.set_tile(16, 16)
 
 
@@ -293,7 +304,9 @@ def test_render_batch_matches_oracle_and_plain(R, small_floor):
         assert np.array_equal(a, b)
     # tile lists of the last camera (plain mode leaves each camera's buffers in turn)
     R.set_mode("plain")
+    R.set_node_ids(True)
     R.render([cams[2]])
+    R.set_node_ids(False)
     ref = O.render(small_floor, cams[2])
     rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
     compare_tile_lists(rng, nodes, ref, (16, 16))
@@ -351,7 +364,9 @@ def test_lod_blend_matches_oracle(R, small_floor):
         R.set_mode("plain")
         for a, b in zip(imgs, [t.cpu().numpy() for t in R.render(cams)]):
             assert np.array_equal(a, b)
+        R.set_node_ids(True)
         R.render([cams[2]])
+        R.set_node_ids(False)
         ref = O.render(small_floor, cams[2], blend=True)
         rng, nodes = R.tile_lists(0, len(ref.ranges), len(ref.keys) + 65536)
         compare_tile_lists(rng, nodes, ref, (16, 16))
